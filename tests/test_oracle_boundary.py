@@ -1,0 +1,97 @@
+"""Pins of the oracle's wall contact (Eq. coulomb_friction, Sec. 5.3) and grid
+update (Sec. 2.2) against the Coulomb law and a sliding-block solution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_04192_gb300 import inputs
+
+
+def _unit(v):
+    return v / np.linalg.norm(v)
+
+
+def test_coulomb_law_per_node():
+    rng = np.random.default_rng(0)
+    for _ in range(2000):
+        n = _unit(rng.normal(size=3))
+        v = rng.normal(size=3)
+        mu = rng.choice([0.0, rng.uniform(0.0, 1.5)])
+        out = oracle.friction(v, n, mu)
+        vn = v @ n
+        vt = v - vn * n
+        if vn <= 0.0:                                   # separating: untouched
+            np.testing.assert_allclose(out, v, atol=1e-15)
+            continue
+        assert abs(out @ n) < 1e-12                     # normal approach removed
+        ot = out - (out @ n) * n
+        if mu == 0.0:
+            np.testing.assert_allclose(out, vt, atol=1e-12)   # slip wall
+        elif np.linalg.norm(vt) <= mu * vn:
+            np.testing.assert_allclose(out, 0.0, atol=1e-12)  # sticking
+        else:                                           # sliding: |v_t| reduced by mu v_n, same direction
+            assert np.linalg.norm(ot) == pytest.approx(np.linalg.norm(vt) - mu * vn, rel=1e-10, abs=1e-12)
+            assert ot @ vt > 0.0
+            np.testing.assert_allclose(np.cross(ot, vt), 0.0, atol=1e-10)
+
+
+def test_grid_update_walls_and_segments():
+    """Nodes on or beyond a face get the contact correction with their segment's mu."""
+    N = 8
+    dx = 1.0 / N
+    mu = np.array([0.0, 0.2, 0.5, 1.0])
+    orc = oracle.Oracle(2, (N, N), dx, 1e-3, (0.0, 0.0), dict(inputs.FLUID_WATER), dx * dx,
+                        friction=[(2, (4, 1), mu)])
+    G = orc.num_nodes
+    gm = np.ones(G)
+    v = np.array([0.3, -0.4])                           # moving down and right
+    gq = np.tile(v, (G, 1))
+    gv = orc.grid_update(gm, gq, np.zeros((G, 2)))
+    shape = orc.node_shape
+    for idx in range(G):
+        jx, jy = idx % shape[0], idx // shape[0]
+        x, y = (jx - 1) * dx, (jy - 1) * dx
+        out = v.copy()
+        if x >= 1.0:                                    # right wall: moving outward
+            out[0] = 0.0
+        if y <= 0.0:                                    # floor, last
+            seg = min(max(int(np.floor((jx - 1) * 4 / N)) if jx >= 1 else 0, 0), 3)
+            m = mu[seg]
+            vt = abs(out[0])
+            vn = -out[1]
+            out[1] = 0.0
+            if m > 0:
+                out[0] = 0.0 if vt <= m * vn else np.sign(out[0]) * (vt - m * vn)
+        np.testing.assert_allclose(gv[idx], out, atol=1e-15, err_msg=f"node {jx},{jy}")
+
+
+def test_mass_threshold_and_acceleration():
+    N = 4
+    orc = oracle.Oracle(2, (N, N), 0.25, 0.01, (0.0, -10.0), dict(inputs.FLUID_WATER), 0.01)
+    G = orc.num_nodes
+    gm = np.full(G, 2.0); gm[7] = 0.0
+    gq = np.tile([1.0, 0.5], (G, 1))
+    gf = np.tile([4.0, 2.0], (G, 1))
+    gv = orc.grid_update(gm, gq, gf)
+    interior = (1 + 2 * (N + 3)) + 1                    # node (2, 2)
+    np.testing.assert_allclose(gv[interior], [0.5 + 0.01 * 2.0, 0.25 + 0.01 * 1.0], atol=1e-15)
+    np.testing.assert_allclose(gv[7], 0.0)
+
+
+@pytest.mark.slow
+def test_sliding_block_decelerates_at_mu_g():
+    """An elastic block sliding on a floor of friction mu decelerates at mu g."""
+    dx = 1.0 / 64
+    mat = dict(kind=1, rho0=2000.0, E=2e6, nu=0.3, phi_deg=30.0, psi_deg=0.0, cohesion=1e6, sigma_t=1e6)
+    mu = 0.3
+    w = inputs.dam_break_2d(64, 0.125, 0.0625, ppc_axis=2)
+    x0 = w.x + np.array([0.2, 0.0])
+    dt = 2e-5
+    orc = oracle.Oracle(2, (64, 64), dx, dt, (0.0, -9.81), mat, dx * dx / 4, friction=[(2, (1, 1), [mu])])
+    st = orc.initial_state(x0, np.tile([1.0, 0.0], (len(x0), 1)))
+    orc.step(st, 500)                                   # settle on the floor
+    v1 = st.v[:, 0].mean()
+    orc.step(st, 1500)
+    v2 = st.v[:, 0].mean()
+    decel = (v1 - v2) / (1500 * dt)
+    assert decel == pytest.approx(mu * 9.81, rel=0.08)
