@@ -1,0 +1,320 @@
+"""Benchmark of the explicit MPM step on the 2.76M-particle 3D granular
+cylinder collapse (256 x 256 x 128 cells, Drucker-Prager sand, frictional
+floor), the workload of the paper's cylinder-collapse timing (Sec. 4.2.3).
+
+One bench step is one MPM time step (sort every k steps, P2G, grid update,
+G2P) of the whole particle set.  Prints one JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle as it stands on the host cores
+(bounded samples of the same workload).  With N > 1 (torchrun) every rank runs
+an independent replica of the simulation (the step does not shard), and the
+value is all ranks' particle-steps divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (2.7M 3D collapse, FP32 vs FP64 plain); adjoint/forward ratio"
+WORKLOAD = "granular_cylinder_3d_256x256x128"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.QUERY}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=self.fh, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes_per_particle(kernel: str, dim: int, material: int, rsz: int) -> int:
+    """Compulsory particle bytes of one launch per particle (the state each kernel must
+    read and write once; grid traffic excluded)."""
+    d = dim
+    x, v, C, F, rho = d, d, d * d, d * d, 1
+    sig, eps = (6, 1) if material == 1 else (0, 0)
+    if kernel == "p2g":            # reads x, v, C, rho (and sigma)
+        words = x + v + C + rho + sig
+    elif kernel == "g2p":          # reads x, F, rho, sigma, eps; writes the whole state
+        words = (x + F + rho + sig + eps) + (x + v + C + F + rho + sig + eps)
+    else:
+        return 0
+    return words * rsz
+
+
+def oracle_sample(n_particles: int):
+    """A bounded sample of the 3D collapse for the CPU oracle: the first
+    n_particles of the cylinder in load order (its bottom layers), on a grid
+    cropped around them."""
+    from paper_2507_04192_gb300 import inputs
+    w = inputs.granular_cylinder_3d()
+    x = w.x[:n_particles].copy()
+    lo = np.floor(x.min(axis=0) / w.dx) - 2
+    lo[2] = 0.0
+    x -= lo * w.dx
+    n_cells = tuple(int(np.ceil(x[:, a].max() / w.dx)) + 3 for a in range(3))
+    return w, x, n_cells
+
+
+def run_oracle_steps(n_particles: int, steps: int, warmup: int = 0):
+    import oracle
+    w, x, n_cells = oracle_sample(n_particles)
+    orc = oracle.Oracle(3, n_cells, w.dx, w.dt, w.gravity, w.material, w.particle_volume, w.friction)
+    st = orc.initial_state(x)
+    if warmup:
+        orc.step(st, warmup)
+    t0 = time.perf_counter()
+    orc.step(st, steps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_full_step():
+    """The oracle on one full step of the whole 2.76M-particle workload."""
+    import oracle
+    from paper_2507_04192_gb300 import inputs
+    w = inputs.granular_cylinder_3d()
+    orc = oracle.Oracle.from_workload(w)
+    st = orc.initial_state(w.x)
+    t0 = time.perf_counter()
+    orc.step(st, 1)
+    dt = time.perf_counter() - t0
+    return {"value": w.n / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 full step of all {w.n} particles on the 256x256x128 grid, FP64, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # calibrate: per-step sample sized so that warmup + steps fit in ~120 s
+    probe_n = 20000
+    t = run_oracle_steps(probe_n, 1)
+    per_particle = t / probe_n
+    budget = 120.0
+    n = int(max(2000, min(200000, budget / max(1, args.steps + args.warmup) / per_particle)))
+    dt = run_oracle_steps(n, args.steps, args.warmup)
+    value = n * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_particles": n, "precision": "fp64",
+                       "l2": "CPU run"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the first {n} particles of the 2.76M-particle cylinder "
+                                       f"(bottom layers) on a grid cropped around them, FP64, single thread"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import torch
+
+    from paper_2507_04192_gb300 import inputs, mpm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)          # a real stream handle: the library and the events share it
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    w = inputs.granular_cylinder_3d()
+    n = w.n
+
+    def timed_run(precision, steps, warmup, timing=False):
+        sim = mpm.Simulation.from_workload(w, precision, stream=stream.cuda_stream)
+        sim.step(warmup)
+        sim.synchronize()
+        if timing:
+            mpm.mpm_set_timing(sim.ctx, True)
+            mpm.mpm_reset_timing(sim.ctx)
+        barrier()
+        torch.cuda.synchronize(dev)
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        l0 = sim.stats()["launches"]
+        start.record(stream)
+        sim.step(steps)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = start.elapsed_time(end)
+        sim.synchronize()
+        launches = sim.stats()["launches"] - l0
+        ktimes = {k: mpm.mpm_get_timing(sim.ctx, k) for k in mpm.KERNELS} if timing else None
+        sim.close()
+        return ms, launches, ktimes
+
+    # FP32 headline (clean timed region), with clocks sampled during it
+    sampler = ClockSampler(local)
+    ms32, launches, _ = timed_run(mpm.MPM_FP32, args.steps, args.warmup)
+    clocks = sampler.stop()
+    # per-kernel device times (library CUDA events on the launch stream), same workload
+    _, _, kt = timed_run(mpm.MPM_FP32, args.steps, 3, timing=True)
+    # FP64 mode, fewer steps
+    steps64 = max(1, min(args.steps, 200))
+    ms64, _, _ = timed_run(mpm.MPM_FP64, steps64, 3)
+
+    def reduce_max(v):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    ms32 = reduce_max(ms32)
+    ms64 = reduce_max(ms64)
+    value = world * n * args.steps / (ms32 * 1e-3)
+    value64 = world * n * steps64 / (ms64 * 1e-3)
+
+    # end to end through the C-ABI with host buffers: load (h2d), steps, read back (d2h)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    sim = mpm.Simulation.from_workload(w, mpm.MPM_FP32, stream=stream.cuda_stream, load=False)
+    sim.load(w.x, None, w.particle_volume)
+    for wall, nseg, mu in w.friction:
+        sim.set_friction(wall, nseg, mu)
+    sim.step(args.steps)
+    xout = sim.get("x")
+    e2e_s = time.perf_counter() - t0
+    sim.close()
+    e2e_s = reduce_max(e2e_s)
+    assert np.isfinite(xout).all()
+
+    # roofline of the dominant kernel
+    peak, peak_kind = load_peaks()
+    dom = max(("p2g", "g2p"), key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    per_launch_ms = dom_ms / max(1, dom_n)
+    bpp = algorithmic_bytes_per_particle(dom, 3, 1, 4)
+    achieved = bpp * n / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get(dom)
+
+    if rank == 0:
+        cpu = cpu_baseline_full_step() if (world == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": n, "grid": "256x256x128", "precision": "fp32",
+                       "material": "drucker_prager", "sort_every": w.sort_every,
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (353 MB particle state per step)"},
+            "fp64": {"value": value64, "unit": "particle-steps/s", "steps": steps64,
+                     "ms_per_step": ms64 / steps64},
+            "kernels_ms_per_step": {k: kt[k][0] / max(1, args.steps) for k in kt},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_particle": bpp},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * n * args.steps / e2e_s, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": n * 3 * 8 / args.steps, "d2h_bytes_per_step": n * 3 * 8 / args.steps,
+                    "note": "one mpm_load_particles from host, K steps, one mpm_get_particles to host"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

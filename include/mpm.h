@@ -1,0 +1,201 @@
+/*
+ * libmpm: the explicit material point method (MPM) time step of JAX-MPM
+ * (Du & He, "JAX-MPM: A Learning-Augmented Differentiable Meshfree Framework
+ * for GPU-Accelerated Lagrangian Simulation and Geophysical Inverse Modeling",
+ * arXiv 2507.04192), on hand-written CUDA kernels for sm_103a.
+ *
+ * One step (Sec. 2.2, restated as the map S^{t+1} = Phi(S^t; alpha) of Eq.
+ * mapping in Sec. 3.1) is: particle-to-grid transfer of mass, APIC momentum
+ * (Appendix B) and stress force (Eq. update_m, Eq. semi); the explicit grid
+ * update with gravity (Eq. semi_eq) and Coulomb wall friction (Eq.
+ * coulomb_friction, Sec. 5.3); and the grid-to-particle transfer with the
+ * velocity gradient (Eq. update_v_gradient), deformation gradient, density
+ * and stress update (Sec. 2.3, Appendix A), updated stress last.  Particles
+ * are re-sorted by grid cell every few steps so that the transfers work on
+ * shared-memory tiles of the grid.
+ *
+ * Conventions for every call:
+ *  - Every function returns an mpm_status (MPM_OK = 0 or a negative code);
+ *    mpm_last_error() gives a one-line message for the last failure.
+ *  - Host buffers are owned by the caller; the library copies from them
+ *    before the call returns and keeps no pointer to them.
+ *  - Particle arrays are indexed in load order (the order of
+ *    mpm_load_particles), whatever the internal sorted order.
+ *  - Per-particle tensors are row-major: x and v are n x dim, C and F are
+ *    n x dim x dim, sigma is n x 3 x 3 (plane strain in 2D).
+ *  - Device work is queued on the context's CUDA stream and runs
+ *    asynchronously; device-side faults (a non-finite particle state) are
+ *    recorded in a device status word and reported by the next call that
+ *    synchronises (mpm_synchronize, mpm_get_particles), never by a trap.
+ *  - A context is not thread-safe: use one context per host thread/stream.
+ */
+#ifndef LIBMPM_MPM_H
+#define LIBMPM_MPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_ctx mpm_ctx;
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_EINVAL = -1,     /* invalid argument or unsupported configuration */
+    MPM_ENOMEM = -2,     /* device or host allocation failed */
+    MPM_ECUDA = -3,      /* a CUDA runtime call failed */
+    MPM_ENAN = -4,       /* a particle state became non-finite */
+    MPM_EDOMAIN = -5,    /* a particle index left the grid (never expected: positions are clamped) */
+    MPM_ETIMEOUT = -6,   /* a bounded host wait ran out */
+    MPM_ECORRUPT = -7,   /* a state blob failed its checksum */
+    MPM_ESTATE = -8      /* call not valid in the context's current state */
+} mpm_status;
+
+enum { MPM_FP32 = 0, MPM_FP64 = 1 };
+enum { MPM_FLUID = 0, MPM_DRUCKER_PRAGER = 1 };
+
+/* Particle fields for mpm_get_particles / mpm_set_particle_field.
+ * Widths per particle: X, V: dim; C, F: dim*dim; RHO, EPS: 1; SIGMA: 9. */
+enum {
+    MPM_FIELD_X = 0,      /* position x_p */
+    MPM_FIELD_V = 1,      /* velocity v_p */
+    MPM_FIELD_C = 2,      /* APIC affine matrix C_p = B_p D_p^{-1} (Appendix B) */
+    MPM_FIELD_F = 3,      /* deformation gradient F_p */
+    MPM_FIELD_RHO = 4,    /* density rho_p */
+    MPM_FIELD_SIGMA = 5,  /* Cauchy stress sigma_p (fluid: -p I from the equation of state) */
+    MPM_FIELD_EPS = 6     /* equivalent plastic strain (Drucker-Prager) */
+};
+
+/*
+ * Grid and time step.  The domain is [0, n_cells[a] * dx] per axis a < dim;
+ * walls sit on its faces (Sec. 2.2, ghost cells: one node beyond each face).
+ *   dim        2 or 3
+ *   n_cells    cells per axis (entries >= dim are ignored), each in [1, 4096]
+ *   dx, dt     grid spacing and fixed time step (> 0)
+ *   gravity    body force per unit mass b (Eq. semi)
+ *   precision  MPM_FP32 (all particle and grid arithmetic in float) or MPM_FP64
+ *   sort_every re-sort particles by cell every this many steps (>= 1); a
+ *              particle that has moved more than one cell since the last sort
+ *              stays correct through a slower path
+ *   batch      number of independent simulations sharing the grid shape (>= 1);
+ *              particles carry a simulation id (mpm_load_particles)
+ */
+typedef struct {
+    int dim;
+    int n_cells[3];
+    double dx;
+    double dt;
+    double gravity[3];
+    int precision;
+    int sort_every;
+    int batch;
+} mpm_grid_desc;
+
+/*
+ * Material (Sec. 2.3).
+ *   kind = MPM_FLUID: weakly compressible fluid, Tait equation of state
+ *       p = (bulk_K / gamma) ((rho / rho0)^gamma - 1); gamma = 1 is the paper's
+ *       linear EOS c^2 (rho - rho0) with c^2 = bulk_K / rho0 (Eq. eos).
+ *       viscosity must be 0 (the paper's inviscid cases; MPM_EINVAL otherwise).
+ *   kind = MPM_DRUCKER_PRAGER: Drucker-Prager with tension cutoff and the
+ *       Jaumann rate (Eq. dp_stress, Appendix A); Young's modulus E, Poisson
+ *       ratio nu, friction and dilation angles in degrees, cohesion, tensile
+ *       strength sigma_t (capped at the cone apex k_phi / q_phi).
+ *       dp_literal = 1 applies Appendix A exactly as printed; 0 (default) adds
+ *       the corner return when a return lands past the tension cutoff.
+ *   rho0: reference density (fluid) or initial density (sand); particle mass
+ *       is rho0 * particle_volume.
+ */
+typedef struct {
+    int kind;
+    double rho0, bulk_K, gamma, viscosity;
+    double E, nu, phi_deg, psi_deg, cohesion, sigma_t;
+    int dp_literal;
+} mpm_material;
+
+/*
+ * Create a context for one grid shape and material.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates its own non-blocking stream).
+ * The context owns all its device memory.  Returns MPM_EINVAL for an invalid
+ * descriptor, MPM_ENOMEM/MPM_ECUDA on device failures; *out is set only on
+ * success.
+ */
+int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream,
+               mpm_ctx **out);
+
+/* Free the context and all its device memory (NULL is accepted). */
+void mpm_destroy(mpm_ctx *ctx);
+
+/*
+ * Load n particles (the initial state S^0 of Sec. 3.1): positions x (n x dim,
+ * host, inside the domain), optional velocities v (n x dim, NULL = at rest),
+ * the common initial volume V_p^0, and optional simulation ids (n, each in
+ * [0, batch), NULL = all 0).  The rest of the state starts at C = 0, F = I,
+ * rho = rho0, sigma = 0, eps = 0.  Replaces any previous particles.
+ */
+int mpm_load_particles(mpm_ctx *ctx, int64_t n, const double *x, const double *v,
+                       double particle_volume, const int32_t *sim_id);
+
+/* Overwrite one particle field (host, load order, the field's width per particle). */
+int mpm_set_particle_field(mpm_ctx *ctx, int field, const double *values);
+
+/*
+ * Friction field of one wall (Eq. coulomb_friction).  Walls are numbered
+ * 2*axis + side (side 0 = low face, 1 = high face); the floor is the low face
+ * of the last axis (wall 2 in 2D, 4 in 3D).  The wall is cut into
+ * n_seg[0] x n_seg[1] equal segments along its tangential axes in increasing
+ * axis order (n_seg[1] = 1 in 2D); mu holds batch * n_seg[1] * n_seg[0]
+ * coefficients >= 0, row-major [sim][s1][s0].  A node at tangential coordinate
+ * x_t belongs to segment floor(x_t / L_t * n_seg) clamped to [0, n_seg - 1].
+ * Walls without a friction field are slip walls (mu = 0).
+ */
+int mpm_set_friction_field(mpm_ctx *ctx, int wall, const int n_seg[2], const double *mu);
+
+/* Queue n_steps explicit MPM steps on the context's stream (asynchronous). */
+int mpm_step(mpm_ctx *ctx, int n_steps);
+
+/* Wait for queued work; returns MPM_ENAN if any particle state became non-finite. */
+int mpm_synchronize(mpm_ctx *ctx);
+
+/* Copy one particle field to host memory (load order, doubles); synchronises. */
+int mpm_get_particles(mpm_ctx *ctx, int field, double *out);
+
+/* Number of doubles per particle of a field (or a negative status). */
+int mpm_field_width(const mpm_ctx *ctx, int field);
+
+/* Number of loaded particles (0 before mpm_load_particles). */
+int64_t mpm_num_particles(const mpm_ctx *ctx);
+
+/* Copy the last error message (NUL-terminated, truncated to len). */
+int mpm_last_error(const mpm_ctx *ctx, char *buf, int len);
+
+/*
+ * Kernel timing.  When enabled, every kernel launch is bracketed by CUDA
+ * events on the context's stream; mpm_get_timing returns, for one kernel
+ * class, the summed device time in milliseconds and the launch count since
+ * the last reset (synchronises).  Kernel classes: see MPM_KERNEL_*.
+ */
+enum {
+    MPM_KERNEL_SORT = 0,        /* keys, radix passes, permutation, tile lists */
+    MPM_KERNEL_P2G = 1,
+    MPM_KERNEL_GRID = 2,
+    MPM_KERNEL_G2P = 3,
+    MPM_KERNEL_COUNT = 4
+};
+int mpm_set_timing(mpm_ctx *ctx, int enable);
+int mpm_get_timing(mpm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+int mpm_reset_timing(mpm_ctx *ctx);
+
+/*
+ * Counters (synchronises).  out[0] active tiles, out[1] work chunks after the
+ * last sort, out[2] particles that took the out-of-tile path since creation,
+ * out[3] sorts, out[4] steps, out[5] kernel launches since creation.
+ */
+int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBMPM_MPM_H */

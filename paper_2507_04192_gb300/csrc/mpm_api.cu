@@ -1,0 +1,569 @@
+// Host side of libmpm: context lifetime, device memory, the step sequence
+// and the C-ABI declared in include/mpm.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.cuh"
+
+using namespace mpm;
+
+struct PendingTiming {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+struct mpm_ctx {
+    mpm_grid_desc grid{};
+    mpm_material mat{};
+    HostParams hp{};
+    DevState ds{};
+    const Ops *ops = nullptr;
+    bool own_stream = false;
+    bool need_sort = true;
+    int64_t steps_since_sort = 0;
+    int64_t steps = 0, sorts = 0, launches = 0;
+    std::string err;
+    // timing
+    bool timing = false;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double kt_ms[MPM_KERNEL_COUNT] = {0};
+    int64_t kt_n[MPM_KERNEL_COUNT] = {0};
+    int32_t *h_status = nullptr;       // pinned
+};
+
+namespace {
+
+int fail(mpm_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(mpm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, MPM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+bool forced_alloc_failure()
+{
+    const char *e = std::getenv("MPM_FAIL_ALLOC");
+    return e && e[0] == '1';
+}
+
+template <class T> int dalloc(mpm_ctx *c, T **p, size_t count, const char *what)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (forced_alloc_failure()) return fail(c, MPM_ENOMEM, std::string("forced allocation failure: ") + what);
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? MPM_ENOMEM : MPM_ECUDA,
+                    std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    }
+    return MPM_OK;
+}
+
+template <class T> void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_particles(mpm_ctx *c)
+{
+    DevState &d = c->ds;
+    dfree(d.S); dfree(d.S2);
+    dfree(d.id); dfree(d.id2); dfree(d.sim); dfree(d.sim2);
+    dfree(d.keys[0]); dfree(d.keys[1]); dfree(d.vals[0]); dfree(d.vals[1]);
+    dfree(d.hist); dfree(d.chunks); dfree(d.staging);
+    c->hp.n = 0;
+}
+
+// Kernel timing brackets.
+cudaEvent_t take_event(mpm_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct TimingScope {
+    mpm_ctx *c;
+    int kernel;
+    cudaEvent_t start = nullptr;
+    TimingScope(mpm_ctx *c_, int k) : c(c_), kernel(k)
+    {
+        if (c->timing) {
+            start = take_event(c);
+            cudaEventRecord(start, c->ds.stream);
+        }
+    }
+    ~TimingScope()
+    {
+        if (c->timing) {
+            cudaEvent_t stop = take_event(c);
+            cudaEventRecord(stop, c->ds.stream);
+            c->pending.push_back({kernel, start, stop});
+        }
+    }
+};
+
+void collect_timing(mpm_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+            c->kt_ms[p.kernel] += ms;
+            c->kt_n[p.kernel] += 1;
+        }
+        c->event_pool.push_back(p.start);
+        c->event_pool.push_back(p.stop);
+    }
+    c->pending.clear();
+}
+
+int check_launch(mpm_ctx *c, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return MPM_OK;
+}
+
+int do_sort(mpm_ctx *c)
+{
+    TimingScope ts(c, MPM_KERNEL_SORT);
+    c->ops->keys(c->hp, c->ds);
+    radix_sort_pairs(c->hp, c->ds);
+    c->ops->permute(c->hp, c->ds);
+    std::swap(c->ds.S, c->ds.S2);
+    std::swap(c->ds.id, c->ds.id2);
+    std::swap(c->ds.sim, c->ds.sim2);
+    build_tiles(c->hp, c->ds);
+    c->launches += 4 + 3 * ((c->ds.key_bits + kRadixBits - 1) / kRadixBits);
+    c->sorts++;
+    c->need_sort = false;
+    c->steps_since_sort = 0;
+    return check_launch(c, "sort");
+}
+
+int read_status(mpm_ctx *c)
+{
+    DevState &d = c->ds;
+    cudaError_t e = cudaMemcpyAsync(c->h_status, d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, d.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    collect_timing(c);
+    const int32_t s = *c->h_status;
+    if (s & kStatusNaN) return fail(c, MPM_ENAN, "a particle state became non-finite");
+    if (s & kStatusChunkOverflow) return fail(c, MPM_ECUDA, "work chunk list overflow (internal)");
+    return MPM_OK;
+}
+
+int field_width(const mpm_ctx *c, int field)
+{
+    const int d = c->grid.dim;
+    switch (field) {
+    case MPM_FIELD_X: case MPM_FIELD_V: return d;
+    case MPM_FIELD_C: case MPM_FIELD_F: return d * d;
+    case MPM_FIELD_RHO: case MPM_FIELD_EPS: return 1;
+    case MPM_FIELD_SIGMA: return 9;
+    default: return MPM_EINVAL;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream, mpm_ctx **out)
+{
+    if (!grid || !material || !out) return MPM_EINVAL;
+    const mpm_grid_desc &g = *grid;
+    const mpm_material &m = *material;
+    if (g.dim != 2 && g.dim != 3) return MPM_EINVAL;
+    for (int a = 0; a < g.dim; ++a)
+        if (g.n_cells[a] < 1 || g.n_cells[a] > 4096) return MPM_EINVAL;
+    if (!(g.dx > 0) || !(g.dt > 0) || g.sort_every < 1 || g.batch < 1) return MPM_EINVAL;
+    if (g.precision != MPM_FP32 && g.precision != MPM_FP64) return MPM_EINVAL;
+    if (m.kind != MPM_FLUID && m.kind != MPM_DRUCKER_PRAGER) return MPM_EINVAL;
+    if (!(m.rho0 > 0)) return MPM_EINVAL;
+    if (m.kind == MPM_FLUID && (!(m.bulk_K > 0) || !(m.gamma > 0) || m.viscosity != 0.0)) return MPM_EINVAL;
+    if (m.kind == MPM_DRUCKER_PRAGER && (!(m.E > 0) || !(m.nu > -1.0 && m.nu < 0.5))) return MPM_EINVAL;
+
+    mpm_ctx *c = new mpm_ctx();
+    c->grid = g;
+    c->mat = m;
+    HostParams &h = c->hp;
+    h.dim = g.dim;
+    h.batch = g.batch;
+    h.precision = g.precision;
+    h.material = m.kind;
+    h.dp_literal = m.dp_literal ? 1 : 0;
+    h.dx = g.dx;
+    h.dt = g.dt;
+    for (int a = 0; a < 3; ++a) {
+        h.n_cells[a] = a < g.dim ? g.n_cells[a] : 1;
+        h.gravity[a] = a < g.dim ? g.gravity[a] : 0.0;
+    }
+    h.rho0 = m.rho0;
+    h.bulk_K = m.bulk_K;
+    h.gamma = m.gamma;
+    h.m_eps = 1e-10 * m.rho0 * std::pow(g.dx, g.dim);
+    if (m.kind == MPM_DRUCKER_PRAGER) {
+        const double pi = 3.14159265358979323846;
+        const double phi = m.phi_deg * pi / 180.0, psi = m.psi_deg * pi / 180.0;
+        h.K = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+        h.G = m.E / (2.0 * (1.0 + m.nu));
+        h.q_phi = 6.0 * std::sin(phi) / (std::sqrt(3.0) * (3.0 + std::sin(phi)));
+        h.k_phi = 6.0 * m.cohesion * std::cos(phi) / (std::sqrt(3.0) * (3.0 + std::sin(phi)));
+        h.q_psi = 6.0 * std::sin(psi) / (std::sqrt(3.0) * (3.0 + std::sin(psi)));
+        h.sig_t = m.sigma_t;
+        if (h.q_phi > 0.0 && h.k_phi / h.q_phi < h.sig_t) h.sig_t = h.k_phi / h.q_phi;
+        h.tau_P = h.k_phi - h.q_phi * h.sig_t;
+        h.alpha_P = std::sqrt(1.0 + h.q_phi * h.q_phi) - h.q_phi;
+    }
+    const int T = g.dim == 2 ? Geo<2>::T : Geo<3>::T;
+    h.T = T;
+    h.W = T + 4;
+    h.nodes_per_sim = 1;
+    h.tiles_per_sim = 1;
+    h.node_tiles_per_sim = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a < g.dim) {
+            h.n_tiles[a] = h.n_cells[a] / T + 1;
+            h.G_nodes[a] = h.n_tiles[a] * T + 4;
+            h.node_tiles[a] = (h.G_nodes[a] + T - 1) / T;
+        } else {
+            h.n_tiles[a] = h.G_nodes[a] = h.node_tiles[a] = 1;
+        }
+        h.nodes_per_sim *= h.G_nodes[a];
+        h.tiles_per_sim *= h.n_tiles[a];
+        h.node_tiles_per_sim *= h.node_tiles[a];
+    }
+    const int cell_bits = g.dim == 2 ? Geo<2>::CELL_BITS : Geo<3>::CELL_BITS;
+    int tbits = 0;
+    while ((int64_t(1) << tbits) < (int64_t)g.batch * h.tiles_per_sim) ++tbits;
+    c->ds.key_bits = tbits + cell_bits;
+    if (c->ds.key_bits > 32) {
+        delete c;
+        return MPM_EINVAL;
+    }
+    const int d = g.dim;
+    h.off_x = 0;
+    h.off_v = d;
+    h.off_C = 2 * d;
+    h.off_F = 2 * d + d * d;
+    h.off_rho = 2 * d + 2 * d * d;
+    h.off_sig = h.off_rho + 1;
+    h.off_eps = h.off_sig + 6;
+    h.ncomp = m.kind == MPM_DRUCKER_PRAGER ? h.off_eps + 1 : h.off_rho + 1;
+    h.chunk = 1024;
+    c->ops = g.precision == MPM_FP64 ? &ops_f64 : &ops_f32;
+
+    DevState &ds = c->ds;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return MPM_ECUDA;
+    }
+    if (cuda_stream) {
+        ds.stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ds.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return MPM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    const size_t rsz = g.precision == MPM_FP64 ? 8 : 4;
+    const int64_t nodes = (int64_t)g.batch * h.nodes_per_sim;
+    const int64_t ntiles = (int64_t)g.batch * h.tiles_per_sim;
+    int rc = MPM_OK;
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.A, nodes * 4 * rsz, "grid accumulators");
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.V, nodes * 4 * rsz, "grid velocities");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.flags, (size_t)g.batch * h.node_tiles_per_sim, "node tile flags");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.tile_start, ntiles, "tile starts");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.tile_end, ntiles, "tile ends");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.counters, 4, "counters");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.status, 1, "status");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.escaped, 1, "escape counter");
+    if (rc == MPM_OK && cudaMallocHost((void **)&c->h_status, sizeof(int32_t)) != cudaSuccess) rc = MPM_ENOMEM;
+    if (rc == MPM_OK) {
+        cudaMemsetAsync(ds.A, 0, nodes * 4 * rsz, ds.stream);
+        cudaMemsetAsync(ds.V, 0, nodes * 4 * rsz, ds.stream);
+        cudaMemsetAsync(ds.flags, 0, sizeof(uint32_t) * g.batch * h.node_tiles_per_sim, ds.stream);
+        cudaMemsetAsync(ds.counters, 0, sizeof(int32_t) * 4, ds.stream);
+        cudaMemsetAsync(ds.status, 0, sizeof(int32_t), ds.stream);
+        cudaMemsetAsync(ds.escaped, 0, sizeof(unsigned long long), ds.stream);
+        if (cudaStreamSynchronize(ds.stream) != cudaSuccess) rc = MPM_ECUDA;
+    }
+    if (rc != MPM_OK) {
+        mpm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MPM_OK;
+}
+
+void mpm_destroy(mpm_ctx *c)
+{
+    if (!c) return;
+    DevState &d = c->ds;
+    if (d.stream) cudaStreamSynchronize(d.stream);
+    collect_timing(c);
+    free_particles(c);
+    dfree(d.A); dfree(d.V); dfree(d.flags); dfree(d.tile_start); dfree(d.tile_end);
+    dfree(d.counters); dfree(d.status); dfree(d.escaped);
+    for (int w = 0; w < kMaxWalls; ++w) dfree(d.mu_dev[w]);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->own_stream && d.stream) cudaStreamDestroy(d.stream);
+    delete c;
+}
+
+int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, double particle_volume,
+                       const int32_t *sim_id)
+{
+    if (!c || n <= 0 || !x || !(particle_volume > 0)) return fail(c, MPM_EINVAL, "mpm_load_particles: bad argument");
+    if (n > (int64_t)1 << 30) return fail(c, MPM_EINVAL, "mpm_load_particles: too many particles");
+    const int d = c->grid.dim;
+    for (int64_t p = 0; p < n; ++p)
+        for (int a = 0; a < d; ++a) {
+            const double xa = x[p * d + a];
+            if (!(xa >= 0.0 && xa <= c->hp.n_cells[a] * c->hp.dx))
+                return fail(c, MPM_EINVAL, "mpm_load_particles: position outside the domain or not finite");
+        }
+    if (sim_id)
+        for (int64_t p = 0; p < n; ++p)
+            if (sim_id[p] < 0 || sim_id[p] >= c->grid.batch)
+                return fail(c, MPM_EINVAL, "mpm_load_particles: simulation id out of range");
+    DevState &ds = c->ds;
+    HostParams &h = c->hp;
+    CK(cudaStreamSynchronize(ds.stream), "synchronize before load");
+    free_particles(c);
+    h.n = n;
+    h.npad = (n + 63) / 64 * 64;
+    h.vol0 = particle_volume;
+    h.mass = h.rho0 * particle_volume;
+    const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
+    const int nblk = (int)((n + kSortChunk - 1) / kSortChunk);
+    ds.max_chunks = n / h.chunk + (int64_t)c->grid.batch * h.tiles_per_sim + 1;
+    int rc = MPM_OK;
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, (size_t)h.ncomp * h.npad * rsz, "particle state");
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S2, (size_t)h.ncomp * h.npad * rsz, "particle state (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.id, n, "ids");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.id2, n, "ids (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.sim, n, "sim ids");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.sim2, n, "sim ids (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[0], n, "keys");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[1], n, "keys");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk, "histogram");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.chunks, ds.max_chunks, "chunks");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.staging, (size_t)n * 9, "staging");
+    if (rc != MPM_OK) {
+        free_particles(c);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(ds.staging, x, sizeof(double) * n * d, cudaMemcpyHostToDevice, ds.stream), "copy x");
+    double *vdev = nullptr;
+    if (v) {
+        vdev = ds.staging + (size_t)n * d;
+        CK(cudaMemcpyAsync(vdev, v, sizeof(double) * n * d, cudaMemcpyHostToDevice, ds.stream), "copy v");
+    }
+    if (sim_id) {
+        CK(cudaMemcpyAsync(ds.sim, sim_id, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ds.stream), "copy sim ids");
+    } else {
+        CK(cudaMemsetAsync(ds.sim, 0, sizeof(int32_t) * n, ds.stream), "zero sim ids");
+    }
+    c->ops->init_state(h, ds, ds.staging, vdev);
+    c->launches++;
+    CK(cudaGetLastError(), "init state");
+    CK(cudaStreamSynchronize(ds.stream), "load particles");
+    c->need_sort = true;
+    return MPM_OK;
+}
+
+int mpm_set_particle_field(mpm_ctx *c, int field, const double *values)
+{
+    if (!c || !values) return fail(c, MPM_EINVAL, "mpm_set_particle_field: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_set_particle_field: no particles loaded");
+    const int wdt = field_width(c, field);
+    if (wdt < 0) return fail(c, MPM_EINVAL, "mpm_set_particle_field: unknown field");
+    if (field == MPM_FIELD_SIGMA && c->mat.kind != MPM_DRUCKER_PRAGER)
+        return fail(c, MPM_EINVAL, "mpm_set_particle_field: fluid stress follows from the density");
+    if (field == MPM_FIELD_EPS && c->mat.kind != MPM_DRUCKER_PRAGER)
+        return fail(c, MPM_EINVAL, "mpm_set_particle_field: no plastic strain in a fluid");
+    DevState &ds = c->ds;
+    CK(cudaMemcpyAsync(ds.staging, values, sizeof(double) * c->hp.n * wdt, cudaMemcpyHostToDevice, ds.stream),
+       "copy field");
+    c->ops->set_field(c->hp, ds, field, ds.staging);
+    c->launches++;
+    CK(cudaGetLastError(), "set field");
+    CK(cudaStreamSynchronize(ds.stream), "set field");
+    if (field == MPM_FIELD_X) c->need_sort = true;
+    return MPM_OK;
+}
+
+int mpm_set_friction_field(mpm_ctx *c, int wall, const int n_seg[2], const double *mu)
+{
+    if (!c || !n_seg || !mu) return fail(c, MPM_EINVAL, "mpm_set_friction_field: bad argument");
+    if (wall < 0 || wall >= 2 * c->grid.dim) return fail(c, MPM_EINVAL, "mpm_set_friction_field: bad wall");
+    const int ns1 = c->grid.dim == 2 ? 1 : n_seg[1];
+    if (n_seg[0] < 1 || ns1 < 1 || n_seg[0] > 65536 || ns1 > 65536)
+        return fail(c, MPM_EINVAL, "mpm_set_friction_field: bad segment count");
+    const int64_t count = (int64_t)c->grid.batch * n_seg[0] * ns1;
+    for (int64_t i = 0; i < count; ++i)
+        if (!(mu[i] >= 0.0)) return fail(c, MPM_EINVAL, "mpm_set_friction_field: negative or non-finite mu");
+    DevState &ds = c->ds;
+    CK(cudaStreamSynchronize(ds.stream), "synchronize before friction update");
+    dfree(ds.mu_dev[wall]);
+    const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
+    unsigned char *buf = nullptr;
+    int rc = dalloc(c, &buf, (size_t)count * rsz, "friction field");
+    if (rc != MPM_OK) return rc;
+    if (c->grid.precision == MPM_FP64) {
+        CK(cudaMemcpy(buf, mu, sizeof(double) * count, cudaMemcpyHostToDevice), "copy friction");
+    } else {
+        std::vector<float> tmp(count);
+        for (int64_t i = 0; i < count; ++i) tmp[i] = (float)mu[i];
+        CK(cudaMemcpy(buf, tmp.data(), sizeof(float) * count, cudaMemcpyHostToDevice), "copy friction");
+    }
+    ds.mu_dev[wall] = buf;
+    ds.n_seg[wall][0] = n_seg[0];
+    ds.n_seg[wall][1] = ns1;
+    return MPM_OK;
+}
+
+int mpm_step(mpm_ctx *c, int n_steps)
+{
+    if (!c || n_steps < 0) return fail(c, MPM_EINVAL, "mpm_step: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step: no particles loaded");
+    for (int s = 0; s < n_steps; ++s) {
+        if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
+            int rc = do_sort(c);
+            if (rc != MPM_OK) return rc;
+        }
+        {
+            TimingScope ts(c, MPM_KERNEL_P2G);
+            c->ops->p2g(c->hp, c->ds);
+        }
+        {
+            TimingScope ts(c, MPM_KERNEL_GRID);
+            c->ops->grid(c->hp, c->ds);
+        }
+        {
+            TimingScope ts(c, MPM_KERNEL_G2P);
+            c->ops->g2p(c->hp, c->ds);
+        }
+        c->launches += 3;
+        int rc = check_launch(c, "mpm_step");
+        if (rc != MPM_OK) return rc;
+        c->steps_since_sort++;
+        c->steps++;
+    }
+    return MPM_OK;
+}
+
+int mpm_synchronize(mpm_ctx *c)
+{
+    if (!c) return MPM_EINVAL;
+    return read_status(c);
+}
+
+int mpm_get_particles(mpm_ctx *c, int field, double *out)
+{
+    if (!c || !out) return fail(c, MPM_EINVAL, "mpm_get_particles: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_get_particles: no particles loaded");
+    const int wdt = field_width(c, field);
+    if (wdt < 0) return fail(c, MPM_EINVAL, "mpm_get_particles: unknown field");
+    DevState &ds = c->ds;
+    c->ops->get_field(c->hp, ds, field, ds.staging);
+    c->launches++;
+    CK(cudaGetLastError(), "get field");
+    CK(cudaMemcpyAsync(out, ds.staging, sizeof(double) * c->hp.n * wdt, cudaMemcpyDeviceToHost, ds.stream),
+       "copy field to host");
+    return read_status(c);
+}
+
+int mpm_field_width(const mpm_ctx *c, int field)
+{
+    if (!c) return MPM_EINVAL;
+    return field_width(c, field);
+}
+
+int64_t mpm_num_particles(const mpm_ctx *c) { return c ? c->hp.n : 0; }
+
+int mpm_last_error(const mpm_ctx *c, char *buf, int len)
+{
+    if (!c || !buf || len <= 0) return MPM_EINVAL;
+    std::snprintf(buf, (size_t)len, "%s", c->err.c_str());
+    return MPM_OK;
+}
+
+int mpm_set_timing(mpm_ctx *c, int enable)
+{
+    if (!c) return MPM_EINVAL;
+    c->timing = enable != 0;
+    return MPM_OK;
+}
+
+int mpm_get_timing(mpm_ctx *c, int kernel, double *total_ms, int64_t *launches)
+{
+    if (!c || kernel < 0 || kernel >= MPM_KERNEL_COUNT || !total_ms || !launches) return MPM_EINVAL;
+    CK(cudaStreamSynchronize(c->ds.stream), "timing synchronize");
+    collect_timing(c);
+    *total_ms = c->kt_ms[kernel];
+    *launches = c->kt_n[kernel];
+    return MPM_OK;
+}
+
+int mpm_reset_timing(mpm_ctx *c)
+{
+    if (!c) return MPM_EINVAL;
+    CK(cudaStreamSynchronize(c->ds.stream), "timing synchronize");
+    collect_timing(c);
+    for (int k = 0; k < MPM_KERNEL_COUNT; ++k) {
+        c->kt_ms[k] = 0.0;
+        c->kt_n[k] = 0;
+    }
+    return MPM_OK;
+}
+
+int mpm_get_stats(mpm_ctx *c, int64_t *out, int n)
+{
+    if (!c || !out || n < 0) return MPM_EINVAL;
+    int32_t cnt[2] = {0, 0};
+    unsigned long long esc = 0;
+    CK(cudaMemcpyAsync(cnt, c->ds.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->ds.stream), "stats");
+    CK(cudaMemcpyAsync(&esc, c->ds.escaped, sizeof(esc), cudaMemcpyDeviceToHost, c->ds.stream), "stats");
+    CK(cudaStreamSynchronize(c->ds.stream), "stats");
+    const int64_t vals[6] = {cnt[1], cnt[0], (int64_t)esc, c->sorts, c->steps, c->launches};
+    for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
+    return MPM_OK;
+}
+
+}  // extern "C"

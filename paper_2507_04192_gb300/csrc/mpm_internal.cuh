@@ -1,0 +1,128 @@
+// Internal definitions of libmpm shared by its translation units.
+//
+// Grid geometry.  A physical node j (0 <= j <= N + 2 per axis) sits at
+// (j - 1) dx: one ghost node below the wall at 0 and one beyond the wall at
+// L = N dx (Sec. 2.2, ghost cells).  The device arrays use the shifted index
+// a = j + 1, with one extra pad node below so that the shared-memory window
+// of every tile starts at a non-negative index.  A particle's first stencil
+// node ("base") is s = floor(x / dx - 0.5) + 2 in a-space, s in [1, N + 1].
+// Particles are grouped by the tile of their base node: tile t covers
+// s in [t T + 1, t T + T] (a-space) at sort time, and its window covers the
+// nodes [t T, t T + T + 4), which holds the 3^d stencil of any particle whose
+// base has moved at most one node since the sort.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpm {
+
+constexpr int kMaxWalls = 6;
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortChunk = kSortThreads * kSortItems;
+
+template <int D> struct Geo;
+template <> struct Geo<2> {
+    static constexpr int T = 16;                 // cells per tile edge
+    static constexpr int W = T + 4;              // window edge (nodes)
+    static constexpr int WN = W * W;             // window nodes
+    static constexpr int TN = T * T;             // cells per tile
+    static constexpr int CELL_BITS = 8;          // log2(TN)
+    static constexpr int STENCIL = 9;
+};
+template <> struct Geo<3> {
+    static constexpr int T = 8;
+    static constexpr int W = T + 4;
+    static constexpr int WN = W * W * W;
+    static constexpr int TN = T * T * T;
+    static constexpr int CELL_BITS = 9;
+    static constexpr int STENCIL = 27;
+};
+
+// Friction field of one wall on the device.
+struct WallDev {
+    int n_seg[2];
+    int seg_axis[2];       // tangential axes
+    const void *mu;        // batch x n_seg1 x n_seg0 reals (R), nullptr = slip
+};
+
+// Host-side parameters (double), converted to Params<R> at launch.
+struct HostParams {
+    int dim, batch, precision, material, dp_literal;
+    int n_cells[3];
+    double dx, dt, gravity[3];
+    double rho0, bulk_K, gamma, mass, vol0, m_eps;
+    double K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P;
+    int T, W, n_tiles[3], G_nodes[3], node_tiles[3];
+    int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
+    int64_t n, npad;
+    int ncomp, off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
+    int chunk;             // particles per work chunk
+};
+
+template <class R>
+struct Params {
+    int n_cells[3];
+    R dx, inv_dx, dt, gravity[3], L[3];
+    R rho0, bulk_K, gamma, inv_rho0, mass, m_eps;
+    R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef;
+    int material, dp_literal, gamma_int;
+    int n_tiles[3], G_nodes[3], node_tiles[3];
+    int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
+    int64_t n, npad;
+    int off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
+    WallDev wall[kMaxWalls];
+};
+
+template <class R> struct R4 { R x, y, z, w; };
+template <> struct alignas(16) R4<float> { float x, y, z, w; };
+template <> struct alignas(32) R4<double> { double x, y, z, w; };
+
+// Device pointers and launch state of one context.
+struct DevState {
+    cudaStream_t stream;
+    int num_sms;
+    void *S, *S2;                 // particle SoA, ncomp x npad reals
+    int32_t *id, *id2;            // load-order id of each sorted slot
+    int32_t *sim, *sim2;          // simulation id of each slot
+    uint32_t *keys[2];
+    int32_t *vals[2];
+    uint32_t *hist;               // kRadixBins x n_sort_blocks
+    int32_t *tile_start, *tile_end;   // per tile (batch x tiles_per_sim)
+    int4 *chunks;                 // (tile key, start, count, 0)
+    int64_t max_chunks;
+    int32_t *counters;            // [0] n_chunks, [1] n_active_tiles, [2] chunk overflow
+    void *A, *V;                  // grid accumulators and velocities, R4 per node
+    uint32_t *flags;              // per node tile: touched since the last grid update
+    int32_t *status;              // device status word (bit 0: non-finite state)
+    unsigned long long *escaped;  // particles that took the out-of-window path
+    double *staging;              // n x 9 doubles for host transfers
+    void *mu_dev[kMaxWalls];
+    int n_seg[kMaxWalls][2];
+    int key_bits;
+};
+
+enum StatusBits { kStatusNaN = 1, kStatusChunkOverflow = 2 };
+
+// Launchers implemented per precision (mpm_kernels_f32.cu, mpm_kernels_f64.cu).
+struct Ops {
+    void (*init_state)(const HostParams &, DevState &, const double *x_dev, const double *v_dev);
+    void (*keys)(const HostParams &, DevState &);
+    void (*permute)(const HostParams &, DevState &);
+    void (*p2g)(const HostParams &, DevState &);
+    void (*grid)(const HostParams &, DevState &);
+    void (*g2p)(const HostParams &, DevState &);
+    void (*get_field)(const HostParams &, DevState &, int field, double *out_dev);
+    void (*set_field)(const HostParams &, DevState &, int field, const double *in_dev);
+};
+extern const Ops ops_f32;
+extern const Ops ops_f64;
+
+// Sort helpers (mpm_sort.cu), precision independent.
+void radix_sort_pairs(const HostParams &hp, DevState &ds);
+void build_tiles(const HostParams &hp, DevState &ds);
+
+}  // namespace mpm

@@ -1,0 +1,834 @@
+// CUDA kernels of the explicit MPM step, templated on the real type R
+// (float or double) and the dimension D (2 or 3).  Included once per
+// precision by mpm_kernels_f32.cu / mpm_kernels_f64.cu.
+//
+// Step (Sec. 2.2): P2G scatters mass, APIC momentum (Appendix B) and the
+// stress force of Eq. semi into a shared-memory window of the grid per tile of
+// sorted particles, then adds the window to the global grid with one vector
+// atomic per touched node; the grid update turns node momentum into velocity
+// with gravity and the wall contact of Eq. coulomb_friction; G2P gathers the
+// node velocities back to the particles and applies the velocity gradient of
+// Eq. update_v_gradient to position, deformation gradient, density and stress.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ float rfloor(float v) { return floorf(v); }
+__device__ __forceinline__ double rfloor(double v) { return floor(v); }
+__device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
+__device__ __forceinline__ bool rfinite(float v) { return isfinite(v); }
+__device__ __forceinline__ bool rfinite(double v) { return isfinite(v); }
+
+__device__ __forceinline__ void red_add4(R4<float> *addr, float a, float b, float c, float d)
+{
+    atomicAdd(reinterpret_cast<float4 *>(addr), make_float4(a, b, c, d));
+}
+__device__ __forceinline__ void red_add4(R4<double> *addr, double a, double b, double c, double d)
+{
+    atomicAdd(&addr->x, a);
+    atomicAdd(&addr->y, b);
+    atomicAdd(&addr->z, c);
+    atomicAdd(&addr->w, d);
+}
+
+// First stencil cell b = floor(x / dx - 0.5), clamped to [-1, N - 1] (a NaN or
+// infinite position therefore still yields an in-grid index).
+template <class R>
+__device__ __forceinline__ int base_cell(R x, R inv_dx, int N)
+{
+    int b = (int)rfloor(x * inv_dx - R(0.5));
+    return min(max(b, -1), N - 1);
+}
+
+// Quadratic B-spline weights of the three stencil nodes at offset fx = x/dx - b
+// and their derivatives with respect to x (closed form of the spline of Sec. 2.1
+// on [0.5, 1.5)).
+template <class R>
+__device__ __forceinline__ void bspline(R fx, R inv_dx, R w[3], R dw[3])
+{
+    const R a = R(1.5) - fx, b = fx - R(1), c = fx - R(0.5);
+    w[0] = R(0.5) * a * a;
+    w[1] = R(0.75) - b * b;
+    w[2] = R(0.5) * c * c;
+    dw[0] = -a * inv_dx;
+    dw[1] = R(-2) * b * inv_dx;
+    dw[2] = c * inv_dx;
+}
+
+// Tait pressure p = (K / gamma) ((rho / rho0)^gamma - 1).
+template <class R>
+__device__ __forceinline__ R tait(const Params<R> &P, R rho)
+{
+    const R r = rho * P.inv_rho0;
+    R rg;
+    if (P.gamma_int > 0) {
+        rg = R(1);
+        for (int k = 0; k < P.gamma_int; ++k) rg *= r;
+    } else {
+        rg = pow(r, P.gamma);
+    }
+    return P.bulk_K / P.gamma * (rg - R(1));
+}
+
+template <int D> __device__ __forceinline__ int64_t lin3(const int a[3], const int G[3])
+{
+    if constexpr (D == 2) return (int64_t)a[1] * G[0] + a[0];
+    return ((int64_t)a[2] * G[1] + a[1]) * G[0] + a[0];
+}
+
+// Friction coefficient of the wall segment holding node a (a-space).
+template <class R, int D>
+__device__ __forceinline__ R wall_mu(const Params<R> &P, int w, int sim, const int a[3])
+{
+    const WallDev &wd = P.wall[w];
+    if (wd.mu == nullptr) return R(0);
+    int s[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < D - 1; ++q) {
+        const int ax = wd.seg_axis[q];
+        const int c = a[ax] - 2;                       // node coordinate / dx
+        int sq = c > 0 ? (int)(((int64_t)c * wd.n_seg[q]) / P.n_cells[ax]) : 0;
+        s[q] = min(sq, wd.n_seg[q] - 1);
+    }
+    const int64_t per_sim = (int64_t)wd.n_seg[0] * wd.n_seg[1];
+    return static_cast<const R *>(wd.mu)[sim * per_sim + (int64_t)s[1] * wd.n_seg[0] + s[0]];
+}
+
+// ------------------------------------------------------------------ P2G
+
+// Contribution of particle p to the 3^D stencil nodes: m w, and
+// m w (v + C (x_i - x_p)) - dt V sigma grad w (momentum plus dt times the
+// internal force; gravity is added in the grid update).
+template <class R, int D>
+__device__ __forceinline__ void p2g_particle(const Params<R> &P, const R *__restrict__ S, int64_t p,
+                                             const int org[3], R *sm, R4<R> *Asim, uint32_t *flags_sim,
+                                             bool &escaped)
+{
+    using Gm = Geo<D>;
+    const int64_t np = P.npad;
+    R x[D], v[D], C[D * D], Fm[D * D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = S[(P.off_x + a) * np + p];
+        v[a] = S[(P.off_v + a) * np + p];
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) C[q] = S[(P.off_C + q) * np + p];
+    const R rho = S[P.off_rho * np + p];
+    const R Vp = P.mass / rho;
+    if (P.material == 0) {
+        const R c = P.dt * Vp * tait(P, rho);          // -dt V (-p I)
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Fm[q] = (q % (D + 1) == 0) ? c : R(0);
+    } else {
+        // symmetric storage xx, yy, zz, xy, xz, yz; in-plane block acts on the grid
+        R s6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
+        const R c = -P.dt * Vp;
+        if constexpr (D == 2) {
+            Fm[0] = c * s6[0]; Fm[1] = c * s6[3];
+            Fm[2] = c * s6[3]; Fm[3] = c * s6[1];
+        } else {
+            Fm[0] = c * s6[0]; Fm[1] = c * s6[3]; Fm[2] = c * s6[4];
+            Fm[3] = c * s6[3]; Fm[4] = c * s6[1]; Fm[5] = c * s6[5];
+            Fm[6] = c * s6[4]; Fm[7] = c * s6[5]; Fm[8] = c * s6[2];
+        }
+    }
+    int b[D], l[D];
+    R fx[D], w[D][3], dw[D][3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+        fx[a] = x[a] * P.inv_dx - R(b[a]);
+        bspline(fx[a], P.inv_dx, w[a], dw[a]);
+        l[a] = b[a] + 2 - org[a];
+        inside = inside && (l[a] >= 0) && (l[a] <= Gm::W - 3);
+    }
+    escaped = !inside;
+    // affine velocity at node offset k: v + C (k - fx) dx
+    R u0[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R s = v[a];
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) s -= C[a * D + c2] * fx[c2] * P.dx;
+        u0[a] = s;
+    }
+    const R mp = P.mass;
+#pragma unroll
+    for (int k = 0; k < Gm::STENCIL; ++k) {
+        const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
+        const int kk[3] = {k0, k1, k2};
+        R wt = w[0][k0] * w[1][k1];
+        R g[D];
+        if constexpr (D == 2) {
+            g[0] = dw[0][k0] * w[1][k1];
+            g[1] = w[0][k0] * dw[1][k1];
+        } else {
+            const R w2 = w[D - 1][k2];
+            g[0] = dw[0][k0] * w[1][k1] * w2;
+            g[1] = w[0][k0] * dw[1][k1] * w2;
+            g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
+            wt *= w2;
+        }
+        const R mw = mp * wt;
+        R mom[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            R ua = u0[a];
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) ua += C[a * D + c2] * R(kk[c2]) * P.dx;
+            R f = R(0);
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) f += Fm[a * D + c2] * g[c2];
+            mom[a] = mw * ua + f;
+        }
+        if (inside) {
+            int li;
+            if constexpr (D == 2) li = (l[1] + k1) * Gm::W + (l[0] + k0);
+            else li = ((l[D - 1] + k2) * Gm::W + (l[1] + k1)) * Gm::W + (l[0] + k0);
+            atomicAdd(&sm[li], mw);
+            atomicAdd(&sm[Gm::WN + li], mom[0]);
+            atomicAdd(&sm[2 * Gm::WN + li], mom[1]);
+            if constexpr (D == 3) atomicAdd(&sm[3 * Gm::WN + li], mom[2]);
+        } else {
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = b[a] + 2 + kk[a];
+            const int64_t gi = lin3<D>(a3, P.G_nodes);
+            red_add4(&Asim[gi], mw, mom[0], mom[1], mom[2]);
+            int u[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = a3[a] / Gm::T;
+            flags_sim[lin3<D>(u, P.node_tiles)] = 1u;
+        }
+    }
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restrict__ S,
+                                             const int4 *__restrict__ chunks,
+                                             const int32_t *__restrict__ counters, R4<R> *__restrict__ A,
+                                             uint32_t *__restrict__ flags,
+                                             unsigned long long *__restrict__ escaped_count)
+{
+    using Gm = Geo<D>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    __shared__ uint32_t tile_mask;
+    const int n_chunks = counters[0];
+    for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const int4 ch = chunks[c];
+        for (int i = threadIdx.x; i < (D + 1) * Gm::WN; i += blockDim.x) sm[i] = R(0);
+        if (threadIdx.x == 0) tile_mask = 0u;
+        __syncthreads();
+        const int sim = (int)(ch.x / P.tiles_per_sim);
+        int64_t tl = ch.x - (int64_t)sim * P.tiles_per_sim;
+        int org[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
+            tl /= P.n_tiles[a];
+        }
+        R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
+        uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
+        bool any_escape = false;
+        for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
+            bool esc = false;
+            p2g_particle<R, D>(P, S, (int64_t)ch.y + i, org, sm, Asim, fsim, esc);
+            any_escape |= esc;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
+        if (ball && (threadIdx.x & 31) == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
+        __syncthreads();
+        for (int i = threadIdx.x; i < Gm::WN; i += blockDim.x) {
+            const R m = sm[i];
+            const R q0 = sm[Gm::WN + i], q1 = sm[2 * Gm::WN + i];
+            const R q2 = D == 3 ? sm[3 * Gm::WN + i] : R(0);
+            if (m != R(0) || q0 != R(0) || q1 != R(0) || q2 != R(0)) {
+                int l[3] = {0, 0, 0}, a3[3] = {0, 0, 0};
+                int r = i;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    l[a] = r % Gm::W;
+                    r /= Gm::W;
+                    a3[a] = org[a] + l[a];
+                }
+                red_add4(&Asim[lin3<D>(a3, P.G_nodes)], m, q0, q1, q2);
+                unsigned bit = 0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) bit |= (l[a] >= Gm::T ? 1u : 0u) << a;
+                atomicOr(&tile_mask, 1u << bit);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < (1 << D) && ((tile_mask >> threadIdx.x) & 1u)) {
+            int u[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((threadIdx.x >> a) & 1);
+            fsim[lin3<D>(u, P.node_tiles)] = 1u;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ grid update
+
+// One CTA per node tile; tiles not touched by the last P2G return at once.
+// Reads (m, q + dt f), writes the contact-corrected velocity and clears the
+// accumulator for the next step.
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restrict__ A,
+                                              R4<R> *__restrict__ V, uint32_t *__restrict__ flags)
+{
+    using Gm = Geo<D>;
+    const int64_t ut = blockIdx.x;
+    if (flags[ut] == 0u) return;
+    const int sim = (int)(ut / P.node_tiles_per_sim);
+    int64_t r = ut - (int64_t)sim * P.node_tiles_per_sim;
+    int u[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = (int)(r % P.node_tiles[a]);
+        r /= P.node_tiles[a];
+    }
+    R4<R> *As = A + (int64_t)sim * P.nodes_per_sim;
+    R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
+    constexpr int floor_w = 2 * (D - 1);
+    for (int i = threadIdx.x; i < Gm::TN; i += blockDim.x) {
+        int a3[3] = {0, 0, 0};
+        int rr = i;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            a3[a] = u[a] * Gm::T + rr % Gm::T;
+            rr /= Gm::T;
+            ok = ok && a3[a] < P.G_nodes[a];
+        }
+        if (!ok) continue;
+        const int64_t idx = lin3<D>(a3, P.G_nodes);
+        const R4<R> acc = As[idx];
+        if (acc.x == R(0) && acc.y == R(0) && acc.z == R(0) && acc.w == R(0)) continue;
+        As[idx] = R4<R>{R(0), R(0), R(0), R(0)};
+        R vel[3] = {R(0), R(0), R(0)};
+        if (acc.x > P.m_eps) {
+            const R inv_m = R(1) / acc.x;
+            vel[0] = acc.y * inv_m + P.dt * P.gravity[0];
+            vel[1] = acc.z * inv_m + P.dt * P.gravity[1];
+            if (D == 3) vel[2] = acc.w * inv_m + P.dt * P.gravity[2];
+        }
+        // walls x-, x+, y-, y+, (z-, z+), floor last
+#pragma unroll
+        for (int q = 0; q < 2 * D; ++q) {
+            const int w = q < 2 * D - 1 ? (q < floor_w ? q : q + 1) : floor_w;
+            const int ax = w >> 1, hi = w & 1;
+            const int c = a3[ax] - 2;
+            const bool on = hi ? (c >= P.n_cells[ax]) : (c <= 0);
+            if (!on) continue;
+            const R vn = hi ? vel[ax] : -vel[ax];
+            if (!(vn > R(0))) continue;
+            const R mu = wall_mu<R, D>(P, w, sim, a3);
+            vel[ax] = R(0);
+            if (mu > R(0)) {
+                R vt2 = R(0);
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) vt2 += vel[bb] * vel[bb];
+                const R vt = rsqrt_(vt2);
+                const R scale = (vt <= mu * vn) ? R(0) : R(1) - mu * vn / vt;
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) vel[bb] *= scale;
+            }
+        }
+        Vs[idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) flags[ut] = 0u;
+}
+
+// ------------------------------------------------------------------ G2P
+
+// Drucker-Prager update of Appendix A in symmetric storage (xx, yy, zz, xy,
+// xz, yz).  L is the 3 x 3 velocity gradient (zero third row/column in 2D).
+template <class R>
+__device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[6], R &eps)
+{
+    const R dt = P.dt;
+    const R d0 = dt * L[0], d1 = dt * L[4], d2 = dt * L[8];
+    const R d3 = R(0.5) * dt * (L[1] + L[3]);
+    const R d4 = R(0.5) * dt * (L[2] + L[6]);
+    const R d5 = R(0.5) * dt * (L[5] + L[7]);
+    const R w01 = R(0.5) * dt * (L[1] - L[3]);
+    const R w02 = R(0.5) * dt * (L[2] - L[6]);
+    const R w12 = R(0.5) * dt * (L[5] - L[7]);
+    // full stress and spin W (W_01 = w01, W_02 = w02, W_12 = w12, antisymmetric)
+    const R S00 = s[0], S11 = s[1], S22 = s[2], S01 = s[3], S02 = s[4], S12 = s[5];
+    // M = W S
+    const R M00 = w01 * S01 + w02 * S02;
+    const R M01 = w01 * S11 + w02 * S12;
+    const R M02 = w01 * S12 + w02 * S22;
+    const R M10 = -w01 * S00 + w12 * S02;
+    const R M11 = -w01 * S01 + w12 * S12;
+    const R M12 = -w01 * S02 + w12 * S22;
+    const R M20 = -w02 * S00 - w12 * S01;
+    const R M21 = -w02 * S01 - w12 * S11;
+    const R M22 = -w02 * S02 - w12 * S12;
+    // rotated stress S + M + M^T, then trial stress with isotropic elasticity
+    const R lam_tr = (P.K - R(2) / R(3) * P.G) * (d0 + d1 + d2);
+    const R twoG = R(2) * P.G;
+    R t[6];
+    t[0] = S00 + R(2) * M00 + lam_tr + twoG * d0;
+    t[1] = S11 + R(2) * M11 + lam_tr + twoG * d1;
+    t[2] = S22 + R(2) * M22 + lam_tr + twoG * d2;
+    t[3] = S01 + M01 + M10 + twoG * d3;
+    t[4] = S02 + M02 + M20 + twoG * d4;
+    t[5] = S12 + M12 + M21 + twoG * d5;
+    const R sm = (t[0] + t[1] + t[2]) / R(3);
+    R dev[6] = {t[0] - sm, t[1] - sm, t[2] - sm, t[3], t[4], t[5]};
+    const R tau = rsqrt_(R(0.5) * (dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]) +
+                         dev[3] * dev[3] + dev[4] * dev[4] + dev[5] * dev[5]);
+    const R fs = tau - P.k_phi + P.q_phi * sm;
+    const R ft = sm - P.sig_t;
+    const R h = tau - P.tau_P - P.alpha_P * (sm - P.sig_t);
+    if (fs <= R(0) && ft < R(0)) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s[k] = t[k];
+        return;
+    }
+    if ((fs > R(0) && ft < R(0)) || (h > R(0) && ft >= R(0))) {
+        const R dl = fs / (P.G + P.K * P.q_phi * P.q_psi);
+        R smn = sm - P.K * P.q_psi * dl;
+        R taun = P.k_phi - P.q_phi * smn;
+        if (!P.dp_literal && smn > P.sig_t) {
+            smn = P.sig_t;
+            taun = P.tau_P;
+        }
+        const R r = tau > R(0) ? taun / tau : R(0);
+        s[0] = r * dev[0] + smn; s[1] = r * dev[1] + smn; s[2] = r * dev[2] + smn;
+        s[3] = r * dev[3]; s[4] = r * dev[4]; s[5] = r * dev[5];
+        eps += dl * P.eps2_coef;
+        return;
+    }
+    eps += (sm - P.sig_t) / P.K * (R(1.4142135623730951) / R(3));
+    R r = R(1);
+    if (!P.dp_literal && tau > P.tau_P) r = P.tau_P / tau;
+    s[0] = r * dev[0] + P.sig_t; s[1] = r * dev[1] + P.sig_t; s[2] = r * dev[2] + P.sig_t;
+    s[3] = r * dev[3]; s[4] = r * dev[4]; s[5] = r * dev[5];
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_g2p(const Params<R> P, R *__restrict__ S,
+                                             const int32_t *__restrict__ sim_of,
+                                             const R4<R> *__restrict__ V, int32_t *__restrict__ status)
+{
+    using Gm = Geo<D>;
+    const int64_t np = P.npad;
+    bool bad = false;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        R x[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = S[(P.off_x + a) * np + p];
+        const R4<R> *Vs = V + (int64_t)sim_of[p] * P.nodes_per_sim;
+        int b[D];
+        R fx[D], w[D][3], dw[D][3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+            fx[a] = x[a] * P.inv_dx - R(b[a]);
+            bspline(fx[a], P.inv_dx, w[a], dw[a]);
+        }
+        R vp[D], Bm[D * D], L[D * D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) vp[q] = R(0);
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) { Bm[q] = R(0); L[q] = R(0); }
+#pragma unroll
+        for (int k = 0; k < Gm::STENCIL; ++k) {
+            const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
+            const int kk[3] = {k0, k1, k2};
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = b[a] + 2 + kk[a];
+            const R4<R> vn = Vs[lin3<D>(a3, P.G_nodes)];
+            const R vi[3] = {vn.x, vn.y, vn.z};
+            R wt = w[0][k0] * w[1][k1];
+            R g[D];
+            if constexpr (D == 2) {
+                g[0] = dw[0][k0] * w[1][k1];
+                g[1] = w[0][k0] * dw[1][k1];
+            } else {
+                const R w2 = w[D - 1][k2];
+                g[0] = dw[0][k0] * w[1][k1] * w2;
+                g[1] = w[0][k0] * dw[1][k1] * w2;
+                g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
+                wt *= w2;
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const R wv = wt * vi[a];
+                vp[a] += wv;
+#pragma unroll
+                for (int c2 = 0; c2 < D; ++c2) {
+                    Bm[a * D + c2] += wv * (R(kk[c2]) - fx[c2]);
+                    L[a * D + c2] += vi[a] * g[c2];
+                }
+            }
+        }
+        // C = B D^{-1} with D = dx^2 / 4 I; B was accumulated in units of dx
+        const R cscale = R(4) * P.inv_dx;
+        R trL = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) trL += L[a * D + a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            R xn = x[a] + P.dt * vp[a];
+            xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
+            bad |= !rfinite(xn) || !rfinite(vp[a]);
+            S[(P.off_x + a) * np + p] = xn;
+            S[(P.off_v + a) * np + p] = vp[a];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = Bm[q] * cscale;
+        // F <- (I + dt L) F
+        R F[D * D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) F[q] = S[(P.off_F + q) * np + p];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) {
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) s += L[a * D + k] * F[k * D + c2];
+                S[(P.off_F + a * D + c2) * np + p] = F[a * D + c2] + P.dt * s;
+            }
+        const R rho = S[P.off_rho * np + p] / (R(1) + P.dt * trL);
+        S[P.off_rho * np + p] = rho;
+        bad |= !rfinite(rho);
+        if (P.material == 1) {
+            R L3[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) L3[q] = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int c2 = 0; c2 < D; ++c2) L3[a * 3 + c2] = L[a * D + c2];
+            R s6[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
+            R e = S[P.off_eps * np + p];
+            dp_update(P, L3, s6, e);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                S[(P.off_sig + k) * np + p] = s6[k];
+                bad |= !rfinite(s6[k]);
+            }
+            S[P.off_eps * np + p] = e;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, (int32_t)kStatusNaN);
+}
+
+// ------------------------------------------------------------------ state management
+
+template <class R, int D>
+__global__ void k_init_state(const Params<R> P, R *__restrict__ S, int32_t *__restrict__ id,
+                             const double *__restrict__ x, const double *__restrict__ v)
+{
+    const int64_t np = P.npad;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            S[(P.off_x + a) * np + p] = (R)x[p * D + a];
+            S[(P.off_v + a) * np + p] = v ? (R)v[p * D + a] : R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) {
+            S[(P.off_C + q) * np + p] = R(0);
+            S[(P.off_F + q) * np + p] = (q % (D + 1) == 0) ? R(1) : R(0);
+        }
+        S[P.off_rho * np + p] = P.rho0;
+        if (P.material == 1) {
+            for (int k = 0; k < 6; ++k) S[(P.off_sig + k) * np + p] = R(0);
+            S[P.off_eps * np + p] = R(0);
+        }
+        id[p] = (int32_t)p;
+    }
+}
+
+template <class R, int D>
+__global__ void k_keys(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ sim,
+                       uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
+{
+    using Gm = Geo<D>;
+    const int64_t np = P.npad;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t tile = 0, cell = 0, tstride = 1, cstride = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int s = base_cell(S[(P.off_x + a) * np + p], P.inv_dx, P.n_cells[a]) + 1;   // [0, N]
+            tile += (int64_t)(s / Gm::T) * tstride;
+            cell += (int64_t)(s % Gm::T) * cstride;
+            tstride *= P.n_tiles[a];
+            cstride *= Gm::T;
+        }
+        const int64_t tkey = (int64_t)sim[p] * P.tiles_per_sim + tile;
+        keys[p] = (uint32_t)((tkey << Gm::CELL_BITS) | cell);
+        vals[p] = (int32_t)p;
+    }
+}
+
+template <class R>
+__global__ void k_permute(int ncomp, int64_t n, int64_t npad, const R *__restrict__ S, R *__restrict__ S2,
+                          const int32_t *__restrict__ perm, const int32_t *__restrict__ id,
+                          int32_t *__restrict__ id2, const int32_t *__restrict__ sim,
+                          int32_t *__restrict__ sim2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = perm[i];
+        for (int c = 0; c < ncomp; ++c) S2[c * npad + i] = S[c * npad + o];
+        id2[i] = id[o];
+        sim2[i] = sim[o];
+    }
+}
+
+// Field readback in load order (doubles).
+template <class R, int D>
+__global__ void k_get_field(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
+                            int field, double *__restrict__ out)
+{
+    const int64_t np = P.npad;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = id[p];
+        switch (field) {
+        case 0:
+            for (int a = 0; a < D; ++a) out[o * D + a] = (double)S[(P.off_x + a) * np + p];
+            break;
+        case 1:
+            for (int a = 0; a < D; ++a) out[o * D + a] = (double)S[(P.off_v + a) * np + p];
+            break;
+        case 2:
+            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)S[(P.off_C + q) * np + p];
+            break;
+        case 3:
+            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)S[(P.off_F + q) * np + p];
+            break;
+        case 4:
+            out[o] = (double)S[P.off_rho * np + p];
+            break;
+        case 5: {
+            double s9[9];
+            if (P.material == 0) {
+                const double pr = (double)tait(P, S[P.off_rho * np + p]);
+                for (int q = 0; q < 9; ++q) s9[q] = (q % 4 == 0) ? -pr : 0.0;
+            } else {
+                const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+                for (int q = 0; q < 9; ++q) s9[q] = (double)S[(P.off_sig + map[q]) * np + p];
+            }
+            for (int q = 0; q < 9; ++q) out[o * 9 + q] = s9[q];
+            break;
+        }
+        case 6:
+            out[o] = P.material == 1 ? (double)S[P.off_eps * np + p] : 0.0;
+            break;
+        default:
+            break;
+        }
+    }
+}
+
+template <class R, int D>
+__global__ void k_set_field(const Params<R> P, R *__restrict__ S, const int32_t *__restrict__ id, int field,
+                            const double *__restrict__ in)
+{
+    const int64_t np = P.npad;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = id[p];
+        switch (field) {
+        case 0:
+            for (int a = 0; a < D; ++a) S[(P.off_x + a) * np + p] = (R)in[o * D + a];
+            break;
+        case 1:
+            for (int a = 0; a < D; ++a) S[(P.off_v + a) * np + p] = (R)in[o * D + a];
+            break;
+        case 2:
+            for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = (R)in[o * D * D + q];
+            break;
+        case 3:
+            for (int q = 0; q < D * D; ++q) S[(P.off_F + q) * np + p] = (R)in[o * D * D + q];
+            break;
+        case 4:
+            S[P.off_rho * np + p] = (R)in[o];
+            break;
+        case 5: {
+            const double *s9 = in + o * 9;
+            S[(P.off_sig + 0) * np + p] = (R)s9[0];
+            S[(P.off_sig + 1) * np + p] = (R)s9[4];
+            S[(P.off_sig + 2) * np + p] = (R)s9[8];
+            S[(P.off_sig + 3) * np + p] = (R)(0.5 * (s9[1] + s9[3]));
+            S[(P.off_sig + 4) * np + p] = (R)(0.5 * (s9[2] + s9[6]));
+            S[(P.off_sig + 5) * np + p] = (R)(0.5 * (s9[5] + s9[7]));
+            break;
+        }
+        case 6:
+            S[P.off_eps * np + p] = (R)in[o];
+            break;
+        default:
+            break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class R>
+Params<R> make_params(const HostParams &h, const DevState &ds)
+{
+    Params<R> P{};
+    for (int a = 0; a < 3; ++a) {
+        P.n_cells[a] = h.n_cells[a];
+        P.gravity[a] = (R)h.gravity[a];
+        P.L[a] = (R)(h.n_cells[a] * h.dx);
+        P.n_tiles[a] = h.n_tiles[a];
+        P.G_nodes[a] = h.G_nodes[a];
+        P.node_tiles[a] = h.node_tiles[a];
+    }
+    P.dx = (R)h.dx;
+    P.inv_dx = (R)(1.0 / h.dx);
+    P.dt = (R)h.dt;
+    P.rho0 = (R)h.rho0;
+    P.inv_rho0 = (R)(1.0 / h.rho0);
+    P.bulk_K = (R)h.bulk_K;
+    P.gamma = (R)h.gamma;
+    const double gr = std::floor(h.gamma);
+    P.gamma_int = (gr == h.gamma && h.gamma >= 1.0 && h.gamma <= 16.0) ? (int)gr : 0;
+    P.mass = (R)h.mass;
+    P.m_eps = (R)h.m_eps;
+    P.K = (R)h.K; P.G = (R)h.G;
+    P.q_phi = (R)h.q_phi; P.k_phi = (R)h.k_phi; P.q_psi = (R)h.q_psi;
+    P.sig_t = (R)h.sig_t; P.tau_P = (R)h.tau_P; P.alpha_P = (R)h.alpha_P;
+    P.eps2_coef = (R)std::sqrt(1.0 / 3.0 + 2.0 / 9.0 * h.q_psi * h.q_psi);
+    P.material = h.material;
+    P.dp_literal = h.dp_literal;
+    P.nodes_per_sim = h.nodes_per_sim;
+    P.tiles_per_sim = h.tiles_per_sim;
+    P.node_tiles_per_sim = h.node_tiles_per_sim;
+    P.n = h.n;
+    P.npad = h.npad;
+    P.off_x = h.off_x; P.off_v = h.off_v; P.off_C = h.off_C; P.off_F = h.off_F;
+    P.off_rho = h.off_rho; P.off_sig = h.off_sig; P.off_eps = h.off_eps;
+    for (int w = 0; w < kMaxWalls; ++w) {
+        P.wall[w].mu = ds.mu_dev[w];
+        P.wall[w].n_seg[0] = ds.n_seg[w][0];
+        P.wall[w].n_seg[1] = ds.n_seg[w][1];
+        int nt = 0;
+        for (int b = 0; b < h.dim; ++b)
+            if (b != w / 2) P.wall[w].seg_axis[nt++] = b;
+        if (nt < 2) P.wall[w].seg_axis[1] = 0;
+    }
+    return P;
+}
+
+inline int grid_blocks(int64_t n, int threads, int num_sms, int per_sm = 16)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * per_sm;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <class R, int D> struct Launch {
+    static void init_state(const HostParams &h, DevState &ds, const double *x, const double *v)
+    {
+        auto P = make_params<R>(h, ds);
+        k_init_state<R, D><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(
+            P, (R *)ds.S, ds.id, x, v);
+    }
+    static void keys(const HostParams &h, DevState &ds)
+    {
+        auto P = make_params<R>(h, ds);
+        k_keys<R, D><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.sim,
+                                                                               ds.keys[0], ds.vals[0]);
+    }
+    static void permute(const HostParams &h, DevState &ds)
+    {
+        k_permute<R><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(
+            h.ncomp, h.n, h.npad, (const R *)ds.S, (R *)ds.S2, ds.vals[0], ds.id, ds.id2, ds.sim, ds.sim2);
+    }
+    static size_t p2g_smem() { return (size_t)(D + 1) * Geo<D>::WN * sizeof(R); }
+    static void p2g(const HostParams &h, DevState &ds)
+    {
+        auto P = make_params<R>(h, ds);
+        const size_t smem = p2g_smem();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_p2g<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        int64_t nb = ds.max_chunks;
+        const int64_t cap = (int64_t)ds.num_sms * 8;
+        if (nb > cap) nb = cap;
+        if (nb < 1) nb = 1;
+        k_p2g<R, D><<<(int)nb, 256, smem, ds.stream>>>(P, (const R *)ds.S, ds.chunks, ds.counters,
+                                                       (R4<R> *)ds.A, ds.flags, ds.escaped);
+    }
+    static void grid(const HostParams &h, DevState &ds)
+    {
+        auto P = make_params<R>(h, ds);
+        const int64_t nb = h.batch * h.node_tiles_per_sim;
+        k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags);
+    }
+    static void g2p(const HostParams &h, DevState &ds)
+    {
+        auto P = make_params<R>(h, ds);
+        k_g2p<R, D><<<grid_blocks(h.n, 256, ds.num_sms, 8), 256, 0, ds.stream>>>(
+            P, (R *)ds.S, ds.sim, (const R4<R> *)ds.V, ds.status);
+    }
+    static void get_field(const HostParams &h, DevState &ds, int field, double *out)
+    {
+        auto P = make_params<R>(h, ds);
+        k_get_field<R, D><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.id,
+                                                                                    field, out);
+    }
+    static void set_field(const HostParams &h, DevState &ds, int field, const double *in)
+    {
+        auto P = make_params<R>(h, ds);
+        k_set_field<R, D><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(P, (R *)ds.S, ds.id, field,
+                                                                                    in);
+    }
+};
+
+template <class R> struct Dispatch {
+#define MPM_DISPATCH(name, args, call)                       \
+    static void name args                                    \
+    {                                                        \
+        if (h.dim == 2) Launch<R, 2>::call;                  \
+        else Launch<R, 3>::call;                             \
+    }
+    MPM_DISPATCH(init_state, (const HostParams &h, DevState &ds, const double *x, const double *v),
+                 init_state(h, ds, x, v))
+    MPM_DISPATCH(keys, (const HostParams &h, DevState &ds), keys(h, ds))
+    MPM_DISPATCH(permute, (const HostParams &h, DevState &ds), permute(h, ds))
+    MPM_DISPATCH(p2g, (const HostParams &h, DevState &ds), p2g(h, ds))
+    MPM_DISPATCH(grid, (const HostParams &h, DevState &ds), grid(h, ds))
+    MPM_DISPATCH(g2p, (const HostParams &h, DevState &ds), g2p(h, ds))
+    MPM_DISPATCH(get_field, (const HostParams &h, DevState &ds, int f, double *o), get_field(h, ds, f, o))
+    MPM_DISPATCH(set_field, (const HostParams &h, DevState &ds, int f, const double *i), set_field(h, ds, f, i))
+#undef MPM_DISPATCH
+};
+
+}  // namespace mpm

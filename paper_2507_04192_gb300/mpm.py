@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libmpm (include/mpm.h).
+
+Argument marshalling only: every step of the MPM path runs in the CUDA
+kernels of ``libmpm.so``.  There is no CPU fallback: if the library is
+missing or cannot be built, loading fails with an error.
+
+The module-level functions carry the C names (``mpm_create``, ``mpm_step``,
+...); :class:`Simulation` is a small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECUDA, MPM_ENAN = 0, -1, -2, -3, -4
+MPM_EDOMAIN, MPM_ETIMEOUT, MPM_ECORRUPT, MPM_ESTATE = -5, -6, -7, -8
+STATUS_NAMES = {0: "MPM_OK", -1: "MPM_EINVAL", -2: "MPM_ENOMEM", -3: "MPM_ECUDA", -4: "MPM_ENAN",
+                -5: "MPM_EDOMAIN", -6: "MPM_ETIMEOUT", -7: "MPM_ECORRUPT", -8: "MPM_ESTATE"}
+MPM_FP32, MPM_FP64 = 0, 1
+MPM_FLUID, MPM_DRUCKER_PRAGER = 0, 1
+FIELDS = {"x": 0, "v": 1, "C": 2, "F": 3, "rho": 4, "sigma": 5, "eps": 6}
+KERNELS = {"sort": 0, "p2g": 1, "grid": 2, "g2p": 3}
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_cells", C.c_int * 3), ("dx", C.c_double), ("dt", C.c_double),
+                ("gravity", C.c_double * 3), ("precision", C.c_int), ("sort_every", C.c_int),
+                ("batch", C.c_int)]
+
+
+class Material(C.Structure):
+    _fields_ = [("kind", C.c_int), ("rho0", C.c_double), ("bulk_K", C.c_double), ("gamma", C.c_double),
+                ("viscosity", C.c_double), ("E", C.c_double), ("nu", C.c_double), ("phi_deg", C.c_double),
+                ("psi_deg", C.c_double), ("cohesion", C.c_double), ("sigma_t", C.c_double),
+                ("dp_literal", C.c_int)]
+
+
+class MPMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libmpm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmpm is not built ({path}); run paper_2507_04192_gb300/build.py")
+        lib = C.CDLL(path)
+        P, I, L, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sigs = {
+            "mpm_create": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, C.POINTER(P)]),
+            "mpm_destroy": (None, [P]),
+            "mpm_load_particles": (I, [P, L, P, P, D, P]),
+            "mpm_set_particle_field": (I, [P, I, P]),
+            "mpm_set_friction_field": (I, [P, I, P, P]),
+            "mpm_step": (I, [P, I]),
+            "mpm_synchronize": (I, [P]),
+            "mpm_get_particles": (I, [P, I, P]),
+            "mpm_field_width": (I, [P, I]),
+            "mpm_num_particles": (L, [P]),
+            "mpm_last_error": (I, [P, C.c_char_p, I]),
+            "mpm_set_timing": (I, [P, I]),
+            "mpm_get_timing": (I, [P, I, C.POINTER(D), C.POINTER(L)]),
+            "mpm_reset_timing": (I, [P]),
+            "mpm_get_stats": (I, [P, C.POINTER(L), I]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, rc: int):
+    if rc != MPM_OK:
+        buf = C.create_string_buffer(512)
+        if ctx:
+            load_library().mpm_last_error(ctx, buf, 512)
+        raise MPMError(rc, buf.value.decode(errors="replace"))
+
+
+# ---------------------------------------------------------------- C-named wrappers
+
+def mpm_create(grid: GridDesc, material: Material, stream: int = 0):
+    h = C.c_void_p()
+    _check(None, load_library().mpm_create(C.byref(grid), C.byref(material), C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def mpm_destroy(ctx):
+    load_library().mpm_destroy(ctx)
+
+
+def mpm_load_particles(ctx, x: np.ndarray, v: Optional[np.ndarray], particle_volume: float,
+                       sim_id: Optional[np.ndarray] = None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    sid = None if sim_id is None else np.ascontiguousarray(sim_id, dtype=np.int32)
+    _check(ctx, load_library().mpm_load_particles(ctx, x.shape[0], _dptr(x), None if vv is None else _dptr(vv),
+                                                  float(particle_volume), None if sid is None else _dptr(sid)))
+
+
+def mpm_set_particle_field(ctx, field: str, values: np.ndarray):
+    a = np.ascontiguousarray(values, dtype=np.float64)
+    _check(ctx, load_library().mpm_set_particle_field(ctx, FIELDS[field], _dptr(a)))
+
+
+def mpm_set_friction_field(ctx, wall: int, n_seg: Sequence[int], mu: np.ndarray):
+    ns = (C.c_int * 2)(int(n_seg[0]), int(n_seg[1]) if len(n_seg) > 1 else 1)
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    _check(ctx, load_library().mpm_set_friction_field(ctx, int(wall), ns, _dptr(m)))
+
+
+def mpm_step(ctx, n_steps: int):
+    _check(ctx, load_library().mpm_step(ctx, int(n_steps)))
+
+
+def mpm_synchronize(ctx):
+    _check(ctx, load_library().mpm_synchronize(ctx))
+
+
+def mpm_field_width(ctx, field: str) -> int:
+    return int(load_library().mpm_field_width(ctx, FIELDS[field]))
+
+
+def mpm_num_particles(ctx) -> int:
+    return int(load_library().mpm_num_particles(ctx))
+
+
+def mpm_get_particles(ctx, field: str, out: Optional[np.ndarray] = None) -> np.ndarray:
+    n = mpm_num_particles(ctx)
+    w = mpm_field_width(ctx, field)
+    if out is None:
+        out = np.empty((n, w), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.size == n * w
+    _check(ctx, load_library().mpm_get_particles(ctx, FIELDS[field], _dptr(out)))
+    return out
+
+
+def mpm_set_timing(ctx, enable: bool):
+    _check(ctx, load_library().mpm_set_timing(ctx, int(bool(enable))))
+
+
+def mpm_get_timing(ctx, kernel: str):
+    ms, n = C.c_double(), C.c_int64()
+    _check(ctx, load_library().mpm_get_timing(ctx, KERNELS[kernel], C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def mpm_reset_timing(ctx):
+    _check(ctx, load_library().mpm_reset_timing(ctx))
+
+
+def mpm_get_stats(ctx) -> dict:
+    out = (C.c_int64 * 6)()
+    _check(ctx, load_library().mpm_get_stats(ctx, out, 6))
+    keys = ("active_tiles", "chunks", "escaped", "sorts", "steps", "launches")
+    return dict(zip(keys, list(out)))
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+def material_struct(mat: dict, dp_literal: bool = False) -> Material:
+    m = Material()
+    m.kind = int(mat.get("kind", 0))
+    for k in ("rho0", "bulk_K", "gamma", "viscosity", "E", "nu", "phi_deg", "psi_deg", "cohesion", "sigma_t"):
+        setattr(m, k, float(mat.get(k, 0.0)))
+    m.dp_literal = int(bool(dp_literal or mat.get("dp_literal", False)))
+    return m
+
+
+def grid_struct(dim, n_cells, dx, dt, gravity, precision=MPM_FP32, sort_every=8, batch=1) -> GridDesc:
+    g = GridDesc()
+    g.dim = int(dim)
+    for a in range(3):
+        g.n_cells[a] = int(n_cells[a]) if a < dim else 1
+        g.gravity[a] = float(gravity[a]) if a < dim else 0.0
+    g.dx, g.dt = float(dx), float(dt)
+    g.precision = int(precision)
+    g.sort_every = int(sort_every)
+    g.batch = int(batch)
+    return g
+
+
+class Simulation:
+    """One libmpm context: a grid, a material and a set of particles."""
+
+    def __init__(self, dim, n_cells, dx, dt, gravity, material: dict, precision=MPM_FP32, sort_every=8,
+                 batch=1, stream: int = 0, dp_literal=False):
+        self.dim = dim
+        self._grid = grid_struct(dim, n_cells, dx, dt, gravity, precision, sort_every, batch)
+        self._mat = material_struct(material, dp_literal)
+        self.ctx = mpm_create(self._grid, self._mat, stream)
+
+    @classmethod
+    def from_workload(cls, w, precision=MPM_FP32, sort_every=None, batch=1, stream=0, load=True, dt=None):
+        sim = cls(w.dim, w.n_cells, w.dx, w.dt if dt is None else dt, w.gravity, w.material, precision,
+                  w.sort_every if sort_every is None else sort_every, batch, stream)
+        if load:
+            sim.load(w.x, w.v, w.particle_volume)
+            for wall, nseg, mu in w.friction:
+                sim.set_friction(wall, nseg, np.tile(np.asarray(mu, dtype=np.float64).reshape(-1), batch))
+        return sim
+
+    def close(self):
+        if self.ctx:
+            mpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, x, v=None, particle_volume=1.0, sim_id=None):
+        mpm_load_particles(self.ctx, x, v, particle_volume, sim_id)
+
+    def set_field(self, field, values):
+        mpm_set_particle_field(self.ctx, field, values)
+
+    def set_friction(self, wall, n_seg, mu):
+        mpm_set_friction_field(self.ctx, wall, n_seg, mu)
+
+    def step(self, n=1):
+        mpm_step(self.ctx, n)
+
+    def synchronize(self):
+        mpm_synchronize(self.ctx)
+
+    def get(self, field):
+        a = mpm_get_particles(self.ctx, field)
+        d = self.dim
+        if field in ("C", "F"):
+            return a.reshape(-1, d, d)
+        if field == "sigma":
+            return a.reshape(-1, 3, 3)
+        if field in ("rho", "eps"):
+            return a.reshape(-1)
+        return a
+
+    @property
+    def n(self):
+        return mpm_num_particles(self.ctx)
+
+    def stats(self):
+        return mpm_get_stats(self.ctx)
