@@ -188,7 +188,7 @@ int mpm_get_timing(mpm_ctx *ctx, int kernel, double *total_ms, int64_t *launches
 int mpm_reset_timing(mpm_ctx *ctx);
 
 /*
- * Counters (synchronises).  out[0] active tiles, out[1] work chunks after the
+ * Counters (synchronises).  out[0] active tiles, out[1] work units (tiles) after the
  * last sort, out[2] particles that took the out-of-tile path since creation,
  * out[3] sorts, out[4] steps, out[5] kernel launches since creation.
  */

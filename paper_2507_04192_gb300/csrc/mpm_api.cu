@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/mpm.h"
 #include "mpm_internal.cuh"
 
@@ -89,7 +91,7 @@ void free_particles(mpm_ctx *c)
     dfree(d.S); dfree(d.S2);
     dfree(d.id); dfree(d.id2); dfree(d.sim); dfree(d.sim2);
     dfree(d.keys[0]); dfree(d.keys[1]); dfree(d.vals[0]); dfree(d.vals[1]);
-    dfree(d.hist); dfree(d.chunks); dfree(d.staging);
+    dfree(d.hist); dfree(d.tiles); dfree(d.perm); dfree(d.posmap); dfree(d.cell_off); dfree(d.staging);
     c->hp.n = 0;
 }
 
@@ -153,12 +155,12 @@ int do_sort(mpm_ctx *c)
     TimingScope ts(c, MPM_KERNEL_SORT);
     c->ops->keys(c->hp, c->ds);
     radix_sort_pairs(c->hp, c->ds);
+    build_tiles(c->hp, c->ds);             // tile list, (rank, cell) order, gather permutation
     c->ops->permute(c->hp, c->ds);
     std::swap(c->ds.S, c->ds.S2);
     std::swap(c->ds.id, c->ds.id2);
     std::swap(c->ds.sim, c->ds.sim2);
-    build_tiles(c->hp, c->ds);
-    c->launches += 4 + 3 * ((c->ds.key_bits + kRadixBits - 1) / kRadixBits);
+    c->launches += 5 + 3 * ((c->ds.key_bits + kRadixBits - 1) / kRadixBits);
     c->sorts++;
     c->need_sort = false;
     c->steps_since_sort = 0;
@@ -174,6 +176,7 @@ int read_status(mpm_ctx *c)
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
     collect_timing(c);
     const int32_t s = *c->h_status;
+    if (s & kStatusTimeout) return fail(c, MPM_ETIMEOUT, "a bounded device wait ran out (grid window copy)");
     if (s & kStatusNaN) return fail(c, MPM_ENAN, "a particle state became non-finite");
     if (s & kStatusChunkOverflow) return fail(c, MPM_ECUDA, "work chunk list overflow (internal)");
     return MPM_OK;
@@ -189,6 +192,42 @@ int field_width(const mpm_ctx *c, int field)
     case MPM_FIELD_SIGMA: return 9;
     default: return MPM_EINVAL;
     }
+}
+
+// TMA descriptor of the grid velocities V: dims (4 components, G_x, G_y, [G_z], batch),
+// box (4, W, W, [W], 1) = the shared-memory window of one tile.
+int make_tensor_map_V(mpm_ctx *c)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess)
+        return fail(c, MPM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const HostParams &h = c->hp;
+    const int d = h.dim;
+    const cuuint64_t rsz = h.precision == MPM_FP64 ? 8 : 4;
+    cuuint64_t gdim[5], gstride[4];
+    cuuint32_t box[5], estr[5];
+    gdim[0] = 4;
+    box[0] = 4;
+    cuuint64_t stride = 4 * rsz;
+    for (int a = 0; a < d; ++a) {
+        gdim[1 + a] = (cuuint64_t)h.G_nodes[a];
+        gstride[a] = stride;
+        stride *= (cuuint64_t)h.G_nodes[a];
+        box[1 + a] = (cuuint32_t)h.W;
+    }
+    gdim[d + 1] = (cuuint64_t)h.batch;
+    gstride[d] = stride;
+    box[d + 1] = 1;
+    for (int i = 0; i < 5; ++i) estr[i] = 1;
+    CUresult r = encode(&c->ds.tmap_V, rsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        (cuuint32_t)(d + 2), c->ds.V, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, MPM_ECUDA, "cuTensorMapEncodeTiled failed for the grid velocities");
+    return MPM_OK;
 }
 
 }  // namespace
@@ -277,7 +316,6 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     h.off_sig = h.off_rho + 1;
     h.off_eps = h.off_sig + 6;
     h.ncomp = m.kind == MPM_DRUCKER_PRAGER ? h.off_eps + 1 : h.off_rho + 1;
-    h.chunk = 1024;
     c->ops = g.precision == MPM_FP64 ? &ops_f64 : &ops_f32;
 
     DevState &ds = c->ds;
@@ -319,6 +357,7 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
         cudaMemsetAsync(ds.escaped, 0, sizeof(unsigned long long), ds.stream);
         if (cudaStreamSynchronize(ds.stream) != cudaSuccess) rc = MPM_ECUDA;
     }
+    if (rc == MPM_OK) rc = make_tensor_map_V(c);
     if (rc != MPM_OK) {
         mpm_destroy(c);
         return rc;
@@ -369,7 +408,11 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     h.mass = h.rho0 * particle_volume;
     const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
     const int nblk = (int)((n + kSortChunk - 1) / kSortChunk);
-    ds.max_chunks = n / h.chunk + (int64_t)c->grid.batch * h.tiles_per_sim + 1;
+    {
+        const int64_t all_tiles = (int64_t)c->grid.batch * h.tiles_per_sim;
+        ds.max_tiles = all_tiles < n ? all_tiles : n;
+    }
+    const int TN = c->grid.dim == 2 ? Geo<2>::TN : Geo<3>::TN;
     int rc = MPM_OK;
     if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, (size_t)h.ncomp * h.npad * rsz, "particle state");
     if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S2, (size_t)h.ncomp * h.npad * rsz, "particle state (sort)");
@@ -382,7 +425,10 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
     if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk, "histogram");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.chunks, ds.max_chunks, "chunks");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, ds.max_tiles, "tile list");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.perm, n, "permutation");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.posmap, n, "position map");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.cell_off, (size_t)ds.max_tiles * (TN + 1), "cell offsets");
     if (rc == MPM_OK) rc = dalloc(c, &ds.staging, (size_t)n * 9, "staging");
     if (rc != MPM_OK) {
         free_particles(c);
@@ -561,7 +607,7 @@ int mpm_get_stats(mpm_ctx *c, int64_t *out, int n)
     CK(cudaMemcpyAsync(cnt, c->ds.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->ds.stream), "stats");
     CK(cudaMemcpyAsync(&esc, c->ds.escaped, sizeof(esc), cudaMemcpyDeviceToHost, c->ds.stream), "stats");
     CK(cudaStreamSynchronize(c->ds.stream), "stats");
-    const int64_t vals[6] = {cnt[1], cnt[0], (int64_t)esc, c->sorts, c->steps, c->launches};
+    const int64_t vals[6] = {cnt[1], cnt[1], (int64_t)esc, c->sorts, c->steps, c->launches};
     for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
     return MPM_OK;
 }

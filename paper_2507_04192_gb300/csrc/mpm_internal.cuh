@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace mpm {
@@ -60,7 +61,6 @@ struct HostParams {
     int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
     int64_t n, npad;
     int ncomp, off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
-    int chunk;             // particles per work chunk
 };
 
 template <class R>
@@ -92,20 +92,24 @@ struct DevState {
     int32_t *vals[2];
     uint32_t *hist;               // kRadixBins x n_sort_blocks
     int32_t *tile_start, *tile_end;   // per tile (batch x tiles_per_sim)
-    int4 *chunks;                 // (tile key, start, count, 0)
-    int64_t max_chunks;
-    int32_t *counters;            // [0] n_chunks, [1] n_active_tiles, [2] chunk overflow
+    int4 *tiles;                  // compact non-empty tiles: (tile key, start, count, 0)
+    int64_t max_tiles;
+    int32_t *perm;                // gather permutation of the last sort
+    int32_t *posmap;              // per particle in (cell, rank) order: slot within its tile
+    int32_t *cell_off;            // per compact tile: TN + 1 offsets into (cell, rank) order
+    int32_t *counters;            // [1] n_active_tiles
     void *A, *V;                  // grid accumulators and velocities, R4 per node
     uint32_t *flags;              // per node tile: touched since the last grid update
     int32_t *status;              // device status word (bit 0: non-finite state)
     unsigned long long *escaped;  // particles that took the out-of-window path
     double *staging;              // n x 9 doubles for host transfers
+    CUtensorMap tmap_V;           // TMA descriptor of V: (4, G_x, G_y, [G_z], batch)
     void *mu_dev[kMaxWalls];
     int n_seg[kMaxWalls][2];
     int key_bits;
 };
 
-enum StatusBits { kStatusNaN = 1, kStatusChunkOverflow = 2 };
+enum StatusBits { kStatusNaN = 1, kStatusChunkOverflow = 2, kStatusTimeout = 4 };
 
 // Launchers implemented per precision (mpm_kernels_f32.cu, mpm_kernels_f64.cu).
 struct Ops {

@@ -102,17 +102,85 @@ __device__ __forceinline__ R wall_mu(const Params<R> &P, int w, int sim, const i
     return static_cast<const R *>(wd.mu)[sim * per_sim + (int64_t)s[1] * wd.n_seg[0] + s[0]];
 }
 
+// ------------------------------------------------------------------ TMA / mbarrier helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(phase)
+                 : "memory");
+    return ok != 0u;
+}
+// Bounded wait: false after kMaxWaitIters unsuccessful polls.
+constexpr int kMaxWaitIters = 1 << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
+{
+    for (int it = 0; it < kMaxWaitIters; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+// TMA tiled load of the grid window of one tile: coordinates (component, node x, y, [z], sim).
+__device__ __forceinline__ void tma_load_window(void *dst, const CUtensorMap *map, const int org[3], int sim,
+                                                int dim, uint64_t *bar)
+{
+    if (dim == 3) {
+        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+                     "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(org[0]), "r"(org[1]), "r"(org[2]), "r"(sim),
+                     "r"(smem_u32(bar))
+                     : "memory");
+    } else {
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+                     "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(org[0]), "r"(org[1]), "r"(sim),
+                     "r"(smem_u32(bar))
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ P2G
 
-// Contribution of particle p to the 3^D stencil nodes: m w, and
-// m w (v + C (x_i - x_p)) - dt V sigma grad w (momentum plus dt times the
-// internal force; gravity is added in the grid update).
+// Separable form of one particle's P2G contribution.  With per-axis weights
+// w_a[j] and derivatives dw_a[j] (j = stencil offset), node k receives
+//   mass      m_p w_0[k0] w_1[k1] (w_2[k2])
+//   momentum  sum_b E[a][b][k_b] prod_{c != b} w_c[k_c]       (component a)
+// where E[a][b][j] = m_p C_ab dx j w_b[j] + Fm_ab dw_b[j] (+ m_p u0_a w_b[j] for b = 0),
+// u0 = v_p - C_p fx dx and Fm = -dt V_p sigma_p.  This is m_p w (v_p + C_p (x_i - x_p))
+// - dt V_p sigma_p grad w expanded over the tensor-product weights.
+template <class R, int D> struct P2GFactors {
+    int b[D];
+    R w[D][3];
+    R E[D][D][3];
+};
+
 template <class R, int D>
-__device__ __forceinline__ void p2g_particle(const Params<R> &P, const R *__restrict__ S, int64_t p,
-                                             const int org[3], R *sm, R4<R> *Asim, uint32_t *flags_sim,
-                                             bool &escaped)
+__device__ __forceinline__ void p2g_load_factors(const Params<R> &P, const R *__restrict__ S, int64_t p,
+                                                 P2GFactors<R, D> &f)
 {
-    using Gm = Geo<D>;
     const int64_t np = P.npad;
     R x[D], v[D], C[D * D], Fm[D * D];
 #pragma unroll
@@ -129,7 +197,6 @@ __device__ __forceinline__ void p2g_particle(const Params<R> &P, const R *__rest
 #pragma unroll
         for (int q = 0; q < D * D; ++q) Fm[q] = (q % (D + 1) == 0) ? c : R(0);
     } else {
-        // symmetric storage xx, yy, zz, xy, xz, yz; in-plane block acts on the grid
         R s6[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
@@ -143,97 +210,123 @@ __device__ __forceinline__ void p2g_particle(const Params<R> &P, const R *__rest
             Fm[6] = c * s6[4]; Fm[7] = c * s6[5]; Fm[8] = c * s6[2];
         }
     }
-    int b[D], l[D];
-    R fx[D], w[D][3], dw[D][3];
-    bool inside = true;
+    R fx[D], dw[D][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
-        fx[a] = x[a] * P.inv_dx - R(b[a]);
-        bspline(fx[a], P.inv_dx, w[a], dw[a]);
-        l[a] = b[a] + 2 - org[a];
-        inside = inside && (l[a] >= 0) && (l[a] <= Gm::W - 3);
-    }
-    escaped = !inside;
-    // affine velocity at node offset k: v + C (k - fx) dx
-    R u0[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        R s = v[a];
-#pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) s -= C[a * D + c2] * fx[c2] * P.dx;
-        u0[a] = s;
+        f.b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+        fx[a] = x[a] * P.inv_dx - R(f.b[a]);
+        bspline(fx[a], P.inv_dx, f.w[a], dw[a]);
     }
     const R mp = P.mass;
 #pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R u0 = v[a];
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) u0 -= C[a * D + c2] * fx[c2] * P.dx;
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) {
+            const R mc = mp * C[a * D + b2] * P.dx;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                R e = mc * R(j) * f.w[b2][j] + Fm[a * D + b2] * dw[b2][j];
+                if (b2 == 0) e += mp * u0 * f.w[0][j];
+                f.E[a][b2][j] = e;
+            }
+        }
+    }
+}
+
+// Mass and momentum (+ dt force) of stencil node k = (k0, k1, k2).
+template <class R, int D>
+__device__ __forceinline__ void p2g_node(const P2GFactors<R, D> &f, R mp, int k0, int k1, int k2, R &m, R mom[D])
+{
+    if constexpr (D == 2) {
+        m = mp * f.w[0][k0] * f.w[1][k1];
+#pragma unroll
+        for (int a = 0; a < D; ++a) mom[a] = f.E[a][0][k0] * f.w[1][k1] + f.w[0][k0] * f.E[a][1][k1];
+    } else {
+        const R wxy = f.w[0][k0] * f.w[1][k1];
+        const R wz = f.w[2][k2];
+        m = mp * wxy * wz;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            mom[a] = wz * (f.E[a][0][k0] * f.w[1][k1] + f.w[0][k0] * f.E[a][1][k1]) + wxy * f.E[a][2][k2];
+    }
+}
+
+template <int D> __device__ __forceinline__ int win_index(const int l[D], int k0, int k1, int k2)
+{
+    using Gm = Geo<D>;
+    if constexpr (D == 2) return (l[1] + k1) * Gm::W + (l[0] + k0);
+    else return ((l[2] + k2) * Gm::W + (l[1] + k1)) * Gm::W + (l[0] + k0);
+}
+
+// Scatter one particle's 3^D contributions: shared-memory atomics when its stencil
+// lies in the window (l = window coordinates of its base), else global atomics.
+template <class R, int D>
+__device__ __forceinline__ void p2g_scatter(const Params<R> &P, const P2GFactors<R, D> &f, const int org[3], R *sm,
+                                            R4<R> *Asim, uint32_t *flags_sim, bool &escaped)
+{
+    using Gm = Geo<D>;
+    int l[D];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        l[a] = f.b[a] + 2 - org[a];
+        inside = inside && l[a] >= 0 && l[a] <= Gm::W - 3;
+    }
+    escaped = !inside;
+#pragma unroll
     for (int k = 0; k < Gm::STENCIL; ++k) {
         const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
-        const int kk[3] = {k0, k1, k2};
-        R wt = w[0][k0] * w[1][k1];
-        R g[D];
-        if constexpr (D == 2) {
-            g[0] = dw[0][k0] * w[1][k1];
-            g[1] = w[0][k0] * dw[1][k1];
-        } else {
-            const R w2 = w[D - 1][k2];
-            g[0] = dw[0][k0] * w[1][k1] * w2;
-            g[1] = w[0][k0] * dw[1][k1] * w2;
-            g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
-            wt *= w2;
-        }
-        const R mw = mp * wt;
-        R mom[3] = {R(0), R(0), R(0)};
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            R ua = u0[a];
-#pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) ua += C[a * D + c2] * R(kk[c2]) * P.dx;
-            R f = R(0);
-#pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) f += Fm[a * D + c2] * g[c2];
-            mom[a] = mw * ua + f;
-        }
+        R m, mom[D];
+        p2g_node<R, D>(f, P.mass, k0, k1, k2, m, mom);
         if (inside) {
-            int li;
-            if constexpr (D == 2) li = (l[1] + k1) * Gm::W + (l[0] + k0);
-            else li = ((l[D - 1] + k2) * Gm::W + (l[1] + k1)) * Gm::W + (l[0] + k0);
-            atomicAdd(&sm[li], mw);
-            atomicAdd(&sm[Gm::WN + li], mom[0]);
-            atomicAdd(&sm[2 * Gm::WN + li], mom[1]);
-            if constexpr (D == 3) atomicAdd(&sm[3 * Gm::WN + li], mom[2]);
+            const int li = win_index<D>(l, k0, k1, k2);
+            atomicAdd(&sm[li], m);
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(&sm[(a + 1) * Gm::WN + li], mom[a]);
         } else {
-            int a3[3] = {0, 0, 0};
+            int a3[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+            const int kk[3] = {k0, k1, k2};
 #pragma unroll
-            for (int a = 0; a < D; ++a) a3[a] = b[a] + 2 + kk[a];
-            const int64_t gi = lin3<D>(a3, P.G_nodes);
-            red_add4(&Asim[gi], mw, mom[0], mom[1], mom[2]);
-            int u[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = a3[a] / Gm::T;
+            for (int a = 0; a < D; ++a) {
+                a3[a] = f.b[a] + 2 + kk[a];
+                u[a] = a3[a] / Gm::T;
+            }
+            red_add4(&Asim[lin3<D>(a3, P.G_nodes)], m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
             flags_sim[lin3<D>(u, P.node_tiles)] = 1u;
         }
     }
 }
 
-template <class R, int D>
+// One CTA per tile (grid-stride over the compact tile list), one thread per cell.
+// With REG, a thread sums the contributions of the particles still in its cell in
+// registers (3^D nodes x (1 + D) values) and adds them to the shared-memory window
+// once; a particle that has left its cell since the sort is scattered on its own.
+// The window is then added to the grid with one vector atomic per touched node.
+template <class R, int D, bool REG>
 __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restrict__ S,
-                                             const int4 *__restrict__ chunks,
-                                             const int32_t *__restrict__ counters, R4<R> *__restrict__ A,
+                                             const int4 *__restrict__ tiles, const int32_t *__restrict__ counters,
+                                             const int32_t *__restrict__ posmap,
+                                             const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A,
                                              uint32_t *__restrict__ flags,
                                              unsigned long long *__restrict__ escaped_count)
 {
     using Gm = Geo<D>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
+    int32_t *off = reinterpret_cast<int32_t *>(sm + (D + 1) * Gm::WN);
     __shared__ uint32_t tile_mask;
-    const int n_chunks = counters[0];
-    for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-        const int4 ch = chunks[c];
+    const int n_tiles = counters[1];
+    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+        const int4 t = tiles[k];
         for (int i = threadIdx.x; i < (D + 1) * Gm::WN; i += blockDim.x) sm[i] = R(0);
+        for (int c = threadIdx.x; c <= Gm::TN; c += blockDim.x) off[c] = cell_off[(int64_t)k * (Gm::TN + 1) + c];
         if (threadIdx.x == 0) tile_mask = 0u;
         __syncthreads();
-        const int sim = (int)(ch.x / P.tiles_per_sim);
-        int64_t tl = ch.x - (int64_t)sim * P.tiles_per_sim;
+        const int sim = (int)(t.x / P.tiles_per_sim);
+        int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
         int org[3] = {0, 0, 0};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -243,10 +336,59 @@ __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restr
         R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
         bool any_escape = false;
-        for (int i = threadIdx.x; i < ch.z; i += blockDim.x) {
-            bool esc = false;
-            p2g_particle<R, D>(P, S, (int64_t)ch.y + i, org, sm, Asim, fsim, esc);
-            any_escape |= esc;
+        for (int c = threadIdx.x; c < Gm::TN; c += blockDim.x) {
+            const int q0 = off[c], q1 = off[c + 1];
+            if (q0 == q1) continue;
+            int lc[D], bown[D];
+            {
+                int r = c;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int cc = r % Gm::T;
+                    r /= Gm::T;
+                    lc[a] = cc + 1;                    // window coordinates of the cell's base
+                    bown[a] = org[a] + cc - 1;         // base cell index of the cell
+                }
+            }
+            R acc[Gm::STENCIL][D + 1];
+            if constexpr (REG) {
+#pragma unroll
+                for (int kk = 0; kk < Gm::STENCIL; ++kk)
+#pragma unroll
+                    for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
+            }
+            for (int q = q0; q < q1; ++q) {
+                const int64_t p = (int64_t)t.y + posmap[(int64_t)t.y + q];
+                P2GFactors<R, D> f;
+                p2g_load_factors<R, D>(P, S, p, f);
+                bool own = REG;
+#pragma unroll
+                for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
+                if (own) {
+                    if constexpr (REG) {
+#pragma unroll
+                        for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+                            R m, mom[D];
+                            p2g_node<R, D>(f, P.mass, kk % 3, (kk / 3) % 3, kk / 9, m, mom);
+                            acc[kk][0] += m;
+#pragma unroll
+                            for (int a = 0; a < D; ++a) acc[kk][a + 1] += mom[a];
+                        }
+                    }
+                } else {
+                    bool esc = false;
+                    p2g_scatter<R, D>(P, f, org, sm, Asim, fsim, esc);
+                    any_escape |= esc;
+                }
+            }
+            if constexpr (REG) {
+#pragma unroll
+                for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+                    const int li = win_index<D>(lc, kk % 3, (kk / 3) % 3, kk / 9);
+#pragma unroll
+                    for (int v = 0; v <= D; ++v) atomicAdd(&sm[v * Gm::WN + li], acc[kk][v]);
+                }
+            }
         }
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
         if (ball && (threadIdx.x & 31) == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
@@ -425,116 +567,177 @@ __device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[
     s[3] = r * dev[3]; s[4] = r * dev[4]; s[5] = r * dev[5];
 }
 
+// G2P of one particle: gathers the 3^D node velocities from the shared-memory
+// window (or from the global grid if its stencil left the window), then
+// updates v, C, x, F, rho and the stress.  Returns false on a non-finite state.
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_g2p(const Params<R> P, R *__restrict__ S,
-                                             const int32_t *__restrict__ sim_of,
-                                             const R4<R> *__restrict__ V, int32_t *__restrict__ status)
+__device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__ S, int64_t p,
+                                             const R4<R> *Vw, const int org[3], const R4<R> *__restrict__ Vs)
 {
     using Gm = Geo<D>;
     const int64_t np = P.npad;
     bool bad = false;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        R x[D];
+    R x[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) x[a] = S[(P.off_x + a) * np + p];
-        const R4<R> *Vs = V + (int64_t)sim_of[p] * P.nodes_per_sim;
-        int b[D];
-        R fx[D], w[D][3], dw[D][3];
+    for (int a = 0; a < D; ++a) x[a] = S[(P.off_x + a) * np + p];
+    int b[D], l[D];
+    R fx[D], w[D][3], dw[D][3];
+    bool inside = true;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
-            fx[a] = x[a] * P.inv_dx - R(b[a]);
-            bspline(fx[a], P.inv_dx, w[a], dw[a]);
-        }
-        R vp[D], Bm[D * D], L[D * D];
+    for (int a = 0; a < D; ++a) {
+        b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+        fx[a] = x[a] * P.inv_dx - R(b[a]);
+        bspline(fx[a], P.inv_dx, w[a], dw[a]);
+        l[a] = b[a] + 2 - org[a];
+        inside = inside && l[a] >= 0 && l[a] <= Gm::W - 3;
+    }
+    R vp[D], Bm[D * D], L[D * D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) vp[q] = R(0);
+    for (int q = 0; q < D; ++q) vp[q] = R(0);
 #pragma unroll
-        for (int q = 0; q < D * D; ++q) { Bm[q] = R(0); L[q] = R(0); }
+    for (int q = 0; q < D * D; ++q) {
+        Bm[q] = R(0);
+        L[q] = R(0);
+    }
 #pragma unroll
-        for (int k = 0; k < Gm::STENCIL; ++k) {
-            const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
-            const int kk[3] = {k0, k1, k2};
+    for (int k = 0; k < Gm::STENCIL; ++k) {
+        const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
+        const int kk[3] = {k0, k1, k2};
+        R4<R> vn;
+        if (inside) {
+            vn = Vw[win_index<D>(l, k0, k1, k2)];
+        } else {
             int a3[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < D; ++a) a3[a] = b[a] + 2 + kk[a];
-            const R4<R> vn = Vs[lin3<D>(a3, P.G_nodes)];
-            const R vi[3] = {vn.x, vn.y, vn.z};
-            R wt = w[0][k0] * w[1][k1];
-            R g[D];
-            if constexpr (D == 2) {
-                g[0] = dw[0][k0] * w[1][k1];
-                g[1] = w[0][k0] * dw[1][k1];
-            } else {
-                const R w2 = w[D - 1][k2];
-                g[0] = dw[0][k0] * w[1][k1] * w2;
-                g[1] = w[0][k0] * dw[1][k1] * w2;
-                g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
-                wt *= w2;
-            }
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const R wv = wt * vi[a];
-                vp[a] += wv;
-#pragma unroll
-                for (int c2 = 0; c2 < D; ++c2) {
-                    Bm[a * D + c2] += wv * (R(kk[c2]) - fx[c2]);
-                    L[a * D + c2] += vi[a] * g[c2];
-                }
-            }
+            vn = Vs[lin3<D>(a3, P.G_nodes)];
         }
-        // C = B D^{-1} with D = dx^2 / 4 I; B was accumulated in units of dx
-        const R cscale = R(4) * P.inv_dx;
-        R trL = R(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) trL += L[a * D + a];
+        const R vi[3] = {vn.x, vn.y, vn.z};
+        R wt = w[0][k0] * w[1][k1];
+        R g[D];
+        if constexpr (D == 2) {
+            g[0] = dw[0][k0] * w[1][k1];
+            g[1] = w[0][k0] * dw[1][k1];
+        } else {
+            const R w2 = w[D - 1][k2];
+            g[0] = dw[0][k0] * w[1][k1] * w2;
+            g[1] = w[0][k0] * dw[1][k1] * w2;
+            g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
+            wt *= w2;
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            R xn = x[a] + P.dt * vp[a];
-            xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
-            bad |= !rfinite(xn) || !rfinite(vp[a]);
-            S[(P.off_x + a) * np + p] = xn;
-            S[(P.off_v + a) * np + p] = vp[a];
+            const R wv = wt * vi[a];
+            vp[a] += wv;
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) {
+                Bm[a * D + c2] += wv * (R(kk[c2]) - fx[c2]);
+                L[a * D + c2] += vi[a] * g[c2];
+            }
         }
+    }
+    // C = B D^{-1} with D = dx^2 / 4 I; B was accumulated in units of dx
+    const R cscale = R(4) * P.inv_dx;
+    R trL = R(0);
 #pragma unroll
-        for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = Bm[q] * cscale;
-        // F <- (I + dt L) F
-        R F[D * D];
+    for (int a = 0; a < D; ++a) trL += L[a * D + a];
 #pragma unroll
-        for (int q = 0; q < D * D; ++q) F[q] = S[(P.off_F + q) * np + p];
+    for (int a = 0; a < D; ++a) {
+        R xn = x[a] + P.dt * vp[a];
+        xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
+        bad |= !rfinite(xn) || !rfinite(vp[a]);
+        S[(P.off_x + a) * np + p] = xn;
+        S[(P.off_v + a) * np + p] = vp[a];
+    }
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = Bm[q] * cscale;
+    // F <- (I + dt L) F
+    R F[D * D];
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) F[q] = S[(P.off_F + q) * np + p];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) {
+            R s = R(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += L[a * D + k] * F[k * D + c2];
+            S[(P.off_F + a * D + c2) * np + p] = F[a * D + c2] + P.dt * s;
+        }
+    const R rho = S[P.off_rho * np + p] / (R(1) + P.dt * trL);
+    S[P.off_rho * np + p] = rho;
+    bad |= !rfinite(rho);
+    if (P.material == 1) {
+        R L3[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) L3[q] = R(0);
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) {
-                R s = R(0);
+            for (int c2 = 0; c2 < D; ++c2) L3[a * 3 + c2] = L[a * D + c2];
+        R s6[6];
 #pragma unroll
-                for (int k = 0; k < D; ++k) s += L[a * D + k] * F[k * D + c2];
-                S[(P.off_F + a * D + c2) * np + p] = F[a * D + c2] + P.dt * s;
-            }
-        const R rho = S[P.off_rho * np + p] / (R(1) + P.dt * trL);
-        S[P.off_rho * np + p] = rho;
-        bad |= !rfinite(rho);
-        if (P.material == 1) {
-            R L3[9];
+        for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
+        R e = S[P.off_eps * np + p];
+        dp_update(P, L3, s6, e);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) L3[q] = R(0);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int c2 = 0; c2 < D; ++c2) L3[a * 3 + c2] = L[a * D + c2];
-            R s6[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
-            R e = S[P.off_eps * np + p];
-            dp_update(P, L3, s6, e);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                S[(P.off_sig + k) * np + p] = s6[k];
-                bad |= !rfinite(s6[k]);
-            }
-            S[P.off_eps * np + p] = e;
+        for (int k = 0; k < 6; ++k) {
+            S[(P.off_sig + k) * np + p] = s6[k];
+            bad |= !rfinite(s6[k]);
         }
+        S[P.off_eps * np + p] = e;
+    }
+    return !bad;
+}
+
+// One CTA per tile (grid-stride), one thread per particle.  The tile's grid
+// window of velocities is staged in shared memory by one TMA tiled load
+// (completion tracked by an mbarrier, waits bounded).
+template <class R, int D>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV,
+                                             R *__restrict__ S, const R4<R> *__restrict__ V,
+                                             const int4 *__restrict__ tiles, const int32_t *__restrict__ counters,
+                                             int32_t *__restrict__ status)
+{
+    using Gm = Geo<D>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R4<R> *Vw = reinterpret_cast<R4<R> *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool bad = false;
+    const int n_tiles = counters[1];
+    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+        const int4 t = tiles[k];
+        const int sim = (int)(t.x / P.tiles_per_sim);
+        int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
+        int org[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
+            tl /= P.n_tiles[a];
+        }
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(&mbar, (uint32_t)(Gm::WN * sizeof(R4<R>)));
+            tma_load_window(Vw, &tmapV, org, sim, D, &mbar);
+        }
+        const bool ok = mbar_wait_bounded(&mbar, phase);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not complete: report, give it one more bounded wait, leave
+            if (threadIdx.x == 0) atomicOr(status, (int32_t)kStatusTimeout);
+            mbar_wait_bounded(&mbar, phase);
+            return;
+        }
+        phase ^= 1u;
+        const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
+        for (int i = threadIdx.x; i < t.z; i += blockDim.x)
+            bad |= !g2p_particle<R, D>(P, S, (int64_t)t.y + i, Vw, org, Vs);
+        __syncthreads();
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, (int32_t)kStatusNaN);
 }
@@ -597,7 +800,8 @@ __global__ void k_permute(int ncomp, int64_t n, int64_t npad, const R *__restric
                           int32_t *__restrict__ sim2)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = perm[i];
+        int64_t o = perm[i];
+        o = o < 0 ? 0 : (o >= n ? n - 1 : o);       // defensive: never gather outside the state
         for (int c = 0; c < ncomp; ++c) S2[c * npad + i] = S[c * npad + o];
         id2[i] = id[o];
         sim2[i] = sim[o];
@@ -767,24 +971,25 @@ template <class R, int D> struct Launch {
     static void permute(const HostParams &h, DevState &ds)
     {
         k_permute<R><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(
-            h.ncomp, h.n, h.npad, (const R *)ds.S, (R *)ds.S2, ds.vals[0], ds.id, ds.id2, ds.sim, ds.sim2);
+            h.ncomp, h.n, h.npad, (const R *)ds.S, (R *)ds.S2, ds.perm, ds.id, ds.id2, ds.sim, ds.sim2);
     }
-    static size_t p2g_smem() { return (size_t)(D + 1) * Geo<D>::WN * sizeof(R); }
+    static constexpr bool kReg = (sizeof(R) == 4) || (D == 2);
+    static size_t p2g_smem() { return (size_t)(D + 1) * Geo<D>::WN * sizeof(R) + (Geo<D>::TN + 1) * sizeof(int32_t); }
     static void p2g(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
         const size_t smem = p2g_smem();
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_p2g<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_p2g<R, D, kReg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
-        int64_t nb = ds.max_chunks;
-        const int64_t cap = (int64_t)ds.num_sms * 8;
+        int64_t nb = ds.max_tiles;
+        const int64_t cap = (int64_t)ds.num_sms * 2;
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_p2g<R, D><<<(int)nb, 256, smem, ds.stream>>>(P, (const R *)ds.S, ds.chunks, ds.counters,
-                                                       (R4<R> *)ds.A, ds.flags, ds.escaped);
+        k_p2g<R, D, kReg><<<(int)nb, 256, smem, ds.stream>>>(P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap,
+                                                             ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
     }
     static void grid(const HostParams &h, DevState &ds)
     {
@@ -792,11 +997,22 @@ template <class R, int D> struct Launch {
         const int64_t nb = h.batch * h.node_tiles_per_sim;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags);
     }
+    static size_t g2p_smem() { return (size_t)Geo<D>::WN * sizeof(R4<R>) + 128; }
     static void g2p(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
-        k_g2p<R, D><<<grid_blocks(h.n, 256, ds.num_sms, 8), 256, 0, ds.stream>>>(
-            P, (R *)ds.S, ds.sim, (const R4<R> *)ds.V, ds.status);
+        const size_t smem = g2p_smem();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_g2p<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        int64_t nb = ds.max_tiles;
+        const int64_t cap = (int64_t)ds.num_sms * 4;
+        if (nb > cap) nb = cap;
+        if (nb < 1) nb = 1;
+        k_g2p<R, D><<<(int)nb, 256, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V, ds.tiles,
+                                                       ds.counters, ds.status);
     }
     static void get_field(const HostParams &h, DevState &ds, int field, double *out)
     {

@@ -174,39 +174,135 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp
     return excl;
 }
 
-__global__ void __launch_bounds__(1024) k_build_chunks(const int32_t *__restrict__ tstart,
-                                                       const int32_t *__restrict__ tend, int64_t ntiles,
-                                                       int chunk, int4 *__restrict__ chunks, int64_t max_chunks,
-                                                       int32_t *__restrict__ counters, int32_t *__restrict__ status)
+// Compact list of the non-empty tiles: (tile key, first particle, count, 0).
+__global__ void __launch_bounds__(1024) k_build_tiles(const int32_t *__restrict__ tstart,
+                                                      const int32_t *__restrict__ tend, int64_t ntiles,
+                                                      int4 *__restrict__ tiles, int64_t max_tiles,
+                                                      int32_t *__restrict__ counters, int32_t *__restrict__ status)
 {
     __shared__ int32_t warp_sum[33];
-    int64_t carry_c = 0, carry_t = 0;
+    int64_t carry = 0;
     bool overflow = false;
     for (int64_t base = 0; base < ntiles; base += 1024) {
         const int64_t t = base + threadIdx.x;
         const int32_t s = t < ntiles ? tstart[t] : -1;
         const int32_t cnt = s >= 0 ? tend[t] - s : 0;
-        const int32_t nch = cnt > 0 ? (cnt + chunk - 1) / chunk : 0;
-        int32_t tot_c, tot_t;
-        const int32_t off = block_exclusive_scan(nch, warp_sum, tot_c);
-        block_exclusive_scan(cnt > 0 ? 1 : 0, warp_sum, tot_t);
-        for (int32_t j = 0; j < nch; ++j) {
-            const int64_t idx = carry_c + off + j;
-            if (idx < max_chunks) {
-                const int32_t st = s + j * chunk;
-                const int32_t c = min(chunk, cnt - j * chunk);
-                chunks[idx] = make_int4((int32_t)t, st, c, 0);
-            } else {
-                overflow = true;
-            }
+        int32_t total;
+        const int32_t off = block_exclusive_scan(cnt > 0 ? 1 : 0, warp_sum, total);
+        if (cnt > 0) {
+            const int64_t idx = carry + off;
+            if (idx < max_tiles) tiles[idx] = make_int4((int32_t)t, s, cnt, 0);
+            else overflow = true;
         }
-        carry_c += tot_c;
-        carry_t += tot_t;
+        carry += total;
     }
     if (overflow) atomicOr(status, (int32_t)kStatusChunkOverflow);
-    if (threadIdx.x == 0) {
-        counters[0] = (int32_t)(carry_c < max_chunks ? carry_c : max_chunks);
-        counters[1] = (int32_t)carry_t;
+    if (threadIdx.x == 0) counters[1] = (int32_t)(carry < max_tiles ? carry : max_tiles);
+}
+
+// Block-wide exclusive scan over TN cells held in shared memory (256 threads,
+// TN / 256 consecutive cells per thread).  out[c] = sum of in[c'] for c' < c;
+// returns the total.
+template <int TN, class F>
+__device__ __forceinline__ int32_t scan_cells(F value, int32_t *out, int32_t *warp_sum)
+{
+    constexpr int PER = TN / 256;
+    const int tid = threadIdx.x;
+    int32_t v[PER], local = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        v[j] = value(tid * PER + j);
+        local += v[j];
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    int32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t ws = lane < 8 ? warp_sum[lane] : 0;
+        int32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < 8) warp_sum[lane] = wi - ws;
+        if (lane == 7) warp_sum[32] = wi;
+    }
+    __syncthreads();
+    int32_t run = warp_sum[warp] + incl - local;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        out[tid * PER + j] = run;
+        run += v[j];
+    }
+    const int32_t total = warp_sum[32];
+    __syncthreads();
+    return total;
+}
+
+// Reorder each tile from (cell, rank) to (rank, cell) order, where rank is a
+// particle's position within its cell: consecutive slots then hold particles of
+// distinct cells, so one thread per cell reads coalesced and one warp of
+// particles writes distinct grid nodes.  Writes the gather permutation
+// (perm[slot] = source slot), posmap (for the i-th particle in (cell, rank)
+// order, its slot relative to the tile start) and the per-tile cell offsets
+// into the (cell, rank) order.
+constexpr int kRankCap = 32;
+
+template <int TN>
+__global__ void __launch_bounds__(256) k_tile_reorder(const int4 *__restrict__ tiles,
+                                                      const int32_t *__restrict__ counters,
+                                                      const uint32_t *__restrict__ keys,
+                                                      const int32_t *__restrict__ vals, int32_t *__restrict__ perm,
+                                                      int32_t *__restrict__ posmap, int32_t *__restrict__ cell_off)
+{
+    __shared__ int32_t cnt[TN];
+    __shared__ int32_t cst[TN];
+    __shared__ int32_t ovf[TN];
+    __shared__ uint16_t Pr[kRankCap][TN];
+    __shared__ int32_t Rr[kRankCap + 1];
+    __shared__ int32_t warp_sum[33];
+    __shared__ int32_t maxcnt;
+    const int n_tiles = counters[1];
+    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+        const int4 t = tiles[k];
+        const int32_t start = t.y, count = t.z;
+        for (int c = threadIdx.x; c < TN; c += blockDim.x) cnt[c] = 0;
+        if (threadIdx.x == 0) maxcnt = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < count; i += blockDim.x) atomicAdd(&cnt[keys[start + i] & (TN - 1)], 1);
+        __syncthreads();
+        for (int c = threadIdx.x; c < TN; c += blockDim.x) atomicMax(&maxcnt, cnt[c]);
+        scan_cells<TN>([&](int c) { return cnt[c]; }, cst, warp_sum);
+        const int rmax = min(maxcnt, kRankCap);
+        if (threadIdx.x == 0) Rr[0] = 0;
+        for (int r = 0; r < rmax; ++r) {
+            int32_t *row = ovf;                 // scratch row, copied to 16-bit storage below
+            const int32_t tot = scan_cells<TN>([&](int c) { return cnt[c] > r ? 1 : 0; }, row, warp_sum);
+            for (int c = threadIdx.x; c < TN; c += blockDim.x) Pr[r][c] = (uint16_t)row[c];
+            if (threadIdx.x == 0) Rr[r + 1] = Rr[r] + tot;
+            __syncthreads();
+        }
+        const bool has_ovf = maxcnt > kRankCap;
+        if (has_ovf) scan_cells<TN>([&](int c) { return cnt[c] > kRankCap ? cnt[c] - kRankCap : 0; }, ovf, warp_sum);
+        __syncthreads();
+        for (int i = threadIdx.x; i < count; i += blockDim.x) {
+            const int c = keys[start + i] & (TN - 1);
+            const int r = i - cst[c];
+            const int pos = r < kRankCap ? Rr[r] + Pr[r][c] : Rr[rmax] + ovf[c] + (r - kRankCap);
+            perm[start + pos] = vals[start + i];
+            posmap[start + i] = pos;
+        }
+        int32_t *co = cell_off + (int64_t)k * (TN + 1);
+        for (int c = threadIdx.x; c < TN; c += blockDim.x) co[c] = cst[c];
+        if (threadIdx.x == 0) co[TN] = count;
+        __syncthreads();
     }
 }
 
@@ -240,8 +336,16 @@ void build_tiles(const HostParams &hp, DevState &ds)
     if (nb > (int64_t)ds.num_sms * 16) nb = (int64_t)ds.num_sms * 16;
     k_tile_bounds<<<(int)(nb < 1 ? 1 : nb), 256, 0, ds.stream>>>(ds.keys[0], hp.n, cell_bits, ds.tile_start,
                                                                  ds.tile_end);
-    k_build_chunks<<<1, 1024, 0, ds.stream>>>(ds.tile_start, ds.tile_end, ntiles, hp.chunk, ds.chunks,
-                                              ds.max_chunks, ds.counters, ds.status);
+    k_build_tiles<<<1, 1024, 0, ds.stream>>>(ds.tile_start, ds.tile_end, ntiles, ds.tiles, ds.max_tiles,
+                                             ds.counters, ds.status);
+    int64_t tb = ds.max_tiles < (int64_t)ds.num_sms * 4 ? ds.max_tiles : (int64_t)ds.num_sms * 4;
+    if (tb < 1) tb = 1;
+    if (hp.dim == 2)
+        k_tile_reorder<Geo<2>::TN><<<(int)tb, 256, 0, ds.stream>>>(ds.tiles, ds.counters, ds.keys[0], ds.vals[0],
+                                                                   ds.perm, ds.posmap, ds.cell_off);
+    else
+        k_tile_reorder<Geo<3>::TN><<<(int)tb, 256, 0, ds.stream>>>(ds.tiles, ds.counters, ds.keys[0], ds.vals[0],
+                                                                   ds.perm, ds.posmap, ds.cell_off);
 }
 
 }  // namespace mpm
