@@ -414,8 +414,10 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     }
     const int TN = c->grid.dim == 2 ? Geo<2>::TN : Geo<3>::TN;
     int rc = MPM_OK;
-    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, (size_t)h.ncomp * h.npad * rsz, "particle state");
-    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S2, (size_t)h.ncomp * h.npad * rsz, "particle state (sort)");
+    // 64 elements of slack: bulk copies of the last component may read up to 7 past npad
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state");
+    if (rc == MPM_OK)
+        rc = dalloc(c, (unsigned char **)&ds.S2, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state (sort)");
     if (rc == MPM_OK) rc = dalloc(c, &ds.id, n, "ids");
     if (rc == MPM_OK) rc = dalloc(c, &ds.id2, n, "ids (sort)");
     if (rc == MPM_OK) rc = dalloc(c, &ds.sim, n, "sim ids");

@@ -33,6 +33,7 @@ template <> struct Geo<2> {
     static constexpr int TN = T * T;             // cells per tile
     static constexpr int CELL_BITS = 8;          // log2(TN)
     static constexpr int STENCIL = 9;
+    static constexpr int NG = 256;               // cells per group (= threads of a P2G block)
 };
 template <> struct Geo<3> {
     static constexpr int T = 8;
@@ -41,6 +42,7 @@ template <> struct Geo<3> {
     static constexpr int TN = T * T * T;
     static constexpr int CELL_BITS = 9;
     static constexpr int STENCIL = 27;
+    static constexpr int NG = 64;                // cells per group: one 8 x 8 layer of the tile
 };
 
 // Friction field of one wall on the device.
@@ -95,9 +97,9 @@ struct DevState {
     int4 *tiles;                  // compact non-empty tiles: (tile key, start, count, 0)
     int64_t max_tiles;
     int32_t *perm;                // gather permutation of the last sort
-    int32_t *posmap;              // per particle in (cell, rank) order: slot within its tile
-    int32_t *cell_off;            // per compact tile: TN + 1 offsets into (cell, rank) order
-    int32_t *counters;            // [1] n_active_tiles
+    int32_t *posmap;              // per particle in (cell, rank) order: its slot relative to the tile start
+    int32_t *cell_off;            // per compact tile: TN + 1 exclusive prefix sums of the cell counts
+    int32_t *counters;            // [1] n_active_tiles, [2] P2G tile cursor, [3] G2P tile cursor
     void *A, *V;                  // grid accumulators and velocities, R4 per node
     uint32_t *flags;              // per node tile: touched since the last grid update
     int32_t *status;              // device status word (bit 0: non-finite state)

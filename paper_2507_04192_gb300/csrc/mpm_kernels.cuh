@@ -162,6 +162,38 @@ __device__ __forceinline__ void tma_load_window(void *dst, const CUtensorMap *ma
     }
 }
 
+// One-dimensional bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Stage particle positions [p0, p0 + count) of nc state components into a
+// shared buffer (component j at buf + j * pitch), issued by warp 0: lane 0 sets
+// the expected bytes, lanes j < nc copy component comp(j).  The copy starts at
+// p0 rounded down to 8 elements; returns that start.
+template <class R, class CompOf>
+__device__ __forceinline__ int64_t stage_rows(R *buf, int pitch, const R *__restrict__ S, int64_t npad, int64_t p0,
+                                              int count, int nc, CompOf comp, uint64_t *bar)
+{
+    const int64_t a = p0 & ~int64_t(7);
+    const int len = (int)(((p0 + count - a) + 7) & ~int64_t(7));
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, (uint32_t)(nc * len * sizeof(R)));
+        }
+        __syncwarp();
+        for (int j = threadIdx.x; j < nc; j += 32)
+            bulk_g2s(buf + (int64_t)j * pitch, S + (int64_t)comp(j) * npad + a, (uint32_t)(len * sizeof(R)), bar);
+    }
+    return a;
+}
+
 // ------------------------------------------------------------------ P2G
 
 // Separable form of one particle's P2G contribution.  With per-axis weights
@@ -177,20 +209,28 @@ template <class R, int D> struct P2GFactors {
     R E[D][D][3];
 };
 
-template <class R, int D>
-__device__ __forceinline__ void p2g_load_factors(const Params<R> &P, const R *__restrict__ S, int64_t p,
-                                                 P2GFactors<R, D> &f)
+// Components of the particle state P2G reads, in staging order: x (D), v (D),
+// C (D^2), rho, and for Drucker-Prager sigma (6).  x, v, C are consecutive in
+// the state, as are rho and sigma.
+template <int D> __host__ __device__ __forceinline__ constexpr int p2g_ncomp(int material)
 {
-    const int64_t np = P.npad;
+    return 2 * D + D * D + 1 + (material == 1 ? 6 : 0);
+}
+
+// P2G factors of one particle from its raw components raw(j) (staging order).
+template <class R, int D, class Raw>
+__device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFactors<R, D> &f)
+{
+    constexpr int J_RHO = 2 * D + D * D;
     R x[D], v[D], C[D * D], Fm[D * D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        x[a] = S[(P.off_x + a) * np + p];
-        v[a] = S[(P.off_v + a) * np + p];
+        x[a] = raw(a);
+        v[a] = raw(D + a);
     }
 #pragma unroll
-    for (int q = 0; q < D * D; ++q) C[q] = S[(P.off_C + q) * np + p];
-    const R rho = S[P.off_rho * np + p];
+    for (int q = 0; q < D * D; ++q) C[q] = raw(2 * D + q);
+    const R rho = raw(J_RHO);
     const R Vp = P.mass / rho;
     if (P.material == 0) {
         const R c = P.dt * Vp * tait(P, rho);          // -dt V (-p I)
@@ -199,7 +239,7 @@ __device__ __forceinline__ void p2g_load_factors(const Params<R> &P, const R *__
     } else {
         R s6[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
+        for (int k = 0; k < 6; ++k) s6[k] = raw(J_RHO + 1 + k);
         const R c = -P.dt * Vp;
         if constexpr (D == 2) {
             Fm[0] = c * s6[0]; Fm[1] = c * s6[3];
@@ -254,6 +294,45 @@ __device__ __forceinline__ void p2g_node(const P2GFactors<R, D> &f, R mp, int k0
     }
 }
 
+// Sum one particle's contributions into per-cell register accumulators (its
+// base is the cell's base).  Products shared by the three nodes of a z-column
+// are formed once per (k0, k1).
+template <class R, int D>
+__device__ __forceinline__ void p2g_accumulate(const P2GFactors<R, D> &f, R mp, R (&acc)[Geo<D>::STENCIL][D + 1])
+{
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const int k = k1 * 3 + k0;
+                acc[k][0] = fma(mp * f.w[0][k0], f.w[1][k1], acc[k][0]);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    acc[k][1 + a] += f.E[a][0][k0] * f.w[1][k1] + f.w[0][k0] * f.E[a][1][k1];
+            }
+    } else {
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const R wxy = f.w[0][k0] * f.w[1][k1];
+                const R mwxy = mp * wxy;
+                R Tm[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) Tm[a] = fma(f.E[a][0][k0], f.w[1][k1], f.w[0][k0] * f.E[a][1][k1]);
+#pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2) {
+                    const int k = (k2 * 3 + k1) * 3 + k0;
+                    acc[k][0] = fma(mwxy, f.w[2][k2], acc[k][0]);
+#pragma unroll
+                    for (int a = 0; a < D; ++a)
+                        acc[k][1 + a] = fma(f.w[2][k2], Tm[a], fma(wxy, f.E[a][2][k2], acc[k][1 + a]));
+                }
+            }
+    }
+}
+
 template <int D> __device__ __forceinline__ int win_index(const int l[D], int k0, int k1, int k2)
 {
     using Gm = Geo<D>;
@@ -300,29 +379,44 @@ __device__ __forceinline__ void p2g_scatter(const Params<R> &P, const P2GFactors
     }
 }
 
-// One CTA per tile (grid-stride over the compact tile list), one thread per cell.
-// With REG, a thread sums the contributions of the particles still in its cell in
-// registers (3^D nodes x (1 + D) values) and adds them to the shared-memory window
-// once; a particle that has left its cell since the sort is scattered on its own.
-// The window is then added to the grid with one vector atomic per touched node.
-template <class R, int D, bool REG>
-__global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restrict__ S,
-                                             const int4 *__restrict__ tiles, const int32_t *__restrict__ counters,
-                                             const int32_t *__restrict__ posmap,
-                                             const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A,
-                                             uint32_t *__restrict__ flags,
-                                             unsigned long long *__restrict__ escaped_count)
+// Claim the next tile of the compact list (block-uniform); -1 when done.
+__device__ __forceinline__ int next_tile(int32_t *cursor, int n_tiles, int *s_slot)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *s_slot = atomicAdd(cursor, 1);
+    __syncthreads();
+    const int k = *s_slot;
+    return k < n_tiles ? k : -1;
+}
+
+// P2G.  Blocks of 128 threads claim tiles dynamically; one thread per cell.  A
+// thread walks its cell's particles (slots from the position map; within a
+// group the rank planes are contiguous and cell-ordered, so the loads of a warp
+// are coalesced) and sums the contributions of the particles still in its cell
+// in registers (3^D nodes x (1 + D) values), adding them to the shared-memory
+// window once.  A particle that has left its cell since the sort is scattered on
+// its own: into the window, or straight to the grid if it has also left the
+// window.  The window is added to the grid with one vector atomic per touched
+// node.  Without REG (FP64 in 3D) every particle is scattered on its own.
+template <class R, int D, bool REG, int NT>
+__global__ void __launch_bounds__(NT, (D == 3 && REG) ? 3 : 1)
+    k_p2g(const Params<R> P, const R *__restrict__ S, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
+          const int32_t *__restrict__ posmap, const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A,
+          uint32_t *__restrict__ flags, unsigned long long *__restrict__ escaped_count)
 {
     using Gm = Geo<D>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     int32_t *off = reinterpret_cast<int32_t *>(sm + (D + 1) * Gm::WN);
     __shared__ uint32_t tile_mask;
+    __shared__ int s_slot;
     const int n_tiles = counters[1];
-    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    for (;;) {
+        const int k = next_tile(&counters[2], n_tiles, &s_slot);
+        if (k < 0) break;
         const int4 t = tiles[k];
-        for (int i = threadIdx.x; i < (D + 1) * Gm::WN; i += blockDim.x) sm[i] = R(0);
-        for (int c = threadIdx.x; c <= Gm::TN; c += blockDim.x) off[c] = cell_off[(int64_t)k * (Gm::TN + 1) + c];
+        for (int i = threadIdx.x; i < (D + 1) * Gm::WN; i += NT) sm[i] = R(0);
+        for (int c = threadIdx.x; c <= Gm::TN; c += NT) off[c] = cell_off[(int64_t)k * (Gm::TN + 1) + c];
         if (threadIdx.x == 0) tile_mask = 0u;
         __syncthreads();
         const int sim = (int)(t.x / P.tiles_per_sim);
@@ -335,8 +429,9 @@ __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restr
         }
         R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
+        const int64_t pm0 = (int64_t)t.y;
         bool any_escape = false;
-        for (int c = threadIdx.x; c < Gm::TN; c += blockDim.x) {
+        for (int c = threadIdx.x; c < Gm::TN; c += NT) {
             const int q0 = off[c], q1 = off[c + 1];
             if (q0 == q1) continue;
             int lc[D], bown[D];
@@ -357,24 +452,17 @@ __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restr
 #pragma unroll
                     for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
             }
+            int32_t pos_next = posmap[pm0 + q0];
             for (int q = q0; q < q1; ++q) {
-                const int64_t p = (int64_t)t.y + posmap[(int64_t)t.y + q];
+                const int64_t p = pm0 + pos_next;
+                if (q + 1 < q1) pos_next = posmap[pm0 + q + 1];
                 P2GFactors<R, D> f;
-                p2g_load_factors<R, D>(P, S, p, f);
+                p2g_factors<R, D>(P, [&](int j) { return S[(int64_t)(j < 2 * D + D * D ? j : P.off_rho + (j - 2 * D - D * D)) * P.npad + p]; }, f);
                 bool own = REG;
 #pragma unroll
                 for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
                 if (own) {
-                    if constexpr (REG) {
-#pragma unroll
-                        for (int kk = 0; kk < Gm::STENCIL; ++kk) {
-                            R m, mom[D];
-                            p2g_node<R, D>(f, P.mass, kk % 3, (kk / 3) % 3, kk / 9, m, mom);
-                            acc[kk][0] += m;
-#pragma unroll
-                            for (int a = 0; a < D; ++a) acc[kk][a + 1] += mom[a];
-                        }
-                    }
+                    if constexpr (REG) p2g_accumulate<R, D>(f, P.mass, acc);
                 } else {
                     bool esc = false;
                     p2g_scatter<R, D>(P, f, org, sm, Asim, fsim, esc);
@@ -393,7 +481,7 @@ __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restr
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
         if (ball && (threadIdx.x & 31) == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
         __syncthreads();
-        for (int i = threadIdx.x; i < Gm::WN; i += blockDim.x) {
+        for (int i = threadIdx.x; i < Gm::WN; i += NT) {
             const R m = sm[i];
             const R q0 = sm[Gm::WN + i], q1 = sm[2 * Gm::WN + i];
             const R q2 = D == 3 ? sm[3 * Gm::WN + i] : R(0);
@@ -420,8 +508,8 @@ __global__ void __launch_bounds__(256) k_p2g(const Params<R> P, const R *__restr
             for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((threadIdx.x >> a) & 1);
             fsim[lin3<D>(u, P.node_tiles)] = 1u;
         }
-        __syncthreads();
     }
+    if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
 }
 
 // ------------------------------------------------------------------ grid update
@@ -567,19 +655,110 @@ __device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[
     s[3] = r * dev[3]; s[4] = r * dev[4]; s[5] = r * dev[5];
 }
 
+// Separable G2P sums over the 3^D stencil: with tensor-product weights
+//   vp_a = sum w v_a,  M_ab = sum w v_a k_b,  L_ab = sum (grad w)_b v_a,
+// contracted one axis at a time (x, then y, then z).
+template <class R, int D, class Load>
+__device__ __forceinline__ void g2p_contract(const R w[D][3], const R dw[D][3], Load load, R vp[D], R M[D * D],
+                                             R L[D * D])
+{
+#pragma unroll
+    for (int q = 0; q < D; ++q) vp[q] = R(0);
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) {
+        M[q] = R(0);
+        L[q] = R(0);
+    }
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            R Xw[2] = {R(0), R(0)}, Xk[2] = {R(0), R(0)}, Xd[2] = {R(0), R(0)};
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const R4<R> v4 = load(k0, k1, 0);
+                const R v[2] = {v4.x, v4.y};
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    Xw[a] = fma(w[0][k0], v[a], Xw[a]);
+                    if (k0 > 0) Xk[a] = fma(R(k0) * w[0][k0], v[a], Xk[a]);
+                    Xd[a] = fma(dw[0][k0], v[a], Xd[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                vp[a] = fma(w[1][k1], Xw[a], vp[a]);
+                M[a * 2 + 0] = fma(w[1][k1], Xk[a], M[a * 2 + 0]);
+                if (k1 > 0) M[a * 2 + 1] = fma(R(k1) * w[1][k1], Xw[a], M[a * 2 + 1]);
+                L[a * 2 + 0] = fma(w[1][k1], Xd[a], L[a * 2 + 0]);
+                L[a * 2 + 1] = fma(dw[1][k1], Xw[a], L[a * 2 + 1]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) {
+            R Yww[3], Ykw[3], Ydw[3], Ywk[3], Ywd[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Yww[a] = Ykw[a] = Ydw[a] = Ywk[a] = Ywd[a] = R(0);
+#pragma unroll
+            for (int k1 = 0; k1 < 3; ++k1) {
+                R Xw[3], Xk[3], Xd[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Xw[a] = Xk[a] = Xd[a] = R(0);
+#pragma unroll
+                for (int k0 = 0; k0 < 3; ++k0) {
+                    const R4<R> v4 = load(k0, k1, k2);
+                    const R v[3] = {v4.x, v4.y, v4.z};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Xw[a] = fma(w[0][k0], v[a], Xw[a]);
+                        if (k0 > 0) Xk[a] = fma(R(k0) * w[0][k0], v[a], Xk[a]);
+                        Xd[a] = fma(dw[0][k0], v[a], Xd[a]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Yww[a] = fma(w[1][k1], Xw[a], Yww[a]);
+                    Ykw[a] = fma(w[1][k1], Xk[a], Ykw[a]);
+                    Ydw[a] = fma(w[1][k1], Xd[a], Ydw[a]);
+                    if (k1 > 0) Ywk[a] = fma(R(k1) * w[1][k1], Xw[a], Ywk[a]);
+                    Ywd[a] = fma(dw[1][k1], Xw[a], Ywd[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                vp[a] = fma(w[2][k2], Yww[a], vp[a]);
+                M[a * 3 + 0] = fma(w[2][k2], Ykw[a], M[a * 3 + 0]);
+                M[a * 3 + 1] = fma(w[2][k2], Ywk[a], M[a * 3 + 1]);
+                if (k2 > 0) M[a * 3 + 2] = fma(R(k2) * w[2][k2], Yww[a], M[a * 3 + 2]);
+                L[a * 3 + 0] = fma(w[2][k2], Ydw[a], L[a * 3 + 0]);
+                L[a * 3 + 1] = fma(w[2][k2], Ywd[a], L[a * 3 + 1]);
+                L[a * 3 + 2] = fma(dw[2][k2], Yww[a], L[a * 3 + 2]);
+            }
+        }
+    }
+}
+
 // G2P of one particle: gathers the 3^D node velocities from the shared-memory
 // window (or from the global grid if its stencil left the window), then
 // updates v, C, x, F, rho and the stress.  Returns false on a non-finite state.
-template <class R, int D>
-__device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__ S, int64_t p,
+// Components of the particle state G2P reads, in staging order: x (D), F (D^2),
+// rho, and for Drucker-Prager sigma (6) and eps.  rho, sigma, eps are consecutive.
+template <int D> __host__ __device__ __forceinline__ constexpr int g2p_ncomp(int material)
+{
+    return D + D * D + 1 + (material == 1 ? 7 : 0);
+}
+
+template <class R, int D, class Raw>
+__device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__restrict__ S, int64_t p,
                                              const R4<R> *Vw, const int org[3], const R4<R> *__restrict__ Vs)
 {
     using Gm = Geo<D>;
+    constexpr int J_F = D, J_RHO = D + D * D;
     const int64_t np = P.npad;
     bool bad = false;
     R x[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) x[a] = S[(P.off_x + a) * np + p];
+    for (int a = 0; a < D; ++a) x[a] = raw(a);
     int b[D], l[D];
     R fx[D], w[D][3], dw[D][3];
     bool inside = true;
@@ -591,51 +770,21 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__
         l[a] = b[a] + 2 - org[a];
         inside = inside && l[a] >= 0 && l[a] <= Gm::W - 3;
     }
-    R vp[D], Bm[D * D], L[D * D];
-#pragma unroll
-    for (int q = 0; q < D; ++q) vp[q] = R(0);
-#pragma unroll
-    for (int q = 0; q < D * D; ++q) {
-        Bm[q] = R(0);
-        L[q] = R(0);
+    R vp[D], M[D * D], L[D * D];
+    if (inside) {
+        g2p_contract<R, D>(w, dw, [&](int k0, int k1, int k2) { return Vw[win_index<D>(l, k0, k1, k2)]; }, vp, M, L);
+    } else {
+        g2p_contract<R, D>(w, dw, [&](int k0, int k1, int k2) {
+            int a3[3] = {b[0] + 2 + k0, b[1] + 2 + k1, D == 3 ? b[D - 1] + 2 + k2 : 0};
+            return Vs[lin3<D>(a3, P.G_nodes)];
+        }, vp, M, L);
     }
+    // B_ab = sum w v_a (k_b - fx_b) (units of dx) = M_ab - fx_b vp_a
+    R Bm[D * D];
 #pragma unroll
-    for (int k = 0; k < Gm::STENCIL; ++k) {
-        const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
-        const int kk[3] = {k0, k1, k2};
-        R4<R> vn;
-        if (inside) {
-            vn = Vw[win_index<D>(l, k0, k1, k2)];
-        } else {
-            int a3[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int a = 0; a < D; ++a) a3[a] = b[a] + 2 + kk[a];
-            vn = Vs[lin3<D>(a3, P.G_nodes)];
-        }
-        const R vi[3] = {vn.x, vn.y, vn.z};
-        R wt = w[0][k0] * w[1][k1];
-        R g[D];
-        if constexpr (D == 2) {
-            g[0] = dw[0][k0] * w[1][k1];
-            g[1] = w[0][k0] * dw[1][k1];
-        } else {
-            const R w2 = w[D - 1][k2];
-            g[0] = dw[0][k0] * w[1][k1] * w2;
-            g[1] = w[0][k0] * dw[1][k1] * w2;
-            g[D - 1] = w[0][k0] * w[1][k1] * dw[D - 1][k2];
-            wt *= w2;
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const R wv = wt * vi[a];
-            vp[a] += wv;
-#pragma unroll
-            for (int c2 = 0; c2 < D; ++c2) {
-                Bm[a * D + c2] += wv * (R(kk[c2]) - fx[c2]);
-                L[a * D + c2] += vi[a] * g[c2];
-            }
-        }
-    }
+        for (int c2 = 0; c2 < D; ++c2) Bm[a * D + c2] = M[a * D + c2] - fx[c2] * vp[a];
     // C = B D^{-1} with D = dx^2 / 4 I; B was accumulated in units of dx
     const R cscale = R(4) * P.inv_dx;
     R trL = R(0);
@@ -654,7 +803,7 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__
     // F <- (I + dt L) F
     R F[D * D];
 #pragma unroll
-    for (int q = 0; q < D * D; ++q) F[q] = S[(P.off_F + q) * np + p];
+    for (int q = 0; q < D * D; ++q) F[q] = raw(J_F + q);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -664,7 +813,7 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__
             for (int k = 0; k < D; ++k) s += L[a * D + k] * F[k * D + c2];
             S[(P.off_F + a * D + c2) * np + p] = F[a * D + c2] + P.dt * s;
         }
-    const R rho = S[P.off_rho * np + p] / (R(1) + P.dt * trL);
+    const R rho = raw(J_RHO) / (R(1) + P.dt * trL);
     S[P.off_rho * np + p] = rho;
     bad |= !rfinite(rho);
     if (P.material == 1) {
@@ -677,8 +826,8 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__
             for (int c2 = 0; c2 < D; ++c2) L3[a * 3 + c2] = L[a * D + c2];
         R s6[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s6[k] = S[(P.off_sig + k) * np + p];
-        R e = S[P.off_eps * np + p];
+        for (int k = 0; k < 6; ++k) s6[k] = raw(J_RHO + 1 + k);
+        R e = raw(J_RHO + 7);
         dp_update(P, L3, s6, e);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -690,28 +839,53 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, R *__restrict__
     return !bad;
 }
 
-// One CTA per tile (grid-stride), one thread per particle.  The tile's grid
-// window of velocities is staged in shared memory by one TMA tiled load
-// (completion tracked by an mbarrier, waits bounded).
+// Shared-memory layout of the G2P block.
+template <class R, int D> struct G2PSmem {
+    static constexpr int NT = 256;
+    static constexpr int PB = NT + 8;
+    static constexpr int NCMAX = D + D * D + 8;
+    static constexpr size_t win_bytes = (size_t)Geo<D>::WN * sizeof(R4<R>);
+    static constexpr size_t buf_bytes = (size_t)2 * NCMAX * PB * sizeof(R);
+    static constexpr size_t total = win_bytes + buf_bytes + 128;
+};
+
+// G2P.  Blocks claim tiles dynamically, one thread per particle.  The tile's
+// grid window of velocities is staged by one TMA tiled load; the particles'
+// inputs are staged 256 at a time by TMA bulk copies, double-buffered.  All
+// waits are bounded; a timeout is reported in the status word.
 template <class R, int D>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV,
-                                             R *__restrict__ S, const R4<R> *__restrict__ V,
-                                             const int4 *__restrict__ tiles, const int32_t *__restrict__ counters,
-                                             int32_t *__restrict__ status)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV, R *__restrict__ S,
+          const R4<R> *__restrict__ V, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
+          int32_t *__restrict__ status)
 {
     using Gm = Geo<D>;
+    using L = G2PSmem<R, D>;
+    constexpr int NT = L::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R4<R> *Vw = reinterpret_cast<R4<R> *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t mbar;
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar, 1);
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                            ~uintptr_t(127));
+    R4<R> *Vw = reinterpret_cast<R4<R> *>(base);
+    R *bufs = reinterpret_cast<R *>(base + L::win_bytes);
+    __shared__ __align__(8) uint64_t mbar[3];      // [0], [1]: particle buffers, [2]: grid window
+    __shared__ int s_slot;
+    const int tid = threadIdx.x;
+    const int nc = g2p_ncomp<D>(P.material);
+    constexpr int J_RHO = D + D * D;
+    const int off_F = P.off_F, off_rho = P.off_rho;
+    auto comp = [&](int j) { return j < D ? j : (j < J_RHO ? off_F + (j - D) : off_rho + (j - J_RHO)); };
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[2], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    uint32_t phase = 0;
-    bool bad = false;
+    uint32_t phases = 0u;                          // bit i: parity of the next wait on mbar[i]
+    bool bad = false, timed_out = false;
     const int n_tiles = counters[1];
-    for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    for (;;) {
+        const int k = next_tile(&counters[3], n_tiles, &s_slot);
+        if (k < 0) break;
         const int4 t = tiles[k];
         const int sim = (int)(t.x / P.tiles_per_sim);
         int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
@@ -721,25 +895,44 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_g2p(const Param
             org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
             tl /= P.n_tiles[a];
         }
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_expect_tx(&mbar, (uint32_t)(Gm::WN * sizeof(R4<R>)));
-            tma_load_window(Vw, &tmapV, org, sim, D, &mbar);
+            mbar_expect_tx(&mbar[2], (uint32_t)(Gm::WN * sizeof(R4<R>)));
+            tma_load_window(Vw, &tmapV, org, sim, D, &mbar[2]);
         }
-        const bool ok = mbar_wait_bounded(&mbar, phase);
-        if (__syncthreads_or(!ok)) {
-            // the copy did not complete: report, give it one more bounded wait, leave
-            if (threadIdx.x == 0) atomicOr(status, (int32_t)kStatusTimeout);
-            mbar_wait_bounded(&mbar, phase);
-            return;
-        }
-        phase ^= 1u;
+        const int nb = (t.z + NT - 1) / NT;
+        int cur = 0;
+        int64_t a_cur = stage_rows(bufs, L::PB, S, P.npad, (int64_t)t.y, min(NT, t.z), nc, comp, &mbar[0]);
+        bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
+        phases ^= 4u;
         const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
-        for (int i = threadIdx.x; i < t.z; i += blockDim.x)
-            bad |= !g2p_particle<R, D>(P, S, (int64_t)t.y + i, Vw, org, Vs);
-        __syncthreads();
+        for (int j = 0; j < nb; ++j) {
+            int64_t a_next = 0;
+            if (j + 1 < nb)
+                a_next = stage_rows(bufs + (size_t)(cur ^ 1) * L::NCMAX * L::PB, L::PB, S, P.npad,
+                                    (int64_t)t.y + (int64_t)(j + 1) * NT, min(NT, t.z - (j + 1) * NT), nc, comp,
+                                    &mbar[cur ^ 1]);
+            const bool okb = mbar_wait_bounded(&mbar[cur], (phases >> cur) & 1u);
+            phases ^= 1u << cur;
+            ok = ok && okb;
+            const int i = j * NT + tid;
+            if (ok && i < t.z) {
+                const int64_t p = (int64_t)t.y + i;
+                const R *bb = bufs + (size_t)cur * L::NCMAX * L::PB + (p - a_cur);
+                bad |= !g2p_particle<R, D>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org, Vs);
+            }
+            __syncthreads();
+            a_cur = a_next;
+            cur ^= 1;
+        }
+        timed_out |= !ok;
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicOr(status, (int32_t)kStatusTimeout);
+            break;
+        }
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, (int32_t)kStatusNaN);
+    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(status, (int32_t)kStatusNaN);
+    if (tid == 0) counters[2] = 0;                 // P2G cursor for the next kernel (P2G follows)
 }
 
 // ------------------------------------------------------------------ state management
@@ -974,6 +1167,7 @@ template <class R, int D> struct Launch {
             h.ncomp, h.n, h.npad, (const R *)ds.S, (R *)ds.S2, ds.perm, ds.id, ds.id2, ds.sim, ds.sim2);
     }
     static constexpr bool kReg = (sizeof(R) == 4) || (D == 2);
+    static constexpr int kP2GThreads = (D == 3 && kReg) ? 128 : 256;
     static size_t p2g_smem() { return (size_t)(D + 1) * Geo<D>::WN * sizeof(R) + (Geo<D>::TN + 1) * sizeof(int32_t); }
     static void p2g(const HostParams &h, DevState &ds)
     {
@@ -981,15 +1175,16 @@ template <class R, int D> struct Launch {
         const size_t smem = p2g_smem();
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_p2g<R, D, kReg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_p2g<R, D, kReg, kP2GThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
             attr = true;
         }
         int64_t nb = ds.max_tiles;
-        const int64_t cap = (int64_t)ds.num_sms * 2;
+        const int64_t cap = (int64_t)ds.num_sms * (kP2GThreads == 128 ? 3 : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_p2g<R, D, kReg><<<(int)nb, 256, smem, ds.stream>>>(P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap,
-                                                             ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
+        k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
+            P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
     }
     static void grid(const HostParams &h, DevState &ds)
     {
@@ -997,22 +1192,21 @@ template <class R, int D> struct Launch {
         const int64_t nb = h.batch * h.node_tiles_per_sim;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags);
     }
-    static size_t g2p_smem() { return (size_t)Geo<D>::WN * sizeof(R4<R>) + 128; }
     static void g2p(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
-        const size_t smem = g2p_smem();
+        const size_t smem = G2PSmem<R, D>::total;
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_g2p<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
         int64_t nb = ds.max_tiles;
-        const int64_t cap = (int64_t)ds.num_sms * 4;
+        const int64_t cap = (int64_t)ds.num_sms * 2;
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_g2p<R, D><<<(int)nb, 256, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V, ds.tiles,
-                                                       ds.counters, ds.status);
+        k_g2p<R, D><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V,
+                                                                     ds.tiles, ds.counters, ds.status);
     }
     static void get_field(const HostParams &h, DevState &ds, int field, double *out)
     {

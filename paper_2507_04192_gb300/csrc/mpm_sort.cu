@@ -200,108 +200,100 @@ __global__ void __launch_bounds__(1024) k_build_tiles(const int32_t *__restrict_
     if (threadIdx.x == 0) counters[1] = (int32_t)(carry < max_tiles ? carry : max_tiles);
 }
 
-// Block-wide exclusive scan over TN cells held in shared memory (256 threads,
-// TN / 256 consecutive cells per thread).  out[c] = sum of in[c'] for c' < c;
-// returns the total.
-template <int TN, class F>
-__device__ __forceinline__ int32_t scan_cells(F value, int32_t *out, int32_t *warp_sum)
+// Reorder each tile from (cell, rank) order to (group, rank, cell) order, where
+// a group is NG consecutive cells (an 8 x 8 x 2 slab in 3D, the whole tile in
+// 2D) and rank is a particle's position within its cell.  The particles of
+// rank r of one group ("rank plane") are then contiguous and ordered by cell,
+// so one thread per cell reads a plane coalesced and a warp of particles
+// touches distinct grid nodes.  A particle of cell c (group g, local cell l)
+// and rank r lands at
+//     off[g NG] + sum_{r' < r} T_g(r') + #{l' < l : cnt[g NG + l'] > r}
+// where off is the exclusive prefix of the cell counts and T_g(r') the number
+// of cells of group g holding more than r' particles.  One block of NG threads per
+// tile; writes the gather permutation, the position map (slot of each
+// (cell, rank) particle) and the per-tile cell offsets.
+template <int TN, int NG>
+__global__ void __launch_bounds__(NG) k_tile_reorder(const int4 *__restrict__ tiles,
+                                                     const int32_t *__restrict__ counters,
+                                                     const uint32_t *__restrict__ keys,
+                                                     const int32_t *__restrict__ vals, int32_t *__restrict__ perm,
+                                                     int32_t *__restrict__ posmap, int32_t *__restrict__ cell_off)
 {
-    constexpr int PER = TN / 256;
-    const int tid = threadIdx.x;
-    int32_t v[PER], local = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        v[j] = value(tid * PER + j);
-        local += v[j];
-    }
-    const int lane = tid & 31, warp = tid >> 5;
-    int32_t incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_sum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int32_t ws = lane < 8 ? warp_sum[lane] : 0;
-        int32_t wi = ws;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < 8) warp_sum[lane] = wi - ws;
-        if (lane == 7) warp_sum[32] = wi;
-    }
-    __syncthreads();
-    int32_t run = warp_sum[warp] + incl - local;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        out[tid * PER + j] = run;
-        run += v[j];
-    }
-    const int32_t total = warp_sum[32];
-    __syncthreads();
-    return total;
-}
-
-// Reorder each tile from (cell, rank) to (rank, cell) order, where rank is a
-// particle's position within its cell: consecutive slots then hold particles of
-// distinct cells, so one thread per cell reads coalesced and one warp of
-// particles writes distinct grid nodes.  Writes the gather permutation
-// (perm[slot] = source slot), posmap (for the i-th particle in (cell, rank)
-// order, its slot relative to the tile start) and the per-tile cell offsets
-// into the (cell, rank) order.
-constexpr int kRankCap = 32;
-
-template <int TN>
-__global__ void __launch_bounds__(256) k_tile_reorder(const int4 *__restrict__ tiles,
-                                                      const int32_t *__restrict__ counters,
-                                                      const uint32_t *__restrict__ keys,
-                                                      const int32_t *__restrict__ vals, int32_t *__restrict__ perm,
-                                                      int32_t *__restrict__ posmap, int32_t *__restrict__ cell_off)
-{
+    constexpr int NW = NG / 32;
+    constexpr int PER = TN / NG;
     __shared__ int32_t cnt[TN];
-    __shared__ int32_t cst[TN];
-    __shared__ int32_t ovf[TN];
-    __shared__ uint16_t Pr[kRankCap][TN];
-    __shared__ int32_t Rr[kRankCap + 1];
-    __shared__ int32_t warp_sum[33];
-    __shared__ int32_t maxcnt;
+    __shared__ int32_t cst[TN + 1];
+    __shared__ int32_t wsum[NW + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_tiles = counters[1];
     for (int k = blockIdx.x; k < n_tiles; k += gridDim.x) {
         const int4 t = tiles[k];
         const int32_t start = t.y, count = t.z;
-        for (int c = threadIdx.x; c < TN; c += blockDim.x) cnt[c] = 0;
-        if (threadIdx.x == 0) maxcnt = 0;
+        for (int c = tid; c < TN; c += NG) cnt[c] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < count; i += blockDim.x) atomicAdd(&cnt[keys[start + i] & (TN - 1)], 1);
+        for (int i = tid; i < count; i += NG) atomicAdd(&cnt[keys[start + i] & (TN - 1)], 1);
         __syncthreads();
-        for (int c = threadIdx.x; c < TN; c += blockDim.x) atomicMax(&maxcnt, cnt[c]);
-        scan_cells<TN>([&](int c) { return cnt[c]; }, cst, warp_sum);
-        const int rmax = min(maxcnt, kRankCap);
-        if (threadIdx.x == 0) Rr[0] = 0;
-        for (int r = 0; r < rmax; ++r) {
-            int32_t *row = ovf;                 // scratch row, copied to 16-bit storage below
-            const int32_t tot = scan_cells<TN>([&](int c) { return cnt[c] > r ? 1 : 0; }, row, warp_sum);
-            for (int c = threadIdx.x; c < TN; c += blockDim.x) Pr[r][c] = (uint16_t)row[c];
-            if (threadIdx.x == 0) Rr[r + 1] = Rr[r] + tot;
+        // exclusive prefix of the counts over the TN cells (PER consecutive cells per thread)
+        {
+            int32_t v[PER], local = 0;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                v[j] = cnt[tid * PER + j];
+                local += v[j];
+            }
+            int32_t incl = local;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            if (tid == 0) {
+                int32_t run = 0;
+                for (int w = 0; w < NW; ++w) {
+                    const int32_t x = wsum[w];
+                    wsum[w] = run;
+                    run += x;
+                }
+                wsum[NW] = run;
+            }
+            __syncthreads();
+            int32_t run = wsum[warp] + incl - local;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                cst[tid * PER + j] = run;
+                run += v[j];
+            }
+            if (tid == 0) cst[TN] = wsum[NW];
             __syncthreads();
         }
-        const bool has_ovf = maxcnt > kRankCap;
-        if (has_ovf) scan_cells<TN>([&](int c) { return cnt[c] > kRankCap ? cnt[c] - kRankCap : 0; }, ovf, warp_sum);
-        __syncthreads();
-        for (int i = threadIdx.x; i < count; i += blockDim.x) {
-            const int c = keys[start + i] & (TN - 1);
-            const int r = i - cst[c];
-            const int pos = r < kRankCap ? Rr[r] + Pr[r][c] : Rr[rmax] + ovf[c] + (r - kRankCap);
-            perm[start + pos] = vals[start + i];
-            posmap[start + i] = pos;
+        const uint32_t lt = (1u << lane) - 1u;
+        for (int g = 0; g < TN / NG; ++g) {
+            const int c = g * NG + tid;
+            const int32_t my = cnt[c];
+            const int32_t gbase = cst[g * NG];
+            int32_t R = 0;
+            for (int r = 0;; ++r) {
+                const bool pred = my > r;
+                const int32_t T = __syncthreads_count(pred);
+                if (T == 0) break;
+                const uint32_t ball = __ballot_sync(0xffffffffu, pred);
+                if (lane == 0) wsum[warp] = __popc(ball);
+                __syncthreads();
+                int32_t before = 0;
+                for (int w = 0; w < warp; ++w) before += wsum[w];
+                if (pred) {
+                    const int32_t pos = gbase + R + before + __popc(ball & lt);
+                    perm[start + pos] = vals[start + cst[c] + r];
+                    posmap[start + cst[c] + r] = pos;
+                }
+                R += T;
+                __syncthreads();
+            }
         }
         int32_t *co = cell_off + (int64_t)k * (TN + 1);
-        for (int c = threadIdx.x; c < TN; c += blockDim.x) co[c] = cst[c];
-        if (threadIdx.x == 0) co[TN] = count;
+        for (int c = tid; c <= TN; c += NG) co[c] = cst[c];
         __syncthreads();
     }
 }
@@ -338,14 +330,15 @@ void build_tiles(const HostParams &hp, DevState &ds)
                                                                  ds.tile_end);
     k_build_tiles<<<1, 1024, 0, ds.stream>>>(ds.tile_start, ds.tile_end, ntiles, ds.tiles, ds.max_tiles,
                                              ds.counters, ds.status);
-    int64_t tb = ds.max_tiles < (int64_t)ds.num_sms * 4 ? ds.max_tiles : (int64_t)ds.num_sms * 4;
+    int64_t tb = ds.max_tiles < (int64_t)ds.num_sms * 8 ? ds.max_tiles : (int64_t)ds.num_sms * 8;
     if (tb < 1) tb = 1;
     if (hp.dim == 2)
-        k_tile_reorder<Geo<2>::TN><<<(int)tb, 256, 0, ds.stream>>>(ds.tiles, ds.counters, ds.keys[0], ds.vals[0],
-                                                                   ds.perm, ds.posmap, ds.cell_off);
+        k_tile_reorder<Geo<2>::TN, Geo<2>::NG><<<(int)tb, Geo<2>::NG, 0, ds.stream>>>(
+            ds.tiles, ds.counters, ds.keys[0], ds.vals[0], ds.perm, ds.posmap, ds.cell_off);
     else
-        k_tile_reorder<Geo<3>::TN><<<(int)tb, 256, 0, ds.stream>>>(ds.tiles, ds.counters, ds.keys[0], ds.vals[0],
-                                                                   ds.perm, ds.posmap, ds.cell_off);
+        k_tile_reorder<Geo<3>::TN, Geo<3>::NG><<<(int)tb, Geo<3>::NG, 0, ds.stream>>>(
+            ds.tiles, ds.counters, ds.keys[0], ds.vals[0], ds.perm, ds.posmap, ds.cell_off);
+    cudaMemsetAsync(ds.counters + 2, 0, 2 * sizeof(int32_t), ds.stream);   // tile cursors
 }
 
 }  // namespace mpm
