@@ -194,6 +194,37 @@ int mpm_reset_timing(mpm_ctx *ctx);
  */
 int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
 
+/*
+ * One explicit step that allocates no memory (the paper has no counterpart:
+ * this is a deployment entry point of this library).
+ *
+ * For callers that cannot call cudaMalloc: code running while a stream is
+ * captured into a CUDA graph, plugins inside an application that owns all
+ * device memory, real-time loops that must not enter the allocator.  The
+ * particle state comes in and goes out through caller-owned device buffers
+ * (layouts as for mpm_get_particles, doubles, n particles); the only scratch,
+ * the background grid, lives in a static device array of this library holding
+ * at most 131072 grid nodes (4 MiB, kept by every GPU that loads the library
+ * until the process exits).  Supports dim 2 or 3, MPM_FP64, batch 1, slip walls
+ * (no friction fields), no sorting; gravity, Tait fluid and Drucker-Prager as
+ * in mpm_step.  `out` may alias `in` particle by particle.
+ *
+ * Rules: the call queues its kernels on cuda_stream (NULL = the legacy default
+ * stream) and returns without waiting.  The first call on each device resolves
+ * the device address of the static scratch (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * scratch and clears it before use, so calls whose work overlaps on the GPU
+ * race: serialise them.  A grid of more than 131072 nodes ((N_x + 3)(N_y + 3)
+ * [(N_z + 3)]) is rejected with MPM_EINVAL.  On failure a one-line message is
+ * written to err (when err_len > 0).
+ */
+typedef struct {
+    double *x, *v, *C, *F, *rho, *sigma, *eps;   /* device pointers; sigma/eps for Drucker-Prager only */
+} mpm_state_ptrs;
+
+int mpm_step_noalloc(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream, int64_t n,
+                     double particle_volume, mpm_state_ptrs in, mpm_state_ptrs out, char *err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

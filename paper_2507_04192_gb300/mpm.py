@@ -41,6 +41,11 @@ class Material(C.Structure):
                 ("dp_literal", C.c_int)]
 
 
+class StatePtrs(C.Structure):
+    """Device pointers of one particle state (mpm_state_ptrs)."""
+    _fields_ = [(k, C.c_void_p) for k in ("x", "v", "C", "F", "rho", "sigma", "eps")]
+
+
 class MPMError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -82,6 +87,8 @@ def load_library(build_if_missing: bool = True):
             "mpm_get_timing": (I, [P, I, C.POINTER(D), C.POINTER(L)]),
             "mpm_reset_timing": (I, [P]),
             "mpm_get_stats": (I, [P, C.POINTER(L), I]),
+            "mpm_step_noalloc": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, L, D, StatePtrs, StatePtrs,
+                                     C.c_char_p, I]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -180,6 +187,16 @@ def mpm_get_stats(ctx) -> dict:
     _check(ctx, load_library().mpm_get_stats(ctx, out, 6))
     keys = ("active_tiles", "chunks", "escaped", "sorts", "steps", "launches")
     return dict(zip(keys, list(out)))
+
+
+def mpm_step_noalloc(grid: GridDesc, material: Material, n: int, particle_volume: float, state_in: StatePtrs,
+                     state_out: StatePtrs, stream: int = 0):
+    """One step with caller-owned device buffers and no allocation (see include/mpm.h)."""
+    buf = C.create_string_buffer(256)
+    rc = load_library().mpm_step_noalloc(C.byref(grid), C.byref(material), C.c_void_p(stream), int(n),
+                                         float(particle_volume), state_in, state_out, buf, 256)
+    if rc != MPM_OK:
+        raise MPMError(rc, buf.value.decode(errors="replace"))
 
 
 # ---------------------------------------------------------------- convenience wrapper
