@@ -89,6 +89,7 @@ def lib():
             "orc_dp_constants": (None, [P, p]),
             "orc_tait_pressure": (d, [P, d]),
             "orc_affine_C": (None, [P, l, p, p, p]),
+            "orc_step_vjp": (i, [P, l, p, p, p, p, p, p, p, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -187,6 +188,24 @@ class Oracle:
         Cm = np.zeros_like(st.B)
         lib().orc_affine_C(C.byref(self.P), st.n, _ptr(st.x), _ptr(st.B), _ptr(Cm))
         return Cm
+
+    def step_vjp(self, st: "State", xb, vb, Bb, rhob):
+        """Adjoint of one step (fluid): given the adjoint of S^{t+1} = (x, v, B, rho),
+        return the adjoint of S^t and dL/dmu per wall with a friction field."""
+        n, d = st.n, self.dim
+        out = [np.zeros((n, d)), np.zeros((n, d)), np.zeros((n, d, d)), np.zeros(n)]
+        ins = [np.ascontiguousarray(a, dtype=np.float64) for a in (xb, vb, Bb, rhob)]
+        mub = {}
+        ptrs = (C.c_void_p * MAX_WALLS)()
+        for w in range(MAX_WALLS):
+            if self.P.mu[w]:
+                mub[w] = np.zeros(self.P.n_seg[w][0] * self.P.n_seg[w][1])
+                ptrs[w] = mub[w].ctypes.data
+        rc = lib().orc_step_vjp(C.byref(self.P), n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.rho),
+                                *[_ptr(a) for a in ins], *[_ptr(a) for a in out], ptrs)
+        if rc != 0:
+            raise RuntimeError(f"orc_step_vjp failed ({rc})")
+        return out, mub
 
     # -- constitutive pieces ------------------------------------------------------
     def tait_pressure(self, rho: float) -> float:

@@ -525,3 +525,263 @@ int orc_step(const orc_params *P, long n, double *x, double *v, double *B, doubl
     free(gm); free(gq); free(gf); free(gv);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of one step (reverse mode), weakly compressible fluid.            */
+/*                                                                           */
+/* A separately hand-derived vector-Jacobian product of the step above for   */
+/* the state S = (x, v, B, rho) (the fluid's stress is -p(rho) I, a function */
+/* of rho; F does not feed back).  Given the adjoint of S^{t+1}, returns the */
+/* adjoint of S^t and adds d<adj, S^{t+1}>/d mu to mu_bar for every wall     */
+/* with a friction field (the recursion of Eq. dzda, Sec. 3.1).  D_p is      */
+/* constant in x_p for quadratic B-splines, so it is not differentiated.     */
+/* Branches (clamp, contact, stick/slide, mass threshold) follow the forward */
+/* pass.  mu_bar[w] points to n_seg0*n_seg1 doubles (NULL for slip walls).   */
+/* ------------------------------------------------------------------------- */
+
+/* Hessian of phi_i at x_p: H_ab = d^2 phi_i / dx_a dx_b. */
+static void stencil_hessian(const orc_params *P, const double *xp, const stencil_t *S, int k, double *H)
+{
+    int d = P->dim;
+    double f[3], df[3], ddf[3];
+    for (int a = 0; a < d; ++a) {
+        double xi = (xp[a] - S->xi[k][a]) / P->dx;
+        f[a] = orc_phi_bar(xi);
+        df[a] = orc_dphi_bar(xi) / P->dx;
+        double ax = fabs(xi);
+        ddf[a] = (ax < 0.5 ? -2.0 : (ax < 1.5 ? 1.0 : 0.0)) / (P->dx * P->dx);
+    }
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double h = 1.0;
+            for (int c = 0; c < d; ++c) {
+                int na = (c == a) + (c == b);
+                h *= na == 0 ? f[c] : (na == 1 ? df[c] : ddf[c]);
+            }
+            H[a * d + b] = h;
+        }
+}
+
+/* Contact with one wall in the closed form of Eq. coulomb_friction (v_n > 0):
+ * v_t = v - v_n n; stick if |v_t| <= mu v_n; else slide v_t (1 - mu v_n / |v_t|).
+ * Reverse of that map for the adjoint ob of its output; returns the adjoint of
+ * its input in ib and adds d<ob, out>/d mu to *mub. */
+static void wall_vjp(const double *v, const double *n, double mu, const double *ob, double *ib, double *mub)
+{
+    double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+    for (int a = 0; a < 3; ++a) ib[a] = ob[a];
+    if (vn <= 0.0) return;
+    double vt[3], vtn = 0.0;
+    for (int a = 0; a < 3; ++a) { vt[a] = v[a] - vn * n[a]; vtn += vt[a] * vt[a]; }
+    vtn = sqrt(vtn);
+    /* output = P_t v (slip), 0 (stick), or s P_t v with s = 1 - mu vn / |vt| */
+    double obt[3], obn = ob[0] * n[0] + ob[1] * n[1] + ob[2] * n[2];
+    for (int a = 0; a < 3; ++a) obt[a] = ob[a] - obn * n[a];            /* P_t^T ob = P_t ob */
+    if (mu == 0.0) { for (int a = 0; a < 3; ++a) ib[a] = obt[a]; return; }
+    if (vtn <= mu * vn) { for (int a = 0; a < 3; ++a) ib[a] = 0.0; return; }
+    double s = 1.0 - mu * vn / vtn;
+    double dot = obt[0] * vt[0] + obt[1] * vt[1] + obt[2] * vt[2];      /* ob . vt */
+    /* d(s vt)/dv applied transposed: s P_t ob + vt (ob.vt) * ds/dv, with
+     * ds/dv = -mu (n / |vt| - vn vt / |vt|^3) */
+    for (int a = 0; a < 3; ++a)
+        ib[a] = s * obt[a] - mu * dot * (n[a] / vtn - vn * vt[a] / (vtn * vtn * vtn));
+    if (mub) *mub += -dot * vn / vtn;
+}
+
+static int wall_segment_index(const orc_params *P, int w, const int j[3])
+{
+    int a = w / 2, d = P->dim, t[2], nt = 0;
+    for (int b = 0; b < d; ++b) if (b != a) t[nt++] = b;
+    int s[2] = {0, 0};
+    for (int q = 0; q < nt; ++q) {
+        int ns = P->n_seg[w][q];
+        long num = (long)(j[t[q]] - 1) * ns;
+        long den = P->n_cells[t[q]];
+        long sq = num >= 0 ? num / den : -1;
+        if (sq < 0) sq = 0;
+        if (sq > ns - 1) sq = ns - 1;
+        s[q] = (int)sq;
+    }
+    return s[1] * P->n_seg[w][0] + s[0];
+}
+
+/* dp/drho of the Tait equation of state */
+static double tait_dpdrho(const orc_params *P, double rho)
+{
+    return P->bulk_K / P->rho0 * pow(rho / P->rho0, P->gamma - 1.0);
+}
+
+int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, const double *B,
+                 const double *rho,
+                 const double *xb1, const double *vb1, const double *Bb1, const double *rhob1,
+                 double *xb0, double *vb0, double *Bb0, double *rhob0, double **mu_bar)
+{
+    if (P->material != 0) return -2;
+    int d = P->dim;
+    long G = orc_num_nodes(P);
+    double dt = P->dt;
+    double mp = orc_particle_mass(P);
+    double m_eps = 1e-10 * P->rho0 * pow(P->dx, d);
+    double *gm = calloc(G, sizeof(double)), *gq = calloc(G * d, sizeof(double)), *gf = calloc(G * d, sizeof(double));
+    double *gu = calloc(G * 3, sizeof(double)), *gv = calloc(G * 3, sizeof(double));
+    double *gvb = calloc(G * 3, sizeof(double)), *gqb = calloc(G * d, sizeof(double)), *gfb = calloc(G * d, sizeof(double));
+    double *gmb = calloc(G, sizeof(double));
+    if (!gm || !gq || !gf || !gu || !gv || !gvb || !gqb || !gfb || !gmb) return -1;
+    double *sig = calloc(n * 9, sizeof(double));
+    for (long p = 0; p < n; ++p) {
+        double pr = orc_tait_pressure(P, rho[p]);
+        for (int a = 0; a < 3; ++a) sig[p * 9 + a * 4] = -pr;
+    }
+    /* forward: P2G and grid update, keeping the pre-wall velocity u */
+    orc_p2g(P, n, x, v, B, rho, sig, gm, gq, gf);
+    int order[ORC_MAX_WALLS], nw = 0, floor_w = 2 * (d - 1);
+    for (int w = 0; w < 2 * d; ++w) if (w != floor_w) order[nw++] = w;
+    order[nw++] = floor_w;
+    for (long i = 0; i < G; ++i) {
+        if (gm[i] > m_eps)
+            for (int a = 0; a < d; ++a) gu[i * 3 + a] = gq[i * d + a] / gm[i] + dt * gf[i * d + a] / gm[i];
+    }
+    {
+        /* walls on a copy */
+        double *tmp = malloc(sizeof(double) * G * d);
+        for (long i = 0; i < G; ++i) for (int a = 0; a < d; ++a) tmp[i * d + a] = 0.0;
+        orc_grid_update(P, gm, gq, gf, tmp);
+        for (long i = 0; i < G; ++i) for (int a = 0; a < d; ++a) gv[i * 3 + a] = tmp[i * d + a];
+        free(tmp);
+    }
+    /* reverse G2P */
+    stencil_t S;
+    for (long p = 0; p < n; ++p) {
+        const double *xp = x + p * d;
+        build_stencil(P, xp, &S);
+        double vp[3] = {0, 0, 0}, L[9] = {0};
+        for (int k = 0; k < S.count; ++k)
+            for (int a = 0; a < d; ++a) {
+                vp[a] += S.phi[k] * gv[S.node[k] * 3 + a];
+                for (int b = 0; b < d; ++b) L[a * d + b] += gv[S.node[k] * 3 + a] * S.grad[k][b];
+            }
+        double trL = 0.0;
+        for (int a = 0; a < d; ++a) trL += L[a * d + a];
+        double vbt[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+            double xn = xp[a] + dt * vp[a];
+            int clamped = xn < 0.0 || xn > P->n_cells[a] * P->dx;
+            xb0[p * d + a] = clamped ? 0.0 : xb1[p * d + a];
+            vbt[a] = vb1[p * d + a] + (clamped ? 0.0 : dt * xb1[p * d + a]);
+        }
+        double den = 1.0 + dt * trL;
+        rhob0[p] = rhob1[p] / den;
+        double trLb = -rhob1[p] * rho[p] * dt / (den * den);
+        const double *Bb = Bb1 + p * d * d;
+        for (int k = 0; k < S.count; ++k) {
+            long i = S.node[k];
+            double phi = S.phi[k], r[3];
+            for (int b = 0; b < d; ++b) r[b] = S.xi[k][b] - xp[b];
+            double phib = 0.0, gradb[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) {
+                double via = gv[i * 3 + a];
+                double Br = 0.0;
+                for (int b = 0; b < d; ++b) Br += Bb[a * d + b] * r[b];
+                gvb[i * 3 + a] += phi * vbt[a] + phi * Br + trLb * S.grad[k][a];
+                phib += vbt[a] * via + Br * via;
+                gradb[a] += trLb * via;
+                for (int b = 0; b < d; ++b) xb0[p * d + b] += -Bb[a * d + b] * phi * via;
+            }
+            double H[9];
+            stencil_hessian(P, xp, &S, k, H);
+            for (int b = 0; b < d; ++b) {
+                double hb = 0.0;
+                for (int a = 0; a < d; ++a) hb += H[b * d + a] * gradb[a];
+                xb0[p * d + b] += phib * S.grad[k][b] + hb;
+            }
+        }
+    }
+    /* reverse grid update */
+    for (long i = 0; i < G; ++i) {
+        if (!(gm[i] > m_eps)) continue;
+        int j[3] = {0, 0, 0};
+        long r = i;
+        for (int a = 0; a < d; ++a) { j[a] = (int)(r % nodes_axis(P, a)); r /= nodes_axis(P, a); }
+        /* forward chain through the walls, keeping each wall's input */
+        double chain[ORC_MAX_WALLS + 1][3];
+        for (int a = 0; a < 3; ++a) chain[0][a] = gu[i * 3 + a];
+        int applied[ORC_MAX_WALLS];
+        for (int q = 0; q < nw; ++q) {
+            int w = order[q], a = w / 2, hi = w % 2;
+            double coord = (j[a] - 1) * P->dx, Lw = P->n_cells[a] * P->dx;
+            applied[q] = hi ? (coord >= Lw) : (coord <= 0.0);
+            for (int b = 0; b < 3; ++b) chain[q + 1][b] = chain[q][b];
+            if (applied[q]) {
+                double nrm[3] = {0, 0, 0};
+                nrm[a] = hi ? 1.0 : -1.0;
+                orc_friction(chain[q], nrm, wall_mu(P, w, j), chain[q + 1]);
+            }
+        }
+        double ob[3] = {gvb[i * 3], gvb[i * 3 + 1], gvb[i * 3 + 2]};
+        for (int q = nw - 1; q >= 0; --q) {
+            if (!applied[q]) continue;
+            int w = order[q], a = w / 2, hi = w % 2;
+            double nrm[3] = {0, 0, 0}, ib[3];
+            nrm[a] = hi ? 1.0 : -1.0;
+            double *mub = NULL;
+            if (P->mu[w] && mu_bar && mu_bar[w]) mub = mu_bar[w] + wall_segment_index(P, w, j);
+            wall_vjp(chain[q], nrm, wall_mu(P, w, j), ob, ib, mub);
+            for (int b = 0; b < 3; ++b) ob[b] = ib[b];
+        }
+        for (int a = 0; a < d; ++a) {
+            gqb[i * d + a] = ob[a] / gm[i];
+            gfb[i * d + a] = dt * ob[a] / gm[i];
+            gmb[i] += -ob[a] * (gq[i * d + a] + dt * gf[i * d + a]) / (gm[i] * gm[i]);
+        }
+    }
+    /* reverse P2G */
+    for (long p = 0; p < n; ++p) {
+        const double *xp = x + p * d;
+        const double *vpp = v + p * d;
+        build_stencil(P, xp, &S);
+        double D[9], Dinv[9], M[9], Mb[9] = {0};
+        moment_matrix(P, xp, &S, D);
+        invert(d, D, Dinv);
+        matmul(d, B + p * d * d, Dinv, M);
+        double Vp = mp / rho[p], pr = orc_tait_pressure(P, rho[p]);
+        double Vb = 0.0, prb = 0.0;
+        for (int k = 0; k < S.count; ++k) {
+            long i = S.node[k];
+            double phi = S.phi[k], r[3];
+            for (int b = 0; b < d; ++b) r[b] = S.xi[k][b] - xp[b];
+            double phib = mp * gmb[i], gradb[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) {
+                double qa = vpp[a];
+                for (int b = 0; b < d; ++b) qa += M[a * d + b] * r[b];
+                double qb = gqb[i * d + a], fb = gfb[i * d + a];
+                phib += mp * qb * qa + mp * fb * P->gravity[a];
+                vb0[p * d + a] += phi * mp * qb;
+                for (int b = 0; b < d; ++b) {
+                    Mb[a * d + b] += phi * mp * qb * r[b];
+                    xb0[p * d + b] += -phi * mp * qb * M[a * d + b];
+                }
+                /* f_a = V p grad_a (sigma = -p I) */
+                gradb[a] += Vp * pr * fb;
+                Vb += pr * fb * S.grad[k][a];
+                prb += Vp * fb * S.grad[k][a];
+            }
+            double H[9];
+            stencil_hessian(P, xp, &S, k, H);
+            for (int b = 0; b < d; ++b) {
+                double hb = 0.0;
+                for (int a = 0; a < d; ++a) hb += H[b * d + a] * gradb[a];
+                xb0[p * d + b] += phib * S.grad[k][b] + hb;
+            }
+        }
+        /* M = B Dinv -> Bbar = Mbar Dinv^T */
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                double s = 0.0;
+                for (int c = 0; c < d; ++c) s += Mb[a * d + c] * Dinv[b * d + c];
+                Bb0[p * d * d + a * d + b] = s;
+            }
+        rhob0[p] += Vb * (-mp / (rho[p] * rho[p])) + prb * tait_dpdrho(P, rho[p]);
+    }
+    free(gm); free(gq); free(gf); free(gu); free(gv); free(gvb); free(gqb); free(gfb); free(gmb); free(sig);
+    return 0;
+}
