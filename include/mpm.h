@@ -171,6 +171,32 @@ int64_t mpm_num_particles(const mpm_ctx *ctx);
 int mpm_last_error(const mpm_ctx *ctx, char *buf, int len);
 
 /*
+ * Observations for the inverse loss of Eq. inverse_loss (Sec. 3.2), Lagrangian
+ * form (tracked particles, Q_l(z) = [z]_l): n_track load-order particle ids
+ * (distinct), n_obs observation steps (>= 1, increasing, counted from the state
+ * at the start of mpm_step_adjoint) and the observed positions z_obs
+ * (n_obs x n_track x dim, host).  The loss is
+ *     L = sum_obs sum_l |x_{id_l}^{step} - z_obs|^2.
+ */
+int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_obs, const int *steps,
+                         const double *z_obs);
+
+/*
+ * Loss and its gradient with respect to one wall's friction field (the
+ * reverse-mode recursion of Eq. dzda, Sec. 3.1; loss gradient of Sec. 3.2).
+ * Runs n_steps explicit steps from the current state, saving the particle
+ * state every checkpoint_every steps (Sec. 3.3.2); then walks the segments
+ * backwards, recomputing each segment's states from its checkpoint and
+ * applying the adjoint of each step.  Writes the loss and dL/dmu (the wall's
+ * n_seg[0] x n_seg[1] coefficients, set by mpm_set_friction_field) to host
+ * memory and leaves the context at the state after n_steps steps.  Weakly
+ * compressible fluid, batch 1.  Device memory: checkpoints of
+ * (2 dim + dim^2 + 1) reals per particle each, plus checkpoint_every states.
+ */
+int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, double *loss_out,
+                     double *dL_dmu_out);
+
+/*
  * Kernel timing.  When enabled, every kernel launch is bracketed by CUDA
  * events on the context's stream; mpm_get_timing returns, for one kernel
  * class, the summed device time in milliseconds and the launch count since

@@ -1,0 +1,601 @@
+// Adjoint (reverse-mode) kernels of the explicit step for the weakly
+// compressible fluid: the vector-Jacobian product of one step S^t -> S^{t+1}
+// (the recursion of Eq. dzda, Sec. 3.1) with S = (x, v, C, rho), and the
+// gradient of the tracked-particle loss of Eq. inverse_loss (Sec. 3.2) with
+// respect to the wall friction coefficients (Eq. coulomb_friction, Sec. 5.3).
+//
+// The reverse sweep works on particle states stored in load order (id order),
+// independent of the forward pass's sorted order, with its own grid buffers:
+//   k_adj_p2g      P2G of S^t again (grid mass m and P = q + dt f_int)
+//   k_adj_grid     u = P / m + dt g and v = walls(u) per node
+//   k_adj_g2p_bwd  adjoint of G2P: scatters v_bar to the grid, x_bar and
+//                  rho_bar partials to the particles
+//   k_adj_grid_bwd adjoint of the grid update: walls (and d/dmu), division
+//   k_adj_p2g_bwd  adjoint of P2G: gathers (m_bar, P_bar), completes the
+//                  particle adjoint
+// Branches (position clamp, wall contact, stick/slide, mass threshold) follow
+// the forward pass; the weights' dependence on x_p enters through their
+// gradients and Hessians.
+#pragma once
+
+#include "mpm_kernels.cuh"
+
+namespace mpm {
+
+// Per-wall device accumulators of dL/dmu (nullptr for walls without friction).
+struct MuBar {
+    double *w[kMaxWalls];
+};
+
+// Second derivatives of the three stencil weights with respect to x.
+template <class R> __device__ __forceinline__ void bspline_dd(R inv_dx, R ddw[3])
+{
+    const R s = inv_dx * inv_dx;
+    ddw[0] = s;
+    ddw[1] = R(-2) * s;
+    ddw[2] = s;
+}
+
+// Component count of the adjoint state (x, v, C, rho).
+template <int D> __host__ __device__ constexpr int adj_ncomp() { return 2 * D + D * D + 1; }
+
+// Walls in order x-, x+, y-, y+, (z-, z+), floor last, applied to u (in place);
+// chain[q] receives the input of wall q.
+template <class R, int D>
+__device__ __forceinline__ void walls_forward(const Params<R> &P, int sim, const int a3[3], R vel[3],
+                                              R chain[2 * D][3], bool applied[2 * D])
+{
+    constexpr int floor_w = 2 * (D - 1);
+#pragma unroll
+    for (int q = 0; q < 2 * D; ++q) {
+        const int w = q < 2 * D - 1 ? (q < floor_w ? q : q + 1) : floor_w;
+        const int ax = w >> 1, hi = w & 1;
+        const int c = a3[ax] - 2;
+        chain[q][0] = vel[0];
+        chain[q][1] = vel[1];
+        chain[q][2] = vel[2];
+        const bool on = hi ? (c >= P.n_cells[ax]) : (c <= 0);
+        applied[q] = on;
+        if (!on) continue;
+        const R vn = hi ? vel[ax] : -vel[ax];
+        if (!(vn > R(0))) continue;
+        const R mu = wall_mu<R, D>(P, w, sim, a3);
+        vel[ax] = R(0);
+        if (mu > R(0)) {
+            R vt2 = R(0);
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) vt2 += vel[bb] * vel[bb];
+            const R vt = rsqrt_(vt2);
+            const R scale = (vt <= mu * vn) ? R(0) : R(1) - mu * vn / vt;
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) vel[bb] *= scale;
+        }
+    }
+}
+
+// Friction segment index of the node on wall w (as in wall_mu).
+template <class R, int D>
+__device__ __forceinline__ int64_t wall_seg(const Params<R> &P, int w, const int a3[3])
+{
+    const WallDev &wd = P.wall[w];
+    int s[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < D - 1; ++q) {
+        const int ax = wd.seg_axis[q];
+        const int c = a3[ax] - 2;
+        int sq = c > 0 ? (int)(((int64_t)c * wd.n_seg[q]) / P.n_cells[ax]) : 0;
+        s[q] = min(sq, wd.n_seg[q] - 1);
+    }
+    return (int64_t)s[1] * wd.n_seg[0] + s[0];
+}
+
+// Adjoint of the wall chain: ob (adjoint of the output) -> adjoint of u, in place;
+// d<ob, out>/d mu is added to mu_bar (per wall segment) for walls with friction.
+template <class R, int D>
+__device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, const int a3[3],
+                                               const R chain[2 * D][3], const bool applied[2 * D], R ob[3],
+                                               double *const mu_bar[kMaxWalls])
+{
+    constexpr int floor_w = 2 * (D - 1);
+#pragma unroll
+    for (int q = 2 * D - 1; q >= 0; --q) {
+        if (!applied[q]) continue;
+        const int w = q < 2 * D - 1 ? (q < floor_w ? q : q + 1) : floor_w;
+        const int ax = w >> 1, hi = w & 1;
+        const R *u = chain[q];
+        const R sgn = hi ? R(1) : R(-1);
+        const R vn = sgn * u[ax];
+        if (!(vn > R(0))) continue;                  // contact not active: identity
+        const R mu = wall_mu<R, D>(P, w, sim, a3);
+        if (!(mu > R(0))) {                          // slip: normal component removed
+            ob[ax] = R(0);
+            continue;
+        }
+        R vt2 = R(0);
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb)
+            if (bb != ax) vt2 += u[bb] * u[bb];
+        const R vt = rsqrt_(vt2);
+        if (vt <= mu * vn) {                         // stick: output 0
+            ob[0] = ob[1] = ob[2] = R(0);
+            continue;
+        }
+        const R s = R(1) - mu * vn / vt;
+        R dot = R(0);
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb)
+            if (bb != ax) dot += ob[bb] * u[bb];
+        const R k = dot * mu * vn / (vt * vt * vt);
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb)
+            if (bb != ax) ob[bb] = s * ob[bb] + k * u[bb];
+        ob[ax] = -dot * mu * sgn / vt;
+        if (mu_bar[w] != nullptr)
+            atomicAdd(&mu_bar[w][(int64_t)sim * P.wall[w].n_seg[0] * P.wall[w].n_seg[1] + wall_seg<R, D>(P, w, a3)],
+                      (double)(-dot * vn / vt));
+    }
+}
+
+// Particle state gather (slot order -> load order) and scatter.
+template <class R, int D>
+__global__ void k_adj_save(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
+                           R *__restrict__ dst)
+{
+    constexpr int NA = adj_ncomp<D>();
+    const int64_t n = P.n, np = P.npad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = id[i];
+#pragma unroll
+        for (int c = 0; c < NA - 1; ++c) dst[c * n + o] = S[c * np + i];
+        dst[(NA - 1) * n + o] = S[P.off_rho * np + i];
+    }
+}
+
+template <class R, int D>
+__global__ void k_adj_restore(const Params<R> P, R *__restrict__ S, const int32_t *__restrict__ id,
+                              const R *__restrict__ src)
+{
+    constexpr int NA = adj_ncomp<D>();
+    const int64_t n = P.n, np = P.npad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = id[i];
+#pragma unroll
+        for (int c = 0; c < NA - 1; ++c) S[c * np + i] = src[c * n + o];
+        S[P.off_rho * np + i] = src[(NA - 1) * n + o];
+    }
+}
+
+// Positions of the tracked particles (load-order ids) -> out[track].
+template <class R, int D>
+__global__ void k_adj_track(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
+                            const int32_t *__restrict__ track_of_id, double *__restrict__ out)
+{
+    const int64_t np = P.npad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = track_of_id[id[i]];
+        if (l < 0) continue;
+#pragma unroll
+        for (int a = 0; a < D; ++a) out[(int64_t)l * D + a] = (double)S[(P.off_x + a) * np + i];
+    }
+}
+
+// lam.x[id_l] += 2 (x_l - z_l) for the tracked particles of one observation.
+template <class R, int D>
+__global__ void k_adj_seed(int64_t n, int n_track, const int64_t *__restrict__ ids, const double *__restrict__ x_obs,
+                           const double *__restrict__ z_obs, R *__restrict__ lam)
+{
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n_track; l += gridDim.x * blockDim.x) {
+        const int64_t o = ids[l];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            atomicAdd(&lam[a * n + o], (R)(2.0 * (x_obs[(int64_t)l * D + a] - z_obs[(int64_t)l * D + a])));
+    }
+}
+
+template <class R>
+__global__ void k_adj_zero(R *__restrict__ p, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = R(0);
+}
+
+// Re-P2G of a load-order state into GA (m, P = q + dt f_int) with global atomics.
+template <class R, int D>
+__global__ void k_adj_p2g(const Params<R> P, const R *__restrict__ st, R4<R> *__restrict__ GA)
+{
+    const int64_t n = P.n;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        P2GFactors<R, D> f;
+        p2g_factors<R, D>(P, [&](int j) { return st[(int64_t)j * n + p]; }, f);
+#pragma unroll
+        for (int k = 0; k < Geo<D>::STENCIL; ++k) {
+            const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
+            R m, mom[D];
+            p2g_node<R, D>(f, P.mass, k0, k1, k2, m, mom);
+            const int kk[3] = {k0, k1, k2};
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = f.b[a] + 2 + kk[a];
+            red_add4(&GA[lin3<D>(a3, P.G_nodes)], m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
+        }
+    }
+}
+
+// Per node: u = P / m + dt g (m > m_eps, else 0) and v = walls(u).
+template <class R, int D>
+__global__ void k_adj_grid(const Params<R> P, const R4<R> *__restrict__ GA, R4<R> *__restrict__ GU,
+                           R4<R> *__restrict__ GV)
+{
+    const int64_t N = P.nodes_per_sim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> acc = GA[i];
+        R vel[3] = {R(0), R(0), R(0)};
+        if (acc.x > P.m_eps) {
+            const R inv_m = R(1) / acc.x;
+            vel[0] = acc.y * inv_m + P.dt * P.gravity[0];
+            vel[1] = acc.z * inv_m + P.dt * P.gravity[1];
+            if (D == 3) vel[2] = acc.w * inv_m + P.dt * P.gravity[2];
+        }
+        GU[i] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+        int a3[3] = {0, 0, 0};
+        int64_t r = i;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            a3[a] = (int)(r % P.G_nodes[a]);
+            r /= P.G_nodes[a];
+        }
+        R chain[2 * D][3];
+        bool applied[2 * D];
+        walls_forward<R, D>(P, 0, a3, vel, chain, applied);
+        GV[i] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+    }
+}
+
+// Stencil data of one particle for the reverse kernels.
+template <class R, int D> struct AdjStencil {
+    int b[D];
+    R fx[D], w[D][3], dw[D][3], ddw[3];
+};
+
+template <class R, int D>
+__device__ __forceinline__ void adj_stencil(const Params<R> &P, const R x[D], AdjStencil<R, D> &s)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        s.b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+        s.fx[a] = x[a] * P.inv_dx - R(s.b[a]);
+        bspline(s.fx[a], P.inv_dx, s.w[a], s.dw[a]);
+    }
+    bspline_dd(P.inv_dx, s.ddw);
+}
+
+// Weight, gradient and Hessian of stencil node (k0, k1, k2).
+template <class R, int D>
+__device__ __forceinline__ void adj_node(const AdjStencil<R, D> &s, const int kk[3], R &w, R g[D], R H[D][D])
+{
+    R f[D], df[D], ddf[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        f[a] = s.w[a][kk[a]];
+        df[a] = s.dw[a][kk[a]];
+        ddf[a] = s.ddw[kk[a]];
+    }
+    w = R(1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) w *= f[a];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R ga = df[a];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (c != a) ga *= f[c];
+        g[a] = ga;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R h = R(1);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int cnt = (c == a) + (c == b);
+                h *= cnt == 0 ? f[c] : (cnt == 1 ? df[c] : ddf[c]);
+            }
+            H[a][b] = h;
+        }
+    }
+}
+
+// Adjoint of G2P for one particle: lam_in is the adjoint of S^{t+1}; writes the
+// G2P part of the adjoint of x and rho to lam_out and scatters v_bar to GVB.
+template <class R, int D>
+__global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GV,
+                              const R *__restrict__ lam_in, R *__restrict__ lam_out, R4<R> *__restrict__ GVB)
+{
+    const int64_t n = P.n;
+    constexpr int JC = 2 * D, JR = 2 * D + D * D;
+    const R cscale = R(4) * P.inv_dx;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        R x[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = st[a * n + p];
+        AdjStencil<R, D> s;
+        adj_stencil<R, D>(P, x, s);
+        // forward quantities: v_p and tr L
+        R vp[D], trL = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) vp[a] = R(0);
+#pragma unroll
+        for (int k = 0; k < Geo<D>::STENCIL; ++k) {
+            const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+            R w, g[D], H[D][D];
+            adj_node<R, D>(s, kk, w, g, H);
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = s.b[a] + 2 + kk[a];
+            const R4<R> v4 = GV[lin3<D>(a3, P.G_nodes)];
+            const R vi[3] = {v4.x, v4.y, v4.z};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                vp[a] += w * vi[a];
+                trL += vi[a] * g[a];
+            }
+        }
+        // adjoints of the outputs
+        R xb[D], vbt[D], Cb[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R xo = lam_in[a * n + p];
+            const R xn = x[a] + P.dt * vp[a];
+            const bool clamped = xn < R(0) || xn > P.L[a];
+            xb[a] = clamped ? R(0) : xo;
+            vbt[a] = lam_in[(D + a) * n + p] + (clamped ? R(0) : P.dt * xo);
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Cb[q] = lam_in[(JC + q) * n + p];
+        const R rho = st[JR * n + p];
+        const R den = R(1) + P.dt * trL;
+        const R rb1 = lam_in[JR * n + p];
+        const R rhob = rb1 / den;
+        const R trLb = -rb1 * rho * P.dt / (den * den);
+        // x_bar through (k - fx): C = (4 / dx) sum w v (k - fx) and dfx/dx = 1/dx
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R sacc = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) sacc += Cb[a * D + b] * vp[a];
+            xb[b] -= cscale * P.inv_dx * sacc;
+        }
+#pragma unroll
+        for (int k = 0; k < Geo<D>::STENCIL; ++k) {
+            const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+            R w, g[D], H[D][D];
+            adj_node<R, D>(s, kk, w, g, H);
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = s.b[a] + 2 + kk[a];
+            const int64_t gi = lin3<D>(a3, P.G_nodes);
+            const R4<R> v4 = GV[gi];
+            const R vi[3] = {v4.x, v4.y, v4.z};
+            R vb[3] = {R(0), R(0), R(0)};
+            R wbar = R(0), gbar[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R cr = R(0);
+#pragma unroll
+                for (int b = 0; b < D; ++b) cr += Cb[a * D + b] * (R(kk[b]) - s.fx[b]);
+                vb[a] = w * vbt[a] + cscale * w * cr + trLb * g[a];
+                wbar += vbt[a] * vi[a] + cscale * cr * vi[a];
+                gbar[a] = trLb * vi[a];
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                R hb = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) hb += H[b][a] * gbar[a];
+                xb[b] += wbar * g[b] + hb;
+            }
+            red_add4(&GVB[gi], vb[0], vb[1], vb[2], R(0));
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) lam_out[a * n + p] = xb[a];
+        lam_out[JR * n + p] = rhob;
+    }
+}
+
+// Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P).
+template <class R, int D>
+__global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, const R4<R> *__restrict__ GU,
+                               const R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB, MuBar mu_bar)
+{
+    const int64_t N = P.nodes_per_sim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> acc = GA[i];
+        if (!(acc.x > P.m_eps)) {
+            GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
+            continue;
+        }
+        const R4<R> u4 = GU[i];
+        R vel[3] = {u4.x, u4.y, u4.z};
+        int a3[3] = {0, 0, 0};
+        int64_t r = i;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            a3[a] = (int)(r % P.G_nodes[a]);
+            r /= P.G_nodes[a];
+        }
+        R chain[2 * D][3];
+        bool applied[2 * D];
+        walls_forward<R, D>(P, 0, a3, vel, chain, applied);
+        const R4<R> b4 = GVB[i];
+        R ob[3] = {b4.x, b4.y, b4.z};
+        walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w);
+        const R inv_m = R(1) / acc.x;
+        const R Pv[3] = {acc.y, acc.z, acc.w};
+        R mb = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
+        GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
+    }
+}
+
+// Adjoint of P2G for one particle; completes lam_out (adjoint of S^t).
+template <class R, int D>
+__global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GAB,
+                              R *__restrict__ lam_out)
+{
+    const int64_t n = P.n;
+    constexpr int JV = D, JC = 2 * D, JR = 2 * D + D * D;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        R x[D], v[D], C[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = st[a * n + p];
+            v[a] = st[(JV + a) * n + p];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) C[q] = st[(JC + q) * n + p];
+        const R rho = st[JR * n + p];
+        const R mp = P.mass;
+        const R pr = tait(P, rho);
+        const R sforce = P.dt * mp / rho * pr;             // P += sforce * grad w  (sigma = -p I)
+        AdjStencil<R, D> s;
+        adj_stencil<R, D>(P, x, s);
+        R xb[D], vb[D], Cb[D * D], sb = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            xb[a] = R(0);
+            vb[a] = R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Cb[q] = R(0);
+#pragma unroll
+        for (int k = 0; k < Geo<D>::STENCIL; ++k) {
+            const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+            R w, g[D], H[D][D];
+            adj_node<R, D>(s, kk, w, g, H);
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) a3[a] = s.b[a] + 2 + kk[a];
+            const R4<R> ab = GAB[lin3<D>(a3, P.G_nodes)];
+            const R Pb[3] = {ab.y, ab.z, ab.w};
+            R rr[D];
+#pragma unroll
+            for (int b = 0; b < D; ++b) rr[b] = (R(kk[b]) - s.fx[b]) * P.dx;
+            R wbar = mp * ab.x, gbar[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R aff = v[a];
+#pragma unroll
+                for (int b = 0; b < D; ++b) aff += C[a * D + b] * rr[b];
+                wbar += mp * Pb[a] * aff;
+                vb[a] += mp * w * Pb[a];
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    Cb[a * D + b] += mp * w * Pb[a] * rr[b];
+                    xb[b] -= mp * w * Pb[a] * C[a * D + b];
+                }
+                gbar[a] = sforce * Pb[a];
+                sb += Pb[a] * g[a];
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                R hb = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) hb += H[b][a] * gbar[a];
+                xb[b] += wbar * g[b] + hb;
+            }
+        }
+        // sforce = dt m p(rho) / rho
+        const R r1 = rho * P.inv_rho0;
+        R dp = P.bulk_K * P.inv_rho0;                      // dp/drho = (K / rho0) (rho / rho0)^(gamma - 1)
+        if (P.gamma_int > 0) {
+            for (int k = 1; k < P.gamma_int; ++k) dp *= r1;
+        } else {
+            dp *= pow(r1, P.gamma - R(1));
+        }
+        const R dsdrho = P.dt * mp * (dp * rho - pr) / (rho * rho);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            lam_out[a * n + p] += xb[a];
+            lam_out[(JV + a) * n + p] = vb[a];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) lam_out[(JC + q) * n + p] = Cb[q];
+        lam_out[JR * n + p] += sb * dsdrho;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+struct AdjDev {
+    void *GA, *GU, *GV, *GVB, *GAB;     // adjoint grid buffers (R4 per node)
+};
+
+template <class R, int D> struct AdjLaunch {
+    static int pblocks(const HostParams &h, const DevState &ds) { return grid_blocks(h.n, 256, ds.num_sms, 8); }
+    static int nblocks(const HostParams &h, const DevState &ds)
+    {
+        return grid_blocks(h.nodes_per_sim, 256, ds.num_sms, 8);
+    }
+    static void save(const HostParams &h, DevState &ds, void *dst)
+    {
+        auto P = make_params<R>(h, ds);
+        k_adj_save<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.id, (R *)dst);
+    }
+    static void restore(const HostParams &h, DevState &ds, const void *src)
+    {
+        auto P = make_params<R>(h, ds);
+        k_adj_restore<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (R *)ds.S, ds.id, (const R *)src);
+    }
+    static void track(const HostParams &h, DevState &ds, const int32_t *track_of_id, double *out)
+    {
+        auto P = make_params<R>(h, ds);
+        k_adj_track<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.id, track_of_id, out);
+    }
+    static void seed(const HostParams &h, DevState &ds, int n_track, const int64_t *ids, const double *x_obs,
+                     const double *z_obs, void *lam)
+    {
+        k_adj_seed<R, D><<<(n_track + 255) / 256, 256, 0, ds.stream>>>(h.n, n_track, ids, x_obs, z_obs, (R *)lam);
+    }
+    static void zero(DevState &ds, void *p, int64_t count)
+    {
+        k_adj_zero<R><<<grid_blocks(count, 256, ds.num_sms, 8), 256, 0, ds.stream>>>((R *)p, count);
+    }
+    // One reverse step: lam_in (adjoint of S^{t+1}) -> lam_out (adjoint of S^t) for the state st.
+    static void step(const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *lam_in,
+                     void *lam_out, MuBar mub)
+    {
+        auto P = make_params<R>(h, ds);
+        const int64_t nodes4 = h.nodes_per_sim * 4;
+        zero(ds, a.GA, nodes4);
+        zero(ds, a.GVB, nodes4);
+        k_adj_p2g<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (R4<R> *)a.GA);
+        k_adj_grid<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)a.GA, (R4<R> *)a.GU,
+                                                                  (R4<R> *)a.GV);
+        k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GV,
+                                                                     (const R *)lam_in, (R *)lam_out,
+                                                                     (R4<R> *)a.GVB);
+        k_adj_grid_bwd<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)a.GA, (const R4<R> *)a.GU,
+                                                                      (const R4<R> *)a.GVB, (R4<R> *)a.GAB, mub);
+        k_adj_p2g_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
+                                                                     (R *)lam_out);
+    }
+};
+
+template <class R> struct AdjDispatch {
+#define MPM_ADJ_DISPATCH(name, args, call)                   \
+    static void name args                                    \
+    {                                                        \
+        if (h.dim == 2) AdjLaunch<R, 2>::call;               \
+        else AdjLaunch<R, 3>::call;                          \
+    }
+    MPM_ADJ_DISPATCH(save, (const HostParams &h, DevState &ds, void *dst), save(h, ds, dst))
+    MPM_ADJ_DISPATCH(restore, (const HostParams &h, DevState &ds, const void *src), restore(h, ds, src))
+    MPM_ADJ_DISPATCH(track, (const HostParams &h, DevState &ds, const int32_t *t, double *o), track(h, ds, t, o))
+    MPM_ADJ_DISPATCH(seed, (const HostParams &h, DevState &ds, int nt, const int64_t *ids, const double *xo,
+                            const double *zo, void *lam), seed(h, ds, nt, ids, xo, zo, lam))
+    MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *li,
+                            void *lo, MuBar mub), step(h, ds, a, st, li, lo, mub))
+#undef MPM_ADJ_DISPATCH
+    static void zero(const HostParams &, DevState &ds, void *p, int64_t count) { AdjLaunch<R, 2>::zero(ds, p, count); }
+};
+
+}  // namespace mpm

@@ -10,13 +10,34 @@
 #include <cudaTypedefs.h>
 
 #include "../../include/mpm.h"
-#include "mpm_internal.cuh"
+#include "mpm_adjoint.cuh"
 
 using namespace mpm;
 
 struct PendingTiming {
     int kernel;
     cudaEvent_t start, stop;
+};
+
+// Adjoint (reverse sweep) buffers and observations, allocated on first use.
+struct AdjHost {
+    int n_track = 0, n_obs = 0;
+    std::vector<int64_t> ids;
+    std::vector<int> steps;
+    std::vector<double> z;                     // n_obs x n_track x dim
+    int64_t *d_ids = nullptr;
+    int32_t *d_track_of_id = nullptr;
+    double *d_z = nullptr, *d_xobs = nullptr;
+    void *ckpt = nullptr;
+    int64_t ckpt_cap = 0;
+    void *seg = nullptr;
+    int64_t seg_cap = 0;
+    void *lam[2] = {nullptr, nullptr};
+    mpm::AdjDev grid{};
+    double *d_mubar[mpm::kMaxWalls] = {nullptr};
+    void *final_S = nullptr;
+    int32_t *final_id = nullptr, *final_sim = nullptr;
+    bool allocated = false;
 };
 
 struct mpm_ctx {
@@ -37,6 +58,8 @@ struct mpm_ctx {
     double kt_ms[MPM_KERNEL_COUNT] = {0};
     int64_t kt_n[MPM_KERNEL_COUNT] = {0};
     int32_t *h_status = nullptr;       // pinned
+    AdjHost adj;
+    const AdjOps *aops = nullptr;
 };
 
 namespace {
@@ -85,8 +108,22 @@ template <class T> void dfree(T *&p)
     p = nullptr;
 }
 
+void free_adjoint(mpm_ctx *c)
+{
+    AdjHost &a = c->adj;
+    dfree(a.d_ids); dfree(a.d_track_of_id); dfree(a.d_z); dfree(a.d_xobs);
+    dfree(a.ckpt); dfree(a.seg); dfree(a.lam[0]); dfree(a.lam[1]);
+    dfree(a.grid.GA); dfree(a.grid.GU); dfree(a.grid.GV); dfree(a.grid.GVB); dfree(a.grid.GAB);
+    for (int w = 0; w < kMaxWalls; ++w) dfree(a.d_mubar[w]);
+    dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
+    a.ckpt_cap = a.seg_cap = 0;
+    a.allocated = false;
+    a.n_track = a.n_obs = 0;
+}
+
 void free_particles(mpm_ctx *c)
 {
+    free_adjoint(c);
     DevState &d = c->ds;
     dfree(d.S); dfree(d.S2);
     dfree(d.id); dfree(d.id2); dfree(d.sim); dfree(d.sim2);
@@ -317,6 +354,7 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     h.off_eps = h.off_sig + 6;
     h.ncomp = m.kind == MPM_DRUCKER_PRAGER ? h.off_eps + 1 : h.off_rho + 1;
     c->ops = g.precision == MPM_FP64 ? &ops_f64 : &ops_f32;
+    c->aops = g.precision == MPM_FP64 ? &adj_ops_f64 : &adj_ops_f32;
 
     DevState &ds = c->ds;
     int dev = 0;
@@ -506,10 +544,11 @@ int mpm_set_friction_field(mpm_ctx *c, int wall, const int n_seg[2], const doubl
     return MPM_OK;
 }
 
-int mpm_step(mpm_ctx *c, int n_steps)
+}  // extern "C"
+
+namespace {
+int step_many(mpm_ctx *c, int n_steps)
 {
-    if (!c || n_steps < 0) return fail(c, MPM_EINVAL, "mpm_step: bad argument");
-    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step: no particles loaded");
     for (int s = 0; s < n_steps; ++s) {
         if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
             int rc = do_sort(c);
@@ -534,6 +573,16 @@ int mpm_step(mpm_ctx *c, int n_steps)
         c->steps++;
     }
     return MPM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mpm_step(mpm_ctx *c, int n_steps)
+{
+    if (!c || n_steps < 0) return fail(c, MPM_EINVAL, "mpm_step: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step: no particles loaded");
+    return step_many(c, n_steps);
 }
 
 int mpm_synchronize(mpm_ctx *c)
@@ -611,6 +660,178 @@ int mpm_get_stats(mpm_ctx *c, int64_t *out, int n)
     CK(cudaStreamSynchronize(c->ds.stream), "stats");
     const int64_t vals[6] = {cnt[1], cnt[1], (int64_t)esc, c->sorts, c->steps, c->launches};
     for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
+    return MPM_OK;
+}
+
+int mpm_set_observations(mpm_ctx *c, int n_track, const int64_t *ids, int n_obs, const int *steps,
+                         const double *z_obs)
+{
+    if (!c || n_track <= 0 || n_obs <= 0 || !ids || !steps || !z_obs)
+        return fail(c, MPM_EINVAL, "mpm_set_observations: bad argument");
+    const int64_t n = c->hp.n;
+    if (n == 0) return fail(c, MPM_ESTATE, "mpm_set_observations: no particles loaded");
+    std::vector<int32_t> track_of_id(n, -1);
+    for (int l = 0; l < n_track; ++l) {
+        if (ids[l] < 0 || ids[l] >= n) return fail(c, MPM_EINVAL, "mpm_set_observations: id out of range");
+        if (track_of_id[ids[l]] >= 0) return fail(c, MPM_EINVAL, "mpm_set_observations: repeated id");
+        track_of_id[ids[l]] = l;
+    }
+    for (int o = 0; o < n_obs; ++o)
+        if (steps[o] < 1 || (o > 0 && steps[o] <= steps[o - 1]))
+            return fail(c, MPM_EINVAL, "mpm_set_observations: steps must be >= 1 and increasing");
+    AdjHost &a = c->adj;
+    dfree(a.d_ids); dfree(a.d_track_of_id); dfree(a.d_z); dfree(a.d_xobs);
+    const int d = c->grid.dim;
+    int rc = MPM_OK;
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_ids, n_track, "tracked ids");
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_track_of_id, n, "track map");
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_z, (size_t)n_obs * n_track * d, "observations");
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_xobs, (size_t)n_obs * n_track * d, "observed positions");
+    if (rc != MPM_OK) return rc;
+    CK(cudaMemcpy(a.d_ids, ids, sizeof(int64_t) * n_track, cudaMemcpyHostToDevice), "copy ids");
+    CK(cudaMemcpy(a.d_track_of_id, track_of_id.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice), "copy map");
+    CK(cudaMemcpy(a.d_z, z_obs, sizeof(double) * n_obs * n_track * d, cudaMemcpyHostToDevice), "copy z");
+    a.n_track = n_track;
+    a.n_obs = n_obs;
+    a.ids.assign(ids, ids + n_track);
+    a.steps.assign(steps, steps + n_obs);
+    a.z.assign(z_obs, z_obs + (size_t)n_obs * n_track * d);
+    return MPM_OK;
+}
+
+int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, double *loss_out, double *dL_dmu_out)
+{
+    if (!c || n_steps < 1 || checkpoint_every < 1 || !loss_out || !dL_dmu_out)
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no particles loaded");
+    if (c->mat.kind != MPM_FLUID) return fail(c, MPM_EINVAL, "mpm_step_adjoint: the adjoint covers the fluid");
+    if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_step_adjoint: batch must be 1");
+    if (wall < 0 || wall >= 2 * c->grid.dim || c->ds.mu_dev[wall] == nullptr)
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint: the wall has no friction field");
+    AdjHost &a = c->adj;
+    if (a.n_obs == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no observations set");
+    if (a.steps.back() > n_steps) return fail(c, MPM_EINVAL, "mpm_step_adjoint: observation beyond the horizon");
+    const HostParams &h = c->hp;
+    DevState &ds = c->ds;
+    const int d = h.dim;
+    const int K = checkpoint_every;
+    const int NA = 2 * d + d * d + 1;
+    const size_t rsz = h.precision == MPM_FP64 ? 8 : 4;
+    const int64_t n = h.n;
+    const size_t st_bytes = (size_t)NA * n * rsz;
+    const int64_t n_ckpt = (n_steps + K - 1) / K;
+    // buffers
+    if (a.ckpt_cap < n_ckpt) {
+        dfree(a.ckpt);
+        int rc = dalloc(c, (unsigned char **)&a.ckpt, st_bytes * n_ckpt, "checkpoints");
+        if (rc != MPM_OK) return rc;
+        a.ckpt_cap = n_ckpt;
+    }
+    if (a.seg_cap < K) {
+        dfree(a.seg);
+        int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * K, "segment states");
+        if (rc != MPM_OK) return rc;
+        a.seg_cap = K;
+    }
+    if (!a.allocated) {
+        int rc = MPM_OK;
+        const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[0], st_bytes, "adjoint state");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[1], st_bytes, "adjoint state");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GA, gbytes, "adjoint grid");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GU, gbytes, "adjoint grid");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GV, gbytes, "adjoint grid");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GVB, gbytes, "adjoint grid");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GAB, gbytes, "adjoint grid");
+        if (rc == MPM_OK)
+            rc = dalloc(c, (unsigned char **)&a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, "final state");
+        if (rc == MPM_OK) rc = dalloc(c, &a.final_id, n, "final ids");
+        if (rc == MPM_OK) rc = dalloc(c, &a.final_sim, n, "final sims");
+        if (rc != MPM_OK) return rc;
+        a.allocated = true;
+    }
+    MuBar mub{};
+    for (int w = 0; w < kMaxWalls; ++w) {
+        if (ds.mu_dev[w] == nullptr) continue;
+        const int64_t cnt = (int64_t)ds.n_seg[w][0] * ds.n_seg[w][1];
+        if (a.d_mubar[w] == nullptr) {
+            int rc = dalloc(c, &a.d_mubar[w], cnt, "dL/dmu");
+            if (rc != MPM_OK) return rc;
+        }
+        CK(cudaMemsetAsync(a.d_mubar[w], 0, sizeof(double) * cnt, ds.stream), "zero dL/dmu");
+        mub.w[w] = a.d_mubar[w];
+    }
+    std::vector<int> obs_of_step(n_steps + 1, -1);
+    for (int o = 0; o < a.n_obs; ++o) obs_of_step[a.steps[o]] = o;
+    auto ckpt_ptr = [&](int64_t k) { return (void *)((char *)a.ckpt + k * st_bytes); };
+    auto seg_ptr = [&](int64_t j) { return (void *)((char *)a.seg + j * st_bytes); };
+    const size_t obs_stride = (size_t)a.n_track * d;
+    // forward pass with checkpoints and observations
+    c->aops->save(h, ds, ckpt_ptr(0));
+    for (int t = 1; t <= n_steps; ++t) {
+        int rc = step_many(c, 1);
+        if (rc != MPM_OK) return rc;
+        if (obs_of_step[t] >= 0) c->aops->track(h, ds, a.d_track_of_id, a.d_xobs + obs_of_step[t] * obs_stride);
+        if (t % K == 0 && t < n_steps) c->aops->save(h, ds, ckpt_ptr(t / K));
+    }
+    CK(cudaMemcpyAsync(a.final_S, ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, cudaMemcpyDeviceToDevice, ds.stream),
+       "save final state");
+    CK(cudaMemcpyAsync(a.final_id, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream), "save ids");
+    CK(cudaMemcpyAsync(a.final_sim, ds.sim, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream), "save sims");
+    std::vector<double> xobs((size_t)a.n_obs * obs_stride);
+    CK(cudaMemcpyAsync(xobs.data(), a.d_xobs, sizeof(double) * xobs.size(), cudaMemcpyDeviceToHost, ds.stream),
+       "copy observed positions");
+    {
+        int rc = read_status(c);
+        if (rc != MPM_OK) return rc;
+    }
+    double loss = 0.0;
+    for (size_t i = 0; i < xobs.size(); ++i) {
+        const double e = xobs[i] - a.z[i];
+        loss += e * e;
+    }
+    // reverse sweep, one segment at a time (recomputed from its checkpoint)
+    int cur = 0;
+    c->aops->zero(h, ds, a.lam[cur], (int64_t)NA * n);
+    if (obs_of_step[n_steps] >= 0) {
+        const int o = obs_of_step[n_steps];
+        c->aops->seed(h, ds, a.n_track, a.d_ids, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride, a.lam[cur]);
+    }
+    for (int64_t k = n_ckpt - 1; k >= 0; --k) {
+        const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
+        c->aops->restore(h, ds, ckpt_ptr(k));
+        c->need_sort = true;
+        CK(cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(k), st_bytes, cudaMemcpyDeviceToDevice, ds.stream), "segment start");
+        for (int j = 1; j < t1 - t0; ++j) {
+            int rc = step_many(c, 1);
+            if (rc != MPM_OK) return rc;
+            c->aops->save(h, ds, seg_ptr(j));
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            c->aops->step(h, ds, a.grid, seg_ptr(t - t0), a.lam[cur], a.lam[cur ^ 1], mub);
+            cur ^= 1;
+            if (t >= 1 && obs_of_step[t] >= 0) {
+                const int o = obs_of_step[t];
+                c->aops->seed(h, ds, a.n_track, a.d_ids, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride,
+                              a.lam[cur]);
+            }
+        }
+        int rc = check_launch(c, "mpm_step_adjoint");
+        if (rc != MPM_OK) return rc;
+    }
+    // leave the context at the end-of-horizon state
+    CK(cudaMemcpyAsync(ds.S, a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, cudaMemcpyDeviceToDevice, ds.stream),
+       "restore final state");
+    CK(cudaMemcpyAsync(ds.id, a.final_id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream), "restore ids");
+    CK(cudaMemcpyAsync(ds.sim, a.final_sim, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream),
+       "restore sims");
+    c->need_sort = true;
+    const int64_t cnt = (int64_t)ds.n_seg[wall][0] * ds.n_seg[wall][1];
+    CK(cudaMemcpyAsync(dL_dmu_out, a.d_mubar[wall], sizeof(double) * cnt, cudaMemcpyDeviceToHost, ds.stream),
+       "copy dL/dmu");
+    int rc = read_status(c);
+    if (rc != MPM_OK) return rc;
+    *loss_out = loss;
     return MPM_OK;
 }
 

@@ -127,6 +127,22 @@ struct Ops {
 extern const Ops ops_f32;
 extern const Ops ops_f64;
 
+struct AdjDev;
+struct MuBar;
+// Adjoint launchers per precision (fluid only).
+struct AdjOps {
+    void (*save)(const HostParams &, DevState &, void *dst);
+    void (*restore)(const HostParams &, DevState &, const void *src);
+    void (*track)(const HostParams &, DevState &, const int32_t *track_of_id, double *out);
+    void (*seed)(const HostParams &, DevState &, int n_track, const int64_t *ids, const double *x_obs,
+                 const double *z_obs, void *lam);
+    void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *lam_in, void *lam_out,
+                 MuBar mub);
+    void (*zero)(const HostParams &, DevState &, void *p, int64_t count);
+};
+extern const AdjOps adj_ops_f32;
+extern const AdjOps adj_ops_f64;
+
 // Sort helpers (mpm_sort.cu), precision independent.
 void radix_sort_pairs(const HostParams &hp, DevState &ds);
 void build_tiles(const HostParams &hp, DevState &ds);

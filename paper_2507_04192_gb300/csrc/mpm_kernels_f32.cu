@@ -1,5 +1,5 @@
 // Instantiation of the MPM kernels for float arithmetic.
-#include "mpm_kernels.cuh"
+#include "mpm_adjoint.cuh"
 
 namespace mpm {
 
@@ -7,6 +7,11 @@ const Ops ops_f32 = {
     Dispatch<float>::init_state, Dispatch<float>::keys,      Dispatch<float>::permute,
     Dispatch<float>::p2g,        Dispatch<float>::grid,      Dispatch<float>::g2p,
     Dispatch<float>::get_field,  Dispatch<float>::set_field,
+};
+
+const AdjOps adj_ops_f32 = {
+    AdjDispatch<float>::save, AdjDispatch<float>::restore, AdjDispatch<float>::track,
+    AdjDispatch<float>::seed, AdjDispatch<float>::step,    AdjDispatch<float>::zero,
 };
 
 }  // namespace mpm

@@ -1,5 +1,5 @@
 // Instantiation of the MPM kernels for double arithmetic.
-#include "mpm_kernels.cuh"
+#include "mpm_adjoint.cuh"
 
 namespace mpm {
 
@@ -7,6 +7,11 @@ const Ops ops_f64 = {
     Dispatch<double>::init_state, Dispatch<double>::keys,      Dispatch<double>::permute,
     Dispatch<double>::p2g,        Dispatch<double>::grid,      Dispatch<double>::g2p,
     Dispatch<double>::get_field,  Dispatch<double>::set_field,
+};
+
+const AdjOps adj_ops_f64 = {
+    AdjDispatch<double>::save, AdjDispatch<double>::restore, AdjDispatch<double>::track,
+    AdjDispatch<double>::seed, AdjDispatch<double>::step,    AdjDispatch<double>::zero,
 };
 
 }  // namespace mpm

@@ -89,6 +89,8 @@ def load_library(build_if_missing: bool = True):
             "mpm_get_stats": (I, [P, C.POINTER(L), I]),
             "mpm_step_noalloc": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, L, D, StatePtrs, StatePtrs,
                                      C.c_char_p, I]),
+            "mpm_set_observations": (I, [P, I, P, I, P, P]),
+            "mpm_step_adjoint": (I, [P, I, I, I, C.POINTER(D), P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -187,6 +189,22 @@ def mpm_get_stats(ctx) -> dict:
     _check(ctx, load_library().mpm_get_stats(ctx, out, 6))
     keys = ("active_tiles", "chunks", "escaped", "sorts", "steps", "launches")
     return dict(zip(keys, list(out)))
+
+
+def mpm_set_observations(ctx, ids: np.ndarray, steps: Sequence[int], z_obs: np.ndarray):
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    st = np.ascontiguousarray(steps, dtype=np.int32)
+    z = np.ascontiguousarray(z_obs, dtype=np.float64)
+    assert z.size == len(st) * len(ids) * (z.shape[-1] if z.ndim else 1)
+    _check(ctx, load_library().mpm_set_observations(ctx, len(ids), _dptr(ids), len(st), _dptr(st), _dptr(z)))
+
+
+def mpm_step_adjoint(ctx, n_steps: int, checkpoint_every: int, wall: int, n_mu: int):
+    loss = C.c_double()
+    g = np.zeros(n_mu, dtype=np.float64)
+    _check(ctx, load_library().mpm_step_adjoint(ctx, int(n_steps), int(checkpoint_every), int(wall),
+                                                C.byref(loss), _dptr(g)))
+    return loss.value, g
 
 
 def mpm_step_noalloc(grid: GridDesc, material: Material, n: int, particle_volume: float, state_in: StatePtrs,
