@@ -197,6 +197,26 @@ int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, 
                      double *dL_dmu_out);
 
 /*
+ * Device state slots (0..15): copy of the whole particle state (all fields, in
+ * the current internal order).  mpm_restore_state puts it back; used to rerun
+ * a trajectory from the same start (inversion loops).  Slots are freed with
+ * the particles.
+ */
+int mpm_save_state(mpm_ctx *ctx, int slot);
+int mpm_restore_state(mpm_ctx *ctx, int slot);
+
+/*
+ * Host blob of the particle state for checkpoint/resume across processes.
+ * mpm_state_blob_size gives the bytes needed; mpm_export_state writes the blob
+ * (header, all fields, ids, simulation ids, FNV-1a checksum of the payload);
+ * mpm_import_state verifies it (MPM_ECORRUPT on a bad magic, truncation or
+ * checksum mismatch; MPM_EINVAL if it does not match the loaded particles).
+ */
+int64_t mpm_state_blob_size(const mpm_ctx *ctx);
+int mpm_export_state(mpm_ctx *ctx, void *blob, int64_t size);
+int mpm_import_state(mpm_ctx *ctx, const void *blob, int64_t size);
+
+/*
  * Kernel timing.  When enabled, every kernel launch is bracketed by CUDA
  * events on the context's stream; mpm_get_timing returns, for one kernel
  * class, the summed device time in milliseconds and the launch count since

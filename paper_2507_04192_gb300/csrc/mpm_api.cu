@@ -40,6 +40,14 @@ struct AdjHost {
     bool allocated = false;
 };
 
+// One saved copy of the particle state on the device.
+struct StateSlot {
+    void *S = nullptr;
+    int32_t *id = nullptr, *sim = nullptr;
+    int64_t n = 0;
+};
+constexpr int kMaxSlots = 16;
+
 struct mpm_ctx {
     mpm_grid_desc grid{};
     mpm_material mat{};
@@ -60,6 +68,7 @@ struct mpm_ctx {
     int32_t *h_status = nullptr;       // pinned
     AdjHost adj;
     const AdjOps *aops = nullptr;
+    StateSlot slots[kMaxSlots];
 };
 
 namespace {
@@ -121,9 +130,20 @@ void free_adjoint(mpm_ctx *c)
     a.n_track = a.n_obs = 0;
 }
 
+void free_slots(mpm_ctx *c)
+{
+    for (auto &sl : c->slots) {
+        dfree(sl.S);
+        dfree(sl.id);
+        dfree(sl.sim);
+        sl.n = 0;
+    }
+}
+
 void free_particles(mpm_ctx *c)
 {
     free_adjoint(c);
+    free_slots(c);
     DevState &d = c->ds;
     dfree(d.S); dfree(d.S2);
     dfree(d.id); dfree(d.id2); dfree(d.sim); dfree(d.sim2);
@@ -832,6 +852,124 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     int rc = read_status(c);
     if (rc != MPM_OK) return rc;
     *loss_out = loss;
+    return MPM_OK;
+}
+
+int mpm_save_state(mpm_ctx *c, int slot)
+{
+    if (!c || slot < 0 || slot >= kMaxSlots) return fail(c, MPM_EINVAL, "mpm_save_state: bad slot");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_save_state: no particles loaded");
+    const HostParams &h = c->hp;
+    StateSlot &sl = c->slots[slot];
+    const size_t bytes = ((size_t)h.ncomp * h.npad + 64) * (h.precision == MPM_FP64 ? 8 : 4);
+    if (sl.n != h.n) {
+        dfree(sl.S); dfree(sl.id); dfree(sl.sim);
+        int rc = dalloc(c, (unsigned char **)&sl.S, bytes, "state slot");
+        if (rc == MPM_OK) rc = dalloc(c, &sl.id, h.n, "state slot ids");
+        if (rc == MPM_OK) rc = dalloc(c, &sl.sim, h.n, "state slot sims");
+        if (rc != MPM_OK) {
+            sl.n = 0;
+            return rc;
+        }
+        sl.n = h.n;
+    }
+    DevState &ds = c->ds;
+    CK(cudaMemcpyAsync(sl.S, ds.S, bytes, cudaMemcpyDeviceToDevice, ds.stream), "save state");
+    CK(cudaMemcpyAsync(sl.id, ds.id, sizeof(int32_t) * h.n, cudaMemcpyDeviceToDevice, ds.stream), "save ids");
+    CK(cudaMemcpyAsync(sl.sim, ds.sim, sizeof(int32_t) * h.n, cudaMemcpyDeviceToDevice, ds.stream), "save sims");
+    return MPM_OK;
+}
+
+int mpm_restore_state(mpm_ctx *c, int slot)
+{
+    if (!c || slot < 0 || slot >= kMaxSlots) return fail(c, MPM_EINVAL, "mpm_restore_state: bad slot");
+    const HostParams &h = c->hp;
+    StateSlot &sl = c->slots[slot];
+    if (h.n == 0 || sl.n != h.n) return fail(c, MPM_ESTATE, "mpm_restore_state: slot is empty");
+    const size_t bytes = ((size_t)h.ncomp * h.npad + 64) * (h.precision == MPM_FP64 ? 8 : 4);
+    DevState &ds = c->ds;
+    CK(cudaMemcpyAsync(ds.S, sl.S, bytes, cudaMemcpyDeviceToDevice, ds.stream), "restore state");
+    CK(cudaMemcpyAsync(ds.id, sl.id, sizeof(int32_t) * h.n, cudaMemcpyDeviceToDevice, ds.stream), "restore ids");
+    CK(cudaMemcpyAsync(ds.sim, sl.sim, sizeof(int32_t) * h.n, cudaMemcpyDeviceToDevice, ds.stream), "restore sims");
+    c->need_sort = true;
+    return MPM_OK;
+}
+
+namespace {
+// FNV-1a 64-bit hash (Fowler-Noll-Vo) of a byte range.
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+struct BlobHeader {
+    uint64_t magic, n, ncomp, npad, precision, dim, payload, checksum;
+};
+constexpr uint64_t kBlobMagic = 0x4d504d5354415445ull;   // "MPMSTATE"
+}  // namespace
+
+int64_t mpm_state_blob_size(const mpm_ctx *c)
+{
+    if (!c || c->hp.n == 0) return MPM_ESTATE;
+    const HostParams &h = c->hp;
+    const int64_t rs = h.precision == MPM_FP64 ? 8 : 4;
+    return (int64_t)sizeof(BlobHeader) + (int64_t)h.ncomp * h.n * rs + 2 * h.n * (int64_t)sizeof(int32_t);
+}
+
+int mpm_export_state(mpm_ctx *c, void *blob, int64_t size)
+{
+    if (!c || !blob) return fail(c, MPM_EINVAL, "mpm_export_state: bad argument");
+    const int64_t need = mpm_state_blob_size(c);
+    if (need < 0) return fail(c, MPM_ESTATE, "mpm_export_state: no particles loaded");
+    if (size < need) return fail(c, MPM_EINVAL, "mpm_export_state: buffer too small");
+    const HostParams &h = c->hp;
+    DevState &ds = c->ds;
+    const int64_t rs = h.precision == MPM_FP64 ? 8 : 4;
+    BlobHeader hd{kBlobMagic, (uint64_t)h.n, (uint64_t)h.ncomp, (uint64_t)h.npad, (uint64_t)h.precision,
+                  (uint64_t)h.dim, (uint64_t)(need - (int64_t)sizeof(BlobHeader)), 0};
+    unsigned char *out = (unsigned char *)blob + sizeof(BlobHeader);
+    for (int comp = 0; comp < h.ncomp; ++comp)
+        CK(cudaMemcpyAsync(out + (size_t)comp * h.n * rs, (const char *)ds.S + (size_t)comp * h.npad * rs,
+                           (size_t)h.n * rs, cudaMemcpyDeviceToHost, ds.stream),
+           "export state");
+    unsigned char *ids = out + (size_t)h.ncomp * h.n * rs;
+    CK(cudaMemcpyAsync(ids, ds.id, sizeof(int32_t) * h.n, cudaMemcpyDeviceToHost, ds.stream), "export ids");
+    CK(cudaMemcpyAsync(ids + sizeof(int32_t) * h.n, ds.sim, sizeof(int32_t) * h.n, cudaMemcpyDeviceToHost, ds.stream),
+       "export sims");
+    CK(cudaStreamSynchronize(ds.stream), "export state");
+    hd.checksum = fnv1a(out, hd.payload);
+    std::memcpy(blob, &hd, sizeof hd);
+    return MPM_OK;
+}
+
+int mpm_import_state(mpm_ctx *c, const void *blob, int64_t size)
+{
+    if (!c || !blob || size < (int64_t)sizeof(BlobHeader)) return fail(c, MPM_EINVAL, "mpm_import_state: bad argument");
+    BlobHeader hd;
+    std::memcpy(&hd, blob, sizeof hd);
+    const HostParams &h = c->hp;
+    if (hd.magic != kBlobMagic) return fail(c, MPM_ECORRUPT, "mpm_import_state: not a state blob");
+    if (h.n == 0 || hd.n != (uint64_t)h.n || hd.ncomp != (uint64_t)h.ncomp || hd.precision != (uint64_t)h.precision ||
+        hd.dim != (uint64_t)h.dim)
+        return fail(c, MPM_EINVAL, "mpm_import_state: blob does not match the loaded particles");
+    if ((int64_t)(sizeof(BlobHeader) + hd.payload) > size) return fail(c, MPM_ECORRUPT, "mpm_import_state: truncated");
+    const unsigned char *in = (const unsigned char *)blob + sizeof(BlobHeader);
+    if (fnv1a(in, hd.payload) != hd.checksum) return fail(c, MPM_ECORRUPT, "mpm_import_state: checksum mismatch");
+    DevState &ds = c->ds;
+    const int64_t rs = h.precision == MPM_FP64 ? 8 : 4;
+    for (int comp = 0; comp < h.ncomp; ++comp)
+        CK(cudaMemcpyAsync((char *)ds.S + (size_t)comp * h.npad * rs, in + (size_t)comp * h.n * rs, (size_t)h.n * rs,
+                           cudaMemcpyHostToDevice, ds.stream),
+           "import state");
+    const unsigned char *ids = in + (size_t)h.ncomp * h.n * rs;
+    CK(cudaMemcpyAsync(ds.id, ids, sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import ids");
+    CK(cudaMemcpyAsync(ds.sim, ids + sizeof(int32_t) * h.n, sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream),
+       "import sims");
+    CK(cudaStreamSynchronize(ds.stream), "import state");
+    c->need_sort = true;
     return MPM_OK;
 }
 

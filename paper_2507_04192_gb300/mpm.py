@@ -90,6 +90,11 @@ def load_library(build_if_missing: bool = True):
             "mpm_step_noalloc": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, L, D, StatePtrs, StatePtrs,
                                      C.c_char_p, I]),
             "mpm_set_observations": (I, [P, I, P, I, P, P]),
+            "mpm_save_state": (I, [P, I]),
+            "mpm_restore_state": (I, [P, I]),
+            "mpm_state_blob_size": (L, [P]),
+            "mpm_export_state": (I, [P, P, L]),
+            "mpm_import_state": (I, [P, P, L]),
             "mpm_step_adjoint": (I, [P, I, I, I, C.POINTER(D), P]),
         }
         for name, (res, args) in sigs.items():
@@ -189,6 +194,28 @@ def mpm_get_stats(ctx) -> dict:
     _check(ctx, load_library().mpm_get_stats(ctx, out, 6))
     keys = ("active_tiles", "chunks", "escaped", "sorts", "steps", "launches")
     return dict(zip(keys, list(out)))
+
+
+def mpm_save_state(ctx, slot: int):
+    _check(ctx, load_library().mpm_save_state(ctx, int(slot)))
+
+
+def mpm_restore_state(ctx, slot: int):
+    _check(ctx, load_library().mpm_restore_state(ctx, int(slot)))
+
+
+def mpm_export_state(ctx) -> bytes:
+    size = int(load_library().mpm_state_blob_size(ctx))
+    if size < 0:
+        _check(ctx, size)
+    buf = (C.c_ubyte * size)()
+    _check(ctx, load_library().mpm_export_state(ctx, buf, size))
+    return bytes(buf)
+
+
+def mpm_import_state(ctx, blob: bytes):
+    buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+    _check(ctx, load_library().mpm_import_state(ctx, buf, len(blob)))
 
 
 def mpm_set_observations(ctx, ids: np.ndarray, steps: Sequence[int], z_obs: np.ndarray):
