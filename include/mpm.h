@@ -271,6 +271,48 @@ typedef struct {
 int mpm_step_noalloc(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream, int64_t n,
                      double particle_volume, mpm_state_ptrs in, mpm_state_ptrs out, char *err, int err_len);
 
+/*
+ * BF16 GEMM on the tcgen05 tensor cores: C = A B^T with A (M x K) and B (N x K)
+ * bf16 row-major device matrices (leading dimensions lda, ldb >= K, multiples
+ * of 8; 16-byte aligned pointers) and C (M x N) fp32 device, ldc >= N.  Accumulates
+ * in fp32 (TMEM).  Queued on cuda_stream; a tensor-core wait that runs out sets
+ * bit 2 of *status_dev (a device int32 the caller owns).  MPM_EINVAL on bad
+ * shapes or alignment.  The building block of the MLP below.
+ */
+int mpm_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                  int32_t *status_dev, void *cuda_stream);
+
+/*
+ * A fully connected network on the tensor cores: the learned warm start of the
+ * basal-friction inversion (a map from tracked-particle displacements to the
+ * per-segment friction field; the paper's coordinate network of Eq. nn_apprx,
+ * Sec. 3.2, is the same kind of component).  widths[0..n_layers] (multiples of
+ * 8); hidden layers use GELU (exact erf form), the output y = out_lo +
+ * (out_hi - out_lo) sigmoid(z).  Weights and Adam state in fp32 with bf16
+ * copies as GEMM operands; activations enter GEMMs as bf16; fp32 accumulation.
+ * Parameter vectors (host, fp32) list, per layer, W (out x in, row-major) then b.
+ */
+typedef struct mpm_mlp mpm_mlp;
+int mpm_mlp_create(int n_layers, const int *widths, int max_batch, double out_lo, double out_hi, void *cuda_stream,
+                   mpm_mlp **out);
+void mpm_mlp_destroy(mpm_mlp *mlp);
+int64_t mpm_mlp_num_params(const mpm_mlp *mlp);
+/* Set the parameters (and reset the Adam state). */
+int mpm_mlp_set_params(mpm_mlp *mlp, const float *params);
+/* Copy the parameters (which = 0) or the gradients of the last train step (which = 1). */
+int mpm_mlp_get_params(mpm_mlp *mlp, float *params, int which);
+/* y (batch x widths[L]) = network(x (batch x widths[0])); host or device pointers. */
+int mpm_mlp_infer(mpm_mlp *mlp, int batch, const float *x, float *y, int device_ptrs);
+/*
+ * One training step on the mean squared error to target (batch x widths[L]):
+ * forward, backward, and (update != 0) one Adam step (beta 0.9 / 0.999, eps
+ * 1e-8, bias-corrected) with rate lr.  batch must be a multiple of 8.  Writes
+ * the loss before the update.  Synchronises.
+ */
+int mpm_mlp_train_step(mpm_mlp *mlp, int batch, const float *x, const float *target, double lr, int update,
+                       double *loss_out, int device_ptrs);
+int mpm_mlp_last_error(const mpm_mlp *mlp, char *buf, int len);
+
 #ifdef __cplusplus
 }
 #endif

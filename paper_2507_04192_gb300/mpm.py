@@ -90,6 +90,15 @@ def load_library(build_if_missing: bool = True):
             "mpm_step_noalloc": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, L, D, StatePtrs, StatePtrs,
                                      C.c_char_p, I]),
             "mpm_set_observations": (I, [P, I, P, I, P, P]),
+            "mpm_gemm_bf16": (I, [I, I, I, P, I, P, I, P, I, P, P]),
+            "mpm_mlp_create": (I, [I, P, I, D, D, P, C.POINTER(P)]),
+            "mpm_mlp_destroy": (None, [P]),
+            "mpm_mlp_num_params": (L, [P]),
+            "mpm_mlp_set_params": (I, [P, P]),
+            "mpm_mlp_get_params": (I, [P, P, I]),
+            "mpm_mlp_infer": (I, [P, I, P, P, I]),
+            "mpm_mlp_train_step": (I, [P, I, P, P, D, I, C.POINTER(D), I]),
+            "mpm_mlp_last_error": (I, [P, C.c_char_p, I]),
             "mpm_save_state": (I, [P, I]),
             "mpm_restore_state": (I, [P, I]),
             "mpm_state_blob_size": (L, [P]),
@@ -242,6 +251,73 @@ def mpm_step_noalloc(grid: GridDesc, material: Material, n: int, particle_volume
                                          float(particle_volume), state_in, state_out, buf, 256)
     if rc != MPM_OK:
         raise MPMError(rc, buf.value.decode(errors="replace"))
+
+
+def mpm_gemm_bf16(M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, status_ptr, stream=0):
+    rc = load_library().mpm_gemm_bf16(M, N, K, C.c_void_p(A_ptr), lda, C.c_void_p(B_ptr), ldb, C.c_void_p(C_ptr),
+                                      ldc, C.c_void_p(status_ptr), C.c_void_p(stream))
+    if rc != MPM_OK:
+        raise MPMError(rc, "mpm_gemm_bf16")
+
+
+class MLP:
+    """Binding of mpm_mlp_* (argument marshalling only)."""
+
+    def __init__(self, widths, max_batch, out_lo=0.1, out_hi=0.6, stream=0):
+        lib = load_library()
+        self.widths = list(widths)
+        w = (C.c_int * len(widths))(*widths)
+        h = C.c_void_p()
+        rc = lib.mpm_mlp_create(len(widths) - 1, w, int(max_batch), float(out_lo), float(out_hi),
+                                C.c_void_p(stream), C.byref(h))
+        if rc != MPM_OK:
+            raise MPMError(rc, "mpm_mlp_create")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != MPM_OK:
+            buf = C.create_string_buffer(256)
+            load_library().mpm_mlp_last_error(self.h, buf, 256)
+            raise MPMError(rc, buf.value.decode(errors="replace"))
+
+    @property
+    def num_params(self):
+        return int(load_library().mpm_mlp_num_params(self.h))
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        self._check(load_library().mpm_mlp_set_params(self.h, _dptr(p)))
+
+    def get_params(self, which=0):
+        p = np.empty(self.num_params, dtype=np.float32)
+        self._check(load_library().mpm_mlp_get_params(self.h, _dptr(p), int(which)))
+        return p
+
+    def infer(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.empty((x.shape[0], self.widths[-1]), dtype=np.float32)
+        self._check(load_library().mpm_mlp_infer(self.h, x.shape[0], _dptr(x), _dptr(y), 0))
+        return y
+
+    def train_step(self, x, target, lr, update=True):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        loss = C.c_double()
+        self._check(load_library().mpm_mlp_train_step(self.h, x.shape[0], _dptr(x), _dptr(t), float(lr),
+                                                      int(bool(update)), C.byref(loss), 0))
+        return loss.value
+
+    def close(self):
+        if self.h:
+            load_library().mpm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience wrapper

@@ -1,0 +1,82 @@
+"""Pins of the FP64 oracle of the warm-start network (oracle/mlp.py).
+
+The rounding helper against torch's bfloat16 cast (round to nearest even) and
+hand-worked ties; GELU against torch's exact-erf GELU and its odd-part identity;
+the loss gradient against central finite differences with rounding off; a
+one-layer network against its closed form.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    rng = np.random.default_rng(0)
+    a = np.concatenate([rng.standard_normal(4096) * 10.0 ** rng.integers(-6, 6, 4096), [0.0, -0.0, 1e-40]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16(a), ref)
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 (even mantissa: 1);
+    # 1 + 3 2^-8 halfway between 1 + 2^-7 and 1 + 2^-6 (even: 1 + 2^-6)
+    assert mlp.bf16(np.array([1 + 2.0 ** -8]))[0] == 1.0
+    assert mlp.bf16(np.array([1 + 3 * 2.0 ** -8]))[0] == 1 + 2.0 ** -6
+    assert mlp.bf16(np.array([-(1 + 3 * 2.0 ** -8)]))[0] == -(1 + 2.0 ** -6)
+
+
+def test_gelu_exact_erf_form():
+    z = np.linspace(-6, 6, 241)
+    ref = torch.nn.functional.gelu(torch.tensor(z, dtype=torch.float64), approximate="none").numpy()
+    np.testing.assert_allclose(mlp.gelu(z), ref, rtol=0, atol=1e-14)
+    # Phi(z) + Phi(-z) = 1  =>  gelu(z) - gelu(-z) = z
+    np.testing.assert_allclose(mlp.gelu(z) - mlp.gelu(-z), z, rtol=0, atol=1e-14)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    np.testing.assert_allclose(mlp.gelu_grad(z), fd, rtol=0, atol=1e-8)
+
+
+def test_one_layer_network_is_a_scaled_sigmoid_of_an_affine_map():
+    rng = np.random.default_rng(1)
+    W, b = rng.standard_normal((8, 16)), rng.standard_normal(8)
+    x = rng.standard_normal((5, 16))
+    y, _, _ = mlp.forward(mlp.pack([(W, b)]), [16, 8], x, 0.1, 0.6, bf16_round=False)
+    ref = 0.1 + 0.5 * torch.sigmoid(torch.tensor(x @ W.T + b)).numpy()
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-14)
+    # zero weights: the middle of the output range
+    y0, _, _ = mlp.forward(np.zeros(8 * 16 + 8), [16, 8], x, 0.1, 0.6)
+    np.testing.assert_allclose(y0, 0.35, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("widths", [[16, 24, 8], [8, 16, 16, 8]])
+def test_loss_gradient_matches_central_differences(widths):
+    rng = np.random.default_rng(2)
+    n_par = sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+    p = rng.standard_normal(n_par) * 0.5
+    x = rng.standard_normal((6, widths[0]))
+    t = rng.uniform(0.1, 0.6, (6, widths[-1]))
+    loss, g = mlp.loss_and_grad(p, widths, x, t, bf16_round=False)
+    h = 1e-6
+    idx = rng.choice(n_par, 60, replace=False)
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.loss_and_grad(pp, widths, x, t, bf16_round=False)[0] -
+              mlp.loss_and_grad(pm, widths, x, t, bf16_round=False)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-10)
+    # the loss is the mean squared error of the forward output
+    y, _, _ = mlp.forward(p, widths, x, bf16_round=False)
+    assert loss == pytest.approx(((y - t) ** 2).mean(), rel=1e-14)
+
+
+def test_bf16_rounding_points_change_little():
+    rng = np.random.default_rng(3)
+    widths = [64, 32, 32, 8]
+    n_par = sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+    p = rng.standard_normal(n_par) * 0.2
+    x = rng.standard_normal((16, 64))
+    t = rng.uniform(0.1, 0.6, (16, 8))
+    l0, g0 = mlp.loss_and_grad(p, widths, x, t, bf16_round=False)
+    l1, g1 = mlp.loss_and_grad(p, widths, x, t, bf16_round=True)
+    assert l1 == pytest.approx(l0, rel=2e-2)
+    assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0)
