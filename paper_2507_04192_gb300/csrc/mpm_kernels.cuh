@@ -16,6 +16,11 @@
 
 #include "mpm_internal.cuh"
 
+// Resident P2G blocks per SM the 3D single-precision kernel is compiled for.
+#ifndef MPM_P2G_MINB
+#define MPM_P2G_MINB 3
+#endif
+
 namespace mpm {
 
 // ------------------------------------------------------------------ helpers
@@ -333,6 +338,17 @@ __device__ __forceinline__ void p2g_accumulate(const P2GFactors<R, D> &f, R mp, 
     }
 }
 
+// Byte offset of the P2G per-thread staging slots in dynamic shared memory
+// (after the window and the cell offsets, 16-byte aligned) and the total size.
+template <class R, int D> __host__ __device__ constexpr size_t p2g_stage_offset()
+{
+    return ((size_t)(D + 1) * Geo<D>::WN * sizeof(R) + (Geo<D>::TN + 1) * sizeof(int32_t) + 15) & ~size_t(15);
+}
+template <class R, int D, int NT> __host__ __device__ constexpr size_t p2g_smem_bytes()
+{
+    return p2g_stage_offset<R, D>() + (size_t)2 * p2g_ncomp<D>(1) * NT * sizeof(R);
+}
+
 template <int D> __device__ __forceinline__ int win_index(const int l[D], int k0, int k1, int k2)
 {
     using Gm = Geo<D>;
@@ -389,35 +405,73 @@ __device__ __forceinline__ int next_tile(int32_t *cursor, int n_tiles, int *s_sl
     return k < n_tiles ? k : -1;
 }
 
-// P2G.  Blocks of 128 threads claim tiles dynamically; one thread per cell.  A
-// thread walks its cell's particles (slots from the position map; within a
-// group the rank planes are contiguous and cell-ordered, so the loads of a warp
-// are coalesced) and sums the contributions of the particles still in its cell
-// in registers (3^D nodes x (1 + D) values), adding them to the shared-memory
-// window once.  A particle that has left its cell since the sort is scattered on
-// its own: into the window, or straight to the grid if it has also left the
-// window.  The window is added to the grid with one vector atomic per touched
-// node.  Without REG (FP64 in 3D) every particle is scattered on its own.
+// Per-thread asynchronous copy of one element global -> shared (cp.async), in
+// commit groups the issuing thread waits for.
+template <class R> __device__ __forceinline__ void cp_async_elem(R *dst, const R *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"((int)sizeof(R))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Walks one thread's particles of a tile: cells c = threadIdx.x, +NT, ... and
+// the slots q of each cell (cell_off ranges); next() moves to the next particle.
+template <int TN, int NT> struct CellCursor {
+    int c, q, q1;
+    __device__ __forceinline__ void start() { c = (int)threadIdx.x - NT; q = 0; q1 = 0; }
+    __device__ __forceinline__ bool next(const int32_t *off)
+    {
+        ++q;
+        while (q >= q1) {
+            c += NT;
+            if (c >= TN) return false;
+            q = off[c];
+            q1 = off[c + 1];
+        }
+        return true;
+    }
+};
+
+template <int D> constexpr int kP2GStageComps = p2g_ncomp<D>(1);
+
+// P2G.  Blocks of NT threads claim tiles dynamically; one thread per cell.  A
+// thread walks its cells' particles (slots from the position map; within a
+// group the rank planes are contiguous and cell-ordered, so the copies of a warp
+// are coalesced) through a two-stage pipeline: the components of the particle
+// after next are copied into the thread's shared-memory slots (cp.async) while
+// the current one is summed.  It sums the contributions of the particles still
+// in their cell in registers (3^D nodes x (1 + D) values) and adds them to the
+// shared-memory window when it leaves the cell.  A particle that has left its
+// cell since the sort is scattered on its own: into the window, or straight to
+// the grid if it has also left the window.  The window is added to the grid with
+// one vector atomic per touched node.  Without REG (FP64 in 3D) every particle
+// is scattered on its own.
 template <class R, int D, bool REG, int NT>
-__global__ void __launch_bounds__(NT, (D == 3 && REG) ? 3 : 1)
+__global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     k_p2g(const Params<R> P, const R *__restrict__ S, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
           const int32_t *__restrict__ posmap, const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A,
           uint32_t *__restrict__ flags, unsigned long long *__restrict__ escaped_count)
 {
     using Gm = Geo<D>;
+    constexpr int NCM = kP2GStageComps<D>;
+    constexpr int NXC = 2 * D + D * D;                // x, v, C: consecutive in the state
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     int32_t *off = reinterpret_cast<int32_t *>(sm + (D + 1) * Gm::WN);
+    R *stg = reinterpret_cast<R *>(smem_raw + p2g_stage_offset<R, D>());
     __shared__ uint32_t tile_mask;
     __shared__ int s_slot;
     const int n_tiles = counters[1];
+    const int nc = p2g_ncomp<D>(P.material);
+    const int tid = threadIdx.x;
     for (;;) {
         const int k = next_tile(&counters[2], n_tiles, &s_slot);
         if (k < 0) break;
         const int4 t = tiles[k];
-        for (int i = threadIdx.x; i < (D + 1) * Gm::WN; i += NT) sm[i] = R(0);
-        for (int c = threadIdx.x; c <= Gm::TN; c += NT) off[c] = cell_off[(int64_t)k * (Gm::TN + 1) + c];
-        if (threadIdx.x == 0) tile_mask = 0u;
+        for (int i = tid; i < (D + 1) * Gm::WN; i += NT) sm[i] = R(0);
+        for (int c = tid; c <= Gm::TN; c += NT) off[c] = cell_off[(int64_t)k * (Gm::TN + 1) + c];
+        if (tid == 0) tile_mask = 0u;
         __syncthreads();
         const int sim = (int)(t.x / P.tiles_per_sim);
         int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
@@ -429,55 +483,88 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? 3 : 1)
         }
         R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
-        const int64_t pm0 = (int64_t)t.y;
+        const int32_t *pmap = posmap + t.y;
+        const R *St = S + t.y;
         bool any_escape = false;
-        for (int c = threadIdx.x; c < Gm::TN; c += NT) {
-            const int q0 = off[c], q1 = off[c + 1];
-            if (q0 == q1) continue;
-            int lc[D], bown[D];
-            {
-                int r = c;
+
+        auto issue = [&](int stage, int32_t pos) {
+            R *dst = stg + stage * NCM * NT + tid;
+            const R *src = St + pos;
+            for (int j = 0; j < nc; ++j) {
+                const int comp = j < NXC ? j : P.off_rho + (j - NXC);
+                cp_async_elem(dst + j * NT, src + (int64_t)comp * P.npad);
+            }
+        };
+        // producer: two particles ahead of the consumer, its next slot's position prefetched
+        CellCursor<Gm::TN, NT> pc, cc;
+        pc.start();
+        cc.start();
+        bool hp = pc.next(off);
+        if (hp) issue(0, pmap[pc.q]);
+        cp_async_commit();
+        hp = hp && pc.next(off);
+        if (hp) issue(1, pmap[pc.q]);
+        cp_async_commit();
+        hp = hp && pc.next(off);
+        int32_t ppos = hp ? pmap[pc.q] : 0;
+
+        bool hc = cc.next(off);
+        int stage = 0;
+        int cur = -1;                                  // cell whose accumulators are live
+        int lc[D], bown[D];
+        R acc[Gm::STENCIL][D + 1];
+        while (hc) {
+            if (cc.c != cur) {
+                cur = cc.c;
+                int r = cur;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const int cc = r % Gm::T;
+                    const int ci = r % Gm::T;
                     r /= Gm::T;
-                    lc[a] = cc + 1;                    // window coordinates of the cell's base
-                    bown[a] = org[a] + cc - 1;         // base cell index of the cell
+                    lc[a] = ci + 1;                    // window coordinates of the cell's base
+                    bown[a] = org[a] + ci - 1;         // base cell index of the cell
+                }
+                if constexpr (REG) {
+#pragma unroll
+                    for (int kk = 0; kk < Gm::STENCIL; ++kk)
+#pragma unroll
+                        for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
                 }
             }
-            R acc[Gm::STENCIL][D + 1];
-            if constexpr (REG) {
-#pragma unroll
-                for (int kk = 0; kk < Gm::STENCIL; ++kk)
-#pragma unroll
-                    for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
+            cp_async_wait<1>();
+            P2GFactors<R, D> f;
+            {
+                const R *src = stg + stage * NCM * NT + tid;
+                p2g_factors<R, D>(P, [&](int j) { return src[j * NT]; }, f);
             }
-            int32_t pos_next = posmap[pm0 + q0];
-            for (int q = q0; q < q1; ++q) {
-                const int64_t p = pm0 + pos_next;
-                if (q + 1 < q1) pos_next = posmap[pm0 + q + 1];
-                P2GFactors<R, D> f;
-                p2g_factors<R, D>(P, [&](int j) { return S[(int64_t)(j < 2 * D + D * D ? j : P.off_rho + (j - 2 * D - D * D)) * P.npad + p]; }, f);
-                bool own = REG;
+            if (hp) issue(stage, ppos);
+            cp_async_commit();
+            hp = hp && pc.next(off);
+            if (hp) ppos = pmap[pc.q];
+            bool own = REG;
 #pragma unroll
-                for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
-                if (own) {
-                    if constexpr (REG) p2g_accumulate<R, D>(f, P.mass, acc);
-                } else {
-                    bool esc = false;
-                    p2g_scatter<R, D>(P, f, org, sm, Asim, fsim, esc);
-                    any_escape |= esc;
-                }
+            for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
+            if (own) {
+                if constexpr (REG) p2g_accumulate<R, D>(f, P.mass, acc);
+            } else {
+                bool esc = false;
+                p2g_scatter<R, D>(P, f, org, sm, Asim, fsim, esc);
+                any_escape |= esc;
             }
+            stage ^= 1;
+            hc = cc.next(off);
             if constexpr (REG) {
+                if (!hc || cc.c != cur) {
 #pragma unroll
-                for (int kk = 0; kk < Gm::STENCIL; ++kk) {
-                    const int li = win_index<D>(lc, kk % 3, (kk / 3) % 3, kk / 9);
+                    for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+                        const int li = win_index<D>(lc, kk % 3, (kk / 3) % 3, kk / 9);
 #pragma unroll
-                    for (int v = 0; v <= D; ++v) atomicAdd(&sm[v * Gm::WN + li], acc[kk][v]);
+                        for (int v = 0; v <= D; ++v) atomicAdd(&sm[v * Gm::WN + li], acc[kk][v]);
+                    }
                 }
             }
         }
+        cp_async_wait<0>();
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
         if (ball && (threadIdx.x & 31) == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
         __syncthreads();
@@ -1168,7 +1255,7 @@ template <class R, int D> struct Launch {
     }
     static constexpr bool kReg = (sizeof(R) == 4) || (D == 2);
     static constexpr int kP2GThreads = (D == 3 && kReg) ? 128 : 256;
-    static size_t p2g_smem() { return (size_t)(D + 1) * Geo<D>::WN * sizeof(R) + (Geo<D>::TN + 1) * sizeof(int32_t); }
+    static size_t p2g_smem() { return p2g_smem_bytes<R, D, kP2GThreads>(); }
     static void p2g(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
@@ -1180,7 +1267,7 @@ template <class R, int D> struct Launch {
             attr = true;
         }
         int64_t nb = ds.max_tiles;
-        const int64_t cap = (int64_t)ds.num_sms * (kP2GThreads == 128 ? 3 : 2);
+        const int64_t cap = (int64_t)ds.num_sms * (kP2GThreads == 128 ? MPM_P2G_MINB : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
         k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
