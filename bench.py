@@ -175,6 +175,92 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def read_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of ``kernel`` from the ncu summary
+    table in profiles/traffic.txt (lines: kernel bytes), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 2 and not line.startswith("#") and f[0] == f"k_{kernel}":
+            return float(f[1])
+    return None
+
+
+def _event_ms(stream, fn):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def secondary_measurements(stream, dev):
+    """The other hot-path rows, each on its own workload: the checkpointed
+    adjoint of the 128 x 128 dam-break inverse (FP32, 500 steps, checkpoint 50),
+    a batch of 256 independent 96 x 96 dam breaks (FP32, 300 steps), and the
+    640-256-256-32 network's training step and inference at batch 256."""
+    from paper_2507_04192_gb300 import inputs, mpm
+
+    out = {}
+    # adjoint / forward
+    w = inputs.dam_break_inverse_2d(128)
+    mu = w.extras["mu_true"]
+    z = np.zeros((len(w.extras["obs_steps"]), len(w.extras["track_ids"]), 2))
+    steps = max(w.extras["obs_steps"])
+    sim = mpm.Simulation(2, w.n_cells, w.dx, w.dt, w.gravity, w.material, mpm.MPM_FP32, w.sort_every,
+                         stream=stream.cuda_stream)
+    sim.load(w.x, None, w.particle_volume)
+    sim.set_friction(2, (len(mu), 1), mu)
+    mpm.mpm_save_state(sim.ctx, 0)
+    mpm.mpm_set_observations(sim.ctx, w.extras["track_ids"], w.extras["obs_steps"], z)
+    sim.step(20)
+    mpm.mpm_restore_state(sim.ctx, 0)
+    fwd = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0), sim.step(steps))) for _ in range(3))
+    adj = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
+                                         mpm.mpm_step_adjoint(sim.ctx, steps, 50, 2, len(mu)))) for _ in range(3))
+    sim.close()
+    out["adjoint"] = {"workload": f"dam_break_inverse_2d_128 ({w.n} particles, {steps} steps, checkpoint 50, fp32)",
+                      "forward_ms": fwd, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
+                      "note": "adjoint = forward with checkpoints + segment recompute + reverse sweep"}
+    # batched forward (training data)
+    wb = inputs.dam_break_2d(96)
+    B, nb, bsteps = 256, wb.n, 300
+    sim = mpm.Simulation(2, wb.n_cells, wb.dx, wb.dt, wb.gravity, wb.material, mpm.MPM_FP32, wb.sort_every,
+                         batch=B, stream=stream.cuda_stream)
+    sim.load(np.tile(wb.x, (B, 1)), None, wb.particle_volume, np.repeat(np.arange(B, dtype=np.int32), nb))
+    sim.set_friction(2, (32, 1), np.stack([inputs.friction_field(32, 1_000_000 + i) for i in range(B)]).reshape(-1))
+    sim.step(5)
+    ms = _event_ms(stream, lambda: sim.step(bsteps))
+    sim.close()
+    out["batched_forward"] = {"workload": f"{B} x dam_break_2d_96 ({B * nb} particles, {bsteps} steps, fp32)",
+                              "value": B * nb * bsteps / (ms * 1e-3), "unit": "particle-steps/s",
+                              "ms_per_step": ms / bsteps}
+    # network
+    W = [640, 256, 256, 32]
+    net = mpm.MLP(W, 256, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    net.set_params((rng.standard_normal(net.num_params) * 0.03).astype(np.float32))
+    xs = rng.standard_normal((256, 640)).astype(np.float32)
+    ts = rng.uniform(0.1, 0.6, (256, 32)).astype(np.float32)
+    for _ in range(5):
+        net.train_step(xs, ts, 1e-3)
+    reps = 50
+    tr = _event_ms(stream, lambda: [net.train_step(xs, ts, 1e-3) for _ in range(reps)]) / reps
+    inf = _event_ms(stream, lambda: [net.infer(xs) for _ in range(reps)]) / reps
+    net.close()
+    fl_fwd = 2 * 256 * sum(W[i] * W[i + 1] for i in range(3))
+    out["mlp"] = {"widths": W, "batch": 256, "train_step_ms": tr, "infer_ms": inf,
+                  "train_tflops": 3 * fl_fwd / (tr * 1e-3) / 1e12,
+                  "note": "host-synchronous calls incl. host<->device copies of x, targets and loss"}
+    return out
+
+
 def bench_ours(args):
     import torch
 
@@ -228,7 +314,7 @@ def bench_ours(args):
     _, _, kt = timed_run(mpm.MPM_FP32, args.steps, 3, timing=True)
     # FP64 mode, fewer steps
     steps64 = max(1, min(args.steps, 200))
-    ms64, _, _ = timed_run(mpm.MPM_FP64, steps64, 3)
+    ms64 = timed_run(mpm.MPM_FP64, steps64, 3)[0] if not args.no_fp64 else float("nan")
 
     def reduce_max(v):
         if world > 1:
@@ -265,10 +351,9 @@ def bench_ours(args):
     per_launch_ms = dom_ms / max(1, dom_n)
     bpp = algorithmic_bytes_per_particle(dom, 3, 1, 4)
     achieved = bpp * n / (per_launch_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        traffic = json.load(open(prof)).get(dom)
+    traffic = read_traffic(dom)
+
+    extra = secondary_measurements(stream, dev) if (rank == 0 and not args.headline_only) else {}
 
     if rank == 0:
         cpu = cpu_baseline_full_step() if (world == 1 and not args.no_cpu) else None
@@ -281,8 +366,8 @@ def bench_ours(args):
                        "material": "drucker_prager", "sort_every": w.sort_every,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (353 MB particle state per step)"},
-            "fp64": {"value": value64, "unit": "particle-steps/s", "steps": steps64,
-                     "ms_per_step": ms64 / steps64},
+            "fp64": ({"value": value64, "unit": "particle-steps/s", "steps": steps64,
+                      "ms_per_step": ms64 / steps64} if not args.no_fp64 else None),
             "kernels_ms_per_step": {k: kt[k][0] / max(1, args.steps) for k in kt},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -294,6 +379,7 @@ def bench_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -307,6 +393,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--headline-only", action="store_true", help="skip the adjoint, batched and network lines")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -33,6 +33,7 @@ class FrictionInversion:
         self.sim.load(w.x, w.v, w.particle_volume)
         mpm.mpm_save_state(self.sim.ctx, 0)
         mpm.mpm_set_observations(self.sim.ctx, w.extras["track_ids"], w.extras["obs_steps"], z_obs)
+        self.z_obs = np.asarray(z_obs, dtype=np.float64)
         self.evaluations = 0
 
     def loss_and_grad(self, mu: np.ndarray):
@@ -117,6 +118,24 @@ def invert(problem: FrictionInversion, mu0, mu_true=None, mask=None, tol: float 
         with torch.no_grad():
             mu.clamp_(0.0, 1.0)
     return InversionResult(mu.detach().numpy().copy(), max_iters, False, history)
+
+
+def sensitive_segments(problem: FrictionInversion, mu_true: np.ndarray, z_obs: np.ndarray, rel: float = 1e-2,
+                       shift: float = 1e-3) -> np.ndarray:
+    """Segments whose friction moves the tracked particles along the floor at the
+    true field: with the observations shifted by ``shift`` (in units of dx) along
+    the first axis the loss gradient at ``mu_true`` is -2 shift dx times the
+    summed sensitivities of the tracks' first coordinates (the residuals vanish
+    there), which is zero for segments without sliding contact."""
+    w = problem.w
+    z = np.array(z_obs, dtype=np.float64, copy=True)
+    z[..., 0] += shift * w.dx
+    mpm.mpm_set_observations(problem.sim.ctx, w.extras["track_ids"], w.extras["obs_steps"], z)
+    try:
+        _, g = problem.loss_and_grad(mu_true)
+    finally:
+        mpm.mpm_set_observations(problem.sim.ctx, w.extras["track_ids"], w.extras["obs_steps"], z_obs)
+    return np.abs(g) > rel * np.abs(g).max()
 
 
 def constrained_segments(problem: FrictionInversion, mu: np.ndarray, rel: float = 1e-2) -> np.ndarray:

@@ -1,0 +1,226 @@
+"""Learned warm start of the basal-friction inversion.
+
+The solver's own batched forward runs (many independent dam breaks sharing one
+grid shape, each with its own random 32-segment friction field) give pairs
+(observations, friction field); a small network on the tensor cores
+(mpm_mlp_*) learns the map from the tracked particles' horizontal
+displacements to the field, and its prediction replaces the uniform first
+guess of the adjoint inversion (Sec. 5.3).  The paper parameterises a field
+with a coordinate network (Eq. nn_apprx, Sec. 3.2); this one is an amortised
+observations-to-parameters map of the same kind of component.
+
+Features: one scalar per (observation time, track), (x_t - x_0) / scale along
+the floor, time-major; targets: the per-segment friction coefficients.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+from . import inputs, mpm
+
+MU_LO, MU_HI = 0.1, 0.6
+UNIFORM_GUESS = 0.35
+TRAIN_SEED_BASE = 1_000_000          # friction seeds of training runs; held-out problems use small seeds
+
+
+@dataclass
+class Setup:
+    """Geometry, tracks and horizon shared by every run of one training set."""
+    n_cells: int = 96
+    n_seg: int = 32
+    n_track: int = 64
+    n_obs: int = 10
+    steps: int = 300
+    checkpoint_every: int = 50
+    geometry_seed: int = 0
+
+    def workload(self, mu_seed: Optional[int] = None):
+        w = inputs.dam_break_inverse_2d(self.n_cells, n_seg=self.n_seg, n_track=self.n_track, n_obs=self.n_obs,
+                                        steps=self.steps, seed=self.geometry_seed,
+                                        checkpoint_every=self.checkpoint_every)
+        if mu_seed is not None:
+            mu = inputs.friction_field(self.n_seg, mu_seed, MU_LO, MU_HI)
+            w.extras["mu_true"] = mu
+            w.friction = [(2, (self.n_seg, 1), mu)]
+        return w
+
+    @property
+    def n_features(self):
+        return self.n_obs * self.n_track
+
+    def scale(self, w):
+        return float(w.extras["body_hi"][0] - w.extras["body_lo"][0])
+
+
+def observe_batch(w, mus: np.ndarray, precision=mpm.MPM_FP32, stream: int = 0) -> np.ndarray:
+    """Tracked positions (B, n_obs, n_track, dim) of B independent runs of workload
+    ``w`` that differ only in their floor friction ``mus`` (B, n_seg); one batched
+    context steps them together."""
+    mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
+    B, n_seg = mus.shape
+    n = w.x.shape[0]
+    sim = mpm.Simulation(w.dim, w.n_cells, w.dx, w.dt, w.gravity, w.material, precision, w.sort_every, batch=B,
+                         stream=stream)
+    try:
+        sim.load(np.tile(w.x, (B, 1)), None, w.particle_volume, np.repeat(np.arange(B, dtype=np.int32), n))
+        sim.set_friction(2, (n_seg, 1), mus.reshape(-1))
+        ids = (np.arange(B)[:, None] * n + np.asarray(w.extras["track_ids"])[None, :])
+        out, t = [], 0
+        for s in w.extras["obs_steps"]:
+            sim.step(s - t)
+            t = s
+            out.append(sim.get("x")[ids])
+        return np.stack(out, axis=1)
+    finally:
+        sim.close()
+
+
+def features(setup: Setup, w, z_obs: np.ndarray) -> np.ndarray:
+    """Network input from observations z_obs (n_obs, n_track, dim) or a batch of them."""
+    z = np.asarray(z_obs, dtype=np.float64)
+    x0 = w.x[np.asarray(w.extras["track_ids"])]
+    d = (z[..., 0] - x0[:, 0]) / setup.scale(w)
+    return d.reshape(d.shape[:-2] + (-1,)).astype(np.float32)
+
+
+def generate(setup: Setup, n_runs: int, batch: int = 256, first_seed: int = TRAIN_SEED_BASE,
+             precision=mpm.MPM_FP32):
+    """n_runs (features, friction field) pairs from batched forward runs."""
+    w = setup.workload()
+    X, Y = [], []
+    for b0 in range(0, n_runs, batch):
+        B = min(batch, n_runs - b0)
+        mus = np.stack([inputs.friction_field(setup.n_seg, first_seed + b0 + i, MU_LO, MU_HI) for i in range(B)])
+        X.append(features(setup, w, observe_batch(w, mus, precision)))
+        Y.append(mus.astype(np.float32))
+    return np.concatenate(X), np.concatenate(Y)
+
+
+class WarmStartNet:
+    """n_features -> hidden -> hidden -> n_seg network, output in [MU_LO, MU_HI]."""
+
+    def __init__(self, n_in: int, n_out: int, hidden=(256, 256), max_batch: int = 256, seed: int = 0):
+        self.widths = [n_in, *hidden, n_out]
+        self.max_batch = max_batch
+        self.net = mpm.MLP(self.widths, max_batch, MU_LO, MU_HI)
+        rng = np.random.default_rng(seed)
+        p = []
+        for l in range(len(self.widths) - 1):
+            fan_in = self.widths[l]
+            p.append(rng.standard_normal(self.widths[l + 1] * fan_in) * np.sqrt(2.0 / fan_in))
+            p.append(np.zeros(self.widths[l + 1]))
+        self.net.set_params(np.concatenate(p).astype(np.float32))
+        self.x_mean = np.zeros(n_in)
+        self.x_scale = np.ones(n_in)
+
+    def _standardise(self, X):
+        return ((np.asarray(X, dtype=np.float64) - self.x_mean) / self.x_scale).astype(np.float32)
+
+    def fit(self, X, Y, epochs: int = 40, lr: float = 1e-3, seed: int = 0) -> List[float]:
+        """Adam on the mean squared error over shuffled mini-batches of max_batch.
+        Inputs are standardised per feature with the training set's mean and
+        spread (the displacements friction changes differ by orders of magnitude
+        between tracks near the front and inside the column)."""
+        X = np.asarray(X, dtype=np.float64)
+        self.x_mean = X.mean(axis=0)
+        sd = X.std(axis=0)
+        self.x_scale = np.where(sd > 1e-9, sd, 1.0)          # tracks friction never reaches stay ~0
+        Xs = self._standardise(X)
+        Y = np.asarray(Y, dtype=np.float32)
+        rng = np.random.default_rng(seed)
+        B = self.max_batch
+        n = (len(X) // B) * B
+        hist = []
+        for _ in range(epochs):
+            order = rng.permutation(len(X))[:n]
+            losses = [self.net.train_step(Xs[order[i:i + B]], Y[order[i:i + B]], lr) for i in range(0, n, B)]
+            hist.append(float(np.mean(losses)))
+        return hist
+
+    def predict(self, X) -> np.ndarray:
+        X = self._standardise(np.atleast_2d(X))
+        out = [self.net.infer(X[i:i + self.max_batch]) for i in range(0, len(X), self.max_batch)]
+        return np.concatenate(out).astype(np.float64)
+
+    def close(self):
+        self.net.close()
+
+
+def held_out_problem(setup: Setup, mu_seed: int, precision=mpm.MPM_FP32):
+    """Workload and observations of one inversion problem (friction from ``mu_seed``)."""
+    w = setup.workload(mu_seed)
+    z = observe_batch(w, w.extras["mu_true"][None, :], precision)[0]
+    return w, z
+
+
+def compare(setup: Setup, net: WarmStartNet, mu_seeds, tol: float = 0.05, max_iters: int = 300,
+            precision=mpm.MPM_FP32, mask_rel: float = 1e-2):
+    """Adjoint inversion from the uniform guess and from the network's prediction,
+    per held-out problem: first-guess error and iterations to ``tol`` relative L2
+    error over the segments the observations constrain (gradient test at the
+    true field, see inverse.sensitive_segments)."""
+    from . import inverse
+    rows = []
+    for s in mu_seeds:
+        w, z = held_out_problem(setup, s, precision)
+        mu_true = w.extras["mu_true"]
+        prob = inverse.FrictionInversion(w, z, precision, checkpoint_every=setup.checkpoint_every)
+        try:
+            mask = inverse.sensitive_segments(prob, mu_true, z, mask_rel)
+            mu_warm = np.clip(net.predict(features(setup, w, z)[None, :])[0], 0.0, 1.0)
+            mu_unif = np.full(setup.n_seg, UNIFORM_GUESS)
+            res_u = inverse.invert(prob, mu_unif, mu_true, mask, tol, max_iters)
+            res_w = inverse.invert(prob, mu_warm, mu_true, mask, tol, max_iters)
+        finally:
+            prob.close()
+        rows.append(dict(seed=int(s), constrained=int(mask.sum()),
+                         err0_uniform=inverse.relative_error(mu_unif, mu_true, mask),
+                         err0_warm=inverse.relative_error(mu_warm, mu_true, mask),
+                         iters_uniform=res_u.iterations, converged_uniform=res_u.converged,
+                         iters_warm=res_w.iterations, converged_warm=res_w.converged,
+                         err_uniform=inverse.relative_error(res_u.mu, mu_true, mask),
+                         err_warm=inverse.relative_error(res_w.mu, mu_true, mask),
+                         full_err_uniform=inverse.relative_error(res_u.mu, mu_true),
+                         full_err_warm=inverse.relative_error(res_w.mu, mu_true)))
+    return rows
+
+
+def main(argv=None):
+    """Warm start vs uniform guess on held-out problems; prints one JSON line."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--runs", type=int, default=8192)
+    ap.add_argument("--held-out", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--max-iters", type=int, default=300)
+    args = ap.parse_args(argv)
+    setup = Setup()
+    t0 = time.perf_counter()
+    X, Y = generate(setup, args.runs)
+    t1 = time.perf_counter()
+    net = WarmStartNet(setup.n_features, setup.n_seg)
+    hist = net.fit(X, Y, epochs=args.epochs)
+    t2 = time.perf_counter()
+    rows = compare(setup, net, range(1, args.held_out + 1), max_iters=args.max_iters)
+    net.close()
+    summary = {
+        "setup": setup.__dict__, "runs": args.runs, "generate_s": t1 - t0, "train_s": t2 - t1,
+        "train_loss": [hist[0], hist[-1]],
+        "uniform": {"converged": sum(r["converged_uniform"] for r in rows),
+                    "median_iters": float(np.median([r["iters_uniform"] for r in rows])),
+                    "mean_err0": float(np.mean([r["err0_uniform"] for r in rows]))},
+        "warm": {"converged": sum(r["converged_warm"] for r in rows),
+                 "median_iters": float(np.median([r["iters_warm"] for r in rows])),
+                 "mean_err0": float(np.mean([r["err0_warm"] for r in rows]))},
+        "rows": rows,
+    }
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
