@@ -484,7 +484,7 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     if (rc == MPM_OK) rc = dalloc(c, &ds.keys[1], n, "keys");
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk, "histogram");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk + kScanSegments, "histogram");
     if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, ds.max_tiles, "tile list");
     if (rc == MPM_OK) rc = dalloc(c, &ds.perm, n, "permutation");
     if (rc == MPM_OK) rc = dalloc(c, &ds.posmap, n, "position map");

@@ -24,6 +24,7 @@ constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortChunk = kSortThreads * kSortItems;
+constexpr int kScanSegments = 1024;              // scratch words after the digit histogram
 
 template <int D> struct Geo;
 template <> struct Geo<2> {

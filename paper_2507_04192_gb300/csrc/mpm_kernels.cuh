@@ -20,6 +20,10 @@
 #ifndef MPM_P2G_MINB
 #define MPM_P2G_MINB 3
 #endif
+// Resident G2P blocks per SM the single-precision kernel is compiled for.
+#ifndef MPM_G2P_MINB
+#define MPM_G2P_MINB 2
+#endif
 
 namespace mpm {
 
@@ -941,7 +945,7 @@ template <class R, int D> struct G2PSmem {
 // inputs are staged 256 at a time by TMA bulk copies, double-buffered.  All
 // waits are bounded; a timeout is reported in the status word.
 template <class R, int D>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
     k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV, R *__restrict__ S,
           const R4<R> *__restrict__ V, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
           int32_t *__restrict__ status)
@@ -1289,7 +1293,7 @@ template <class R, int D> struct Launch {
             attr = true;
         }
         int64_t nb = ds.max_tiles;
-        const int64_t cap = (int64_t)ds.num_sms * 2;
+        const int64_t cap = (int64_t)ds.num_sms * (sizeof(R) == 4 ? MPM_G2P_MINB : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
         k_g2p<R, D><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V,

@@ -37,22 +37,23 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__rest
     for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[(int64_t)d * nblk + blockIdx.x] = cnt[d];
 }
 
-// Exclusive scan of len entries by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_exclusive(uint32_t *__restrict__ data, int64_t len)
+// Exclusive scan of data[begin, end) by one block of 1024 threads, starting
+// from carry0.
+__device__ void block_scan_exclusive(uint32_t *__restrict__ data, int64_t begin, int64_t end, uint32_t carry0)
 {
     __shared__ uint32_t warp_sum[32];
     __shared__ uint32_t carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0u;
+    if (tid == 0) carry = carry0;
     __syncthreads();
     constexpr int kPer = 4;
-    for (int64_t base = 0; base < len; base += 1024 * kPer) {
+    for (int64_t base = begin; base < end; base += 1024 * kPer) {
         uint32_t v[kPer];
         uint32_t sum = 0u;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int64_t i = base + (int64_t)tid * kPer + k;
-            v[k] = i < len ? data[i] : 0u;
+            v[k] = i < end ? data[i] : 0u;
             sum += v[k];
         }
         uint32_t incl = sum;
@@ -78,13 +79,46 @@ __global__ void __launch_bounds__(1024) k_scan_exclusive(uint32_t *__restrict__ 
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int64_t i = base + (int64_t)tid * kPer + k;
-            if (i < len) data[i] = run;
+            if (i < end) data[i] = run;
             run += v[k];
         }
         __syncthreads();
         if (tid == 1023) carry = run;
         __syncthreads();
     }
+}
+
+// Three-phase exclusive scan of the digit histogram: per-segment sums, a scan
+// of the sums by one block, then each segment rescanned from its offset.
+__global__ void __launch_bounds__(1024) k_scan_reduce(const uint32_t *__restrict__ data, int64_t len, int64_t seg,
+                                                      uint32_t *__restrict__ partial)
+{
+    __shared__ uint32_t ws[32];
+    const int64_t b0 = (int64_t)blockIdx.x * seg, b1 = b0 + seg < len ? b0 + seg : len;
+    uint32_t s = 0u;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += 1024) s += data[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = ws[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ partial, int nseg)
+{
+    block_scan_exclusive(partial, 0, nseg, 0u);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_down(uint32_t *__restrict__ data, int64_t len, int64_t seg,
+                                                    const uint32_t *__restrict__ partial)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * seg, b1 = b0 + seg < len ? b0 + seg : len;
+    block_scan_exclusive(data, b0, b1, partial[blockIdx.x]);
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t *__restrict__ kin,
@@ -300,6 +334,22 @@ __global__ void __launch_bounds__(NG) k_tile_reorder(const int4 *__restrict__ ti
 
 }  // namespace
 
+// Exclusive scan of len entries in place (partial: kScanSegments scratch words).
+void scan_exclusive(uint32_t *data, int64_t len, uint32_t *partial, cudaStream_t stream)
+{
+    int64_t seg = (len + kScanSegments - 1) / kScanSegments;
+    seg = (seg + 4095) / 4096 * 4096;
+    if (seg < 4096) seg = 4096;
+    const int nseg = (int)((len + seg - 1) / seg);
+    if (nseg <= 1) {
+        k_scan_top<<<1, 1024, 0, stream>>>(data, (int)len);
+        return;
+    }
+    k_scan_reduce<<<nseg, 1024, 0, stream>>>(data, len, seg, partial);
+    k_scan_top<<<1, 1024, 0, stream>>>(partial, nseg);
+    k_scan_down<<<nseg, 1024, 0, stream>>>(data, len, seg, partial);
+}
+
 void radix_sort_pairs(const HostParams &hp, DevState &ds)
 {
     const int64_t n = hp.n;
@@ -307,7 +357,7 @@ void radix_sort_pairs(const HostParams &hp, DevState &ds)
     int cur = 0;
     for (int shift = 0; shift < ds.key_bits; shift += kRadixBits) {
         k_rs_hist<<<nblk, kSortThreads, 0, ds.stream>>>(ds.keys[cur], n, shift, ds.hist, nblk);
-        k_scan_exclusive<<<1, 1024, 0, ds.stream>>>(ds.hist, (int64_t)kRadixBins * nblk);
+        scan_exclusive(ds.hist, (int64_t)kRadixBins * nblk, ds.hist + (int64_t)kRadixBins * nblk, ds.stream);
         k_rs_scatter<<<nblk, kSortThreads, 0, ds.stream>>>(ds.keys[cur], ds.vals[cur], ds.keys[cur ^ 1],
                                                            ds.vals[cur ^ 1], n, shift, ds.hist, nblk);
         cur ^= 1;
