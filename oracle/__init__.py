@@ -89,7 +89,8 @@ def lib():
             "orc_dp_constants": (None, [P, p]),
             "orc_tait_pressure": (d, [P, d]),
             "orc_affine_C": (None, [P, l, p, p, p]),
-            "orc_step_vjp": (i, [P, l, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "orc_step_vjp": (i, [P, l] + [p] * 16),
+            "orc_dp_vjp": (None, [P, p, p, p, p, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -189,23 +190,38 @@ class Oracle:
         lib().orc_affine_C(C.byref(self.P), st.n, _ptr(st.x), _ptr(st.B), _ptr(Cm))
         return Cm
 
-    def step_vjp(self, st: "State", xb, vb, Bb, rhob):
-        """Adjoint of one step (fluid): given the adjoint of S^{t+1} = (x, v, B, rho),
-        return the adjoint of S^t and dL/dmu per wall with a friction field."""
+    def step_vjp(self, st: "State", xb, vb, Bb, rhob, sigb=None):
+        """Adjoint of one step: given the adjoint of S^{t+1} = (x, v, B, rho) and,
+        for Drucker-Prager, of sigma (n x 3 x 3, entries independent), return the
+        adjoint of S^t (same layout) and dL/dmu per wall with a friction field."""
         n, d = st.n, self.dim
+        sand = self.P.material == 1
         out = [np.zeros((n, d)), np.zeros((n, d)), np.zeros((n, d, d)), np.zeros(n)]
         ins = [np.ascontiguousarray(a, dtype=np.float64) for a in (xb, vb, Bb, rhob)]
+        sig = np.ascontiguousarray(st.sigma, dtype=np.float64).reshape(n, 3, 3) if sand else None
+        sigb1 = np.ascontiguousarray(sigb, dtype=np.float64).reshape(n, 3, 3) if sand else None
+        sigb0 = np.zeros((n, 3, 3)) if sand else None
         mub = {}
         ptrs = (C.c_void_p * MAX_WALLS)()
         for w in range(MAX_WALLS):
             if self.P.mu[w]:
                 mub[w] = np.zeros(self.P.n_seg[w][0] * self.P.n_seg[w][1])
                 ptrs[w] = mub[w].ctypes.data
-        rc = lib().orc_step_vjp(C.byref(self.P), n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.rho),
-                                *[_ptr(a) for a in ins], *[_ptr(a) for a in out], ptrs)
+        opt = lambda a: None if a is None else _ptr(a)
+        rc = lib().orc_step_vjp(C.byref(self.P), n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.rho), opt(sig),
+                                *[_ptr(a) for a in ins], opt(sigb1), *[_ptr(a) for a in out], opt(sigb0), ptrs)
         if rc != 0:
             raise RuntimeError(f"orc_step_vjp failed ({rc})")
+        if sand:
+            out.append(sigb0)
         return out, mub
+
+    def dp_vjp(self, dd, dw, sigma, sigb1):
+        """Adjoint of dp_update: (sigma_bar, dd_bar, dw_bar) for the output adjoint sigb1."""
+        a = [np.ascontiguousarray(x, dtype=np.float64).reshape(3, 3) for x in (dd, dw, sigma, sigb1)]
+        sb0, ddb, dwb = np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3))
+        lib().orc_dp_vjp(C.byref(self.P), *[_ptr(x) for x in a], _ptr(sb0), _ptr(ddb), _ptr(dwb))
+        return sb0, ddb, dwb
 
     # -- constitutive pieces ------------------------------------------------------
     def tait_pressure(self, rho: float) -> float:

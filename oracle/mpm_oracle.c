@@ -424,6 +424,118 @@ int orc_dp_update(const orc_params *P, const double *dd, const double *dw, doubl
     return 3;
 }
 
+/*
+ * Vector-Jacobian product of orc_dp_update (Appendix A) for one particle: given
+ * the stress s before the update, the increments dd and dw, and the adjoint sb1
+ * of the updated stress (all 3 x 3, every entry independent), adds the adjoints
+ * of s, dd and dw to sb0, ddb, dwb.  The zone and corner branches taken by the
+ * forward update are held fixed (derivative of the branch taken).
+ */
+void orc_dp_vjp(const orc_params *P, const double *dd, const double *dw, const double *s, const double *sb1,
+                double *sb0, double *ddb, double *dwb)
+{
+    dp_consts c;
+    dp_constants(P, &c);
+    double lam = c.K - 2.0 * c.G / 3.0;
+    /* forward replay */
+    double sR[9], st[9], sdev[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = s[i * 3 + j];
+            for (int k = 0; k < 3; ++k) v += s[i * 3 + k] * dw[j * 3 + k] + s[j * 3 + k] * dw[i * 3 + k];
+            sR[i * 3 + j] = v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = sR[i * 3 + j];
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double C = lam * (i == j) * (k == l) + c.G * ((i == k) * (j == l) + (i == l) * (j == k));
+                    v += C * dd[k * 3 + l];
+                }
+            st[i * 3 + j] = v;
+        }
+    double sm = (st[0] + st[4] + st[8]) / 3.0;
+    double ss = 0.0;
+    for (int q = 0; q < 9; ++q) {
+        sdev[q] = st[q] - (q % 4 == 0 ? sm : 0.0);
+        ss += sdev[q] * sdev[q];
+    }
+    double tau = sqrt(0.5 * ss);
+    double fs = tau - c.k_phi + c.q_phi * sm;
+    double ft = sm - c.sig_t;
+    double h = tau - c.tau_P - c.alpha_P * (sm - c.sig_t);
+    /* reverse: adjoints of the trial stress (stb), its mean (smb) and deviator (sdevb) */
+    double stb[9] = {0.0}, sdevb[9] = {0.0}, smb = 0.0, taub = 0.0;
+    double trb = sb1[0] + sb1[4] + sb1[8];
+    if (fs <= 0.0 && ft < 0.0) {                                     /* Zone I: s' = st */
+        for (int q = 0; q < 9; ++q) stb[q] = sb1[q];
+    } else if ((fs > 0.0 && ft < 0.0) || (h > 0.0 && ft >= 0.0)) {   /* Zone II */
+        double A = c.G + c.K * c.q_phi * c.q_psi;
+        double dl = fs / A;
+        double sm_n = sm - c.K * c.q_psi * dl;
+        double tau_n = c.k_phi - c.q_phi * sm_n;
+        int corner = !P->dp_literal && sm_n > c.sig_t;
+        if (corner) tau_n = c.tau_P;
+        double r = tau > 0.0 ? tau_n / tau : 0.0;
+        /* s'_q = r sdev_q + sm_n delta_q */
+        double rb = 0.0;
+        for (int q = 0; q < 9; ++q) {
+            rb += sb1[q] * sdev[q];
+            sdevb[q] += r * sb1[q];
+        }
+        double sm_nb = corner ? 0.0 : trb;
+        double tau_nb = 0.0;
+        if (tau > 0.0) {
+            if (!corner) tau_nb = rb / tau;
+            taub += -rb * tau_n / (tau * tau);
+        }
+        sm_nb += -c.q_phi * tau_nb;
+        /* sm_n = sm - K q_psi (tau - k_phi + q_phi sm) / A */
+        smb += sm_nb * (1.0 - c.K * c.q_psi * c.q_phi / A);
+        taub += sm_nb * (-c.K * c.q_psi / A);
+    } else {                                                         /* Zone III */
+        int corner = !P->dp_literal && tau > c.tau_P;
+        if (corner) {
+            /* s' = (tau_P / tau) sdev + sig_t I */
+            double r = c.tau_P / tau, rb = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                rb += sb1[q] * sdev[q];
+                sdevb[q] += r * sb1[q];
+            }
+            taub += -rb * c.tau_P / (tau * tau);
+        } else {
+            /* s' = st + (sig_t - sm) I */
+            for (int q = 0; q < 9; ++q) stb[q] = sb1[q];
+            smb += -trb;
+        }
+    }
+    /* tau = sqrt(sdev:sdev / 2), sdev = st - sm I, sm = tr(st) / 3 */
+    if (tau > 0.0)
+        for (int q = 0; q < 9; ++q) sdevb[q] += taub * 0.5 * sdev[q] / tau;
+    double sdev_tr = sdevb[0] + sdevb[4] + sdevb[8];
+    for (int q = 0; q < 9; ++q) stb[q] += sdevb[q];
+    smb += -sdev_tr;
+    for (int a = 0; a < 3; ++a) stb[a * 4] += smb / 3.0;
+    /* st = sR + C:dd */
+    double trstb = stb[0] + stb[4] + stb[8];
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l)
+            ddb[k * 3 + l] += lam * trstb * (k == l) + c.G * (stb[k * 3 + l] + stb[l * 3 + k]);
+    /* sR_ij = s_ij + s_ik dw_jk + s_jk dw_ik */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double g = stb[i * 3 + j];
+            sb0[i * 3 + j] += g;
+            for (int k = 0; k < 3; ++k) {
+                sb0[i * 3 + k] += g * dw[j * 3 + k];
+                dwb[j * 3 + k] += g * s[i * 3 + k];
+                sb0[j * 3 + k] += g * dw[i * 3 + k];
+                dwb[i * 3 + k] += g * s[j * 3 + k];
+            }
+        }
+}
+
 /* ------------------------------------------------------------------------- */
 /* G2P (Sec. 2.2, Appendix B): velocity, affine matrix B_p, velocity         */
 /* gradient, position, deformation gradient, density and stress (USL).       */
@@ -612,11 +724,13 @@ static double tait_dpdrho(const orc_params *P, double rho)
 }
 
 int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, const double *B,
-                 const double *rho,
+                 const double *rho, const double *sigma,
                  const double *xb1, const double *vb1, const double *Bb1, const double *rhob1,
-                 double *xb0, double *vb0, double *Bb0, double *rhob0, double **mu_bar)
+                 const double *sigb1,
+                 double *xb0, double *vb0, double *Bb0, double *rhob0, double *sigb0, double **mu_bar)
 {
-    if (P->material != 0) return -2;
+    const int sand = P->material == 1;
+    if (sand && (!sigma || !sigb1 || !sigb0)) return -2;
     int d = P->dim;
     long G = orc_num_nodes(P);
     double dt = P->dt;
@@ -629,8 +743,12 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
     if (!gm || !gq || !gf || !gu || !gv || !gvb || !gqb || !gfb || !gmb) return -1;
     double *sig = calloc(n * 9, sizeof(double));
     for (long p = 0; p < n; ++p) {
-        double pr = orc_tait_pressure(P, rho[p]);
-        for (int a = 0; a < 3; ++a) sig[p * 9 + a * 4] = -pr;
+        if (sand) {
+            for (int q = 0; q < 9; ++q) sig[p * 9 + q] = sigma[p * 9 + q];
+        } else {
+            double pr = orc_tait_pressure(P, rho[p]);
+            for (int a = 0; a < 3; ++a) sig[p * 9 + a * 4] = -pr;
+        }
     }
     /* forward: P2G and grid update, keeping the pre-wall velocity u */
     orc_p2g(P, n, x, v, B, rho, sig, gm, gq, gf);
@@ -672,6 +790,21 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
         double den = 1.0 + dt * trL;
         rhob0[p] = rhob1[p] / den;
         double trLb = -rhob1[p] * rho[p] * dt / (den * den);
+        /* adjoint of L through the Drucker-Prager update: dd = dt sym(L), dw = dt skew(L) */
+        double Lb[9] = {0.0};
+        if (sand) {
+            double dd[9] = {0.0}, dw[9] = {0.0}, ddb[9] = {0.0}, dwb[9] = {0.0};
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    dd[a * 3 + b] = 0.5 * (L[a * d + b] + L[b * d + a]) * dt;
+                    dw[a * 3 + b] = 0.5 * (L[a * d + b] - L[b * d + a]) * dt;
+                }
+            orc_dp_vjp(P, dd, dw, sigma + p * 9, sigb1 + p * 9, sigb0 + p * 9, ddb, dwb);
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b)
+                    Lb[a * d + b] = 0.5 * dt * (ddb[a * 3 + b] + ddb[b * 3 + a] + dwb[a * 3 + b] - dwb[b * 3 + a]);
+        }
+        for (int a = 0; a < d; ++a) Lb[a * d + a] += trLb;
         const double *Bb = Bb1 + p * d * d;
         for (int k = 0; k < S.count; ++k) {
             long i = S.node[k];
@@ -682,9 +815,13 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
                 double via = gv[i * 3 + a];
                 double Br = 0.0;
                 for (int b = 0; b < d; ++b) Br += Bb[a * d + b] * r[b];
-                gvb[i * 3 + a] += phi * vbt[a] + phi * Br + trLb * S.grad[k][a];
+                double Lg = 0.0;
+                for (int b = 0; b < d; ++b) {
+                    Lg += Lb[a * d + b] * S.grad[k][b];
+                    gradb[b] += Lb[a * d + b] * via;
+                }
+                gvb[i * 3 + a] += phi * vbt[a] + phi * Br + Lg;
                 phib += vbt[a] * via + Br * via;
-                gradb[a] += trLb * via;
                 for (int b = 0; b < d; ++b) xb0[p * d + b] += -Bb[a * d + b] * phi * via;
             }
             double H[9];
@@ -743,8 +880,9 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
         moment_matrix(P, xp, &S, D);
         invert(d, D, Dinv);
         matmul(d, B + p * d * d, Dinv, M);
-        double Vp = mp / rho[p], pr = orc_tait_pressure(P, rho[p]);
+        double Vp = mp / rho[p], pr = sand ? 0.0 : orc_tait_pressure(P, rho[p]);
         double Vb = 0.0, prb = 0.0;
+        const double *sp = sig + p * 9;
         for (int k = 0; k < S.count; ++k) {
             long i = S.node[k];
             double phi = S.phi[k], r[3];
@@ -760,10 +898,18 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
                     Mb[a * d + b] += phi * mp * qb * r[b];
                     xb0[p * d + b] += -phi * mp * qb * M[a * d + b];
                 }
-                /* f_a = V p grad_a (sigma = -p I) */
-                gradb[a] += Vp * pr * fb;
-                Vb += pr * fb * S.grad[k][a];
-                prb += Vp * fb * S.grad[k][a];
+                /* f_a = -V sigma_ab grad_b (fluid: sigma = -p I, f_a = V p grad_a) */
+                if (sand) {
+                    for (int b = 0; b < d; ++b) {
+                        gradb[b] += -Vp * sp[a * 3 + b] * fb;
+                        Vb += -sp[a * 3 + b] * S.grad[k][b] * fb;
+                        sigb0[p * 9 + a * 3 + b] += -Vp * S.grad[k][b] * fb;
+                    }
+                } else {
+                    gradb[a] += Vp * pr * fb;
+                    Vb += pr * fb * S.grad[k][a];
+                    prb += Vp * fb * S.grad[k][a];
+                }
             }
             double H[9];
             stencil_hessian(P, xp, &S, k, H);
@@ -780,7 +926,7 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
                 for (int c = 0; c < d; ++c) s += Mb[a * d + c] * Dinv[b * d + c];
                 Bb0[p * d * d + a * d + b] = s;
             }
-        rhob0[p] += Vb * (-mp / (rho[p] * rho[p])) + prb * tait_dpdrho(P, rho[p]);
+        rhob0[p] += Vb * (-mp / (rho[p] * rho[p])) + (sand ? 0.0 : prb * tait_dpdrho(P, rho[p]));
     }
     free(gm); free(gq); free(gf); free(gu); free(gv); free(gvb); free(gqb); free(gfb); free(gmb); free(sig);
     return 0;
