@@ -175,14 +175,13 @@ def dam_break_2d(n_cells: int = 64, width: float = 0.25, height: float = 0.5,
 def granular_cylinder_3d(n_cells: Tuple[int, int, int] = (256, 256, 128), radius_cells: float = 38,
                          height_cells: float = 76, ppc_axis: int = 2, seed: int = 0,
                          dt: float = 1.0e-5, floor_mu: float = 0.4, steps: int = 1000,
-                         sort_every: int = 16) -> Workload:
+                         sort_every: int = 16, dx: float = 1.0 / 256.0) -> Workload:
     """Drucker-Prager sand cylinder on the floor at the domain centre (dx = 1/256 m).
 
     Radius 38 dx and height 76 dx at 2 points per cell and axis give 2,761,536
     particles on the 256 x 256 x 128 grid; radius 30 dx and height 60 dx on
     192 x 192 x 96 give 1,356,480.
     """
-    dx = 1.0 / 256.0
     cx = 0.5 * n_cells[0] * dx
     cy = 0.5 * n_cells[1] * dx
     r = radius_cells * dx
@@ -213,9 +212,31 @@ def dam_break_inverse_2d(n_cells: int = 128, n_seg: int = 32, n_track: int = 64,
     return w
 
 
+def granular_inverse_3d(n_cells: Tuple[int, int, int] = (192, 192, 96), radius_cells: float = 30,
+                        height_cells: float = 60, patches: Tuple[int, int] = (16, 16), n_track: int = 128,
+                        n_obs: int = 10, steps: int = 600, seed: int = 0, checkpoint_every: int = 60,
+                        dt: float = 1.0e-5, dx: float = 1.0 / 256.0) -> Workload:
+    """Granular collapse with a patch-wise basal friction field and tracked particles.
+
+    The 3D inverse problem: floor friction over patches x patches, drawn
+    uniformly from [0.1, 0.6) by seed; n_track tracked particles observed at
+    n_obs equally spaced steps.
+    """
+    w = granular_cylinder_3d(n_cells, radius_cells, height_cells, seed=seed, dt=dt, steps=steps, dx=dx,
+                             floor_mu=0.0)
+    w.name = f"granular_inverse_3d_{n_cells[0]}x{n_cells[1]}x{n_cells[2]}"
+    mu = friction_field(patches[0] * patches[1], seed)
+    w.friction = [(4, tuple(patches), mu)]
+    ids = tracked_particles(w.x, n_track, seed, np.array(w.extras["body_lo"]), np.array(w.extras["body_hi"]))
+    obs_steps = [steps * (k + 1) // n_obs for k in range(n_obs)]
+    w.extras.update(track_ids=ids, obs_steps=obs_steps, mu_true=mu, checkpoint_every=checkpoint_every)
+    return w
+
+
 WORKLOADS = {
     "dam_break_2d_64": lambda: dam_break_2d(64),
     "granular_cylinder_3d_256x256x128": lambda: granular_cylinder_3d(),
     "dam_break_inverse_2d_128": lambda: dam_break_inverse_2d(128),
     "granular_cylinder_3d_192x192x96": lambda: granular_cylinder_3d((192, 192, 96), 30, 60, steps=600),
+    "granular_inverse_3d_192x192x96": lambda: granular_inverse_3d(),
 }

@@ -1,0 +1,21 @@
+"""Long 3D run: runout and deposit height of the granular collapse, FP32 within
+1 % of FP64 (the parity gate for runs the oracle cannot reach)."""
+import numpy as np
+import pytest
+
+from paper_2507_04192_gb300 import inputs, longrun
+
+pytestmark = pytest.mark.gpu
+
+
+def test_collapse_to_rest_fp32_within_one_percent_of_fp64():
+    # the 2.76M-particle column at a quarter of the resolution (64 x 64 x 32,
+    # dx = 1/64 m, same physical size), 1 s of physical time
+    w = inputs.granular_cylinder_3d((64, 64, 32), 9.5, 19, dt=4e-5, dx=1 / 64)
+    out = longrun.compare(w, 25_000)
+    assert out["fp32"]["finite"] and out["fp64"]["finite"]
+    # the column collapsed and spread
+    assert out["fp64"]["H_f"] < 0.8 * out["initial"]["H"]
+    assert out["fp64"]["R_f"] > 1.3 * out["initial"]["R"]
+    assert out["rel_diff"]["R_f"] <= 0.01, out
+    assert out["rel_diff"]["H_f"] <= 0.01, out
