@@ -248,6 +248,22 @@ def secondary_measurements(stream, dev):
                       "total_over_forward": adj / fwd,
                       "note": "adjoint_ms = checkpointed forward + per-segment recompute + reverse sweep; "
                               "adjoint_over_forward counts the recompute and reverse sweep only"}
+    # adjoint / forward of the 3D granular inverse problem (1.36M particles, 600 steps, checkpoint 60)
+    w3 = inputs.granular_inverse_3d()
+    mu3 = w3.extras["mu_true"]
+    z3 = np.zeros((len(w3.extras["obs_steps"]), len(w3.extras["track_ids"]), 3))
+    steps3 = max(w3.extras["obs_steps"])
+    sim = mpm.Simulation.from_workload(w3, mpm.MPM_FP32, stream=stream.cuda_stream)
+    mpm.mpm_save_state(sim.ctx, 0)
+    mpm.mpm_set_observations(sim.ctx, w3.extras["track_ids"], w3.extras["obs_steps"], z3)
+    fwd3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0), sim.step(steps3))) for _ in range(2))
+    adj3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
+                                          mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3)))) for _ in range(2))
+    sim.close()
+    out["adjoint_3d"] = {"workload": f"granular_inverse_3d_192x192x96 ({w3.n} particles, {steps3} steps, "
+                                     f"checkpoint 60, 16x16 floor patches, fp32)",
+                         "forward_ms": fwd3, "adjoint_ms": adj3, "adjoint_over_forward": (adj3 - fwd3) / fwd3,
+                         "total_over_forward": adj3 / fwd3}
     # batched forward (training data)
     wb = inputs.dam_break_2d(96)
     B, nb, bsteps = 256, wb.n, 300

@@ -189,9 +189,12 @@ int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_ob
  * backwards, recomputing each segment's states from its checkpoint and
  * applying the adjoint of each step.  Writes the loss and dL/dmu (the wall's
  * n_seg[0] x n_seg[1] coefficients, set by mpm_set_friction_field) to host
- * memory and leaves the context at the state after n_steps steps.  Weakly
- * compressible fluid, batch 1.  Device memory: checkpoints of
- * (2 dim + dim^2 + 1) reals per particle each, plus checkpoint_every states.
+ * memory and leaves the context at the state after n_steps steps.  Both
+ * materials (the adjoint state is (x, v, C, rho) for the fluid and (x, v, C,
+ * rho, sigma) for Drucker-Prager; the zone and contact branches of the forward
+ * step are held fixed), batch 1.  Device memory: checkpoints of
+ * (2 dim + dim^2 + 1) reals per particle each (+ 6 for Drucker-Prager), plus
+ * checkpoint_every states.
  */
 int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, double *loss_out,
                      double *dL_dmu_out);

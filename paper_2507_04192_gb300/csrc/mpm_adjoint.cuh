@@ -1,6 +1,8 @@
-// Adjoint (reverse-mode) kernels of the explicit step for the weakly
-// compressible fluid: the vector-Jacobian product of one step S^t -> S^{t+1}
-// (the recursion of Eq. dzda, Sec. 3.1) with S = (x, v, C, rho), and the
+// Adjoint (reverse-mode) kernels of the explicit step: the vector-Jacobian
+// product of one step S^t -> S^{t+1} (the recursion of Eq. dzda, Sec. 3.1) with
+// S = (x, v, C, rho) for the weakly compressible fluid and S = (x, v, C, rho,
+// sigma) for Drucker-Prager sand (F and the plastic strain do not feed the
+// dynamics and carry no adjoint), and the
 // gradient of the tracked-particle loss of Eq. inverse_loss (Sec. 3.2) with
 // respect to the wall friction coefficients (Eq. coulomb_friction, Sec. 5.3).
 //
@@ -36,8 +38,138 @@ template <class R> __device__ __forceinline__ void bspline_dd(R inv_dx, R ddw[3]
     ddw[2] = s;
 }
 
-// Component count of the adjoint state (x, v, C, rho).
+// Component count of the adjoint state: (x, v, C, rho), plus the six stress
+// components (xx, yy, zz, xy, xz, yz) for Drucker-Prager.
 template <int D> __host__ __device__ constexpr int adj_ncomp() { return 2 * D + D * D + 1; }
+__host__ __device__ inline int adj_ncomp_material(int dim, int material)
+{
+    return 2 * dim + dim * dim + 1 + (material == 1 ? 6 : 0);
+}
+
+// Reverse of dp_update (Appendix A) for one particle, on the six-component
+// stress: given the velocity gradient L (3 x 3, row-major), the stress s before
+// the update and the adjoint sb of the updated stress, adds the adjoint of s to
+// s_bar and of L to L_bar.  The zone and corner branches of the forward update
+// are held fixed.
+template <class R>
+__device__ __forceinline__ void dp_update_vjp(const Params<R> &P, const R L[9], const R s[6], const R sb[6],
+                                              R s_bar[6], R L_bar[9])
+{
+    const R dt = P.dt;
+    const R d0 = dt * L[0], d1 = dt * L[4], d2 = dt * L[8];
+    const R d3 = R(0.5) * dt * (L[1] + L[3]);
+    const R d4 = R(0.5) * dt * (L[2] + L[6]);
+    const R d5 = R(0.5) * dt * (L[5] + L[7]);
+    const R w01 = R(0.5) * dt * (L[1] - L[3]);
+    const R w02 = R(0.5) * dt * (L[2] - L[6]);
+    const R w12 = R(0.5) * dt * (L[5] - L[7]);
+    const R S00 = s[0], S11 = s[1], S22 = s[2], S01 = s[3], S02 = s[4], S12 = s[5];
+    const R lamK = P.K - R(2) / R(3) * P.G, twoG = R(2) * P.G;
+    // forward replay of the trial stress and its invariants
+    const R M00 = w01 * S01 + w02 * S02, M11 = -w01 * S01 + w12 * S12, M22 = -w02 * S02 - w12 * S12;
+    const R M01 = w01 * S11 + w02 * S12, M10 = -w01 * S00 + w12 * S02;
+    const R M02 = w01 * S12 + w02 * S22, M20 = -w02 * S00 - w12 * S01;
+    const R M12 = -w01 * S02 + w12 * S22, M21 = -w02 * S01 - w12 * S11;
+    const R lt = lamK * (d0 + d1 + d2);
+    R t[6];
+    t[0] = S00 + R(2) * M00 + lt + twoG * d0;
+    t[1] = S11 + R(2) * M11 + lt + twoG * d1;
+    t[2] = S22 + R(2) * M22 + lt + twoG * d2;
+    t[3] = S01 + M01 + M10 + twoG * d3;
+    t[4] = S02 + M02 + M20 + twoG * d4;
+    t[5] = S12 + M12 + M21 + twoG * d5;
+    const R sm = (t[0] + t[1] + t[2]) / R(3);
+    const R dev[6] = {t[0] - sm, t[1] - sm, t[2] - sm, t[3], t[4], t[5]};
+    const R tau = rsqrt_(R(0.5) * (dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]) +
+                         dev[3] * dev[3] + dev[4] * dev[4] + dev[5] * dev[5]);
+    const R fs = tau - P.k_phi + P.q_phi * sm;
+    const R ft = sm - P.sig_t;
+    const R h = tau - P.tau_P - P.alpha_P * (sm - P.sig_t);
+    // reverse through the return
+    R tb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, devb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    R smb = R(0), taub = R(0);
+    const R trb = sb[0] + sb[1] + sb[2];
+    if (fs <= R(0) && ft < R(0)) {                                   // Zone I: s' = t
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tb[k] = sb[k];
+    } else if ((fs > R(0) && ft < R(0)) || (h > R(0) && ft >= R(0))) {   // Zone II: s' = r dev + smn I
+        const R A = P.G + P.K * P.q_phi * P.q_psi;
+        const R smn = sm - P.K * P.q_psi * fs / A;
+        const bool corner = !P.dp_literal && smn > P.sig_t;
+        const R taun = corner ? P.tau_P : P.k_phi - P.q_phi * smn;
+        const R r = tau > R(0) ? taun / tau : R(0);
+        R rb = R(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            rb += sb[k] * dev[k];
+            devb[k] = r * sb[k];
+        }
+        R smnb = corner ? R(0) : trb, taunb = R(0);
+        if (tau > R(0)) {
+            if (!corner) taunb = rb / tau;
+            taub -= rb * taun / (tau * tau);
+        }
+        smnb -= P.q_phi * taunb;
+        smb += smnb * (R(1) - P.K * P.q_psi * P.q_phi / A);
+        taub -= smnb * P.K * P.q_psi / A;
+    } else {                                                         // Zone III
+        const bool corner = !P.dp_literal && tau > P.tau_P;
+        if (corner) {                                                // s' = (tau_P / tau) dev + sig_t I
+            R rb = R(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                rb += sb[k] * dev[k];
+                devb[k] = P.tau_P / tau * sb[k];
+            }
+            taub -= rb * P.tau_P / (tau * tau);
+        } else {                                                     // s' = dev + sig_t I
+#pragma unroll
+            for (int k = 0; k < 6; ++k) devb[k] = sb[k];
+        }
+    }
+    // tau = sqrt(dev_d . dev_d / 2 + dev_o . dev_o)
+    if (tau > R(0)) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) devb[k] += taub * dev[k] / tau * (k < 3 ? R(0.5) : R(1));
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tb[k] += devb[k];
+    smb -= devb[0] + devb[1] + devb[2];
+    tb[0] += smb / R(3);
+    tb[1] += smb / R(3);
+    tb[2] += smb / R(3);
+    // t -> S, M, d
+    R Sb[6] = {tb[0], tb[1], tb[2], tb[3], tb[4], tb[5]};
+    const R Mb00 = R(2) * tb[0], Mb11 = R(2) * tb[1], Mb22 = R(2) * tb[2];
+    const R Mb01 = tb[3], Mb10 = tb[3], Mb02 = tb[4], Mb20 = tb[4], Mb12 = tb[5], Mb21 = tb[5];
+    const R ltb = tb[0] + tb[1] + tb[2];
+    R db[6] = {twoG * tb[0] + lamK * ltb, twoG * tb[1] + lamK * ltb, twoG * tb[2] + lamK * ltb,
+               twoG * tb[3], twoG * tb[4], twoG * tb[5]};
+    // M -> S, w   (S index: 0 00, 1 11, 2 22, 3 01, 4 02, 5 12)
+    R wb01 = R(0), wb02 = R(0), wb12 = R(0);
+    wb01 += Mb00 * S01; Sb[3] += Mb00 * w01; wb02 += Mb00 * S02; Sb[4] += Mb00 * w02;
+    wb01 += Mb01 * S11; Sb[1] += Mb01 * w01; wb02 += Mb01 * S12; Sb[5] += Mb01 * w02;
+    wb01 += Mb02 * S12; Sb[5] += Mb02 * w01; wb02 += Mb02 * S22; Sb[2] += Mb02 * w02;
+    wb01 -= Mb10 * S00; Sb[0] -= Mb10 * w01; wb12 += Mb10 * S02; Sb[4] += Mb10 * w12;
+    wb01 -= Mb11 * S01; Sb[3] -= Mb11 * w01; wb12 += Mb11 * S12; Sb[5] += Mb11 * w12;
+    wb01 -= Mb12 * S02; Sb[4] -= Mb12 * w01; wb12 += Mb12 * S22; Sb[2] += Mb12 * w12;
+    wb02 -= Mb20 * S00; Sb[0] -= Mb20 * w02; wb12 -= Mb20 * S01; Sb[3] -= Mb20 * w12;
+    wb02 -= Mb21 * S01; Sb[3] -= Mb21 * w02; wb12 -= Mb21 * S11; Sb[1] -= Mb21 * w12;
+    wb02 -= Mb22 * S02; Sb[4] -= Mb22 * w02; wb12 -= Mb22 * S12; Sb[5] -= Mb22 * w12;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_bar[k] += Sb[k];
+    // d, w -> L
+    const R hdt = R(0.5) * dt;
+    L_bar[0] += dt * db[0];
+    L_bar[4] += dt * db[1];
+    L_bar[8] += dt * db[2];
+    L_bar[1] += hdt * (db[3] + wb01);
+    L_bar[3] += hdt * (db[3] - wb01);
+    L_bar[2] += hdt * (db[4] + wb02);
+    L_bar[6] += hdt * (db[4] - wb02);
+    L_bar[5] += hdt * (db[5] + wb12);
+    L_bar[7] += hdt * (db[5] - wb12);
+}
 
 // Walls in order x-, x+, y-, y+, (z-, z+), floor last, applied to u (in place);
 // chain[q] receives the input of wall q.
@@ -142,12 +274,14 @@ __global__ void k_adj_save(const Params<R> P, const R *__restrict__ S, const int
                            R *__restrict__ dst)
 {
     constexpr int NA = adj_ncomp<D>();
+    const int nsig = P.material == 1 ? 6 : 0;
     const int64_t n = P.n, np = P.npad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[i];
 #pragma unroll
         for (int c = 0; c < NA - 1; ++c) dst[c * n + o] = S[c * np + i];
         dst[(NA - 1) * n + o] = S[P.off_rho * np + i];
+        for (int k = 0; k < nsig; ++k) dst[(NA + k) * n + o] = S[(P.off_sig + k) * np + i];
     }
 }
 
@@ -156,12 +290,14 @@ __global__ void k_adj_restore(const Params<R> P, R *__restrict__ S, const int32_
                               const R *__restrict__ src)
 {
     constexpr int NA = adj_ncomp<D>();
+    const int nsig = P.material == 1 ? 6 : 0;
     const int64_t n = P.n, np = P.npad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[i];
 #pragma unroll
         for (int c = 0; c < NA - 1; ++c) S[c * np + i] = src[c * n + o];
         S[P.off_rho * np + i] = src[(NA - 1) * n + o];
+        for (int k = 0; k < nsig; ++k) S[(P.off_sig + k) * np + i] = src[(NA + k) * n + o];
     }
 }
 
@@ -318,10 +454,12 @@ __global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const
         for (int a = 0; a < D; ++a) x[a] = st[a * n + p];
         AdjStencil<R, D> s;
         adj_stencil<R, D>(P, x, s);
-        // forward quantities: v_p and tr L
-        R vp[D], trL = R(0);
+        // forward quantities: v_p and L
+        R vp[D], Lf[D * D];
 #pragma unroll
         for (int a = 0; a < D; ++a) vp[a] = R(0);
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Lf[q] = R(0);
 #pragma unroll
         for (int k = 0; k < Geo<D>::STENCIL; ++k) {
             const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
@@ -335,9 +473,13 @@ __global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 vp[a] += w * vi[a];
-                trL += vi[a] * g[a];
+#pragma unroll
+                for (int b = 0; b < D; ++b) Lf[a * D + b] += vi[a] * g[b];
             }
         }
+        R trL = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) trL += Lf[a * D + a];
         // adjoints of the outputs
         R xb[D], vbt[D], Cb[D * D];
 #pragma unroll
@@ -355,6 +497,34 @@ __global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const
         const R rb1 = lam_in[JR * n + p];
         const R rhob = rb1 / den;
         const R trLb = -rb1 * rho * P.dt / (den * den);
+        // adjoint of L: the density path, and for Drucker-Prager the stress update
+        R Lb[D * D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Lb[q] = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) Lb[a * D + a] = trLb;
+        if (P.material == 1) {
+            R L3[9], Lb3[9], s6[6], sb6[6], s0b[6];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) L3[q] = Lb3[q] = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) L3[a * 3 + b] = Lf[a * D + b];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                s6[k] = st[(JR + 1 + k) * n + p];
+                sb6[k] = lam_in[(JR + 1 + k) * n + p];
+                s0b[k] = R(0);
+            }
+            dp_update_vjp<R>(P, L3, s6, sb6, s0b, Lb3);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) Lb[a * D + b] += Lb3[a * 3 + b];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lam_out[(JR + 1 + k) * n + p] = s0b[k];
+        }
         // x_bar through (k - fx): C = (4 / dx) sum w v (k - fx) and dfx/dx = 1/dx
 #pragma unroll
         for (int b = 0; b < D; ++b) {
@@ -381,9 +551,18 @@ __global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const
                 R cr = R(0);
 #pragma unroll
                 for (int b = 0; b < D; ++b) cr += Cb[a * D + b] * (R(kk[b]) - s.fx[b]);
-                vb[a] = w * vbt[a] + cscale * w * cr + trLb * g[a];
+                R Lg = R(0);
+#pragma unroll
+                for (int b = 0; b < D; ++b) Lg += Lb[a * D + b] * g[b];
+                vb[a] = w * vbt[a] + cscale * w * cr + Lg;
                 wbar += vbt[a] * vi[a] + cscale * cr * vi[a];
-                gbar[a] = trLb * vi[a];
+            }
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                R gb = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) gb += Lb[a * D + b] * vi[a];
+                gbar[b] = gb;
             }
 #pragma unroll
             for (int b = 0; b < D; ++b) {
@@ -454,8 +633,24 @@ __global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const
         for (int q = 0; q < D * D; ++q) C[q] = st[(JC + q) * n + p];
         const R rho = st[JR * n + p];
         const R mp = P.mass;
-        const R pr = tait(P, rho);
-        const R sforce = P.dt * mp / rho * pr;             // P += sforce * grad w  (sigma = -p I)
+        const bool sand = P.material == 1;
+        const R pr = sand ? R(0) : tait(P, rho);
+        const R sforce = P.dt * mp / rho * pr;             // fluid: P += sforce * grad w  (sigma = -p I)
+        // Drucker-Prager: P_a += Fm_ab grad_b w with Fm = -dt (m / rho) sigma
+        R Fm[D * D], Fmb[D * D];
+        if (sand) {
+            R s6[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s6[k] = st[(JR + 1 + k) * n + p];
+            const R c = -P.dt * mp / rho;
+            const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) Fm[a * D + b] = c * s6[ix[a][b]];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Fmb[q] = R(0);
         AdjStencil<R, D> s;
         adj_stencil<R, D>(P, x, s);
         R xb[D], vb[D], Cb[D * D], sb = R(0);
@@ -492,8 +687,22 @@ __global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const
                     Cb[a * D + b] += mp * w * Pb[a] * rr[b];
                     xb[b] -= mp * w * Pb[a] * C[a * D + b];
                 }
-                gbar[a] = sforce * Pb[a];
-                sb += Pb[a] * g[a];
+                if (sand) {
+#pragma unroll
+                    for (int b = 0; b < D; ++b) Fmb[a * D + b] += Pb[a] * g[b];
+                } else {
+                    gbar[a] = sforce * Pb[a];
+                    sb += Pb[a] * g[a];
+                }
+            }
+            if (sand) {
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    R gb = R(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) gb += Fm[a * D + b] * Pb[a];
+                    gbar[b] = gb;
+                }
             }
 #pragma unroll
             for (int b = 0; b < D; ++b) {
@@ -502,6 +711,30 @@ __global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const
                 for (int a = 0; a < D; ++a) hb += H[b][a] * gbar[a];
                 xb[b] += wbar * g[b] + hb;
             }
+        }
+        if (sand) {
+            // Fm = -dt (m / rho) sigma: adjoints of the six stress components and of rho
+            const R c = -P.dt * mp / rho;
+            R s6b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, rhob = R(0);
+            const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    s6b[ix[a][b]] += c * Fmb[a * D + b];
+                    rhob -= Fmb[a * D + b] * Fm[a * D + b] / rho;
+                }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                lam_out[a * n + p] += xb[a];
+                lam_out[(JV + a) * n + p] = vb[a];
+            }
+#pragma unroll
+            for (int q = 0; q < D * D; ++q) lam_out[(JC + q) * n + p] = Cb[q];
+            lam_out[JR * n + p] += rhob;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lam_out[(JR + 1 + k) * n + p] += s6b[k];
+            continue;
         }
         // sforce = dt m p(rho) / rho
         const R r1 = rho * P.inv_rho0;

@@ -485,7 +485,7 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
     if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
     if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk + kScanSegments, "histogram");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, ds.max_tiles, "tile list");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, 2 * ds.max_tiles, "tile list");     // key order + G2P order
     if (rc == MPM_OK) rc = dalloc(c, &ds.perm, n, "permutation");
     if (rc == MPM_OK) rc = dalloc(c, &ds.posmap, n, "position map");
     if (rc == MPM_OK) rc = dalloc(c, &ds.cell_off, (size_t)ds.max_tiles * (TN + 1), "cell offsets");
@@ -724,7 +724,6 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     if (!c || n_steps < 1 || checkpoint_every < 1 || !loss_out || !dL_dmu_out)
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: bad argument");
     if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no particles loaded");
-    if (c->mat.kind != MPM_FLUID) return fail(c, MPM_EINVAL, "mpm_step_adjoint: the adjoint covers the fluid");
     if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_step_adjoint: batch must be 1");
     if (wall < 0 || wall >= 2 * c->grid.dim || c->ds.mu_dev[wall] == nullptr)
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: the wall has no friction field");
@@ -735,7 +734,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     DevState &ds = c->ds;
     const int d = h.dim;
     const int K = checkpoint_every;
-    const int NA = 2 * d + d * d + 1;
+    const int NA = adj_ncomp_material(d, c->mat.kind == MPM_DRUCKER_PRAGER ? 1 : 0);
     const size_t rsz = h.precision == MPM_FP64 ? 8 : 4;
     const int64_t n = h.n;
     const size_t st_bytes = (size_t)NA * n * rsz;

@@ -95,7 +95,8 @@ struct DevState {
     int32_t *vals[2];
     uint32_t *hist;               // kRadixBins x n_sort_blocks
     int32_t *tile_start, *tile_end;   // per tile (batch x tiles_per_sim)
-    int4 *tiles;                  // compact non-empty tiles: (tile key, start, count, 0)
+    int4 *tiles;                  // compact non-empty tiles: (tile key, start, count, 0) in key order,
+                                  // then (at + max_tiles) the same tiles largest first (G2P order)
     int64_t max_tiles;
     int32_t *perm;                // gather permutation of the last sort
     int32_t *posmap;              // per particle in (cell, rank) order: its slot relative to the tile start

@@ -1297,7 +1297,7 @@ template <class R, int D> struct Launch {
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
         k_g2p<R, D><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V,
-                                                                     ds.tiles, ds.counters, ds.status);
+                                                                     ds.tiles + ds.max_tiles, ds.counters, ds.status);
     }
     static void get_field(const HostParams &h, DevState &ds, int field, double *out)
     {

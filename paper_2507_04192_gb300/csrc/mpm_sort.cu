@@ -234,6 +234,38 @@ __global__ void __launch_bounds__(1024) k_build_tiles(const int32_t *__restrict_
     if (threadIdx.x == 0) counters[1] = (int32_t)(carry < max_tiles ? carry : max_tiles);
 }
 
+// Copies the compact tile list, ordered by particle count with the largest
+// first, to tiles + max_tiles: the persistent G2P blocks claim tiles from that
+// copy in order and so finish together (longest-processing-time-first).  P2G
+// keeps the spatial order of the original list, whose neighbouring tiles share
+// the grid nodes of their windows.  Counting sort on buckets of 32 particles.
+__global__ void __launch_bounds__(1024) k_order_tiles(int4 *__restrict__ tiles, const int32_t *__restrict__ counters,
+                                                      int64_t max_tiles)
+{
+    constexpr int NB = 128;
+    __shared__ int32_t hist[NB];
+    const int n = counters[1];
+    int4 *out = tiles + max_tiles;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    auto bucket = [](int cnt) { return NB - 1 - min(cnt >> 5, NB - 1); };
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[bucket(tiles[i].z)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int b = 0; b < NB; ++b) {
+            const int h = hist[b];
+            hist[b] = sum;
+            sum += h;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int4 t = tiles[i];
+        out[atomicAdd(&hist[bucket(t.z)], 1)] = t;
+    }
+}
+
 // Reorder each tile from (cell, rank) order to (group, rank, cell) order, where
 // a group is NG consecutive cells (an 8 x 8 x 2 slab in 3D, the whole tile in
 // 2D) and rank is a particle's position within its cell.  The particles of
@@ -380,6 +412,7 @@ void build_tiles(const HostParams &hp, DevState &ds)
                                                                  ds.tile_end);
     k_build_tiles<<<1, 1024, 0, ds.stream>>>(ds.tile_start, ds.tile_end, ntiles, ds.tiles, ds.max_tiles,
                                              ds.counters, ds.status);
+    k_order_tiles<<<1, 1024, 0, ds.stream>>>(ds.tiles, ds.counters, ds.max_tiles);
     int64_t tb = ds.max_tiles < (int64_t)ds.num_sms * 8 ? ds.max_tiles : (int64_t)ds.num_sms * 8;
     if (tb < 1) tb = 1;
     if (hp.dim == 2)
