@@ -21,11 +21,15 @@ class FrictionInversion:
     """One inversion problem: initial particles, observations, friction wall."""
 
     def __init__(self, workload, z_obs: np.ndarray, precision: int = mpm.MPM_FP32, checkpoint_every: int = 50,
-                 wall: int = 2, n_seg: Optional[int] = None, stream: int = 0):
+                 wall: Optional[int] = None, n_seg: Optional[int] = None, stream: int = 0):
         w = workload
         self.w = w
-        self.wall = wall
+        # the friction wall and its segment layout: from the workload's friction field
+        # (floor segments in 2D, floor patches in 3D) unless given
+        fw, shape = (w.friction[0][0], tuple(w.friction[0][1])) if w.friction else (2 * (w.dim - 1), None)
+        self.wall = fw if wall is None else wall
         self.n_seg = int(n_seg if n_seg is not None else len(w.extras["mu_true"]))
+        self.seg_shape = shape if shape is not None and shape[0] * shape[1] == self.n_seg else (self.n_seg, 1)
         self.steps = int(max(w.extras["obs_steps"]))
         self.K = int(checkpoint_every)
         self.sim = mpm.Simulation(w.dim, w.n_cells, w.dx, w.dt, w.gravity, w.material, precision, w.sort_every,
@@ -39,7 +43,7 @@ class FrictionInversion:
     def loss_and_grad(self, mu: np.ndarray):
         mu = np.clip(np.asarray(mu, dtype=np.float64).reshape(-1), 0.0, None)
         mpm.mpm_restore_state(self.sim.ctx, 0)
-        self.sim.set_friction(self.wall, (self.n_seg, 1), mu)
+        self.sim.set_friction(self.wall, self.seg_shape, mu)
         self.evaluations += 1
         return mpm.mpm_step_adjoint(self.sim.ctx, self.steps, self.K, self.wall, self.n_seg)
 

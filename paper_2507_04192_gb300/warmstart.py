@@ -47,9 +47,52 @@ class Setup:
             w.friction = [(2, (self.n_seg, 1), mu)]
         return w
 
+    feature_axes = (0,)                      # displacement along the floor
+
     @property
     def n_features(self):
-        return self.n_obs * self.n_track
+        return self.n_obs * self.n_track * len(self.feature_axes)
+
+    def scale(self, w):
+        return float(w.extras["body_hi"][0] - w.extras["body_lo"][0])
+
+
+@dataclass
+class Setup3D:
+    """The 3D granular counterpart: a Drucker-Prager cylinder on a floor whose
+    friction is piecewise constant over patches x patches (Sec. 5.3 carried to
+    3D); features are the tracks' displacements along both floor axes."""
+    n_cells: tuple = (64, 64, 32)
+    dx: float = 1.0 / 64.0
+    radius_cells: float = 10.0
+    height_cells: float = 20.0
+    patches: int = 4
+    n_track: int = 64
+    n_obs: int = 10
+    steps: int = 1500
+    dt: float = 4.0e-5
+    checkpoint_every: int = 100
+    geometry_seed: int = 0
+    feature_axes = (0, 1)
+
+    @property
+    def n_seg(self):
+        return self.patches * self.patches
+
+    def workload(self, mu_seed: Optional[int] = None):
+        w = inputs.granular_inverse_3d(tuple(self.n_cells), self.radius_cells, self.height_cells,
+                                       patches=(self.patches, self.patches), n_track=self.n_track, n_obs=self.n_obs,
+                                       steps=self.steps, seed=self.geometry_seed,
+                                       checkpoint_every=self.checkpoint_every, dt=self.dt, dx=self.dx)
+        if mu_seed is not None:
+            mu = inputs.friction_field(self.n_seg, mu_seed, MU_LO, MU_HI)
+            w.extras["mu_true"] = mu
+            w.friction = [(4, (self.patches, self.patches), mu)]
+        return w
+
+    @property
+    def n_features(self):
+        return self.n_obs * self.n_track * len(self.feature_axes)
 
     def scale(self, w):
         return float(w.extras["body_hi"][0] - w.extras["body_lo"][0])
@@ -62,11 +105,12 @@ def observe_batch(w, mus: np.ndarray, precision=mpm.MPM_FP32, stream: int = 0) -
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     B, n_seg = mus.shape
     n = w.x.shape[0]
+    wall, shape = (w.friction[0][0], tuple(w.friction[0][1])) if w.friction else (2 * (w.dim - 1), (n_seg, 1))
     sim = mpm.Simulation(w.dim, w.n_cells, w.dx, w.dt, w.gravity, w.material, precision, w.sort_every, batch=B,
                          stream=stream)
     try:
         sim.load(np.tile(w.x, (B, 1)), None, w.particle_volume, np.repeat(np.arange(B, dtype=np.int32), n))
-        sim.set_friction(2, (n_seg, 1), mus.reshape(-1))
+        sim.set_friction(wall, shape, mus.reshape(-1))
         ids = (np.arange(B)[:, None] * n + np.asarray(w.extras["track_ids"])[None, :])
         out, t = [], 0
         for s in w.extras["obs_steps"]:
@@ -82,8 +126,9 @@ def features(setup: Setup, w, z_obs: np.ndarray) -> np.ndarray:
     """Network input from observations z_obs (n_obs, n_track, dim) or a batch of them."""
     z = np.asarray(z_obs, dtype=np.float64)
     x0 = w.x[np.asarray(w.extras["track_ids"])]
-    d = (z[..., 0] - x0[:, 0]) / setup.scale(w)
-    return d.reshape(d.shape[:-2] + (-1,)).astype(np.float32)
+    ax = list(setup.feature_axes)
+    d = (z[..., ax] - x0[:, ax]) / setup.scale(w)            # (..., n_obs, n_track, n_axes)
+    return d.reshape(d.shape[:-3] + (-1,)).astype(np.float32)
 
 
 def generate(setup: Setup, n_runs: int, batch: int = 256, first_seed: int = TRAIN_SEED_BASE,
@@ -198,10 +243,13 @@ def main(argv=None):
     ap.add_argument("--held-out", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--max-iters", type=int, default=300)
+    ap.add_argument("--setup", choices=["2d", "3d"], default="2d",
+                    help="2d: 96^2 dam breaks, 32 floor segments; 3d: 64x64x32 granular collapses, 4x4 floor patches")
+    ap.add_argument("--batch", type=int, default=256)
     args = ap.parse_args(argv)
-    setup = Setup()
+    setup = Setup() if args.setup == "2d" else Setup3D()
     t0 = time.perf_counter()
-    X, Y = generate(setup, args.runs)
+    X, Y = generate(setup, args.runs, batch=args.batch)
     t1 = time.perf_counter()
     net = WarmStartNet(setup.n_features, setup.n_seg)
     hist = net.fit(X, Y, epochs=args.epochs)
@@ -209,7 +257,7 @@ def main(argv=None):
     rows = compare(setup, net, range(1, args.held_out + 1), max_iters=args.max_iters)
     net.close()
     summary = {
-        "setup": setup.__dict__, "runs": args.runs, "generate_s": t1 - t0, "train_s": t2 - t1,
+        "setup": {k: v for k, v in setup.__dict__.items()}, "runs": args.runs, "generate_s": t1 - t0, "train_s": t2 - t1,
         "train_loss": [hist[0], hist[-1]],
         "uniform": {"converged": sum(r["converged_uniform"] for r in rows),
                     "median_iters": float(np.median([r["iters_uniform"] for r in rows])),
