@@ -7,9 +7,9 @@
 // respect to the wall friction coefficients (Eq. coulomb_friction, Sec. 5.3).
 //
 // The reverse sweep works on particle states stored in load order (id order),
-// independent of the forward pass's sorted order, with its own grid buffers:
-//   k_adj_p2g      P2G of S^t again (grid mass m and P = q + dt f_int)
-//   k_adj_grid     u = P / m + dt g and v = walls(u) per node
+// independent of the forward pass's sorted order; the grid of each step
+// (m, P = q + dt f_int and the post-wall velocity v) is the one the forward
+// recompute of the segment saved, so only the reverse kernels run:
 //   k_adj_g2p_bwd  adjoint of G2P: scatters v_bar to the grid, x_bar and
 //                  rho_bar partials to the particles
 //   k_adj_grid_bwd adjoint of the grid update: walls (and d/dmu), division
@@ -21,6 +21,19 @@
 #pragma once
 
 #include "mpm_kernels.cuh"
+
+// Resident blocks of 256 threads per SM the reverse particle kernels are compiled for.
+#ifndef MPM_ADJ_MINB
+#define MPM_ADJ_MINB 2
+#endif
+// 3D reverse particle kernels in separable (stencil-moment) form, and their
+// resident blocks per SM in single precision.
+#ifndef MPM_ADJ_SEPARABLE
+#define MPM_ADJ_SEPARABLE 1
+#endif
+#ifndef MPM_ADJ3_MINB
+#define MPM_ADJ3_MINB 2
+#endif
 
 namespace mpm {
 
@@ -335,58 +348,6 @@ __global__ void k_adj_zero(R *__restrict__ p, int64_t count)
         p[i] = R(0);
 }
 
-// Re-P2G of a load-order state into GA (m, P = q + dt f_int) with global atomics.
-template <class R, int D>
-__global__ void k_adj_p2g(const Params<R> P, const R *__restrict__ st, R4<R> *__restrict__ GA)
-{
-    const int64_t n = P.n;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        P2GFactors<R, D> f;
-        p2g_factors<R, D>(P, [&](int j) { return st[(int64_t)j * n + p]; }, f);
-#pragma unroll
-        for (int k = 0; k < Geo<D>::STENCIL; ++k) {
-            const int k0 = k % 3, k1 = (k / 3) % 3, k2 = k / 9;
-            R m, mom[D];
-            p2g_node<R, D>(f, P.mass, k0, k1, k2, m, mom);
-            const int kk[3] = {k0, k1, k2};
-            int a3[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < D; ++a) a3[a] = f.b[a] + 2 + kk[a];
-            red_add4(&GA[lin3<D>(a3, P.G_nodes)], m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
-        }
-    }
-}
-
-// Per node: u = P / m + dt g (m > m_eps, else 0) and v = walls(u).
-template <class R, int D>
-__global__ void k_adj_grid(const Params<R> P, const R4<R> *__restrict__ GA, R4<R> *__restrict__ GU,
-                           R4<R> *__restrict__ GV)
-{
-    const int64_t N = P.nodes_per_sim;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> acc = GA[i];
-        R vel[3] = {R(0), R(0), R(0)};
-        if (acc.x > P.m_eps) {
-            const R inv_m = R(1) / acc.x;
-            vel[0] = acc.y * inv_m + P.dt * P.gravity[0];
-            vel[1] = acc.z * inv_m + P.dt * P.gravity[1];
-            if (D == 3) vel[2] = acc.w * inv_m + P.dt * P.gravity[2];
-        }
-        GU[i] = R4<R>{vel[0], vel[1], vel[2], R(0)};
-        int a3[3] = {0, 0, 0};
-        int64_t r = i;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            a3[a] = (int)(r % P.G_nodes[a]);
-            r /= P.G_nodes[a];
-        }
-        R chain[2 * D][3];
-        bool applied[2 * D];
-        walls_forward<R, D>(P, 0, a3, vel, chain, applied);
-        GV[i] = R4<R>{vel[0], vel[1], vel[2], R(0)};
-    }
-}
-
 // Stencil data of one particle for the reverse kernels.
 template <class R, int D> struct AdjStencil {
     int b[D];
@@ -442,7 +403,7 @@ __device__ __forceinline__ void adj_node(const AdjStencil<R, D> &s, const int kk
 // Adjoint of G2P for one particle: lam_in is the adjoint of S^{t+1}; writes the
 // G2P part of the adjoint of x and rho to lam_out and scatters v_bar to GVB.
 template <class R, int D>
-__global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GV,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GV,
                               const R *__restrict__ lam_in, R *__restrict__ lam_out, R4<R> *__restrict__ GVB)
 {
     const int64_t n = P.n;
@@ -581,8 +542,8 @@ __global__ void k_adj_g2p_bwd(const Params<R> P, const R *__restrict__ st, const
 
 // Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P).
 template <class R, int D>
-__global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, const R4<R> *__restrict__ GU,
-                               const R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB, MuBar mu_bar)
+__global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, const R4<R> *__restrict__ GVB,
+                               R4<R> *__restrict__ GAB, MuBar mu_bar)
 {
     const int64_t N = P.nodes_per_sim;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -591,8 +552,9 @@ __global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, 
             GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
             continue;
         }
-        const R4<R> u4 = GU[i];
-        R vel[3] = {u4.x, u4.y, u4.z};
+        const R inv_m0 = R(1) / acc.x;
+        R vel[3] = {acc.y * inv_m0 + P.dt * P.gravity[0], acc.z * inv_m0 + P.dt * P.gravity[1],
+                    D == 3 ? acc.w * inv_m0 + P.dt * P.gravity[2] : R(0)};
         int a3[3] = {0, 0, 0};
         int64_t r = i;
 #pragma unroll
@@ -617,7 +579,7 @@ __global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, 
 
 // Adjoint of P2G for one particle; completes lam_out (adjoint of S^t).
 template <class R, int D>
-__global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GAB,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GAB,
                               R *__restrict__ lam_out)
 {
     const int64_t n = P.n;
@@ -756,10 +718,356 @@ __global__ void k_adj_p2g_bwd(const Params<R> P, const R *__restrict__ st, const
     }
 }
 
+// ------------------------------------------------------------------ 3D reverse kernels in separable form
+
+// Stencil moments of a three-component node field f (and optionally the L
+// moments of a scalar node field g) in 3D, contracted one axis at a time.  With
+// node offsets k_a in {0, 1, 2}, weight w = w_0 w_1 w_2 and d_b w its b-derivative:
+//   V       = sum w f            M[b]    = sum k_b w f       L[b] = sum d_b w f
+//   Q[c][b] = sum k_c d_b w f    H[p]    = sum d_b d_a w f   (p: 00, 11, 22, 01, 02, 12)
+//   Lg[b]   = sum d_b w g
+// (all [..][comp]).  Per axis the factors are w, dw, k w, k dw and the constant
+// second derivative of the quadratic B-spline.
+template <class R> struct Mom3 {
+    R V[3], M[3][3], L[3][3], Q[3][3][3], H[6][3], Lg[3];
+};
+
+template <class R, bool WITH_G, class Load>
+__device__ __forceinline__ void stencil_moments3(const R w[3][3], const R dw[3][3], R inv_dx, Load load, Mom3<R> &m)
+{
+    const R s2 = inv_dx * inv_dx;
+    const R dd[3] = {s2, R(-2) * s2, s2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        m.V[c] = m.Lg[c] = R(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            m.M[b][c] = m.L[b][c] = R(0);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) m.Q[e][b][c] = R(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) m.H[q][c] = R(0);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+        // the slice's nine node values are loaded up front (their latencies overlap)
+        R fs[9][3], gs[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) load(q % 3, q / 3, k2, fs[q], gs[q]);
+        // prefixes over axes 0 and 1 (first letter axis 0, second axis 1)
+        R WW[3], DW[3], WD[3], JW[3], WJ[3], JDW[3], WJD[3], JD[3], DJ[3], DDW[3], WDD[3], DDp[3];
+        R gWW = R(0), gDW = R(0), gWD = R(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            WW[c] = DW[c] = WD[c] = JW[c] = WJ[c] = JDW[c] = WJD[c] = JD[c] = DJ[c] = DDW[c] = WDD[c] = DDp[c] = R(0);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            R XW[3], XD[3], XJ[3], XJD[3], XDD[3];
+            R gW = R(0), gD = R(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) XW[c] = XD[c] = XJ[c] = XJD[c] = XDD[c] = R(0);
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const R *f = fs[k1 * 3 + k0];
+                const R g = gs[k1 * 3 + k0];
+                const R a0 = w[0][k0], b0 = dw[0][k0];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    XW[c] += a0 * f[c];
+                    XD[c] += b0 * f[c];
+                    if (k0 > 0) {
+                        XJ[c] += R(k0) * a0 * f[c];
+                        XJD[c] += R(k0) * b0 * f[c];
+                    }
+                    XDD[c] += dd[k0] * f[c];
+                }
+                if (WITH_G) {
+                    gW += a0 * g;
+                    gD += b0 * g;
+                }
+            }
+            const R a1 = w[1][k1], b1 = dw[1][k1], j1 = R(k1) * a1, jd1 = R(k1) * b1, c1 = dd[k1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                WW[c] += a1 * XW[c];
+                DW[c] += a1 * XD[c];
+                WD[c] += b1 * XW[c];
+                JW[c] += a1 * XJ[c];
+                WJ[c] += j1 * XW[c];
+                JDW[c] += a1 * XJD[c];
+                WJD[c] += jd1 * XW[c];
+                JD[c] += b1 * XJ[c];
+                DJ[c] += j1 * XD[c];
+                DDW[c] += a1 * XDD[c];
+                WDD[c] += c1 * XW[c];
+                DDp[c] += b1 * XD[c];
+            }
+            if (WITH_G) {
+                gWW += a1 * gW;
+                gDW += a1 * gD;
+                gWD += b1 * gW;
+            }
+        }
+        const R a2 = w[2][k2], b2 = dw[2][k2], j2 = R(k2) * a2, jd2 = R(k2) * b2, c2 = dd[k2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            m.V[c] += a2 * WW[c];
+            m.M[0][c] += a2 * JW[c];
+            m.M[1][c] += a2 * WJ[c];
+            m.M[2][c] += j2 * WW[c];
+            m.L[0][c] += a2 * DW[c];
+            m.L[1][c] += a2 * WD[c];
+            m.L[2][c] += b2 * WW[c];
+            m.Q[0][0][c] += a2 * JDW[c];
+            m.Q[1][1][c] += a2 * WJD[c];
+            m.Q[2][2][c] += jd2 * WW[c];
+            m.Q[0][1][c] += a2 * JD[c];
+            m.Q[0][2][c] += b2 * JW[c];
+            m.Q[1][0][c] += a2 * DJ[c];
+            m.Q[1][2][c] += b2 * WJ[c];
+            m.Q[2][0][c] += j2 * DW[c];
+            m.Q[2][1][c] += j2 * WD[c];
+            m.H[0][c] += a2 * DDW[c];
+            m.H[1][c] += a2 * WDD[c];
+            m.H[2][c] += c2 * WW[c];
+            m.H[3][c] += a2 * DDp[c];
+            m.H[4][c] += b2 * DW[c];
+            m.H[5][c] += b2 * WD[c];
+        }
+        if (WITH_G) {
+            m.Lg[0] += a2 * gDW;
+            m.Lg[1] += a2 * gWD;
+            m.Lg[2] += b2 * gWW;
+        }
+    }
+}
+
+__device__ __forceinline__ int hidx3(int b, int a)
+{
+    return b == a ? b : (b + a == 1 ? 3 : (b + a == 2 ? 4 : 5));
+}
+
+// 3D adjoint of G2P (same outputs as k_adj_g2p_bwd): the forward velocity
+// moments and the x-derivatives of the weights enter through stencil moments of
+// the node velocities; only the scatter of v_bar runs node by node.
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
+    k_adj_g2p_bwd3(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GV,
+                   const R *__restrict__ lam_in, R *__restrict__ lam_out, R4<R> *__restrict__ GVB)
+{
+    constexpr int D = 3, JC = 2 * D, JR = 2 * D + D * D;
+    const int64_t n = P.n;
+    const R cscale = R(4) * P.inv_dx;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        R x[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = st[a * n + p];
+        AdjStencil<R, D> s;
+        adj_stencil<R, D>(P, x, s);
+        Mom3<R> m;
+        stencil_moments3<R, false>(s.w, s.dw, P.inv_dx, [&](int k0, int k1, int k2, R f[3], R &g) {
+            const int a3[3] = {s.b[0] + 2 + k0, s.b[1] + 2 + k1, s.b[2] + 2 + k2};
+            const R4<R> v4 = GV[lin3<D>(a3, P.G_nodes)];
+            f[0] = v4.x;
+            f[1] = v4.y;
+            f[2] = v4.z;
+            g = R(0);
+        }, m);
+        R vp[D], Lf[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            vp[a] = m.V[a];
+#pragma unroll
+            for (int b = 0; b < D; ++b) Lf[a * D + b] = m.L[b][a];
+        }
+        const R trL = Lf[0] + Lf[4] + Lf[8];
+        R xb[D], vbt[D], Cb[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R xo = lam_in[a * n + p];
+            const R xn = x[a] + P.dt * vp[a];
+            const bool clamped = xn < R(0) || xn > P.L[a];
+            xb[a] = clamped ? R(0) : xo;
+            vbt[a] = lam_in[(D + a) * n + p] + (clamped ? R(0) : P.dt * xo);
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Cb[q] = lam_in[(JC + q) * n + p];
+        const R rho = st[JR * n + p];
+        const R den = R(1) + P.dt * trL;
+        const R rb1 = lam_in[JR * n + p];
+        const R trLb = -rb1 * rho * P.dt / (den * den);
+        R Lb[D * D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Lb[q] = (q % 4 == 0) ? trLb : R(0);
+        if (P.material == 1) {
+            R s6[6], sb6[6], s0b[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                s6[k] = st[(JR + 1 + k) * n + p];
+                sb6[k] = lam_in[(JR + 1 + k) * n + p];
+                s0b[k] = R(0);
+            }
+            dp_update_vjp<R>(P, Lf, s6, sb6, s0b, Lb);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lam_out[(JR + 1 + k) * n + p] = s0b[k];
+        }
+        // x through C's explicit fx: C = (4 / dx) sum w v (k - fx), dfx/dx = 1 / dx
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R sacc = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) sacc += Cb[a * D + b] * vp[a];
+            xb[b] -= cscale * P.inv_dx * sacc;
+        }
+        // x through the weights: sum_k wbar_k d_b w_k + sum_k d_b d_a w_k gbar_ka with
+        // wbar_k = sum_a v_ka (vbt_a + cscale sum_c Cb_ac (k_c - fx_c)), gbar_ka = sum_d Lb_da v_kd
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R acc = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                acc += vbt[a] * m.L[b][a];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    acc += cscale * Cb[a * D + c] * (m.Q[c][b][a] - s.fx[c] * m.L[b][a]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) acc += Lb[d * D + a] * m.H[hidx3(b, a)][d];
+            }
+            xb[b] += acc;
+        }
+        // v_bar scatter: v_bar_k = w_k (vbt + cscale Cb (k - fx)) + Lb grad w_k
+#pragma unroll
+        for (int k = 0; k < 27; ++k) {
+            const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+            const R wy = s.w[1][kk[1]], wz = s.w[2][kk[2]], wx = s.w[0][kk[0]];
+            const R w = wx * wy * wz;
+            const R g[3] = {s.dw[0][kk[0]] * wy * wz, wx * s.dw[1][kk[1]] * wz, wx * wy * s.dw[2][kk[2]]};
+            R vb[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R cr = R(0), Lg = R(0);
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    cr += Cb[a * D + b] * (R(kk[b]) - s.fx[b]);
+                    Lg += Lb[a * D + b] * g[b];
+                }
+                vb[a] = w * (vbt[a] + cscale * cr) + Lg;
+            }
+            const int a3[3] = {s.b[0] + 2 + kk[0], s.b[1] + 2 + kk[1], s.b[2] + 2 + kk[2]};
+            red_add4(&GVB[lin3<D>(a3, P.G_nodes)], vb[0], vb[1], vb[2], R(0));
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) lam_out[a * n + p] = xb[a];
+        lam_out[JR * n + p] = rb1 / den;
+    }
+}
+
+// 3D adjoint of P2G (same outputs as k_adj_p2g_bwd) from stencil moments of the
+// grid adjoint (P_bar as the three-component field, m_bar as the scalar one).
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
+    k_adj_p2g_bwd3(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GAB,
+                   R *__restrict__ lam_out)
+{
+    constexpr int D = 3, JV = D, JC = 2 * D, JR = 2 * D + D * D;
+    const int64_t n = P.n;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        R x[D], v[D], C[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = st[a * n + p];
+            v[a] = st[(JV + a) * n + p];
+        }
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) C[q] = st[(JC + q) * n + p];
+        const R rho = st[JR * n + p];
+        const R mp = P.mass;
+        AdjStencil<R, D> s;
+        adj_stencil<R, D>(P, x, s);
+        Mom3<R> m;
+        stencil_moments3<R, true>(s.w, s.dw, P.inv_dx, [&](int k0, int k1, int k2, R f[3], R &g) {
+            const int a3[3] = {s.b[0] + 2 + k0, s.b[1] + 2 + k1, s.b[2] + 2 + k2};
+            const R4<R> ab = GAB[lin3<D>(a3, P.G_nodes)];
+            g = ab.x;
+            f[0] = ab.y;
+            f[1] = ab.z;
+            f[2] = ab.w;
+        }, m);
+        // stress-force coefficient Fm (P_a += Fm_ab d_b w)
+        const bool sand = P.material == 1;
+        R Fm[D * D];
+        R pr = R(0);
+        if (sand) {
+            const R c = -P.dt * mp / rho;
+            const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) Fm[a * D + b] = c * st[(JR + 1 + ix[a][b]) * n + p];
+        } else {
+            pr = tait(P, rho);
+            const R sforce = P.dt * mp / rho * pr;
+#pragma unroll
+            for (int q = 0; q < D * D; ++q) Fm[q] = (q % 4 == 0) ? sforce : R(0);
+        }
+        R xb[D];
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R acc = mp * m.Lg[b];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                acc += mp * v[a] * m.L[b][a] - mp * C[a * D + b] * m.V[a];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    acc += mp * C[a * D + c] * P.dx * (m.Q[c][b][a] - s.fx[c] * m.L[b][a]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) acc += Fm[d * D + a] * m.H[hidx3(b, a)][d];
+            }
+            xb[b] = acc;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            lam_out[a * n + p] += xb[a];
+            lam_out[(JV + a) * n + p] = mp * m.V[a];
+#pragma unroll
+            for (int b = 0; b < D; ++b) lam_out[(JC + a * D + b) * n + p] = mp * P.dx * (m.M[b][a] - s.fx[b] * m.V[a]);
+        }
+        // adjoints of the stress and density through Fm (Fm_bar_ab = sum d_b w P_bar_a)
+        if (sand) {
+            const R c = -P.dt * mp / rho;
+            R s6b[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, rhob = R(0);
+            const int ix[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    const R Fmb = m.L[b][a];
+                    s6b[ix[a][b]] += c * Fmb;
+                    rhob -= Fmb * Fm[a * D + b] / rho;
+                }
+            lam_out[JR * n + p] += rhob;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) lam_out[(JR + 1 + k) * n + p] += s6b[k];
+        } else {
+            const R sb = m.L[0][0] + m.L[1][1] + m.L[2][2];
+            const R r1 = rho * P.inv_rho0;
+            R dp = P.bulk_K * P.inv_rho0;
+            if (P.gamma_int > 0) {
+                for (int k = 1; k < P.gamma_int; ++k) dp *= r1;
+            } else {
+                dp *= pow(r1, P.gamma - R(1));
+            }
+            const R dsdrho = P.dt * mp * (dp * rho - pr) / (rho * rho);
+            lam_out[JR * n + p] += sb * dsdrho;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 
 struct AdjDev {
-    void *GA, *GU, *GV, *GVB, *GAB;     // adjoint grid buffers (R4 per node)
+    void *GVB, *GAB;                    // adjoint grid buffers (R4 per node)
 };
 
 template <class R, int D> struct AdjLaunch {
@@ -792,24 +1100,28 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_zero<R><<<grid_blocks(count, 256, ds.num_sms, 8), 256, 0, ds.stream>>>((R *)p, count);
     }
-    // One reverse step: lam_in (adjoint of S^{t+1}) -> lam_out (adjoint of S^t) for the state st.
-    static void step(const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *lam_in,
-                     void *lam_out, MuBar mub)
+    // One reverse step: lam_in (adjoint of S^{t+1}) -> lam_out (adjoint of S^t) for the state st,
+    // whose grid (m, q + dt f) and post-wall velocity the forward recompute saved in GA, GV.
+    static void step(const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *GA,
+                     const void *GV, const void *lam_in, void *lam_out, MuBar mub)
     {
         auto P = make_params<R>(h, ds);
-        const int64_t nodes4 = h.nodes_per_sim * 4;
-        zero(ds, a.GA, nodes4);
-        zero(ds, a.GVB, nodes4);
-        k_adj_p2g<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (R4<R> *)a.GA);
-        k_adj_grid<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)a.GA, (R4<R> *)a.GU,
-                                                                  (R4<R> *)a.GV);
-        k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GV,
-                                                                     (const R *)lam_in, (R *)lam_out,
-                                                                     (R4<R> *)a.GVB);
-        k_adj_grid_bwd<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)a.GA, (const R4<R> *)a.GU,
-                                                                      (const R4<R> *)a.GVB, (R4<R> *)a.GAB, mub);
-        k_adj_p2g_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
-                                                                     (R *)lam_out);
+        zero(ds, a.GVB, h.nodes_per_sim * 4);
+        if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
+            k_adj_g2p_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
+                                                                   (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB);
+        else
+            k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
+                                                                         (const R *)lam_in, (R *)lam_out,
+                                                                         (R4<R> *)a.GVB);
+        k_adj_grid_bwd<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)GA, (const R4<R> *)a.GVB,
+                                                                      (R4<R> *)a.GAB, mub);
+        if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
+            k_adj_p2g_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
+                                                                   (R *)lam_out);
+        else
+            k_adj_p2g_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
+                                                                         (R *)lam_out);
     }
 };
 
@@ -825,8 +1137,8 @@ template <class R> struct AdjDispatch {
     MPM_ADJ_DISPATCH(track, (const HostParams &h, DevState &ds, const int32_t *t, double *o), track(h, ds, t, o))
     MPM_ADJ_DISPATCH(seed, (const HostParams &h, DevState &ds, int nt, const int64_t *ids, const double *xo,
                             const double *zo, void *lam), seed(h, ds, nt, ids, xo, zo, lam))
-    MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *li,
-                            void *lo, MuBar mub), step(h, ds, a, st, li, lo, mub))
+    MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *ga,
+                            const void *gv, const void *li, void *lo, MuBar mub), step(h, ds, a, st, ga, gv, li, lo, mub))
 #undef MPM_ADJ_DISPATCH
     static void zero(const HostParams &, DevState &ds, void *p, int64_t count) { AdjLaunch<R, 2>::zero(ds, p, count); }
 };

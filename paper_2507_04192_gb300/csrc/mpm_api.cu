@@ -32,6 +32,8 @@ struct AdjHost {
     int64_t ckpt_cap = 0;
     void *seg = nullptr;
     int64_t seg_cap = 0;
+    void *seg_grid = nullptr;                  // per segment state: (m, q + dt f) and v of its step
+    int64_t seg_grid_cap = 0;
     void *lam[2] = {nullptr, nullptr};
     mpm::AdjDev grid{};
     double *d_mubar[mpm::kMaxWalls] = {nullptr};
@@ -121,8 +123,8 @@ void free_adjoint(mpm_ctx *c)
 {
     AdjHost &a = c->adj;
     dfree(a.d_ids); dfree(a.d_track_of_id); dfree(a.d_z); dfree(a.d_xobs);
-    dfree(a.ckpt); dfree(a.seg); dfree(a.lam[0]); dfree(a.lam[1]);
-    dfree(a.grid.GA); dfree(a.grid.GU); dfree(a.grid.GV); dfree(a.grid.GVB); dfree(a.grid.GAB);
+    dfree(a.ckpt); dfree(a.seg); dfree(a.seg_grid); dfree(a.lam[0]); dfree(a.lam[1]);
+    dfree(a.grid.GVB); dfree(a.grid.GAB);
     for (int w = 0; w < kMaxWalls; ++w) dfree(a.d_mubar[w]);
     dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
     a.ckpt_cap = a.seg_cap = 0;
@@ -752,14 +754,19 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         if (rc != MPM_OK) return rc;
         a.seg_cap = K;
     }
+    const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+    if (a.seg_grid_cap < K) {
+        dfree(a.seg_grid);
+        int rc = dalloc(c, (unsigned char **)&a.seg_grid, 2 * gbytes * K, "segment grids");
+        if (rc != MPM_OK) return rc;
+        // nodes a step does not touch keep finite values from earlier steps (never read)
+        CK(cudaMemsetAsync(a.seg_grid, 0, 2 * gbytes * K, ds.stream), "zero segment grids");
+        a.seg_grid_cap = K;
+    }
     if (!a.allocated) {
         int rc = MPM_OK;
-        const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[0], st_bytes, "adjoint state");
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[1], st_bytes, "adjoint state");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GA, gbytes, "adjoint grid");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GU, gbytes, "adjoint grid");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GV, gbytes, "adjoint grid");
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GVB, gbytes, "adjoint grid");
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GAB, gbytes, "adjoint grid");
         if (rc == MPM_OK)
@@ -784,6 +791,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     for (int o = 0; o < a.n_obs; ++o) obs_of_step[a.steps[o]] = o;
     auto ckpt_ptr = [&](int64_t k) { return (void *)((char *)a.ckpt + k * st_bytes); };
     auto seg_ptr = [&](int64_t j) { return (void *)((char *)a.seg + j * st_bytes); };
+    auto gridA_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + 2 * j * gbytes); };
+    auto gridV_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + (2 * j + 1) * gbytes); };
     const size_t obs_stride = (size_t)a.n_track * d;
     // forward pass with checkpoints and observations
     c->aops->save(h, ds, ckpt_ptr(0));
@@ -821,13 +830,19 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         c->aops->restore(h, ds, ckpt_ptr(k));
         c->need_sort = true;
         CK(cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(k), st_bytes, cudaMemcpyDeviceToDevice, ds.stream), "segment start");
-        for (int j = 1; j < t1 - t0; ++j) {
+        // recompute the segment: step j saves the grid of state j - 1 (the last
+        // step runs only for the grid of the segment's last state)
+        for (int j = 1; j <= t1 - t0; ++j) {
+            ds.save_A = gridA_ptr(j - 1);
+            ds.save_V = gridV_ptr(j - 1);
             int rc = step_many(c, 1);
+            ds.save_A = ds.save_V = nullptr;
             if (rc != MPM_OK) return rc;
-            c->aops->save(h, ds, seg_ptr(j));
+            if (j < t1 - t0) c->aops->save(h, ds, seg_ptr(j));
         }
         for (int t = t1 - 1; t >= t0; --t) {
-            c->aops->step(h, ds, a.grid, seg_ptr(t - t0), a.lam[cur], a.lam[cur ^ 1], mub);
+            c->aops->step(h, ds, a.grid, seg_ptr(t - t0), gridA_ptr(t - t0), gridV_ptr(t - t0), a.lam[cur],
+                          a.lam[cur ^ 1], mub);
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
                 const int o = obs_of_step[t];

@@ -107,6 +107,8 @@ struct DevState {
     int32_t *status;              // device status word (bit 0: non-finite state)
     unsigned long long *escaped;  // particles that took the out-of-window path
     double *staging;              // n x 9 doubles for host transfers
+    void *save_A = nullptr;       // when set, the grid update also copies (m, q + dt f) ...
+    void *save_V = nullptr;       // ... and the post-wall velocity of every node it updates here
     CUtensorMap tmap_V;           // TMA descriptor of V: (4, G_x, G_y, [G_z], batch)
     void *mu_dev[kMaxWalls];
     int n_seg[kMaxWalls][2];
@@ -131,15 +133,15 @@ extern const Ops ops_f64;
 
 struct AdjDev;
 struct MuBar;
-// Adjoint launchers per precision (fluid only).
+// Adjoint launchers per precision.
 struct AdjOps {
     void (*save)(const HostParams &, DevState &, void *dst);
     void (*restore)(const HostParams &, DevState &, const void *src);
     void (*track)(const HostParams &, DevState &, const int32_t *track_of_id, double *out);
     void (*seed)(const HostParams &, DevState &, int n_track, const int64_t *ids, const double *x_obs,
                  const double *z_obs, void *lam);
-    void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *lam_in, void *lam_out,
-                 MuBar mub);
+    void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *GA, const void *GV,
+                 const void *lam_in, void *lam_out, MuBar mub);
     void (*zero)(const HostParams &, DevState &, void *p, int64_t count);
 };
 extern const AdjOps adj_ops_f32;

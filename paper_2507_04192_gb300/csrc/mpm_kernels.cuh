@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
 // accumulator for the next step.
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restrict__ A,
-                                              R4<R> *__restrict__ V, uint32_t *__restrict__ flags)
+                                              R4<R> *__restrict__ V, uint32_t *__restrict__ flags,
+                                              R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV)
 {
     using Gm = Geo<D>;
     const int64_t ut = blockIdx.x;
@@ -671,6 +672,10 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
             }
         }
         Vs[idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+        if (saveA != nullptr) {                  // forward grid kept for the reverse sweep
+            saveA[(int64_t)sim * P.nodes_per_sim + idx] = acc;
+            saveV[(int64_t)sim * P.nodes_per_sim + idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) flags[ut] = 0u;
@@ -1281,7 +1286,8 @@ template <class R, int D> struct Launch {
     {
         auto P = make_params<R>(h, ds);
         const int64_t nb = h.batch * h.node_tiles_per_sim;
-        k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags);
+        k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags,
+                                                           (R4<R> *)ds.save_A, (R4<R> *)ds.save_V);
     }
     static void g2p(const HostParams &h, DevState &ds)
     {
