@@ -341,6 +341,59 @@ __global__ void k_adj_seed(int64_t n, int n_track, const int64_t *__restrict__ i
     }
 }
 
+// Slot-order save: the adjoint components of the state in the context's current
+// particle order, as contiguous arrays (dst[c n + slot]), and that order's ids.
+template <class R, int D>
+__global__ void k_adj_save_slots(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
+                                 R *__restrict__ dst, int32_t *__restrict__ dst_id)
+{
+    constexpr int NA = adj_ncomp<D>();
+    const int nsig = P.material == 1 ? 6 : 0;
+    const int64_t n = P.n, np = P.npad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < NA - 1; ++c) dst[c * n + i] = S[c * np + i];
+        dst[(NA - 1) * n + i] = S[P.off_rho * np + i];
+        for (int k = 0; k < nsig; ++k) dst[(NA + k) * n + i] = S[(P.off_sig + k) * np + i];
+        dst_id[i] = id[i];
+    }
+}
+
+// pos[id[slot]] = slot.
+template <class R>
+__global__ void k_adj_inverse(int64_t n, const int32_t *__restrict__ id, int32_t *__restrict__ pos)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pos[id[i]] = (int32_t)i;
+}
+
+// Re-order an adjoint state from the order with inverse map pos_old to the
+// order with ids id_new: out[c n + s] = in[c n + pos_old[id_new[s]]].
+template <class R>
+__global__ void k_adj_reorder(int64_t n, int nc, const int32_t *__restrict__ pos_old,
+                              const int32_t *__restrict__ id_new, const R *__restrict__ in, R *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = pos_old[id_new[i]];
+        for (int c = 0; c < nc; ++c) out[c * n + i] = in[c * n + src];
+    }
+}
+
+// lam.x[slot] += 2 (x_l - z_l) for the tracked particles (slot order with ids id).
+template <class R, int D>
+__global__ void k_adj_seed_slots(int64_t n, const int32_t *__restrict__ id, const int32_t *__restrict__ track_of_id,
+                                 const double *__restrict__ x_obs, const double *__restrict__ z_obs,
+                                 R *__restrict__ lam)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = track_of_id[id[i]];
+        if (l < 0) continue;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            lam[a * n + i] += (R)(2.0 * (x_obs[(int64_t)l * D + a] - z_obs[(int64_t)l * D + a]));
+    }
+}
+
 template <class R>
 __global__ void k_adj_zero(R *__restrict__ p, int64_t count)
 {
@@ -1096,6 +1149,23 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_seed<R, D><<<(n_track + 255) / 256, 256, 0, ds.stream>>>(h.n, n_track, ids, x_obs, z_obs, (R *)lam);
     }
+    static void save_slots(const HostParams &h, DevState &ds, void *dst, int32_t *dst_id)
+    {
+        auto P = make_params<R>(h, ds);
+        k_adj_save_slots<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.id, (R *)dst, dst_id);
+    }
+    static void reorder(const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos_scratch,
+                        const int32_t *id_new, const void *in, void *out)
+    {
+        k_adj_inverse<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, id_old, pos_scratch);
+        k_adj_reorder<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, nc, pos_scratch, id_new, (const R *)in,
+                                                                   (R *)out);
+    }
+    static void seed_slots(const HostParams &h, DevState &ds, const int32_t *id, const int32_t *track_of_id,
+                           const double *x_obs, const double *z_obs, void *lam)
+    {
+        k_adj_seed_slots<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, id, track_of_id, x_obs, z_obs, (R *)lam);
+    }
     static void zero(DevState &ds, void *p, int64_t count)
     {
         k_adj_zero<R><<<grid_blocks(count, 256, ds.num_sms, 8), 256, 0, ds.stream>>>((R *)p, count);
@@ -1139,6 +1209,13 @@ template <class R> struct AdjDispatch {
                             const double *zo, void *lam), seed(h, ds, nt, ids, xo, zo, lam))
     MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *ga,
                             const void *gv, const void *li, void *lo, MuBar mub), step(h, ds, a, st, ga, gv, li, lo, mub))
+    MPM_ADJ_DISPATCH(save_slots, (const HostParams &h, DevState &ds, void *dst, int32_t *dst_id),
+                     save_slots(h, ds, dst, dst_id))
+    MPM_ADJ_DISPATCH(reorder, (const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos,
+                               const int32_t *id_new, const void *in, void *out),
+                     reorder(h, ds, nc, id_old, pos, id_new, in, out))
+    MPM_ADJ_DISPATCH(seed_slots, (const HostParams &h, DevState &ds, const int32_t *id, const int32_t *tid,
+                                  const double *xo, const double *zo, void *lam), seed_slots(h, ds, id, tid, xo, zo, lam))
 #undef MPM_ADJ_DISPATCH
     static void zero(const HostParams &, DevState &ds, void *p, int64_t count) { AdjLaunch<R, 2>::zero(ds, p, count); }
 };

@@ -34,6 +34,8 @@ struct AdjHost {
     int64_t seg_cap = 0;
     void *seg_grid = nullptr;                  // per segment state: (m, q + dt f) and v of its step
     int64_t seg_grid_cap = 0;
+    int32_t *seg_id = nullptr;                 // per segment state: the particle order it was saved in
+    int32_t *lam_id = nullptr, *lam_pos = nullptr;   // the adjoint state's order and an inverse-map scratch
     void *lam[2] = {nullptr, nullptr};
     mpm::AdjDev grid{};
     double *d_mubar[mpm::kMaxWalls] = {nullptr};
@@ -124,6 +126,7 @@ void free_adjoint(mpm_ctx *c)
     AdjHost &a = c->adj;
     dfree(a.d_ids); dfree(a.d_track_of_id); dfree(a.d_z); dfree(a.d_xobs);
     dfree(a.ckpt); dfree(a.seg); dfree(a.seg_grid); dfree(a.lam[0]); dfree(a.lam[1]);
+    dfree(a.seg_id); dfree(a.lam_id); dfree(a.lam_pos);
     dfree(a.grid.GVB); dfree(a.grid.GAB);
     for (int w = 0; w < kMaxWalls; ++w) dfree(a.d_mubar[w]);
     dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
@@ -750,7 +753,9 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     }
     if (a.seg_cap < K) {
         dfree(a.seg);
+        dfree(a.seg_id);
         int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * K, "segment states");
+        if (rc == MPM_OK) rc = dalloc(c, &a.seg_id, (size_t)n * K, "segment orders");
         if (rc != MPM_OK) return rc;
         a.seg_cap = K;
     }
@@ -773,6 +778,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
             rc = dalloc(c, (unsigned char **)&a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, "final state");
         if (rc == MPM_OK) rc = dalloc(c, &a.final_id, n, "final ids");
         if (rc == MPM_OK) rc = dalloc(c, &a.final_sim, n, "final sims");
+        if (rc == MPM_OK) rc = dalloc(c, &a.lam_id, n, "adjoint order");
+        if (rc == MPM_OK) rc = dalloc(c, &a.lam_pos, n, "adjoint order");
         if (rc != MPM_OK) return rc;
         a.allocated = true;
     }
@@ -818,36 +825,55 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         const double e = xobs[i] - a.z[i];
         loss += e * e;
     }
-    // reverse sweep, one segment at a time (recomputed from its checkpoint)
+    // Reverse sweep, one segment at a time (recomputed from its checkpoint).  States
+    // are saved in the particle order the context holds at the time (a contiguous
+    // copy); the adjoint state follows the order of the state it belongs to and is
+    // re-ordered only where a sort changed the order between two states.
     int cur = 0;
+    int64_t lam_gen = c->sorts;                // the order of the final state
+    CK(cudaMemcpyAsync(a.lam_id, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream), "adjoint order");
     c->aops->zero(h, ds, a.lam[cur], (int64_t)NA * n);
     if (obs_of_step[n_steps] >= 0) {
         const int o = obs_of_step[n_steps];
-        c->aops->seed(h, ds, a.n_track, a.d_ids, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride, a.lam[cur]);
+        c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride,
+                            a.lam[cur]);
     }
+    std::vector<int64_t> seg_gen(K);
+    auto seg_id_ptr = [&](int64_t j) { return a.seg_id + j * n; };
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
         c->aops->restore(h, ds, ckpt_ptr(k));
         c->need_sort = true;
-        CK(cudaMemcpyAsync(seg_ptr(0), ckpt_ptr(k), st_bytes, cudaMemcpyDeviceToDevice, ds.stream), "segment start");
-        // recompute the segment: step j saves the grid of state j - 1 (the last
-        // step runs only for the grid of the segment's last state)
-        for (int j = 1; j <= t1 - t0; ++j) {
-            ds.save_A = gridA_ptr(j - 1);
-            ds.save_V = gridV_ptr(j - 1);
+        // recompute the segment: state j is saved before step j, which also saves
+        // the grid of state j
+        for (int j = 0; j < t1 - t0; ++j) {
+            if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
+                int rc = do_sort(c);                 // sort first, so the saved order is the step's
+                if (rc != MPM_OK) return rc;
+            }
+            c->aops->save_slots(h, ds, seg_ptr(j), seg_id_ptr(j));
+            seg_gen[j] = c->sorts;
+            ds.save_A = gridA_ptr(j);
+            ds.save_V = gridV_ptr(j);
             int rc = step_many(c, 1);
             ds.save_A = ds.save_V = nullptr;
             if (rc != MPM_OK) return rc;
-            if (j < t1 - t0) c->aops->save(h, ds, seg_ptr(j));
         }
         for (int t = t1 - 1; t >= t0; --t) {
-            c->aops->step(h, ds, a.grid, seg_ptr(t - t0), gridA_ptr(t - t0), gridV_ptr(t - t0), a.lam[cur],
-                          a.lam[cur ^ 1], mub);
+            const int j = t - t0;
+            if (seg_gen[j] != lam_gen) {             // a sort between the two states: re-order
+                c->aops->reorder(h, ds, NA, a.lam_id, a.lam_pos, seg_id_ptr(j), a.lam[cur], a.lam[cur ^ 1]);
+                cur ^= 1;
+                CK(cudaMemcpyAsync(a.lam_id, seg_id_ptr(j), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                   ds.stream), "adjoint order");
+                lam_gen = seg_gen[j];
+            }
+            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), a.lam[cur], a.lam[cur ^ 1], mub);
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
                 const int o = obs_of_step[t];
-                c->aops->seed(h, ds, a.n_track, a.d_ids, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride,
-                              a.lam[cur]);
+                c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride,
+                                    a.d_z + o * obs_stride, a.lam[cur]);
             }
         }
         int rc = check_launch(c, "mpm_step_adjoint");
