@@ -12,7 +12,8 @@
 // recompute of the segment saved, so only the reverse kernels run:
 //   k_adj_g2p_bwd  adjoint of G2P: scatters v_bar to the grid, x_bar and
 //                  rho_bar partials to the particles
-//   k_adj_grid_bwd adjoint of the grid update: walls (and d/dmu), division
+//   k_adj_grid_bwd adjoint of the grid update: walls (and d/dmu), division,
+//                  over the node tiles the forward step updated
 //   k_adj_p2g_bwd  adjoint of P2G: gathers (m_bar, P_bar), completes the
 //                  particle adjoint
 // Branches (position clamp, wall contact, stick/slide, mass threshold) follow
@@ -593,35 +594,51 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_
     }
 }
 
-// Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P).
+// Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P),
+// one block per node tile the forward step updated (tile flags GF); GVB is
+// cleared behind, ready for the next reverse step.
 template <class R, int D>
-__global__ void k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA, const R4<R> *__restrict__ GVB,
-                               R4<R> *__restrict__ GAB, MuBar mu_bar)
+__global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA,
+                                                      R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB,
+                                                      const uint32_t *__restrict__ GF, MuBar mu_bar)
 {
-    const int64_t N = P.nodes_per_sim;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    using Gm = Geo<D>;
+    const int64_t ut = blockIdx.x;
+    if (GF[ut] == 0u) return;
+    int u[3] = {0, 0, 0};
+    int64_t r = ut;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = (int)(r % P.node_tiles[a]);
+        r /= P.node_tiles[a];
+    }
+    for (int t = threadIdx.x; t < Gm::TN; t += blockDim.x) {
+        int a3[3] = {0, 0, 0};
+        int rr = t;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            a3[a] = u[a] * Gm::T + rr % Gm::T;
+            rr /= Gm::T;
+            ok = ok && a3[a] < P.G_nodes[a];
+        }
+        if (!ok) continue;
+        const int64_t i = lin3<D>(a3, P.G_nodes);
+        const R4<R> b4 = GVB[i];
+        GVB[i] = R4<R>{R(0), R(0), R(0), R(0)};
         const R4<R> acc = GA[i];
         if (!(acc.x > P.m_eps)) {
             GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
             continue;
         }
-        const R inv_m0 = R(1) / acc.x;
-        R vel[3] = {acc.y * inv_m0 + P.dt * P.gravity[0], acc.z * inv_m0 + P.dt * P.gravity[1],
-                    D == 3 ? acc.w * inv_m0 + P.dt * P.gravity[2] : R(0)};
-        int a3[3] = {0, 0, 0};
-        int64_t r = i;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            a3[a] = (int)(r % P.G_nodes[a]);
-            r /= P.G_nodes[a];
-        }
+        const R inv_m = R(1) / acc.x;
+        R vel[3] = {acc.y * inv_m + P.dt * P.gravity[0], acc.z * inv_m + P.dt * P.gravity[1],
+                    D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
         R chain[2 * D][3];
         bool applied[2 * D];
         walls_forward<R, D>(P, 0, a3, vel, chain, applied);
-        const R4<R> b4 = GVB[i];
         R ob[3] = {b4.x, b4.y, b4.z};
         walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w);
-        const R inv_m = R(1) / acc.x;
         const R Pv[3] = {acc.y, acc.z, acc.w};
         R mb = R(0);
 #pragma unroll
@@ -1125,10 +1142,6 @@ struct AdjDev {
 
 template <class R, int D> struct AdjLaunch {
     static int pblocks(const HostParams &h, const DevState &ds) { return grid_blocks(h.n, 256, ds.num_sms, 8); }
-    static int nblocks(const HostParams &h, const DevState &ds)
-    {
-        return grid_blocks(h.nodes_per_sim, 256, ds.num_sms, 8);
-    }
     static void save(const HostParams &h, DevState &ds, void *dst)
     {
         auto P = make_params<R>(h, ds);
@@ -1173,10 +1186,9 @@ template <class R, int D> struct AdjLaunch {
     // One reverse step: lam_in (adjoint of S^{t+1}) -> lam_out (adjoint of S^t) for the state st,
     // whose grid (m, q + dt f) and post-wall velocity the forward recompute saved in GA, GV.
     static void step(const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *GA,
-                     const void *GV, const void *lam_in, void *lam_out, MuBar mub)
+                     const void *GV, const uint32_t *GF, const void *lam_in, void *lam_out, MuBar mub)
     {
         auto P = make_params<R>(h, ds);
-        zero(ds, a.GVB, h.nodes_per_sim * 4);
         if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
             k_adj_g2p_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
                                                                    (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB);
@@ -1184,8 +1196,8 @@ template <class R, int D> struct AdjLaunch {
             k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
                                                                          (const R *)lam_in, (R *)lam_out,
                                                                          (R4<R> *)a.GVB);
-        k_adj_grid_bwd<R, D><<<nblocks(h, ds), 256, 0, ds.stream>>>(P, (const R4<R> *)GA, (const R4<R> *)a.GVB,
-                                                                      (R4<R> *)a.GAB, mub);
+        k_adj_grid_bwd<R, D><<<(unsigned)h.node_tiles_per_sim, 256, 0, ds.stream>>>(
+            P, (const R4<R> *)GA, (R4<R> *)a.GVB, (R4<R> *)a.GAB, GF, mub);
         if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
             k_adj_p2g_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
                                                                    (R *)lam_out);
@@ -1208,7 +1220,8 @@ template <class R> struct AdjDispatch {
     MPM_ADJ_DISPATCH(seed, (const HostParams &h, DevState &ds, int nt, const int64_t *ids, const double *xo,
                             const double *zo, void *lam), seed(h, ds, nt, ids, xo, zo, lam))
     MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *ga,
-                            const void *gv, const void *li, void *lo, MuBar mub), step(h, ds, a, st, ga, gv, li, lo, mub))
+                            const void *gv, const uint32_t *gf, const void *li, void *lo, MuBar mub),
+                     step(h, ds, a, st, ga, gv, gf, li, lo, mub))
     MPM_ADJ_DISPATCH(save_slots, (const HostParams &h, DevState &ds, void *dst, int32_t *dst_id),
                      save_slots(h, ds, dst, dst_id))
     MPM_ADJ_DISPATCH(reorder, (const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos,

@@ -738,7 +738,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     const HostParams &h = c->hp;
     DevState &ds = c->ds;
     const int d = h.dim;
-    const int K = checkpoint_every;
+    const int K = std::min(checkpoint_every, n_steps);
     const int NA = adj_ncomp_material(d, c->mat.kind == MPM_DRUCKER_PRAGER ? 1 : 0);
     const size_t rsz = h.precision == MPM_FP64 ? 8 : 4;
     const int64_t n = h.n;
@@ -760,12 +760,13 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         a.seg_cap = K;
     }
     const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+    const size_t fbytes = ((size_t)h.node_tiles_per_sim * sizeof(uint32_t) + 255) / 256 * 256;
     if (a.seg_grid_cap < K) {
         dfree(a.seg_grid);
-        int rc = dalloc(c, (unsigned char **)&a.seg_grid, 2 * gbytes * K, "segment grids");
+        int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * K, "segment grids");
         if (rc != MPM_OK) return rc;
         // nodes a step does not touch keep finite values from earlier steps (never read)
-        CK(cudaMemsetAsync(a.seg_grid, 0, 2 * gbytes * K, ds.stream), "zero segment grids");
+        CK(cudaMemsetAsync(a.seg_grid, 0, (2 * gbytes + fbytes) * K, ds.stream), "zero segment grids");
         a.seg_grid_cap = K;
     }
     if (!a.allocated) {
@@ -800,11 +801,37 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     auto seg_ptr = [&](int64_t j) { return (void *)((char *)a.seg + j * st_bytes); };
     auto gridA_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + 2 * j * gbytes); };
     auto gridV_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + (2 * j + 1) * gbytes); };
+    auto gridF_ptr = [&](int64_t j) { return (uint32_t *)((char *)a.seg_grid + 2 * K * gbytes + j * fbytes); };
+    auto seg_id_ptr = [&](int64_t j) { return a.seg_id + j * n; };
+    std::vector<int64_t> seg_gen(K);
+    // state j of a segment: saved (with its order) after the step's sort, and the
+    // step saves its grid
+    auto keep_state = [&](int j) -> int {
+        if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
+            int rc = do_sort(c);
+            if (rc != MPM_OK) return rc;
+        }
+        c->aops->save_slots(h, ds, seg_ptr(j), seg_id_ptr(j));
+        seg_gen[j] = c->sorts;
+        ds.save_A = gridA_ptr(j);
+        ds.save_V = gridV_ptr(j);
+        ds.save_F = gridF_ptr(j);
+        return MPM_OK;
+    };
+    auto stop_keeping = [&]() { ds.save_A = ds.save_V = ds.save_F = nullptr; };
+    CK(cudaMemsetAsync(a.grid.GVB, 0, gbytes, ds.stream), "zero grid adjoint");
     const size_t obs_stride = (size_t)a.n_track * d;
-    // forward pass with checkpoints and observations
+    // forward pass with checkpoints and observations; the last segment's states
+    // and grids are kept on the way (its reverse needs no recompute)
+    const int64_t last_t0 = (n_ckpt - 1) * K;
     c->aops->save(h, ds, ckpt_ptr(0));
     for (int t = 1; t <= n_steps; ++t) {
+        if (t - 1 >= last_t0) {
+            int rc = keep_state((int)(t - 1 - last_t0));
+            if (rc != MPM_OK) return rc;
+        }
         int rc = step_many(c, 1);
+        stop_keeping();
         if (rc != MPM_OK) return rc;
         if (obs_of_step[t] >= 0) c->aops->track(h, ds, a.d_track_of_id, a.d_xobs + obs_of_step[t] * obs_stride);
         if (t % K == 0 && t < n_steps) c->aops->save(h, ds, ckpt_ptr(t / K));
@@ -838,26 +865,17 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride,
                             a.lam[cur]);
     }
-    std::vector<int64_t> seg_gen(K);
-    auto seg_id_ptr = [&](int64_t j) { return a.seg_id + j * n; };
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
-        c->aops->restore(h, ds, ckpt_ptr(k));
-        c->need_sort = true;
-        // recompute the segment: state j is saved before step j, which also saves
-        // the grid of state j
-        for (int j = 0; j < t1 - t0; ++j) {
-            if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
-                int rc = do_sort(c);                 // sort first, so the saved order is the step's
+        if (k < n_ckpt - 1) {                          // recompute the segment from its checkpoint
+            c->aops->restore(h, ds, ckpt_ptr(k));
+            c->need_sort = true;
+            for (int j = 0; j < t1 - t0; ++j) {
+                int rc = keep_state(j);
+                if (rc == MPM_OK) rc = step_many(c, 1);
+                stop_keeping();
                 if (rc != MPM_OK) return rc;
             }
-            c->aops->save_slots(h, ds, seg_ptr(j), seg_id_ptr(j));
-            seg_gen[j] = c->sorts;
-            ds.save_A = gridA_ptr(j);
-            ds.save_V = gridV_ptr(j);
-            int rc = step_many(c, 1);
-            ds.save_A = ds.save_V = nullptr;
-            if (rc != MPM_OK) return rc;
         }
         for (int t = t1 - 1; t >= t0; --t) {
             const int j = t - t0;
@@ -868,7 +886,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                                    ds.stream), "adjoint order");
                 lam_gen = seg_gen[j];
             }
-            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), a.lam[cur], a.lam[cur ^ 1], mub);
+            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridF_ptr(j), a.lam[cur],
+                          a.lam[cur ^ 1], mub);
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
                 const int o = obs_of_step[t];

@@ -108,7 +108,8 @@ struct DevState {
     unsigned long long *escaped;  // particles that took the out-of-window path
     double *staging;              // n x 9 doubles for host transfers
     void *save_A = nullptr;       // when set, the grid update also copies (m, q + dt f) ...
-    void *save_V = nullptr;       // ... and the post-wall velocity of every node it updates here
+    void *save_V = nullptr;       // ... and the post-wall velocity of every node it updates here,
+    void *save_F = nullptr;       // ... and which node tiles it updated (one word per tile)
     CUtensorMap tmap_V;           // TMA descriptor of V: (4, G_x, G_y, [G_z], batch)
     void *mu_dev[kMaxWalls];
     int n_seg[kMaxWalls][2];
@@ -141,7 +142,7 @@ struct AdjOps {
     void (*seed)(const HostParams &, DevState &, int n_track, const int64_t *ids, const double *x_obs,
                  const double *z_obs, void *lam);
     void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *GA, const void *GV,
-                 const void *lam_in, void *lam_out, MuBar mub);
+                 const uint32_t *GF, const void *lam_in, void *lam_out, MuBar mub);
     void (*zero)(const HostParams &, DevState &, void *p, int64_t count);
     void (*save_slots)(const HostParams &, DevState &, void *dst, int32_t *dst_id);
     void (*reorder)(const HostParams &, DevState &, int nc, const int32_t *id_old, int32_t *pos_scratch,

@@ -611,11 +611,16 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restrict__ A,
                                               R4<R> *__restrict__ V, uint32_t *__restrict__ flags,
-                                              R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV)
+                                              R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV,
+                                              uint32_t *__restrict__ saveF)
 {
     using Gm = Geo<D>;
     const int64_t ut = blockIdx.x;
-    if (flags[ut] == 0u) return;
+    if (flags[ut] == 0u) {
+        if (saveF != nullptr && threadIdx.x == 0) saveF[ut] = 0u;
+        return;
+    }
+    if (saveF != nullptr && threadIdx.x == 0) saveF[ut] = 1u;
     const int sim = (int)(ut / P.node_tiles_per_sim);
     int64_t r = ut - (int64_t)sim * P.node_tiles_per_sim;
     int u[3] = {0, 0, 0};
@@ -1287,7 +1292,8 @@ template <class R, int D> struct Launch {
         auto P = make_params<R>(h, ds);
         const int64_t nb = h.batch * h.node_tiles_per_sim;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags,
-                                                           (R4<R> *)ds.save_A, (R4<R> *)ds.save_V);
+                                                           (R4<R> *)ds.save_A, (R4<R> *)ds.save_V,
+                                                           (uint32_t *)ds.save_F);
     }
     static void g2p(const HostParams &h, DevState &ds)
     {
