@@ -1162,10 +1162,10 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_seed<R, D><<<(n_track + 255) / 256, 256, 0, ds.stream>>>(h.n, n_track, ids, x_obs, z_obs, (R *)lam);
     }
-    static void save_slots(const HostParams &h, DevState &ds, void *dst, int32_t *dst_id)
+    static void save_slots(const HostParams &h, DevState &ds, cudaStream_t stream, void *dst, int32_t *dst_id)
     {
         auto P = make_params<R>(h, ds);
-        k_adj_save_slots<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)ds.S, ds.id, (R *)dst, dst_id);
+        k_adj_save_slots<R, D><<<pblocks(h, ds), 256, 0, stream>>>(P, (const R *)ds.S, ds.id, (R *)dst, dst_id);
     }
     static void reorder(const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos_scratch,
                         const int32_t *id_new, const void *in, void *out)
@@ -1222,8 +1222,8 @@ template <class R> struct AdjDispatch {
     MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *ga,
                             const void *gv, const uint32_t *gf, const void *li, void *lo, MuBar mub),
                      step(h, ds, a, st, ga, gv, gf, li, lo, mub))
-    MPM_ADJ_DISPATCH(save_slots, (const HostParams &h, DevState &ds, void *dst, int32_t *dst_id),
-                     save_slots(h, ds, dst, dst_id))
+    MPM_ADJ_DISPATCH(save_slots, (const HostParams &h, DevState &ds, cudaStream_t st, void *dst, int32_t *dst_id),
+                     save_slots(h, ds, st, dst, dst_id))
     MPM_ADJ_DISPATCH(reorder, (const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos,
                                const int32_t *id_new, const void *in, void *out),
                      reorder(h, ds, nc, id_old, pos, id_new, in, out))

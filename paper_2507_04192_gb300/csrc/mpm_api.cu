@@ -73,6 +73,11 @@ struct mpm_ctx {
     AdjHost adj;
     const AdjOps *aops = nullptr;
     StateSlot slots[kMaxSlots];
+    // the adjoint's segment saves run on a second stream beside P2G and the grid
+    // update; G2P (which overwrites the state) waits for g2p_wait when set
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_sorted = nullptr, ev_saved = nullptr;
+    cudaEvent_t g2p_wait = nullptr;
 };
 
 namespace {
@@ -442,6 +447,9 @@ void mpm_destroy(mpm_ctx *c)
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->own_stream && d.stream) cudaStreamDestroy(d.stream);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
+    if (c->ev_saved) cudaEventDestroy(c->ev_saved);
     delete c;
 }
 
@@ -589,6 +597,10 @@ int step_many(mpm_ctx *c, int n_steps)
         }
         {
             TimingScope ts(c, MPM_KERNEL_G2P);
+            if (c->g2p_wait) {
+                cudaStreamWaitEvent(c->ds.stream, c->g2p_wait, 0);
+                c->g2p_wait = nullptr;
+            }
             c->ops->g2p(c->hp, c->ds);
         }
         c->launches += 3;
@@ -806,12 +818,23 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     std::vector<int64_t> seg_gen(K);
     // state j of a segment: saved (with its order) after the step's sort, and the
     // step saves its grid
+    if (!c->aux) {
+        CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "adjoint stream");
+        CK(cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming), "adjoint event");
+        CK(cudaEventCreateWithFlags(&c->ev_saved, cudaEventDisableTiming), "adjoint event");
+    }
     auto keep_state = [&](int j) -> int {
         if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
             int rc = do_sort(c);
             if (rc != MPM_OK) return rc;
         }
-        c->aops->save_slots(h, ds, seg_ptr(j), seg_id_ptr(j));
+        // the copy overlaps the step's P2G and grid update; its G2P waits for it
+        if (cudaEventRecord(c->ev_sorted, ds.stream) != cudaSuccess ||
+            cudaStreamWaitEvent(c->aux, c->ev_sorted, 0) != cudaSuccess)
+            return fail(c, MPM_ECUDA, "adjoint stream ordering");
+        c->aops->save_slots(h, ds, c->aux, seg_ptr(j), seg_id_ptr(j));
+        if (cudaEventRecord(c->ev_saved, c->aux) != cudaSuccess) return fail(c, MPM_ECUDA, "adjoint stream ordering");
+        c->g2p_wait = c->ev_saved;
         seg_gen[j] = c->sorts;
         ds.save_A = gridA_ptr(j);
         ds.save_V = gridV_ptr(j);

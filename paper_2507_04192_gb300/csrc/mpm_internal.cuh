@@ -144,7 +144,7 @@ struct AdjOps {
     void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *GA, const void *GV,
                  const uint32_t *GF, const void *lam_in, void *lam_out, MuBar mub);
     void (*zero)(const HostParams &, DevState &, void *p, int64_t count);
-    void (*save_slots)(const HostParams &, DevState &, void *dst, int32_t *dst_id);
+    void (*save_slots)(const HostParams &, DevState &, cudaStream_t stream, void *dst, int32_t *dst_id);
     void (*reorder)(const HostParams &, DevState &, int nc, const int32_t *id_old, int32_t *pos_scratch,
                     const int32_t *id_new, const void *in, void *out);
     void (*seed_slots)(const HostParams &, DevState &, const int32_t *id, const int32_t *track_of_id,
