@@ -149,6 +149,13 @@ def cpu_baseline_full_step():
                       f"{dt:.1f} s"}
 
 
+def workload_config(world: int) -> dict:
+    """The headline workload (the same object on both arms)."""
+    return {"workload": WORKLOAD, "particles": 2761536, "grid": "256x256x128", "precision": "fp32",
+            "material": "drucker_prager", "sort_every": 16, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (353 MB particle state per step)"}
+
+
 def bench_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -165,8 +172,7 @@ def bench_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_particles": n, "precision": "fp64",
-                       "l2": "CPU run"},
+            "config": workload_config(world),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: the first {n} particles of the 2.76M-particle cylinder "
                                        f"(bottom layers) on a grid cropped around them, FP64, single thread"},
@@ -317,6 +323,7 @@ def bench_ours(args):
 
     w = inputs.granular_cylinder_3d()
     n = w.n
+    assert n == workload_config(world)["particles"] and w.sort_every == workload_config(world)["sort_every"]
 
     def timed_run(precision, steps, warmup, timing=False):
         sim = mpm.Simulation.from_workload(w, precision, stream=stream.cuda_stream)
@@ -403,10 +410,7 @@ def bench_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "particles": n, "grid": "256x256x128", "precision": "fp32",
-                       "material": "drucker_prager", "sort_every": w.sort_every,
-                       "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (353 MB particle state per step)"},
+            "config": workload_config(world),
             "fp64": ({"value": value64, "unit": "particle-steps/s", "steps": steps64,
                       "ms_per_step": ms64 / steps64} if not args.no_fp64 else None),
             "kernels_ms_per_step": {k: kt[k][0] / max(1, args.steps) for k in kt},
