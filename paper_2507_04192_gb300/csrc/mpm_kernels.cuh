@@ -20,10 +20,6 @@
 #ifndef MPM_P2G_MINB
 #define MPM_P2G_MINB 3
 #endif
-// P2G forms the next particle's factors before summing the current one.
-#ifndef MPM_P2G_LOOKAHEAD
-#define MPM_P2G_LOOKAHEAD 0
-#endif
 // Resident G2P blocks per SM the single-precision kernel is compiled for.
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 2
@@ -516,79 +512,6 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
         hp = hp && pc.next(off);
         int32_t ppos = hp ? pmap[pc.q] : 0;
 
-#if MPM_P2G_LOOKAHEAD
-        // The factors of the next particle are formed before the current one is
-        // summed (two independent instruction streams in one block).
-        bool hc = cc.next(off);
-        int stage = 0;
-        int live = -1;                                 // cell whose accumulators are live
-        int lc[D], bown[D];
-        R acc[Gm::STENCIL][D + 1];
-        P2GFactors<R, D> fcur, fnext;
-        cp_async_wait<1>();
-        {
-            const R *src = stg + tid;
-            p2g_factors<R, D>(P, [&](int j) { return src[j * NT]; }, fcur);
-        }
-        if (hp) issue(0, ppos);
-        cp_async_commit();
-        hp = hp && pc.next(off);
-        if (hp) ppos = pmap[pc.q];
-        while (hc) {
-            if (cc.c != live) {
-                live = cc.c;
-                int r = live;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const int ci = r % Gm::T;
-                    r /= Gm::T;
-                    lc[a] = ci + 1;
-                    bown[a] = org[a] + ci - 1;
-                }
-                if constexpr (REG) {
-#pragma unroll
-                    for (int kk = 0; kk < Gm::STENCIL; ++kk)
-#pragma unroll
-                        for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
-                }
-            }
-            CellCursor<Gm::TN, NT> nc = cc;
-            const bool hn = nc.next(off);
-            stage ^= 1;
-            cp_async_wait<1>();
-            {
-                const R *src = stg + stage * NCM * NT + tid;
-                p2g_factors<R, D>(P, [&](int j) { return src[j * NT]; }, fnext);
-            }
-            if (hp) issue(stage, ppos);
-            cp_async_commit();
-            hp = hp && pc.next(off);
-            if (hp) ppos = pmap[pc.q];
-            bool own = REG;
-#pragma unroll
-            for (int a = 0; a < D; ++a) own = own && (fcur.b[a] == bown[a]);
-            if (own) {
-                if constexpr (REG) p2g_accumulate<R, D>(fcur, P.mass, acc);
-            } else {
-                bool esc = false;
-                p2g_scatter<R, D>(P, fcur, org, sm, Asim, fsim, esc);
-                any_escape |= esc;
-            }
-            if constexpr (REG) {
-                if (!hn || nc.c != live) {
-#pragma unroll
-                    for (int kk = 0; kk < Gm::STENCIL; ++kk) {
-                        const int li = win_index<D>(lc, kk % 3, (kk / 3) % 3, kk / 9);
-#pragma unroll
-                        for (int v = 0; v <= D; ++v) atomicAdd(&sm[v * Gm::WN + li], acc[kk][v]);
-                    }
-                }
-            }
-            fcur = fnext;
-            cc = nc;
-            hc = hn;
-        }
-#else
         bool hc = cc.next(off);
         int stage = 0;
         int cur = -1;                                  // cell whose accumulators are live
@@ -645,7 +568,6 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
                 }
             }
         }
-#endif
         cp_async_wait<0>();
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
         if (ball && (threadIdx.x & 31) == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));

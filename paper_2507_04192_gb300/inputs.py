@@ -212,6 +212,23 @@ def dam_break_inverse_2d(n_cells: int = 128, n_seg: int = 32, n_track: int = 64,
     return w
 
 
+def shallow_dam_break_2d(dx: float = 0.004, length: float = 1.0, height: float = 0.1, domain: float = 2.5,
+                         sound_speed: float = 35.0, ppc_axis: int = 2, seed: int = 0, dt: float = 1.0e-5,
+                         steps: int = 40_000, sort_every: int = 16) -> Workload:
+    """The shallow-water dam break of Sec. 5.1: a water column ``length`` x
+    ``height`` at the left wall of a ``domain``-long channel, inviscid, slip walls,
+    Tait water whose sound speed is ``sound_speed`` (K = rho0 c^2), 4 particles
+    per cell."""
+    nx = int(round(domain / dx))
+    ny = int(round(3.0 * height / dx))
+    x = lattice_particles((nx, ny), dx, ppc_axis, lambda p: (p[:, 0] < length) & (p[:, 1] < height),
+                          (0.0, 0.0), (length, height), seed)
+    mat = dict(FLUID_WATER, bulk_K=1000.0 * sound_speed ** 2)
+    return Workload(name=f"shallow_dam_break_2d_{nx}x{ny}", dim=2, n_cells=(nx, ny), dx=dx, dt=dt,
+                    gravity=(0.0, -9.8), material=mat, x=x, particle_volume=dx * dx / ppc_axis ** 2, steps=steps,
+                    sort_every=sort_every, extras=dict(body_lo=(0.0, 0.0), body_hi=(length, height), seed=seed))
+
+
 def granular_inverse_3d(n_cells: Tuple[int, int, int] = (192, 192, 96), radius_cells: float = 30,
                         height_cells: float = 60, patches: Tuple[int, int] = (16, 16), n_track: int = 128,
                         n_obs: int = 10, steps: int = 600, seed: int = 0, checkpoint_every: int = 60,
