@@ -80,7 +80,15 @@ enum {
  *              stays correct through a slower path
  *   batch      number of independent simulations sharing the grid shape (>= 1);
  *              particles carry a simulation id (mpm_load_particles)
+ *   transfer   G2P transfer (Sec. 2.2 G2P transfer, Appendix B): MPM_TRANSFER_APIC
+ *              (affine matrix C_p = B_p D_p^-1 carried to the next P2G), _TPIC (the
+ *              particle velocity gradient instead), _PIC (no particle matrix),
+ *              _FLIP (v_p += sum phi (v_i^{n+1} - v_i^n), blended with PIC:
+ *              v_p = v_PIC + flip_alpha (v_p - sum phi v_i^n); no particle matrix;
+ *              positions advance with the PIC velocity)
+ *   flip_alpha FLIP share of the blend, in [0, 1] (used by _FLIP only)
  */
+enum { MPM_TRANSFER_APIC = 0, MPM_TRANSFER_TPIC = 1, MPM_TRANSFER_PIC = 2, MPM_TRANSFER_FLIP = 3 };
 typedef struct {
     int dim;
     int n_cells[3];
@@ -90,6 +98,8 @@ typedef struct {
     int precision;
     int sort_every;
     int batch;
+    int transfer;
+    double flip_alpha;
 } mpm_grid_desc;
 
 /*
@@ -254,7 +264,8 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  * (layouts as for mpm_get_particles, doubles, n particles); the only scratch,
  * the background grid, lives in a static device array of this library holding
  * at most 131072 grid nodes (4 MiB, kept by every GPU that loads the library
- * until the process exits).  Supports dim 2 or 3, MPM_FP64, batch 1, slip walls
+ * until the process exits).  Supports dim 2 or 3, MPM_FP64, batch 1, the APIC
+ * transfer, slip walls
  * (no friction fields), no sorting; gravity, Tait fluid and Drucker-Prager as
  * in mpm_step.  `out` may alias `in` particle by particle.
  *

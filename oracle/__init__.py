@@ -51,6 +51,9 @@ class Params(C.Structure):
         ("particle_volume", C.c_double),
         ("n_seg", (C.c_int * 2) * MAX_WALLS),
         ("mu", C.c_void_p * MAX_WALLS),
+        ("transfer", C.c_int),
+        ("flip_alpha", C.c_double),
+        ("flip_grid", C.c_void_p),
     ]
 
 
@@ -108,7 +111,7 @@ class Oracle:
     """Parameters of one scenario plus the numpy arrays kept alive for ctypes."""
 
     def __init__(self, dim, n_cells, dx, dt, gravity, material, particle_volume,
-                 friction=(), dp_literal=False):
+                 friction=(), dp_literal=False, transfer=0, flip_alpha=1.0):
         P = Params()
         P.dim = dim
         for a in range(3):
@@ -117,6 +120,8 @@ class Oracle:
         P.dx, P.dt = float(dx), float(dt)
         P.material = int(material.get("kind", 0))
         P.dp_literal = int(bool(dp_literal))
+        P.transfer = int(transfer)
+        P.flip_alpha = float(flip_alpha)
         for k in ("rho0", "bulk_K", "gamma", "viscosity", "E", "nu", "phi_deg", "psi_deg",
                   "cohesion", "sigma_t"):
             setattr(P, k, float(material.get(k, 0.0)))
@@ -132,9 +137,9 @@ class Oracle:
         self.dim = dim
 
     @classmethod
-    def from_workload(cls, w, dp_literal=False, dt=None):
+    def from_workload(cls, w, dp_literal=False, dt=None, transfer=0, flip_alpha=1.0):
         return cls(w.dim, w.n_cells, w.dx, w.dt if dt is None else dt, w.gravity, w.material,
-                   w.particle_volume, w.friction, dp_literal)
+                   w.particle_volume, w.friction, dp_literal, transfer, flip_alpha)
 
     # -- state ------------------------------------------------------------------
     def initial_state(self, x: np.ndarray, v: Optional[np.ndarray] = None) -> "State":

@@ -48,6 +48,9 @@ typedef struct {
     double particle_volume;     /* initial volume V_p^0; mass m_p = rho0 V_p^0 */
     int n_seg[ORC_MAX_WALLS][2];
     const double *mu[ORC_MAX_WALLS];   /* per wall: mu[s1 * n_seg0 + s0], NULL = slip */
+    int transfer;               /* 0 = APIC, 1 = TPIC, 2 = PIC, 3 = FLIP / PIC blend (Sec. 2.2 G2P transfer) */
+    double flip_alpha;          /* FLIP share of the blended particle velocity (transfer 3) */
+    const double *flip_grid;    /* transfer 3: grid velocity before the update, set inside orc_step */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -202,9 +205,13 @@ void orc_p2g(const orc_params *P, long n, const double *x, const double *v, cons
         double Vp = mp / rho[p];
         build_stencil(P, xp, &S);
         double D[9], Dinv[9], M[9];
-        moment_matrix(P, xp, &S, D);
-        invert(d, D, Dinv);
-        matmul(d, Bp, Dinv, M);                         /* B_p D_p^{-1} */
+        if (P->transfer == 1) {
+            for (int q = 0; q < d * d; ++q) M[q] = Bp[q];   /* TPIC: the stored quantity is grad v_p */
+        } else {
+            moment_matrix(P, xp, &S, D);
+            invert(d, D, Dinv);
+            matmul(d, Bp, Dinv, M);                     /* B_p D_p^{-1} (zero for PIC) */
+        }
         for (int k = 0; k < S.count; ++k) {
             long i = S.node[k];
             double phi = S.phi[k];
@@ -561,15 +568,25 @@ void orc_g2p(const orc_params *P, long n, const double *gv, double *x, double *v
                 }
             }
         }
+        /* FLIP: v_p += sum phi (v_i^{n+1} - v_i^n), blended with PIC: v_p = vp + alpha (v_p - sum phi v_i^n) */
+        double vflip[3] = {vp[0], vp[1], vp[2]};
+        if (P->transfer == 3 && P->flip_grid) {
+            double vo[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < S.count; ++k)
+                for (int a = 0; a < d; ++a) vo[a] += S.phi[k] * P->flip_grid[S.node[k] * d + a];
+            for (int a = 0; a < d; ++a) vflip[a] = vp[a] + P->flip_alpha * (v[p * d + a] - vo[a]);
+        }
         for (int a = 0; a < d; ++a) {
-            v[p * d + a] = vp[a];
+            v[p * d + a] = vflip[a];
             double xn = xp[a] + dt * vp[a];
             double Lmax = P->n_cells[a] * P->dx;
             if (xn < 0.0) xn = 0.0;
             if (xn > Lmax) xn = Lmax;
             xp[a] = xn;
         }
-        for (int q = 0; q < d * d; ++q) B[p * d * d + q] = Bp[q];
+        /* APIC keeps B_p; TPIC keeps the velocity gradient; PIC keeps nothing */
+        for (int q = 0; q < d * d; ++q)
+            B[p * d * d + q] = P->transfer == 1 ? L[q] : (P->transfer >= 2 ? 0.0 : Bp[q]);
         /* F <- (I + dt L) F */
         double A[9], Fn[9];
         for (int a = 0; a < d; ++a)
@@ -607,6 +624,10 @@ void orc_affine_C(const orc_params *P, long n, const double *x, const double *B,
     int d = P->dim;
     stencil_t S;
     for (long p = 0; p < n; ++p) {
+        if (P->transfer == 1) {
+            for (int q = 0; q < d * d; ++q) C[p * d * d + q] = B[p * d * d + q];
+            continue;
+        }
         build_stencil(P, x + p * d, &S);
         double D[9], Dinv[9];
         moment_matrix(P, x + p * d, &S, D);
@@ -626,14 +647,22 @@ int orc_step(const orc_params *P, long n, double *x, double *v, double *B, doubl
     double *gf = (double *)malloc(sizeof(double) * G * d);
     double *gv = (double *)malloc(sizeof(double) * G * d);
     if (!gm || !gq || !gf || !gv) { free(gm); free(gq); free(gf); free(gv); return -1; }
+    double *gvo = P->transfer == 3 ? (double *)malloc(sizeof(double) * G * d) : NULL;
+    orc_params Q = *P;
+    Q.flip_grid = gvo;
+    double m_eps = 1e-10 * P->rho0 * pow(P->dx, d);
     for (int s = 0; s < n_steps; ++s) {
         memset(gm, 0, sizeof(double) * G);                   /* grid reset */
         memset(gq, 0, sizeof(double) * G * d);
         memset(gf, 0, sizeof(double) * G * d);
         orc_p2g(P, n, x, v, B, rho, sigma, gm, gq, gf);
         orc_grid_update(P, gm, gq, gf, gv);
-        orc_g2p(P, n, gv, x, v, B, F, rho, sigma, eps);
+        if (gvo)                                             /* FLIP: the grid velocity before the update */
+            for (long i = 0; i < G; ++i)
+                for (int a = 0; a < d; ++a) gvo[i * d + a] = gm[i] > m_eps ? gq[i * d + a] / gm[i] : 0.0;
+        orc_g2p(&Q, n, gv, x, v, B, F, rho, sigma, eps);
     }
+    free(gvo);
     free(gm); free(gq); free(gf); free(gv);
     return 0;
 }
@@ -731,6 +760,7 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
 {
     const int sand = P->material == 1;
     if (sand && (!sigma || !sigb1 || !sigb0)) return -2;
+    if (P->transfer != 0) return -3;            /* the adjoint follows the APIC transfer */
     int d = P->dim;
     long G = orc_num_nodes(P);
     double dt = P->dt;

@@ -310,6 +310,8 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     for (int a = 0; a < g.dim; ++a)
         if (g.n_cells[a] < 1 || g.n_cells[a] > 4096) return MPM_EINVAL;
     if (!(g.dx > 0) || !(g.dt > 0) || g.sort_every < 1 || g.batch < 1) return MPM_EINVAL;
+    if (g.transfer < MPM_TRANSFER_APIC || g.transfer > MPM_TRANSFER_FLIP) return MPM_EINVAL;
+    if (g.transfer == MPM_TRANSFER_FLIP && !(g.flip_alpha >= 0.0 && g.flip_alpha <= 1.0)) return MPM_EINVAL;
     if (g.precision != MPM_FP32 && g.precision != MPM_FP64) return MPM_EINVAL;
     if (m.kind != MPM_FLUID && m.kind != MPM_DRUCKER_PRAGER) return MPM_EINVAL;
     if (!(m.rho0 > 0)) return MPM_EINVAL;
@@ -322,6 +324,8 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     HostParams &h = c->hp;
     h.dim = g.dim;
     h.batch = g.batch;
+    h.transfer = g.transfer;
+    h.flip_alpha = g.flip_alpha;
     h.precision = g.precision;
     h.material = m.kind;
     h.dp_literal = m.dp_literal ? 1 : 0;
@@ -409,6 +413,12 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     int rc = MPM_OK;
     if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.A, nodes * 4 * rsz, "grid accumulators");
     if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.V, nodes * 4 * rsz, "grid velocities");
+    if (rc == MPM_OK && g.transfer == MPM_TRANSFER_FLIP) {
+        rc = dalloc(c, (unsigned char **)&ds.A2, nodes * 4 * rsz, "FLIP grid momenta");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.V2, nodes * 4 * rsz, "FLIP grid velocities");
+        if (rc == MPM_OK) cudaMemsetAsync(ds.A2, 0, nodes * 4 * rsz, ds.stream);
+        if (rc == MPM_OK) cudaMemsetAsync(ds.V2, 0, nodes * 4 * rsz, ds.stream);
+    }
     if (rc == MPM_OK) rc = dalloc(c, &ds.flags, (size_t)g.batch * h.node_tiles_per_sim, "node tile flags");
     if (rc == MPM_OK) rc = dalloc(c, &ds.tile_start, ntiles, "tile starts");
     if (rc == MPM_OK) rc = dalloc(c, &ds.tile_end, ntiles, "tile ends");
@@ -441,7 +451,7 @@ void mpm_destroy(mpm_ctx *c)
     if (d.stream) cudaStreamSynchronize(d.stream);
     collect_timing(c);
     free_particles(c);
-    dfree(d.A); dfree(d.V); dfree(d.flags); dfree(d.tile_start); dfree(d.tile_end);
+    dfree(d.A); dfree(d.V); dfree(d.A2); dfree(d.V2); dfree(d.flags); dfree(d.tile_start); dfree(d.tile_end);
     dfree(d.counters); dfree(d.status); dfree(d.escaped);
     for (int w = 0; w < kMaxWalls; ++w) dfree(d.mu_dev[w]);
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -742,6 +752,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: bad argument");
     if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no particles loaded");
     if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_step_adjoint: batch must be 1");
+    if (c->grid.transfer != MPM_TRANSFER_APIC)
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint: the adjoint follows the APIC transfer");
     if (wall < 0 || wall >= 2 * c->grid.dim || c->ds.mu_dev[wall] == nullptr)
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: the wall has no friction field");
     AdjHost &a = c->adj;

@@ -55,7 +55,8 @@ struct WallDev {
 
 // Host-side parameters (double), converted to Params<R> at launch.
 struct HostParams {
-    int dim, batch, precision, material, dp_literal;
+    int dim, batch, precision, material, dp_literal, transfer;
+    double flip_alpha;
     int n_cells[3];
     double dx, dt, gravity[3];
     double rho0, bulk_K, gamma, mass, vol0, m_eps;
@@ -72,7 +73,8 @@ struct Params {
     R dx, inv_dx, dt, gravity[3], L[3];
     R rho0, bulk_K, gamma, inv_rho0, mass, m_eps;
     R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef;
-    int material, dp_literal, gamma_int;
+    int material, dp_literal, gamma_int, transfer, no_force;
+    R flip_alpha;
     int n_tiles[3], G_nodes[3], node_tiles[3];
     int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
     int64_t n, npad;
@@ -107,6 +109,7 @@ struct DevState {
     int32_t *status;              // device status word (bit 0: non-finite state)
     unsigned long long *escaped;  // particles that took the out-of-window path
     double *staging;              // n x 9 doubles for host transfers
+    void *A2 = nullptr, *V2 = nullptr;   // FLIP: (m, q) without forces and the pre-update grid velocity
     void *save_A = nullptr;       // when set, the grid update also copies (m, q + dt f) ...
     void *save_V = nullptr;       // ... and the post-wall velocity of every node it updates here,
     void *save_F = nullptr;       // ... and which node tiles it updated (one word per tile)

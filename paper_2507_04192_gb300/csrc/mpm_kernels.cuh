@@ -259,6 +259,10 @@ __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFact
             Fm[6] = c * s6[4]; Fm[7] = c * s6[5]; Fm[8] = c * s6[2];
         }
     }
+    if (P.no_force) {                                   // FLIP's second pass: momentum only
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Fm[q] = R(0);
+    }
     R fx[D], dw[D][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -612,7 +616,8 @@ template <class R, int D>
 __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restrict__ A,
                                               R4<R> *__restrict__ V, uint32_t *__restrict__ flags,
                                               R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV,
-                                              uint32_t *__restrict__ saveF)
+                                              uint32_t *__restrict__ saveF, R4<R> *__restrict__ A2,
+                                              R4<R> *__restrict__ V2)
 {
     using Gm = Geo<D>;
     const int64_t ut = blockIdx.x;
@@ -677,6 +682,13 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
             }
         }
         Vs[idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
+        if (A2 != nullptr) {                     // FLIP: grid velocity before the update, v_i^n = q_i / m_i
+            const int64_t j2 = (int64_t)sim * P.nodes_per_sim + idx;
+            const R4<R> a2 = A2[j2];
+            A2[j2] = R4<R>{R(0), R(0), R(0), R(0)};
+            const R im = a2.x > P.m_eps ? R(1) / a2.x : R(0);
+            V2[j2] = R4<R>{a2.y * im, a2.z * im, a2.w * im, R(0)};
+        }
         if (saveA != nullptr) {                  // forward grid kept for the reverse sweep
             saveA[(int64_t)sim * P.nodes_per_sim + idx] = acc;
             saveV[(int64_t)sim * P.nodes_per_sim + idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
@@ -849,9 +861,10 @@ template <int D> __host__ __device__ __forceinline__ constexpr int g2p_ncomp(int
     return D + D * D + 1 + (material == 1 ? 7 : 0);
 }
 
-template <class R, int D, class Raw>
+template <class R, int D, bool GENERIC = false, class Raw>
 __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__restrict__ S, int64_t p,
-                                             const R4<R> *Vw, const int org[3], const R4<R> *__restrict__ Vs)
+                                             const R4<R> *Vw, const int org[3], const R4<R> *__restrict__ Vs,
+                                             const R4<R> *__restrict__ V2s = nullptr)
 {
     using Gm = Geo<D>;
     constexpr int J_F = D, J_RHO = D + D * D;
@@ -891,16 +904,45 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
     R trL = R(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) trL += L[a * D + a];
+    // FLIP / PIC blend: v_p = v_PIC + alpha (v_p - sum w v_i^n)
+    R vnew[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) vnew[a] = vp[a];
+    if (GENERIC && P.transfer == 3) {
+        R vo[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) vo[a] = R(0);
+#pragma unroll
+        for (int k = 0; k < Gm::STENCIL; ++k) {
+            const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
+            R wk = R(1);
+            int a3[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                wk *= w[a][kk[a]];
+                a3[a] = b[a] + 2 + kk[a];
+            }
+            const R4<R> v4 = V2s[lin3<D>(a3, P.G_nodes)];
+            const R vi[3] = {v4.x, v4.y, v4.z};
+#pragma unroll
+            for (int a = 0; a < D; ++a) vo[a] += wk * vi[a];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) vnew[a] = vp[a] + P.flip_alpha * (S[(P.off_v + a) * np + p] - vo[a]);
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         R xn = x[a] + P.dt * vp[a];
         xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
-        bad |= !rfinite(xn) || !rfinite(vp[a]);
+        bad |= !rfinite(xn) || !rfinite(vnew[a]);
         S[(P.off_x + a) * np + p] = xn;
-        S[(P.off_v + a) * np + p] = vp[a];
+        S[(P.off_v + a) * np + p] = vnew[a];
     }
+    // particle matrix for the next P2G: APIC C = B D^-1, TPIC the velocity gradient, PIC none
 #pragma unroll
-    for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = Bm[q] * cscale;
+    for (int q = 0; q < D * D; ++q)
+        S[(P.off_C + q) * np + p] = !GENERIC ? Bm[q] * cscale
+                                             : (P.transfer == 1 ? L[q] : (P.transfer >= 2 ? R(0) : Bm[q] * cscale));
     // F <- (I + dt L) F
     R F[D * D];
 #pragma unroll
@@ -954,11 +996,11 @@ template <class R, int D> struct G2PSmem {
 // grid window of velocities is staged by one TMA tiled load; the particles'
 // inputs are staged 256 at a time by TMA bulk copies, double-buffered.  All
 // waits are bounded; a timeout is reported in the status word.
-template <class R, int D>
+template <class R, int D, bool GENERIC>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
     k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV, R *__restrict__ S,
           const R4<R> *__restrict__ V, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
-          int32_t *__restrict__ status)
+          int32_t *__restrict__ status, const R4<R> *__restrict__ V2)
 {
     using Gm = Geo<D>;
     using L = G2PSmem<R, D>;
@@ -1007,6 +1049,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
         bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
         phases ^= 4u;
         const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
+        const R4<R> *V2s = V2 != nullptr ? V2 + (int64_t)sim * P.nodes_per_sim : nullptr;
         for (int j = 0; j < nb; ++j) {
             int64_t a_next = 0;
             if (j + 1 < nb)
@@ -1020,7 +1063,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
             if (ok && i < t.z) {
                 const int64_t p = (int64_t)t.y + i;
                 const R *bb = bufs + (size_t)cur * L::NCMAX * L::PB + (p - a_cur);
-                bad |= !g2p_particle<R, D>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org, Vs);
+                bad |= !g2p_particle<R, D, GENERIC>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org, Vs,
+                                                   V2s);
             }
             __syncthreads();
             a_cur = a_next;
@@ -1222,6 +1266,9 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.eps2_coef = (R)std::sqrt(1.0 / 3.0 + 2.0 / 9.0 * h.q_psi * h.q_psi);
     P.material = h.material;
     P.dp_literal = h.dp_literal;
+    P.transfer = h.transfer;
+    P.flip_alpha = (R)h.flip_alpha;
+    P.no_force = 0;
     P.nodes_per_sim = h.nodes_per_sim;
     P.tiles_per_sim = h.tiles_per_sim;
     P.node_tiles_per_sim = h.node_tiles_per_sim;
@@ -1286,6 +1333,14 @@ template <class R, int D> struct Launch {
         if (nb < 1) nb = 1;
         k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
             P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
+        if (h.transfer == 3) {                       // FLIP: the momenta without forces, for v_i^n
+            auto P2 = P;
+            P2.no_force = 1;
+            cudaMemsetAsync(ds.counters + 2, 0, sizeof(int32_t), ds.stream);
+            k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
+                P2, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap, ds.cell_off, (R4<R> *)ds.A2, ds.flags,
+                ds.escaped);
+        }
     }
     static void grid(const HostParams &h, DevState &ds)
     {
@@ -1293,23 +1348,30 @@ template <class R, int D> struct Launch {
         const int64_t nb = h.batch * h.node_tiles_per_sim;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags,
                                                            (R4<R> *)ds.save_A, (R4<R> *)ds.save_V,
-                                                           (uint32_t *)ds.save_F);
+                                                           (uint32_t *)ds.save_F, (R4<R> *)ds.A2, (R4<R> *)ds.V2);
     }
-    static void g2p(const HostParams &h, DevState &ds)
+    // the APIC transfer has its own instantiation; the others (TPIC, PIC, FLIP) share one
+    template <bool GENERIC> static void g2p_launch(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
         const size_t smem = G2PSmem<R, D>::total;
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_g2p<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_g2p<R, D, GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
         int64_t nb = ds.max_tiles;
         const int64_t cap = (int64_t)ds.num_sms * (sizeof(R) == 4 ? MPM_G2P_MINB : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_g2p<R, D><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V,
-                                                                     ds.tiles + ds.max_tiles, ds.counters, ds.status);
+        k_g2p<R, D, GENERIC><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(
+            P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V, ds.tiles + ds.max_tiles, ds.counters, ds.status,
+            (const R4<R> *)ds.V2);
+    }
+    static void g2p(const HostParams &h, DevState &ds)
+    {
+        if (h.transfer != 0) g2p_launch<true>(h, ds);
+        else g2p_launch<false>(h, ds);
     }
     static void get_field(const HostParams &h, DevState &ds, int field, double *out)
     {

@@ -215,10 +215,11 @@ extern "C" int mpm_step_noalloc(const mpm_grid_desc *grid, const mpm_material *m
     }
     const mpm_grid_desc &gd = *grid;
     const mpm_material &m = *material;
-    if ((gd.dim != 2 && gd.dim != 3) || gd.precision != MPM_FP64 || gd.batch != 1 || !(gd.dx > 0) ||
+    if ((gd.dim != 2 && gd.dim != 3) || gd.precision != MPM_FP64 || gd.batch != 1 ||
+        gd.transfer != MPM_TRANSFER_APIC || !(gd.dx > 0) ||
         !(gd.dt > 0) || (m.kind != MPM_FLUID && m.kind != MPM_DRUCKER_PRAGER) || !(m.rho0 > 0) ||
         (m.kind == MPM_FLUID && (m.viscosity != 0.0 || !(m.bulk_K > 0) || !(m.gamma > 0)))) {
-        set_msg(err, err_len, "mpm_step_noalloc: needs dim 2 or 3, MPM_FP64, batch 1 and a valid material");
+        set_msg(err, err_len, "mpm_step_noalloc: needs dim 2 or 3, MPM_FP64, batch 1, APIC and a valid material");
         return MPM_EINVAL;
     }
     if (!in.x || !in.v || !in.C || !in.F || !in.rho || !out.x || !out.v || !out.C || !out.F || !out.rho ||

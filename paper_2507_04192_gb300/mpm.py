@@ -31,7 +31,7 @@ KERNELS = {"sort": 0, "p2g": 1, "grid": 2, "g2p": 3}
 class GridDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_cells", C.c_int * 3), ("dx", C.c_double), ("dt", C.c_double),
                 ("gravity", C.c_double * 3), ("precision", C.c_int), ("sort_every", C.c_int),
-                ("batch", C.c_int)]
+                ("batch", C.c_int), ("transfer", C.c_int), ("flip_alpha", C.c_double)]
 
 
 class Material(C.Structure):
@@ -331,7 +331,11 @@ def material_struct(mat: dict, dp_literal: bool = False) -> Material:
     return m
 
 
-def grid_struct(dim, n_cells, dx, dt, gravity, precision=MPM_FP32, sort_every=8, batch=1) -> GridDesc:
+MPM_TRANSFER_APIC, MPM_TRANSFER_TPIC, MPM_TRANSFER_PIC, MPM_TRANSFER_FLIP = 0, 1, 2, 3
+
+
+def grid_struct(dim, n_cells, dx, dt, gravity, precision=MPM_FP32, sort_every=8, batch=1,
+                transfer=MPM_TRANSFER_APIC, flip_alpha=1.0) -> GridDesc:
     g = GridDesc()
     g.dim = int(dim)
     for a in range(3):
@@ -341,6 +345,8 @@ def grid_struct(dim, n_cells, dx, dt, gravity, precision=MPM_FP32, sort_every=8,
     g.precision = int(precision)
     g.sort_every = int(sort_every)
     g.batch = int(batch)
+    g.transfer = int(transfer)
+    g.flip_alpha = float(flip_alpha)
     return g
 
 
@@ -348,16 +354,18 @@ class Simulation:
     """One libmpm context: a grid, a material and a set of particles."""
 
     def __init__(self, dim, n_cells, dx, dt, gravity, material: dict, precision=MPM_FP32, sort_every=8,
-                 batch=1, stream: int = 0, dp_literal=False):
+                 batch=1, stream: int = 0, dp_literal=False, transfer=MPM_TRANSFER_APIC, flip_alpha=1.0):
         self.dim = dim
-        self._grid = grid_struct(dim, n_cells, dx, dt, gravity, precision, sort_every, batch)
+        self._grid = grid_struct(dim, n_cells, dx, dt, gravity, precision, sort_every, batch, transfer, flip_alpha)
         self._mat = material_struct(material, dp_literal)
         self.ctx = mpm_create(self._grid, self._mat, stream)
 
     @classmethod
-    def from_workload(cls, w, precision=MPM_FP32, sort_every=None, batch=1, stream=0, load=True, dt=None):
+    def from_workload(cls, w, precision=MPM_FP32, sort_every=None, batch=1, stream=0, load=True, dt=None,
+                      transfer=MPM_TRANSFER_APIC, flip_alpha=1.0):
         sim = cls(w.dim, w.n_cells, w.dx, w.dt if dt is None else dt, w.gravity, w.material, precision,
-                  w.sort_every if sort_every is None else sort_every, batch, stream)
+                  w.sort_every if sort_every is None else sort_every, batch, stream, transfer=transfer,
+                  flip_alpha=flip_alpha)
         if load:
             sim.load(w.x, w.v, w.particle_volume)
             for wall, nseg, mu in w.friction:
