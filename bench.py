@@ -40,6 +40,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(v: float, device=None) -> float:
+    """The largest value over the ranks of the default process group (the value
+    itself without one).  Replicas only: this and the barriers are the whole
+    multi-GPU protocol; no data crosses between ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of N replicas: the units all ranks processed over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -360,17 +379,12 @@ def bench_ours(args):
     ms64 = timed_run(mpm.MPM_FP64, steps64, 3)[0] if not args.no_fp64 else float("nan")
 
     def reduce_max(v):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
+        return max_over_ranks(v, dev)
 
     ms32 = reduce_max(ms32)
     ms64 = reduce_max(ms64)
-    value = world * n * args.steps / (ms32 * 1e-3)
-    value64 = world * n * steps64 / (ms64 * 1e-3)
+    value = replica_value(n * args.steps, world, ms32 * 1e-3)
+    value64 = replica_value(n * steps64, world, ms64 * 1e-3)
 
     # end to end through the C-ABI with host buffers: load (h2d), steps, read back (d2h)
     torch.cuda.synchronize(dev)
