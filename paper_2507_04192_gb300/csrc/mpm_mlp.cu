@@ -43,34 +43,9 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, __nv_bflo
     }
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
-
-// Hidden epilogue: z += b; x_next = bf16(GELU(z)).
-__global__ void k_bias_gelu(float *__restrict__ z, const float *__restrict__ b, __nv_bfloat16 *__restrict__ xnext,
-                            int rows, int cols)
-{
-    const int64_t n = (int64_t)rows * cols;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = z[i] + b[i % cols];
-        z[i] = v;
-        xnext[i] = __float2bfloat16_rn(gelu_f(v));
-    }
-}
-
-// Output epilogue: z += b; y = lo + (hi - lo) sigmoid(z).
-__global__ void k_bias_sigmoid(float *__restrict__ z, const float *__restrict__ b, float *__restrict__ y, int rows,
-                               int cols, float lo, float hi)
-{
-    const int64_t n = (int64_t)rows * cols;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = z[i] + b[i % cols];
-        z[i] = v;
-        y[i] = lo + (hi - lo) / (1.0f + expf(-v));
-    }
 }
 
 // Loss and output gradient: L = mean (y - t)^2; dz = dL/dy (hi - lo) s (1 - s).
@@ -172,16 +147,23 @@ int forward(mpm_mlp *m, int B)
 {
     for (int l = 0; l < m->L; ++l) {
         const int K = m->w[l], N = m->w[l + 1];
-        cudaError_t e = umma_gemm(B, N, K, m->X[l], K, m->Wb[l], K, m->Z[l], N, m->status, m->stream);
+        // z = x W^T + b with the activation fused into the GEMM epilogue
+        UmmaEpi epi;
+        epi.bias = m->b[l];
+        if (l + 1 < m->L) {
+            epi.mode = kEpiBiasGelu;
+            epi.xnext = m->X[l + 1];
+        } else {
+            epi.mode = kEpiBiasSigmoid;
+            epi.y = m->Y;
+            epi.lo = m->lo;
+            epi.hi = m->hi;
+        }
+        cudaError_t e = umma_gemm_tma(B, N, K, m->X[l], K, m->Wb[l], K, m->Z[l], N, epi, m->status, m->stream);
         if (e != cudaSuccess) {
             m->err = std::string("gemm launch: ") + cudaGetErrorString(e);
             return MPM_ECUDA;
         }
-        const int64_t n = (int64_t)B * N;
-        if (l + 1 < m->L)
-            k_bias_gelu<<<blocks_for(n), 256, 0, m->stream>>>(m->Z[l], m->b[l], m->X[l + 1], B, N);
-        else
-            k_bias_sigmoid<<<blocks_for(n), 256, 0, m->stream>>>(m->Z[l], m->b[l], m->Y, B, N, m->lo, m->hi);
     }
     return MPM_OK;
 }
@@ -236,7 +218,7 @@ int mpm_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, in
         !status_dev)
         return MPM_EINVAL;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return MPM_EINVAL;
-    cudaError_t e = umma_gemm(M, N, K, (const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, C, ldc,
+    cudaError_t e = umma_gemm_tma(M, N, K, (const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, C, ldc, UmmaEpi{},
                               status_dev, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? MPM_OK : MPM_ECUDA;
 }
@@ -403,12 +385,13 @@ int mpm_mlp_train_step(mpm_mlp *m, int batch, const float *x, const float *targe
         transpose(m, m->dZb[l], m->dZbT[l], B, N);          // N x B
         transpose(m, m->X[l], m->XT[l], B, Kin);             // Kin x B
         // dW = dZ^T X : (N x B) (Kin x B)^T
-        cudaError_t e = umma_gemm(N, Kin, B, m->dZbT[l], B, m->XT[l], B, m->gW[l], Kin, m->status, m->stream);
+        cudaError_t e = umma_gemm_tma(N, Kin, B, m->dZbT[l], B, m->XT[l], B, m->gW[l], Kin, UmmaEpi{}, m->status,
+                                      m->stream);
         if (e != cudaSuccess) return MPM_ECUDA;
         k_col_sum<<<(N + 255) / 256, 256, 0, m->stream>>>(m->dZ[l], m->gb[l], B, N);
         if (l > 0) {
             // dA = dZ W : (B x N) (Kin x N)^T
-            e = umma_gemm(B, Kin, N, m->dZb[l], N, m->WbT[l], N, m->dA, Kin, m->status, m->stream);
+            e = umma_gemm_tma(B, Kin, N, m->dZb[l], N, m->WbT[l], N, m->dA, Kin, UmmaEpi{}, m->status, m->stream);
             if (e != cudaSuccess) return MPM_ECUDA;
             k_gelu_back<<<blocks_for((int64_t)B * Kin), 256, 0, m->stream>>>(m->dA, m->Z[l - 1], m->dZ[l - 1],
                                                                             (int64_t)B * Kin);

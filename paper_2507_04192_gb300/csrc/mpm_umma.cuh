@@ -1,18 +1,16 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a:
 //   C[M x N] (fp32) = A[M x K] (bf16, row-major) * B[N x K]^T (bf16, row-major)
-// Both operands are K-major.  One CTA of 128 threads computes a 128 x NT tile:
-// it stages K-chunks of 64 of A and B in shared memory in the canonical
-// no-swizzle layout (8-row x 16-byte core matrices; consecutive core matrices
-// along K 128 bytes apart, along M/N 8 * 128 bytes apart), one elected thread
-// issues tcgen05.mma (M = 128, N = NT, K = 16 per instruction) into a TMEM
-// accumulator of NT fp32 columns, and tcgen05.commit signals an mbarrier when
-// the MMAs have read the chunk.  The 4 warps then read their 32 TMEM lanes
-// (rows) with tcgen05.ld and store the tile.  Every wait is bounded; on a
-// timeout the kernel records it in the status word, frees its TMEM and leaves.
+// Both operands are K-major.  One CTA of 128 threads computes a 128 x NT tile
+// with an fp32 accumulator of NT columns in TMEM (tcgen05.mma, M = 128, N = NT,
+// K = 16 per instruction); the operand tiles arrive by TMA through a ring of
+// shared-memory stages; the 4 warps read their 32 TMEM lanes (rows) with
+// tcgen05.ld for the epilogue.  Every wait is bounded; on a timeout the kernel
+// records it in the status word, frees its TMEM and leaves.
 #pragma once
 
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "mpm_internal.cuh"
 
@@ -27,17 +25,6 @@ __device__ __forceinline__ uint32_t umma_smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor (tcgen05): start address, leading (K) and
-// stride (M/N) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;                      // version
-    return d;                                    // base offset 0, lbo mode 0, layout 0 (no swizzle)
-}
 
 // Instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A and
 // B, both K-major, shape M x N.
@@ -49,43 +36,76 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
            | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_mbar_init(uint64_t *bar)
+
+// Pipeline: the operand tiles are brought in by TMA (cp.async.bulk.tensor,
+// 128-byte swizzle: a K-chunk of 64 bf16 is one 128-byte swizzle row per M/N
+// row) through a ring of kUmmaStages shared-memory stages.  Thread 0 produces
+// (waits for a free stage, arms its mbarrier with the byte count, issues the
+// two tile loads); thread 32 consumes (waits for a full stage, issues the four
+// K = 16 MMAs, commits them to the stage's "empty" mbarrier so the producer can
+// refill it).  A final commit signals the epilogue, which reads TMEM and either
+// stores C or applies bias + GELU (bf16 copy for the next layer) or bias +
+// scaled sigmoid.  All waits are bounded.
+constexpr int kUmmaStages = 4;
+enum UmmaEpilogue { kEpiStore = 0, kEpiBiasGelu = 1, kEpiBiasSigmoid = 2 };
+
+struct UmmaEpi {
+    int mode = kEpiStore;
+    const float *bias = nullptr;      // N
+    __nv_bfloat16 *xnext = nullptr;   // kEpiBiasGelu: bf16 GELU(z), ld = ldc
+    float *y = nullptr;               // kEpiBiasSigmoid: lo + (hi - lo) sigmoid(z), ld = ldc
+    float lo = 0.f, hi = 1.f;
+};
+
+// Shared-memory descriptor of a K-major tile written by TMA with 128-byte
+// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte
+// offset), layout type SWIZZLE_128B.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused within a swizzle row)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                      // version
+    d |= (uint64_t)2 << 61;                      // layout: 128-byte swizzle
+    return d;
 }
 
-__device__ __forceinline__ bool umma_mbar_wait(uint64_t *bar, uint32_t phase)
+__device__ __forceinline__ bool umma_wait_parity(uint64_t *bar, uint32_t parity)
 {
     for (int it = 0; it < (1 << 22); ++it) {
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(ok)
-                     : "r"(umma_smem_u32(bar)), "r"(phase)
+                     : "r"(umma_smem_u32(bar)), "r"(parity)
                      : "memory");
         if (ok) return true;
     }
     return false;
 }
 
+__device__ __forceinline__ float umma_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
 template <int NT>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
-    k_umma_gemm(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
-                int ldb, float *__restrict__ Cout, int ldc, int32_t *__restrict__ status)
+    k_umma_gemm_tma(int M, int N, int K, const __grid_constant__ CUtensorMap tmA,
+                    const __grid_constant__ CUtensorMap tmB, float *__restrict__ Cout, int ldc, UmmaEpi epi,
+                    int32_t *__restrict__ status)
 {
     static_assert(NT % 16 == 0 && NT >= 32 && NT <= 256, "tile width");
     constexpr int TMEM_COLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
-    constexpr uint32_t LBO = 128, SBO = (kUmmaKC / 8) * 128;
+    constexpr uint32_t A_BYTES = kUmmaM * kUmmaKC * 2, B_BYTES = NT * kUmmaKC * 2;
+    constexpr uint32_t STAGE = A_BYTES + B_BYTES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                              ~uintptr_t(1023));
-    unsigned char *sA = sbase;                                    // 128 x 64 bf16 = 16 KB
-    unsigned char *sB = sbase + kUmmaM * kUmmaKC * 2;             // NT x 64 bf16
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full[kUmmaStages], empty[kUmmaStages], done;
     __shared__ uint32_t tmem_base;
+    __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kUmmaM, n0 = blockIdx.y * NT;
+    const int nk = (K + kUmmaKC - 1) / kUmmaKC;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -94,48 +114,58 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) umma_mbar_init(&mbar);
+    if (tid == 0) {
+        for (int s = 0; s < kUmmaStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    uint32_t phase = 0;
-    bool ok = true;
-    const int nchunks = (K + kUmmaKC - 1) / kUmmaKC;
-    for (int kc = 0; kc < nchunks && ok; ++kc) {
-        const int k0 = kc * kUmmaKC;
-        // stage A and B chunks: one 16-byte row of a core matrix per copy
-        for (int q = tid; q < (kUmmaM + NT) * (kUmmaKC / 8); q += kUmmaThreads) {
-            const bool isA = q < kUmmaM * (kUmmaKC / 8);
-            const int qq = isA ? q : q - kUmmaM * (kUmmaKC / 8);
-            const int r = qq / (kUmmaKC / 8), k8 = qq % (kUmmaKC / 8);
-            const int grow = (isA ? m0 : n0) + r, gk = k0 + k8 * 8;
-            const int rows = isA ? M : N;
-            const __nv_bfloat16 *src = isA ? A + (int64_t)grow * lda + gk : B + (int64_t)grow * ldb + gk;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (grow < rows) {
-                if (gk + 8 <= K) {
-                    v = *reinterpret_cast<const uint4 *>(src);
-                } else {
-                    __nv_bfloat16 t[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) t[e] = gk + e < K ? src[e] : __float2bfloat16(0.f);
-                    v = *reinterpret_cast<const uint4 *>(t);
-                }
+    if (tid == 0) {                                        // producer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kUmmaStages;
+            const uint32_t ph = (uint32_t)(kc / kUmmaStages) & 1u;
+            if (!umma_wait_parity(&empty[s], ph ^ 1u)) {
+                failed = 1;
+                break;
             }
-            unsigned char *dst = (isA ? sA : sB) + ((r >> 3) * (kUmmaKC / 8) + k8) * 128 + (r & 7) * 16;
-            *reinterpret_cast<uint4 *>(dst) = v;
+            const uint32_t sa = umma_smem_u32(sbase + s * STAGE), sb = sa + A_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma_smem_u32(&full[s])),
+                         "r"(STAGE)
+                         : "memory");
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3}], [%4];" ::"r"(sa),
+                         "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kc * kUmmaKC), "r"(m0),
+                         "r"(umma_smem_u32(&full[s]))
+                         : "memory");
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3}], [%4];" ::"r"(sb),
+                         "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kc * kUmmaKC), "r"(n0),
+                         "r"(umma_smem_u32(&full[s]))
+                         : "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == 32) {                                // MMA issuer
+        const uint32_t idesc = umma_idesc_bf16(kUmmaM, NT);
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kUmmaStages;
+            const uint32_t ph = (uint32_t)(kc / kUmmaStages) & 1u;
+            if (!umma_wait_parity(&full[s], ph)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t idesc = umma_idesc_bf16(kUmmaM, NT);
+            const uint32_t sa = umma_smem_u32(sbase + s * STAGE), sb = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < kUmmaKC / 16; ++kk) {
-                const uint64_t da = umma_smem_desc(umma_smem_u32(sA) + kk * 2 * 128, LBO, SBO);
-                const uint64_t db = umma_smem_desc(umma_smem_u32(sB) + kk * 2 * 128, LBO, SBO);
+                const uint64_t da = umma_desc_sw128(sa + kk * 32), db = umma_desc_sw128(sb + kk * 32);
                 const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -143,16 +173,19 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                              : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             umma_smem_u32(&mbar))
+                             umma_smem_u32(&empty[s]))
                          : "memory");
         }
-        const bool done = umma_mbar_wait(&mbar, phase);
-        phase ^= 1u;
-        ok = __syncthreads_and(done);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) failed = 1;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         umma_smem_u32(&done))
+                     : "memory");
     }
+    __syncwarp();
+    const bool fin = umma_wait_parity(&done, 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool ok = __syncthreads_and(fin) && !failed;
     if (ok) {
-        // epilogue: warp w holds TMEM lanes (rows) 32 w .. 32 w + 31
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < NT; c0 += 8) {
             uint32_t r[8];
@@ -167,7 +200,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int col = n0 + c0 + e;
-                    if (col < N) Cout[(int64_t)row * ldc + col] = __uint_as_float(r[e]);
+                    if (col >= N) continue;
+                    float z = __uint_as_float(r[e]);
+                    const int64_t o = (int64_t)row * ldc + col;
+                    if (epi.mode != kEpiStore) z += epi.bias[col];
+                    Cout[o] = z;
+                    if (epi.mode == kEpiBiasGelu) epi.xnext[o] = __float2bfloat16_rn(umma_gelu(z));
+                    else if (epi.mode == kEpiBiasSigmoid) epi.y[o] = epi.lo + (epi.hi - epi.lo) / (1.0f + expf(-z));
                 }
             }
         }
@@ -181,24 +220,53 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                      : "memory");
 }
 
-template <int NT> constexpr size_t umma_smem_bytes() { return (size_t)(kUmmaM + NT) * kUmmaKC * 2 + 1024; }
-
-// C = A B^T for bf16 row-major A (M x K) and B (N x K); fp32 C (M x N).
-inline cudaError_t umma_gemm(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                             float *C, int ldc, int32_t *status, cudaStream_t stream)
+template <int NT> constexpr size_t umma_tma_smem_bytes()
 {
-    if (N <= 32) {
+    return (size_t)kUmmaStages * (kUmmaM + NT) * kUmmaKC * 2 + 1024;
+}
+
+// 2D tensor map of a row-major bf16 matrix (rows x cols, leading dimension ld
+// elements) for boxes of box_rows x 64 with 128-byte swizzle.
+inline bool umma_tensor_map(CUtensorMap *tm, const __nv_bfloat16 *ptr, int rows, int cols, int ld, int box_rows)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kUmmaKC, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), gdim, gstride, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C = A B^T through the pipelined TMA kernel, with an optional fused epilogue.
+inline cudaError_t umma_gemm_tma(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
+                                 int ldb, float *C, int ldc, const UmmaEpi &epi, int32_t *status, cudaStream_t stream)
+{
+    CUtensorMap tmA, tmB;
+    const int NT = N <= 32 ? 32 : 128;
+    if (!umma_tensor_map(&tmA, A, M, K, lda, kUmmaM) || !umma_tensor_map(&tmB, B, N, K, ldb, NT))
+        return cudaErrorInvalidValue;
+    dim3 g((M + kUmmaM - 1) / kUmmaM, (N + NT - 1) / NT);
+    if (NT == 32) {
         static bool a = false;
-        if (!a) { cudaFuncSetAttribute(k_umma_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_smem_bytes<32>()); a = true; }
-        dim3 g((M + kUmmaM - 1) / kUmmaM, (N + 31) / 32);
-        k_umma_gemm<32><<<g, kUmmaThreads, umma_smem_bytes<32>(), stream>>>(M, N, K, A, lda, B, ldb, C, ldc, status);
+        if (!a) { cudaFuncSetAttribute(k_umma_gemm_tma<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_tma_smem_bytes<32>()); a = true; }
+        k_umma_gemm_tma<32><<<g, kUmmaThreads, umma_tma_smem_bytes<32>(), stream>>>(M, N, K, tmA, tmB, C, ldc, epi, status);
     } else {
         static bool a = false;
-        if (!a) { cudaFuncSetAttribute(k_umma_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_smem_bytes<128>()); a = true; }
-        dim3 g((M + kUmmaM - 1) / kUmmaM, (N + 127) / 128);
-        k_umma_gemm<128><<<g, kUmmaThreads, umma_smem_bytes<128>(), stream>>>(M, N, K, A, lda, B, ldb, C, ldc, status);
+        if (!a) { cudaFuncSetAttribute(k_umma_gemm_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_tma_smem_bytes<128>()); a = true; }
+        k_umma_gemm_tma<128><<<g, kUmmaThreads, umma_tma_smem_bytes<128>(), stream>>>(M, N, K, tmA, tmB, C, ldc, epi, status);
     }
     return cudaGetLastError();
 }
+
 
 }  // namespace mpm
