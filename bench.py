@@ -104,6 +104,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def load_peaks_bf16() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("bf16_tflops", 1900.0))
+    return 1900.0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -316,9 +323,25 @@ def secondary_measurements(stream, dev):
     inf = _event_ms(stream, lambda: [net.infer(xs) for _ in range(reps)]) / reps
     net.close()
     fl_fwd = 2 * 256 * sum(W[i] * W[i + 1] for i in range(3))
+    # the tensor-core GEMM itself on a shape large enough to fill the GPU
+    import torch
+    gM, gN, gK = 8192, 2048, 2048
+    ga = torch.randn(gM, gK, device="cuda").to(torch.bfloat16)
+    gb = torch.randn(gN, gK, device="cuda").to(torch.bfloat16)
+    gc = torch.empty(gM, gN, device="cuda")
+    gst = torch.zeros(1, dtype=torch.int32, device="cuda")
+    run = lambda: mpm.mpm_gemm_bf16(gM, gN, gK, ga.data_ptr(), gK, gb.data_ptr(), gK, gc.data_ptr(), gN,
+                                    gst.data_ptr(), stream.cuda_stream)
+    for _ in range(3):
+        run()
+    gms = _event_ms(stream, lambda: [run() for _ in range(10)]) / 10
+    peak_tf = load_peaks_bf16()
+    gemm_tf = 2.0 * gM * gN * gK / (gms * 1e-3) / 1e12
     out["mlp"] = {"widths": W, "batch": 256, "train_step_ms": tr, "infer_ms": inf,
                   "train_tflops": 3 * fl_fwd / (tr * 1e-3) / 1e12,
-                  "note": "host-synchronous calls incl. host<->device copies of x, targets and loss"}
+                  "note": "host-synchronous calls incl. host<->device copies of x, targets and loss",
+                  "gemm": {"shape": [gM, gN, gK], "ms": gms, "tflops": gemm_tf, "peak": peak_tf,
+                           "frac": gemm_tf / peak_tf, "peak_source": "measured bf16_tflops (cuBLAS burst)"}}
     return out
 
 
