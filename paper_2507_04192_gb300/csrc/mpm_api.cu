@@ -422,7 +422,8 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     if (rc == MPM_OK) rc = dalloc(c, &ds.flags, (size_t)g.batch * h.node_tiles_per_sim, "node tile flags");
     if (rc == MPM_OK) rc = dalloc(c, &ds.tile_start, ntiles, "tile starts");
     if (rc == MPM_OK) rc = dalloc(c, &ds.tile_end, ntiles, "tile ends");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.counters, 4, "counters");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.counters, 8, "counters");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.node_list, (size_t)g.batch * h.node_tiles_per_sim, "node tile list");
     if (rc == MPM_OK) rc = dalloc(c, &ds.status, 1, "status");
     if (rc == MPM_OK) rc = dalloc(c, &ds.escaped, 1, "escape counter");
     if (rc == MPM_OK && cudaMallocHost((void **)&c->h_status, sizeof(int32_t)) != cudaSuccess) rc = MPM_ENOMEM;
@@ -430,7 +431,7 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
         cudaMemsetAsync(ds.A, 0, nodes * 4 * rsz, ds.stream);
         cudaMemsetAsync(ds.V, 0, nodes * 4 * rsz, ds.stream);
         cudaMemsetAsync(ds.flags, 0, sizeof(uint32_t) * g.batch * h.node_tiles_per_sim, ds.stream);
-        cudaMemsetAsync(ds.counters, 0, sizeof(int32_t) * 4, ds.stream);
+        cudaMemsetAsync(ds.counters, 0, sizeof(int32_t) * 8, ds.stream);
         cudaMemsetAsync(ds.status, 0, sizeof(int32_t), ds.stream);
         cudaMemsetAsync(ds.escaped, 0, sizeof(unsigned long long), ds.stream);
         if (cudaStreamSynchronize(ds.stream) != cudaSuccess) rc = MPM_ECUDA;
@@ -451,7 +452,8 @@ void mpm_destroy(mpm_ctx *c)
     if (d.stream) cudaStreamSynchronize(d.stream);
     collect_timing(c);
     free_particles(c);
-    dfree(d.A); dfree(d.V); dfree(d.A2); dfree(d.V2); dfree(d.flags); dfree(d.tile_start); dfree(d.tile_end);
+    dfree(d.A); dfree(d.V); dfree(d.A2); dfree(d.V2); dfree(d.flags); dfree(d.node_list);
+    dfree(d.tile_start); dfree(d.tile_end);
     dfree(d.counters); dfree(d.status); dfree(d.escaped);
     for (int w = 0; w < kMaxWalls; ++w) dfree(d.mu_dev[w]);
     for (auto e : c->event_pool) cudaEventDestroy(e);
@@ -851,6 +853,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         ds.save_A = gridA_ptr(j);
         ds.save_V = gridV_ptr(j);
         ds.save_F = gridF_ptr(j);
+        CK(cudaMemsetAsync(ds.save_F, 0, sizeof(uint32_t) * h.node_tiles_per_sim, ds.stream), "tile flags");
         return MPM_OK;
     };
     auto stop_keeping = [&]() { ds.save_A = ds.save_V = ds.save_F = nullptr; };

@@ -75,6 +75,8 @@ struct Params {
     R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef;
     int material, dp_literal, gamma_int, transfer, no_force;
     R flip_alpha;
+    uint32_t *flags;              // node tile flags, the touched-tile list and its length
+    int32_t *node_list, *list_count;
     int n_tiles[3], G_nodes[3], node_tiles[3];
     int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
     int64_t n, npad;
@@ -103,9 +105,11 @@ struct DevState {
     int32_t *perm;                // gather permutation of the last sort
     int32_t *posmap;              // per particle in (cell, rank) order: its slot relative to the tile start
     int32_t *cell_off;            // per compact tile: TN + 1 exclusive prefix sums of the cell counts
-    int32_t *counters;            // [1] n_active_tiles, [2] P2G tile cursor, [3] G2P tile cursor
+    int32_t *counters;            // [1] n_active_tiles, [2] P2G tile cursor, [3] G2P tile cursor,
+                                  // [4] length of the touched node-tile list
     void *A, *V;                  // grid accumulators and velocities, R4 per node
     uint32_t *flags;              // per node tile: touched since the last grid update
+    int32_t *node_list;           // the touched node tiles, in the order P2G touched them
     int32_t *status;              // device status word (bit 0: non-finite state)
     unsigned long long *escaped;  // particles that took the out-of-window path
     double *staging;              // n x 9 doubles for host transfers

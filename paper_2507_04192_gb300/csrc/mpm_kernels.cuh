@@ -364,6 +364,13 @@ template <int D> __device__ __forceinline__ int win_index(const int l[D], int k0
     else return ((l[2] + k2) * Gm::W + (l[1] + k1)) * Gm::W + (l[0] + k0);
 }
 
+// Marks node tile g touched and, the first time, appends it to the list the grid
+// update walks.
+__device__ __forceinline__ void mark_node_tile(uint32_t *flags, int32_t *list, int32_t *count, int64_t g)
+{
+    if (flags[g] == 0u && atomicExch(&flags[g], 1u) == 0u) list[atomicAdd(count, 1)] = (int32_t)g;
+}
+
 // Scatter one particle's 3^D contributions: shared-memory atomics when its stencil
 // lies in the window (l = window coordinates of its base), else global atomics.
 template <class R, int D>
@@ -398,7 +405,7 @@ __device__ __forceinline__ void p2g_scatter(const Params<R> &P, const P2GFactors
                 u[a] = a3[a] / Gm::T;
             }
             red_add4(&Asim[lin3<D>(a3, P.G_nodes)], m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
-            flags_sim[lin3<D>(u, P.node_tiles)] = 1u;
+            mark_node_tile(P.flags, P.node_list, P.list_count, (flags_sim - P.flags) + lin3<D>(u, P.node_tiles));
         }
     }
 }
@@ -601,7 +608,8 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
             int u[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((threadIdx.x >> a) & 1);
-            fsim[lin3<D>(u, P.node_tiles)] = 1u;
+            mark_node_tile(flags, P.node_list, P.list_count,
+                           (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
         }
     }
     if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
@@ -609,7 +617,7 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
 
 // ------------------------------------------------------------------ grid update
 
-// One CTA per node tile; tiles not touched by the last P2G return at once.
+// Blocks walk the list of node tiles the last P2G touched.
 // Reads (m, q + dt f), writes the contact-corrected velocity and clears the
 // accumulator for the next step.
 template <class R, int D>
@@ -617,14 +625,13 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
                                               R4<R> *__restrict__ V, uint32_t *__restrict__ flags,
                                               R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV,
                                               uint32_t *__restrict__ saveF, R4<R> *__restrict__ A2,
-                                              R4<R> *__restrict__ V2)
+                                              R4<R> *__restrict__ V2, const int32_t *__restrict__ list,
+                                              const int32_t *__restrict__ count)
 {
     using Gm = Geo<D>;
-    const int64_t ut = blockIdx.x;
-    if (flags[ut] == 0u) {
-        if (saveF != nullptr && threadIdx.x == 0) saveF[ut] = 0u;
-        return;
-    }
+    const int n_list = *count;
+    for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const int64_t ut = list[li];
     if (saveF != nullptr && threadIdx.x == 0) saveF[ut] = 1u;
     const int sim = (int)(ut / P.node_tiles_per_sim);
     int64_t r = ut - (int64_t)sim * P.node_tiles_per_sim;
@@ -694,8 +701,8 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
             saveV[(int64_t)sim * P.nodes_per_sim + idx] = R4<R>{vel[0], vel[1], vel[2], R(0)};
         }
     }
-    __syncthreads();
     if (threadIdx.x == 0) flags[ut] = 0u;
+    }
 }
 
 // ------------------------------------------------------------------ G2P
@@ -1077,7 +1084,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
         }
     }
     if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(status, (int32_t)kStatusNaN);
-    if (tid == 0) counters[2] = 0;                 // P2G cursor for the next kernel (P2G follows)
+    if (tid == 0) {
+        counters[2] = 0;                           // P2G cursor for the next kernel (P2G follows)
+        counters[4] = 0;                           // the grid update has walked the touched-tile list
+    }
 }
 
 // ------------------------------------------------------------------ state management
@@ -1269,6 +1279,9 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.transfer = h.transfer;
     P.flip_alpha = (R)h.flip_alpha;
     P.no_force = 0;
+    P.flags = ds.flags;
+    P.node_list = ds.node_list;
+    P.list_count = ds.counters + 4;
     P.nodes_per_sim = h.nodes_per_sim;
     P.tiles_per_sim = h.tiles_per_sim;
     P.node_tiles_per_sim = h.node_tiles_per_sim;
@@ -1345,10 +1358,12 @@ template <class R, int D> struct Launch {
     static void grid(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
-        const int64_t nb = h.batch * h.node_tiles_per_sim;
+        int64_t nb = h.batch * h.node_tiles_per_sim;        // blocks walk the touched-tile list
+        if (nb > (int64_t)ds.num_sms * 8) nb = (int64_t)ds.num_sms * 8;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags,
                                                            (R4<R> *)ds.save_A, (R4<R> *)ds.save_V,
-                                                           (uint32_t *)ds.save_F, (R4<R> *)ds.A2, (R4<R> *)ds.V2);
+                                                           (uint32_t *)ds.save_F, (R4<R> *)ds.A2, (R4<R> *)ds.V2,
+                                                           ds.node_list, ds.counters + 4);
     }
     // the APIC transfer has its own instantiation; the others (TPIC, PIC, FLIP) share one
     template <bool GENERIC> static void g2p_launch(const HostParams &h, DevState &ds)
