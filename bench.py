@@ -178,7 +178,7 @@ def cpu_baseline_full_step():
 def workload_config(world: int) -> dict:
     """The headline workload (the same object on both arms)."""
     return {"workload": WORKLOAD, "particles": 2761536, "grid": "256x256x128", "precision": "fp32",
-            "material": "drucker_prager", "sort_every": 16, "parallelism": f"replicas{world}",
+            "material": "drucker_prager", "sort_every": 32, "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (353 MB particle state per step)"}
 
 
@@ -252,9 +252,11 @@ def _event_ms(stream, fn):
 
 def secondary_measurements(stream, dev):
     """The other hot-path rows, each on its own workload: the checkpointed
-    adjoint of the 128 x 128 dam-break inverse (FP32, 500 steps, checkpoint 50),
-    a batch of 256 independent 96 x 96 dam breaks (FP32, 300 steps), and the
-    640-256-256-32 network's training step and inference at batch 256."""
+    adjoint of the 128 x 128 dam-break inverse (FP32, 500 steps, checkpoint 50)
+    and of the 3D granular inverse (1.36M particles, 600 steps, checkpoint 60),
+    a batch of 256 independent 96 x 96 dam breaks (FP32, 300 steps), the 3D dam
+    break with two rigid columns (1.92M particles, FP32), and the 640-256-256-32
+    network's training step and inference at batch 256."""
     from paper_2507_04192_gb300 import inputs, mpm
 
     out = {}
@@ -309,6 +311,30 @@ def secondary_measurements(stream, dev):
     out["batched_forward"] = {"workload": f"{B} x dam_break_2d_96 ({B * nb} particles, {bsteps} steps, fp32)",
                               "value": B * nb * bsteps / (ms * 1e-3), "unit": "particle-steps/s",
                               "ms_per_step": ms / bsteps}
+    # the 3D dam break with two rigid columns (1.92M fluid particles, FP32)
+    wd = inputs.dam_break_3d()
+    sim = mpm.Simulation.from_workload(wd, mpm.MPM_FP32, stream=stream.cuda_stream)
+    sim.step(20)
+    dsteps = 200
+    mpm.mpm_set_timing(sim.ctx, True)
+    mpm.mpm_reset_timing(sim.ctx)
+    ms = _event_ms(stream, lambda: sim.step(dsteps))
+    kt = {k: mpm.mpm_get_timing(sim.ctx, k)[0] / dsteps for k in mpm.KERNELS}
+    xd = sim.get("x")
+    sim.close()
+    dnodes = count_active_nodes(xd, wd.dx, wd.n_cells)
+    dbytes = wd.n * 2 * 25 * 4 + dnodes * 32          # fluid state x v C F rho: 25 words read + written
+    peak, _ = load_peaks()
+    out["dam_break_3d"] = {"workload": f"dam_break_3d_200x100x80 ({wd.n} particles, two rigid columns, "
+                                       f"{dsteps} steps after 20, fp32)",
+                           "value": wd.n * dsteps / (ms * 1e-3), "unit": "particle-steps/s",
+                           "ms_per_step": ms / dsteps, "kernels_ms_per_step": kt,
+                           "step_roofline": {"bytes_per_step": dbytes, "active_nodes": dnodes,
+                                             "achieved": dbytes / (ms / dsteps * 1e-3) / 1e9, "peak": peak,
+                                             "frac": dbytes / (ms / dsteps * 1e-3) / 1e9 / peak, "unit": "GB/s"},
+                           "paper_context": {"value": 1.92e6 * 1000 / 8.2, "unit": "particle-steps/s",
+                                             "note": "paper's FP32 figure for this workload (1000 steps in "
+                                                     "8.2 s, Table 3): context, other GPU"}}
     # network
     W = [640, 256, 256, 32]
     net = mpm.MLP(W, 256, stream=stream.cuda_stream)

@@ -162,6 +162,24 @@ int mpm_set_particle_field(mpm_ctx *ctx, int field, const double *values);
  */
 int mpm_set_friction_field(mpm_ctx *ctx, int wall, const int n_seg[2], const double *mu);
 
+/*
+ * Stationary rigid obstacles with frictionless contact (Sec. 4.1, 3D dam break:
+ * the predicted grid velocity loses its normal component at the obstacle,
+ * v_i = v~_i - (v~_i . n_i) n_i).  boxes holds n_obstacles axis-aligned boxes,
+ * each dim low-corner coordinates then dim high-corner coordinates (metres,
+ * host, copied); at most MPM_MAX_OBSTACLES; n_obstacles = 0 removes them.  A
+ * grid node whose coordinate lies in a closed box (box extents rounded to the
+ * nodes ceil(lo / dx - 1e-9) .. floor(hi / dx + 1e-9)) takes the outward normal
+ * of the nearest box face that lies strictly inside the domain (ties: the first
+ * of x-, x+, y-, y+, z-, z+) and, when it moves into the box (v . n < 0), loses
+ * its normal velocity.  Obstacles act before the walls; they apply to every
+ * simulation of a batch and are differentiated by mpm_step_adjoint.
+ * MPM_EINVAL for a count out of range, a box with lo > hi on some axis, or a
+ * box with no face inside the domain.
+ */
+#define MPM_MAX_OBSTACLES 8
+int mpm_set_obstacles(mpm_ctx *ctx, int n_obstacles, const double *boxes);
+
 /* Queue n_steps explicit MPM steps on the context's stream (asynchronous). */
 int mpm_step(mpm_ctx *ctx, int n_steps);
 
@@ -187,9 +205,33 @@ int mpm_last_error(const mpm_ctx *ctx, char *buf, int len);
  * at the start of mpm_step_adjoint) and the observed positions z_obs
  * (n_obs x n_track x dim, host).  The loss is
  *     L = sum_obs sum_l |x_{id_l}^{step} - z_obs|^2.
+ * n_track = 0 clears them (the other arguments are then ignored).
  */
 int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_obs, const int *steps,
                          const double *z_obs);
+
+/*
+ * Eulerian observations of Eq. inverse_loss (Sec. 5.2, Case 3): velocity
+ * monitors.  n_mon (<= 64) closed boxes (boxes: per monitor dim low-corner then
+ * dim high-corner coordinates, metres), n_obs observation steps (>= 1,
+ * increasing) and the observed mean velocities v_obs (n_obs x n_mon x dim, host,
+ * copied).  At an observation step the monitor's quantity is the mean velocity
+ * Q_l = (1 / |P_l|) sum_{p in P_l} v_p of the particles P_l whose position lies
+ * in the box; the loss adds sum_obs sum_l |Q_l - v_obs|^2 over the monitors
+ * holding particles (an empty monitor adds nothing).  In the adjoint the
+ * membership P_l is held at its forward value.  n_mon = 0 clears the monitors.
+ */
+#define MPM_MAX_MONITORS 64
+int mpm_set_velocity_monitors(mpm_ctx *ctx, int n_mon, const double *boxes, int n_obs, const int *steps,
+                              const double *v_obs);
+
+/*
+ * The monitors' quantities on the current state (boxes as in
+ * mpm_set_velocity_monitors, batch 1): per monitor the mean velocity (dim
+ * values, 0 when empty) and the particle count, out = n_mon x (dim + 1) doubles
+ * (host); synchronises.  Used to record Eulerian observations of a run.
+ */
+int mpm_monitor_means(mpm_ctx *ctx, int n_mon, const double *boxes, double *out);
 
 /*
  * Loss and its gradient with respect to one wall's friction field (the
@@ -197,9 +239,12 @@ int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_ob
  * Runs n_steps explicit steps from the current state, saving the particle
  * state every checkpoint_every steps (Sec. 3.3.2); then walks the segments
  * backwards, recomputing each segment's states from its checkpoint and
- * applying the adjoint of each step.  Writes the loss and dL/dmu (the wall's
- * n_seg[0] x n_seg[1] coefficients, set by mpm_set_friction_field) to host
- * memory and leaves the context at the state after n_steps steps.  Both
+ * applying the adjoint of each step.  Writes the loss (tracked particles and
+ * velocity monitors together) and dL/dmu (the wall's n_seg[0] x n_seg[1]
+ * coefficients, set by mpm_set_friction_field; wall = -1 asks for no friction
+ * gradient and dL_dmu_out may then be NULL) to host memory and leaves the
+ * context at the state after n_steps steps; the adjoint of the initial state
+ * is then available through mpm_get_initial_adjoint.  Both
  * materials (the adjoint state is (x, v, C, rho) for the fluid and (x, v, C,
  * rho, sigma) for Drucker-Prager; the zone and contact branches of the forward
  * step are held fixed), batch 1.  Device memory: checkpoints of
@@ -208,6 +253,17 @@ int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_ob
  */
 int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, double *loss_out,
                      double *dL_dmu_out);
+
+/*
+ * dL/d(field of the initial state) of the last mpm_step_adjoint (the adjoint
+ * state lambda^0 of Eq. dzda): MPM_FIELD_X, MPM_FIELD_V, MPM_FIELD_C (the APIC
+ * affine matrix) or MPM_FIELD_RHO, written to host memory in load order with
+ * the field's width per particle (synchronises).  With it the loss gradient
+ * with respect to any parametrisation of the initial state (Sec. 5.2: an initial
+ * velocity constant or a network field v0(x)) follows by the chain rule.
+ * MPM_ESTATE before any adjoint; MPM_EINVAL for other fields.
+ */
+int mpm_get_initial_adjoint(mpm_ctx *ctx, int field, double *out);
 
 /*
  * Device state slots (0..15): copy of the whole particle state (all fields, in

@@ -27,6 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_WALLS = 6
+MAX_OBSTACLES = 8
 
 
 class Params(C.Structure):
@@ -54,6 +55,8 @@ class Params(C.Structure):
         ("transfer", C.c_int),
         ("flip_alpha", C.c_double),
         ("flip_grid", C.c_void_p),
+        ("n_obstacles", C.c_int),
+        ("obstacle", ((C.c_double * 3) * 2) * MAX_OBSTACLES),
     ]
 
 
@@ -94,6 +97,7 @@ def lib():
             "orc_affine_C": (None, [P, l, p, p, p]),
             "orc_step_vjp": (i, [P, l] + [p] * 16),
             "orc_dp_vjp": (None, [P, p, p, p, p, p, p, p]),
+            "orc_obstacle_normal": (i, [P, i, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -111,7 +115,7 @@ class Oracle:
     """Parameters of one scenario plus the numpy arrays kept alive for ctypes."""
 
     def __init__(self, dim, n_cells, dx, dt, gravity, material, particle_volume,
-                 friction=(), dp_literal=False, transfer=0, flip_alpha=1.0):
+                 friction=(), dp_literal=False, transfer=0, flip_alpha=1.0, obstacles=()):
         P = Params()
         P.dim = dim
         for a in range(3):
@@ -133,13 +137,20 @@ class Oracle:
             self._mu.append(arr)
             P.n_seg[wall][0], P.n_seg[wall][1] = int(nseg[0]), int(nseg[1])
             P.mu[wall] = arr.ctypes.data
+        assert len(obstacles) <= MAX_OBSTACLES
+        P.n_obstacles = len(obstacles)
+        for o, (lo, hi) in enumerate(obstacles):          # stationary boxes (Sec. 4.1)
+            for a in range(dim):
+                P.obstacle[o][0][a] = float(lo[a])
+                P.obstacle[o][1][a] = float(hi[a])
         self.P = P
         self.dim = dim
 
     @classmethod
     def from_workload(cls, w, dp_literal=False, dt=None, transfer=0, flip_alpha=1.0):
         return cls(w.dim, w.n_cells, w.dx, w.dt if dt is None else dt, w.gravity, w.material,
-                   w.particle_volume, w.friction, dp_literal, transfer, flip_alpha)
+                   w.particle_volume, w.friction, dp_literal, transfer, flip_alpha,
+                   getattr(w, "obstacles", ()))
 
     # -- state ------------------------------------------------------------------
     def initial_state(self, x: np.ndarray, v: Optional[np.ndarray] = None) -> "State":
@@ -174,6 +185,14 @@ class Oracle:
         lib().orc_p2g(C.byref(self.P), st.n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.rho),
                       _ptr(st.sigma), _ptr(gm), _ptr(gq), _ptr(gf))
         return gm, gq, gf
+
+    def obstacle_normal(self, o: int, j) -> Optional[np.ndarray]:
+        """Contact normal of oracle node index j with obstacle o (None outside it)."""
+        jj = np.zeros(3, dtype=np.int32)
+        jj[:len(j)] = j
+        nrm = np.zeros(3)
+        hit = lib().orc_obstacle_normal(C.byref(self.P), int(o), jj.ctypes.data_as(C.c_void_p), _ptr(nrm))
+        return nrm if hit else None
 
     def grid_update(self, gm, gq, gf):
         gv = np.zeros((self.num_nodes, self.dim))
@@ -278,3 +297,34 @@ def friction(v, n, mu):
     out = np.zeros(3)
     lib().orc_friction(_ptr(v3), _ptr(n3), float(mu), _ptr(out))
     return out[: len(v)]
+
+
+def monitor_means(x: np.ndarray, v: np.ndarray, boxes):
+    """Eulerian velocity monitors (Sec. 5.2, Case 3): per closed box [lo, hi] the
+    mean velocity of the particles whose position lies inside, and their count
+    (mean 0 for an empty monitor)."""
+    Q = np.zeros((len(boxes), v.shape[1]))
+    cnt = np.zeros(len(boxes), dtype=np.int64)
+    for l, (lo, hi) in enumerate(boxes):
+        inside = np.all((x >= np.asarray(lo, dtype=np.float64)) & (x <= np.asarray(hi, dtype=np.float64)), axis=1)
+        cnt[l] = int(inside.sum())
+        if cnt[l] > 0:
+            Q[l] = v[inside].sum(axis=0) / cnt[l]
+    return Q, cnt
+
+
+def monitor_loss_and_seed(x: np.ndarray, v: np.ndarray, boxes, z: np.ndarray):
+    """sum_l |Q_l - z_l|^2 over the non-empty monitors, and its gradient with
+    respect to the particle velocities at fixed positions (the membership is a
+    step function of x: its derivative is zero almost everywhere)."""
+    Q, cnt = monitor_means(x, v, boxes)
+    loss = 0.0
+    g = np.zeros_like(v)
+    for l, (lo, hi) in enumerate(boxes):
+        if cnt[l] == 0:
+            continue
+        e = Q[l] - z[l]
+        loss += float((e * e).sum())
+        inside = np.all((x >= np.asarray(lo, dtype=np.float64)) & (x <= np.asarray(hi, dtype=np.float64)), axis=1)
+        g[inside] += 2.0 * e / cnt[l]
+    return loss, g

@@ -26,7 +26,11 @@
  * viscous stress from the rate of deformation; Tait EOS (gamma = 1 is the
  * paper's linear EOS); walls at the domain faces with one ghost node beyond;
  * contact applied only to approaching nodes (v.n > 0); friction segment index
- * floor(x_i / L * n_seg) clamped; Drucker-Prager corner guard.
+ * floor(x_i / L * n_seg) clamped; Drucker-Prager corner guard.  Rigid obstacles
+ * (Sec. 4.1, 3D dam break) are stationary axis-aligned boxes with frictionless
+ * contact, applied before the walls: a node inside a box (within 1e-9 dx) takes
+ * the outward normal of the nearest box face that lies inside the domain and,
+ * when it moves into the box, loses its normal velocity.
  */
 #include <math.h>
 #include <stdint.h>
@@ -34,6 +38,7 @@
 #include <string.h>
 
 #define ORC_MAX_WALLS 6
+#define ORC_MAX_OBSTACLES 8
 
 typedef struct {
     int dim;
@@ -51,6 +56,8 @@ typedef struct {
     int transfer;               /* 0 = APIC, 1 = TPIC, 2 = PIC, 3 = FLIP / PIC blend (Sec. 2.2 G2P transfer) */
     double flip_alpha;          /* FLIP share of the blended particle velocity (transfer 3) */
     const double *flip_grid;    /* transfer 3: grid velocity before the update, set inside orc_step */
+    int n_obstacles;            /* stationary rigid boxes, frictionless contact (Sec. 4.1) */
+    double obstacle[ORC_MAX_OBSTACLES][2][3];   /* [o][0] = low corner, [o][1] = high corner (m) */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -289,6 +296,44 @@ static double wall_mu(const orc_params *P, int w, const int j[3])
 /* y-, y+, z-, z+ with the floor (the low wall of the last axis) last.       */
 /* ------------------------------------------------------------------------- */
 
+/* Contact normal of node j (oracle index, coordinate (j - 1) dx) with obstacle o:
+ * returns 1 and the outward normal of the nearest box face when the node lies in
+ * the closed box.  Box extents are taken in node units, ceil(lo / dx - 1e-9) ..
+ * floor(hi / dx + 1e-9); faces on or beyond the domain boundary are not contact
+ * faces; ties go to the first face in the order x-, x+, y-, y+, z-, z+. */
+int orc_obstacle_normal(const orc_params *P, int o, const int j[3], double nrm[3])
+{
+    int d = P->dim, best = -1;
+    long best_dist = 0;
+    for (int a = 0; a < d; ++a) {
+        long lo = (long)ceil(P->obstacle[o][0][a] / P->dx - 1e-9);
+        long hi = (long)floor(P->obstacle[o][1][a] / P->dx + 1e-9);
+        long c = j[a] - 1;
+        if (c < lo || c > hi) return 0;
+    }
+    for (int a = 0; a < d; ++a) {
+        long lo = (long)ceil(P->obstacle[o][0][a] / P->dx - 1e-9);
+        long hi = (long)floor(P->obstacle[o][1][a] / P->dx + 1e-9);
+        long c = j[a] - 1;
+        if (lo > 0 && (best < 0 || c - lo < best_dist)) { best = 2 * a; best_dist = c - lo; }
+        if (hi < P->n_cells[a] && (best < 0 || hi - c < best_dist)) { best = 2 * a + 1; best_dist = hi - c; }
+    }
+    if (best < 0) return 0;
+    nrm[0] = nrm[1] = nrm[2] = 0.0;
+    nrm[best / 2] = (best % 2) ? 1.0 : -1.0;
+    return 1;
+}
+
+/* Frictionless contact with a stationary obstacle: v <- v - (v.n) n for a node
+ * moving into the box (v.n < 0).  Returns 1 when applied. */
+static int obstacle_contact(const double nrm[3], double v[3])
+{
+    double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
+    if (!(vn < 0.0)) return 0;
+    for (int a = 0; a < 3; ++a) v[a] -= vn * nrm[a];
+    return 1;
+}
+
 void orc_grid_update(const orc_params *P, const double *gm, const double *gq, const double *gf,
                      double *gv)
 {
@@ -310,6 +355,10 @@ void orc_grid_update(const orc_params *P, const double *gm, const double *gq, co
                 double an = gf[i * d + a] / gm[i];
                 vi[a] = vn + P->dt * an;
             }
+        }
+        for (int o = 0; o < P->n_obstacles; ++o) {
+            double nrm[3];
+            if (orc_obstacle_normal(P, o, j, nrm)) obstacle_contact(nrm, vi);
         }
         for (int q = 0; q < nw; ++q) {
             int w = order[q], a = w / 2, hi = w % 2;
@@ -869,9 +918,14 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
         int j[3] = {0, 0, 0};
         long r = i;
         for (int a = 0; a < d; ++a) { j[a] = (int)(r % nodes_axis(P, a)); r /= nodes_axis(P, a); }
-        /* forward chain through the walls, keeping each wall's input */
+        /* forward through the obstacles (projections, kept with their normals),
+         * then the walls, keeping each wall's input */
         double chain[ORC_MAX_WALLS + 1][3];
         for (int a = 0; a < 3; ++a) chain[0][a] = gu[i * 3 + a];
+        double onrm[ORC_MAX_OBSTACLES][3];
+        int oapplied[ORC_MAX_OBSTACLES];
+        for (int o = 0; o < P->n_obstacles; ++o)
+            oapplied[o] = orc_obstacle_normal(P, o, j, onrm[o]) && obstacle_contact(onrm[o], chain[0]);
         int applied[ORC_MAX_WALLS];
         for (int q = 0; q < nw; ++q) {
             int w = order[q], a = w / 2, hi = w % 2;
@@ -894,6 +948,11 @@ int orc_step_vjp(const orc_params *P, long n, const double *x, const double *v, 
             if (P->mu[w] && mu_bar && mu_bar[w]) mub = mu_bar[w] + wall_segment_index(P, w, j);
             wall_vjp(chain[q], nrm, wall_mu(P, w, j), ob, ib, mub);
             for (int b = 0; b < 3; ++b) ob[b] = ib[b];
+        }
+        for (int o = P->n_obstacles - 1; o >= 0; --o) {     /* a projection is its own transpose */
+            if (!oapplied[o]) continue;
+            double obn = ob[0] * onrm[o][0] + ob[1] * onrm[o][1] + ob[2] * onrm[o][2];
+            for (int b = 0; b < 3; ++b) ob[b] -= obn * onrm[o][b];
         }
         for (int a = 0; a < d; ++a) {
             gqb[i * d + a] = ob[a] / gm[i];

@@ -342,24 +342,6 @@ __global__ void k_adj_seed(int64_t n, int n_track, const int64_t *__restrict__ i
     }
 }
 
-// Slot-order save: the adjoint components of the state in the context's current
-// particle order, as contiguous arrays (dst[c n + slot]), and that order's ids.
-template <class R, int D>
-__global__ void k_adj_save_slots(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
-                                 R *__restrict__ dst, int32_t *__restrict__ dst_id)
-{
-    constexpr int NA = adj_ncomp<D>();
-    const int nsig = P.material == 1 ? 6 : 0;
-    const int64_t n = P.n, np = P.npad;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < NA - 1; ++c) dst[c * n + i] = S[c * np + i];
-        dst[(NA - 1) * n + i] = S[P.off_rho * np + i];
-        for (int k = 0; k < nsig; ++k) dst[(NA + k) * n + i] = S[(P.off_sig + k) * np + i];
-        dst_id[i] = id[i];
-    }
-}
-
 // pos[id[slot]] = slot.
 template <class R>
 __global__ void k_adj_inverse(int64_t n, const int32_t *__restrict__ id, int32_t *__restrict__ pos)
@@ -393,6 +375,72 @@ __global__ void k_adj_seed_slots(int64_t n, const int32_t *__restrict__ id, cons
         for (int a = 0; a < D; ++a)
             lam[a * n + i] += (R)(2.0 * (x_obs[(int64_t)l * D + a] - z_obs[(int64_t)l * D + a]));
     }
+}
+
+// Velocity monitors (Sec. 5.2, Case 3: the mean velocity of the particles inside
+// each monitor region).  Per closed box [lo, hi] (boxes: n_mon x 2 x D doubles,
+// low corner then high corner) the sum of v_p and the count of the particles
+// with x_p inside: sums[l (D + 1) + a] (a < D) and sums[l (D + 1) + D].  x and v
+// are component arrays with stride ld.  Block sums in shared memory, then one
+// FP64 atomic per monitor and value.
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_monitor_sum(int64_t n, int64_t ld, const R *__restrict__ x,
+                                                     const R *__restrict__ v, int n_mon,
+                                                     const double *__restrict__ boxes, double *__restrict__ sums)
+{
+    __shared__ double acc[kMaxMonitors * (D + 1)];
+    for (int i = threadIdx.x; i < n_mon * (D + 1); i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xp[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xp[a] = (double)x[a * ld + i];
+        for (int l = 0; l < n_mon; ++l) {
+            const double *b = boxes + (int64_t)l * 2 * D;
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) in = in && xp[a] >= b[a] && xp[a] <= b[D + a];
+            if (!in) continue;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(&acc[l * (D + 1) + a], (double)v[a * ld + i]);
+            atomicAdd(&acc[l * (D + 1) + D], 1.0);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_mon * (D + 1); i += blockDim.x)
+        if (acc[i] != 0.0) atomicAdd(&sums[i], acc[i]);
+}
+
+// Adjoint seed of the monitor loss sum_l |Q_l - z_l|^2: for every particle inside
+// monitor l, lam.v += g_l with g_l = 2 (Q_l - z_l) / |P_l| (membership held fixed).
+// x: component arrays with stride ld, in the order of lam.
+template <class R, int D>
+__global__ void k_monitor_seed(int64_t n, int64_t ld, const R *__restrict__ x, int n_mon,
+                               const double *__restrict__ boxes, const double *__restrict__ g, R *__restrict__ lam)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xp[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xp[a] = (double)x[a * ld + i];
+        for (int l = 0; l < n_mon; ++l) {
+            const double *b = boxes + (int64_t)l * 2 * D;
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) in = in && xp[a] >= b[a] && xp[a] <= b[D + a];
+            if (!in) continue;
+#pragma unroll
+            for (int a = 0; a < D; ++a) lam[(D + a) * n + i] += (R)g[l * D + a];
+        }
+    }
+}
+
+// Load-order copy of w components of an adjoint state: out[id[s] w + k] = lam[(off + k) n + s].
+template <class R>
+__global__ void k_adj_gather(int64_t n, int w, int off, const int32_t *__restrict__ id, const R *__restrict__ lam,
+                             double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < w; ++k) out[(int64_t)id[i] * w + k] = (double)lam[(int64_t)(off + k) * n + i];
 }
 
 template <class R>
@@ -594,17 +642,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_
     }
 }
 
-// Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P),
-// one block per node tile the forward step updated (tile flags GF); GVB is
-// cleared behind, ready for the next reverse step.
+// Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P)
+// over the node tiles the forward step updated (the list GL it saved: GL[0] tiles,
+// then their indices), blocks striding the list; GVB is cleared behind, ready for
+// the next reverse step.
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA,
                                                       R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB,
-                                                      const uint32_t *__restrict__ GF, MuBar mu_bar)
+                                                      const int32_t *__restrict__ GL, MuBar mu_bar)
 {
     using Gm = Geo<D>;
-    const int64_t ut = blockIdx.x;
-    if (GF[ut] == 0u) return;
+    const int n_list = GL[0];
+    for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const int64_t ut = GL[1 + li];
     int u[3] = {0, 0, 0};
     int64_t r = ut;
 #pragma unroll
@@ -636,14 +686,19 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
                     D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
         R chain[2 * D][3];
         bool applied[2 * D];
+        const unsigned removed = obstacle_contact<R, D>(P, a3, vel);
         walls_forward<R, D>(P, 0, a3, vel, chain, applied);
         R ob[3] = {b4.x, b4.y, b4.z};
         walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w);
+#pragma unroll
+        for (int a = 0; a < D; ++a)                  // the obstacle projections (their own transposes)
+            if ((removed >> a) & 1u) ob[a] = R(0);
         const R Pv[3] = {acc.y, acc.z, acc.w};
         R mb = R(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
         GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
+    }
     }
 }
 
@@ -1162,11 +1217,6 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_seed<R, D><<<(n_track + 255) / 256, 256, 0, ds.stream>>>(h.n, n_track, ids, x_obs, z_obs, (R *)lam);
     }
-    static void save_slots(const HostParams &h, DevState &ds, cudaStream_t stream, void *dst, int32_t *dst_id)
-    {
-        auto P = make_params<R>(h, ds);
-        k_adj_save_slots<R, D><<<pblocks(h, ds), 256, 0, stream>>>(P, (const R *)ds.S, ds.id, (R *)dst, dst_id);
-    }
     static void reorder(const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos_scratch,
                         const int32_t *id_new, const void *in, void *out)
     {
@@ -1179,6 +1229,23 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_seed_slots<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, id, track_of_id, x_obs, z_obs, (R *)lam);
     }
+    static void monitor_sum(const HostParams &h, DevState &ds, const void *x, const void *v, int64_t ld, int n_mon,
+                            const double *boxes, double *sums)
+    {
+        k_monitor_sum<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, ld, (const R *)x, (const R *)v, n_mon,
+                                                                    boxes, sums);
+    }
+    static void monitor_seed(const HostParams &h, DevState &ds, const void *x, int64_t ld, int n_mon,
+                             const double *boxes, const double *g, void *lam)
+    {
+        k_monitor_seed<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, ld, (const R *)x, n_mon, boxes, g,
+                                                                     (R *)lam);
+    }
+    static void gather(const HostParams &h, DevState &ds, int w, int off, const int32_t *id, const void *lam,
+                       double *out)
+    {
+        k_adj_gather<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, w, off, id, (const R *)lam, out);
+    }
     static void zero(DevState &ds, void *p, int64_t count)
     {
         k_adj_zero<R><<<grid_blocks(count, 256, ds.num_sms, 8), 256, 0, ds.stream>>>((R *)p, count);
@@ -1186,7 +1253,7 @@ template <class R, int D> struct AdjLaunch {
     // One reverse step: lam_in (adjoint of S^{t+1}) -> lam_out (adjoint of S^t) for the state st,
     // whose grid (m, q + dt f) and post-wall velocity the forward recompute saved in GA, GV.
     static void step(const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *GA,
-                     const void *GV, const uint32_t *GF, const void *lam_in, void *lam_out, MuBar mub)
+                     const void *GV, const int32_t *GL, const void *lam_in, void *lam_out, MuBar mub)
     {
         auto P = make_params<R>(h, ds);
         if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
@@ -1196,8 +1263,10 @@ template <class R, int D> struct AdjLaunch {
             k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
                                                                          (const R *)lam_in, (R *)lam_out,
                                                                          (R4<R> *)a.GVB);
-        k_adj_grid_bwd<R, D><<<(unsigned)h.node_tiles_per_sim, 256, 0, ds.stream>>>(
-            P, (const R4<R> *)GA, (R4<R> *)a.GVB, (R4<R> *)a.GAB, GF, mub);
+        int64_t nbg = h.node_tiles_per_sim;             // blocks stride the saved tile list
+        if (nbg > (int64_t)ds.num_sms * 8) nbg = (int64_t)ds.num_sms * 8;
+        k_adj_grid_bwd<R, D><<<(unsigned)nbg, 256, 0, ds.stream>>>(P, (const R4<R> *)GA, (R4<R> *)a.GVB,
+                                                                   (R4<R> *)a.GAB, GL, mub);
         if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
             k_adj_p2g_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
                                                                    (R *)lam_out);
@@ -1220,15 +1289,20 @@ template <class R> struct AdjDispatch {
     MPM_ADJ_DISPATCH(seed, (const HostParams &h, DevState &ds, int nt, const int64_t *ids, const double *xo,
                             const double *zo, void *lam), seed(h, ds, nt, ids, xo, zo, lam))
     MPM_ADJ_DISPATCH(step, (const HostParams &h, DevState &ds, const AdjDev &a, const void *st, const void *ga,
-                            const void *gv, const uint32_t *gf, const void *li, void *lo, MuBar mub),
-                     step(h, ds, a, st, ga, gv, gf, li, lo, mub))
-    MPM_ADJ_DISPATCH(save_slots, (const HostParams &h, DevState &ds, cudaStream_t st, void *dst, int32_t *dst_id),
-                     save_slots(h, ds, st, dst, dst_id))
+                            const void *gv, const int32_t *gl, const void *li, void *lo, MuBar mub),
+                     step(h, ds, a, st, ga, gv, gl, li, lo, mub))
     MPM_ADJ_DISPATCH(reorder, (const HostParams &h, DevState &ds, int nc, const int32_t *id_old, int32_t *pos,
                                const int32_t *id_new, const void *in, void *out),
                      reorder(h, ds, nc, id_old, pos, id_new, in, out))
     MPM_ADJ_DISPATCH(seed_slots, (const HostParams &h, DevState &ds, const int32_t *id, const int32_t *tid,
                                   const double *xo, const double *zo, void *lam), seed_slots(h, ds, id, tid, xo, zo, lam))
+    MPM_ADJ_DISPATCH(monitor_sum, (const HostParams &h, DevState &ds, const void *x, const void *v, int64_t ld,
+                                   int nm, const double *b, double *s), monitor_sum(h, ds, x, v, ld, nm, b, s))
+    MPM_ADJ_DISPATCH(monitor_seed, (const HostParams &h, DevState &ds, const void *x, int64_t ld, int nm,
+                                    const double *b, const double *g, void *lam),
+                     monitor_seed(h, ds, x, ld, nm, b, g, lam))
+    MPM_ADJ_DISPATCH(gather, (const HostParams &h, DevState &ds, int w, int off, const int32_t *id, const void *lam,
+                              double *out), gather(h, ds, w, off, id, lam, out))
 #undef MPM_ADJ_DISPATCH
     static void zero(const HostParams &, DevState &ds, void *p, int64_t count) { AdjLaunch<R, 2>::zero(ds, p, count); }
 };

@@ -1,5 +1,6 @@
 // Host side of libmpm: context lifetime, device memory, the step sequence
 // and the C-ABI declared in include/mpm.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -42,6 +43,13 @@ struct AdjHost {
     void *final_S = nullptr;
     int32_t *final_id = nullptr, *final_sim = nullptr;
     bool allocated = false;
+    // velocity monitors (Eulerian observations): boxes, steps, observed mean velocities
+    int n_mon = 0, n_mobs = 0;
+    std::vector<int> msteps;
+    std::vector<double> mz;                    // n_mobs x n_mon x dim
+    double *d_mboxes = nullptr, *d_msums = nullptr, *d_mg = nullptr;
+    // after mpm_step_adjoint: lam[lam0] is the adjoint of the initial state, in order lam_id
+    int lam0 = -1;
 };
 
 // One saved copy of the particle state on the device.
@@ -73,11 +81,6 @@ struct mpm_ctx {
     AdjHost adj;
     const AdjOps *aops = nullptr;
     StateSlot slots[kMaxSlots];
-    // the adjoint's segment saves run on a second stream beside P2G and the grid
-    // update; G2P (which overwrites the state) waits for g2p_wait when set
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_sorted = nullptr, ev_saved = nullptr;
-    cudaEvent_t g2p_wait = nullptr;
 };
 
 namespace {
@@ -135,9 +138,12 @@ void free_adjoint(mpm_ctx *c)
     dfree(a.grid.GVB); dfree(a.grid.GAB);
     for (int w = 0; w < kMaxWalls; ++w) dfree(a.d_mubar[w]);
     dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
+    dfree(a.d_mboxes); dfree(a.d_msums); dfree(a.d_mg);
     a.ckpt_cap = a.seg_cap = 0;
     a.allocated = false;
     a.n_track = a.n_obs = 0;
+    a.n_mon = a.n_mobs = 0;
+    a.lam0 = -1;
 }
 
 void free_slots(mpm_ctx *c)
@@ -459,9 +465,6 @@ void mpm_destroy(mpm_ctx *c)
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->own_stream && d.stream) cudaStreamDestroy(d.stream);
-    if (c->aux) cudaStreamDestroy(c->aux);
-    if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
-    if (c->ev_saved) cudaEventDestroy(c->ev_saved);
     delete c;
 }
 
@@ -589,6 +592,35 @@ int mpm_set_friction_field(mpm_ctx *c, int wall, const int n_seg[2], const doubl
     return MPM_OK;
 }
 
+int mpm_set_obstacles(mpm_ctx *c, int n_obstacles, const double *boxes)
+{
+    if (!c || n_obstacles < 0 || n_obstacles > MPM_MAX_OBSTACLES || (n_obstacles > 0 && !boxes))
+        return fail(c, MPM_EINVAL, "mpm_set_obstacles: bad argument");
+    const int d = c->grid.dim;
+    Obstacles ob{};
+    ob.n = n_obstacles;
+    for (int o = 0; o < n_obstacles; ++o) {
+        const double *lo = boxes + (size_t)o * 2 * d, *hi = lo + d;
+        int faces = 0;
+        for (int a = 0; a < d; ++a) {
+            if (!(lo[a] <= hi[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a]))
+                return fail(c, MPM_EINVAL, "mpm_set_obstacles: bad box");
+            // node extents of the closed box (1e-9 dx tolerance), clamped to the node range
+            const double l = std::ceil(lo[a] / c->grid.dx - 1e-9), u = std::floor(hi[a] / c->grid.dx + 1e-9);
+            const double big = c->grid.n_cells[a] + 8.0;
+            ob.lo[o][a] = (int)std::max(-8.0, std::min(big, l));
+            ob.hi[o][a] = (int)std::max(-8.0, std::min(big, u));
+            if (l > 0.0) faces |= 1 << (2 * a);
+            if (u < c->grid.n_cells[a]) faces |= 1 << (2 * a + 1);
+        }
+        if (faces == 0) return fail(c, MPM_EINVAL, "mpm_set_obstacles: box has no face inside the domain");
+        ob.faces[o] = faces;
+    }
+    CK(cudaStreamSynchronize(c->ds.stream), "synchronize before obstacle update");
+    c->hp.obs = ob;
+    return MPM_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -609,10 +641,6 @@ int step_many(mpm_ctx *c, int n_steps)
         }
         {
             TimingScope ts(c, MPM_KERNEL_G2P);
-            if (c->g2p_wait) {
-                cudaStreamWaitEvent(c->ds.stream, c->g2p_wait, 0);
-                c->g2p_wait = nullptr;
-            }
             c->ops->g2p(c->hp, c->ds);
         }
         c->launches += 3;
@@ -715,7 +743,11 @@ int mpm_get_stats(mpm_ctx *c, int64_t *out, int n)
 int mpm_set_observations(mpm_ctx *c, int n_track, const int64_t *ids, int n_obs, const int *steps,
                          const double *z_obs)
 {
-    if (!c || n_track <= 0 || n_obs <= 0 || !ids || !steps || !z_obs)
+    if (c && n_track == 0) {                      // clear the tracked-particle observations
+        c->adj.n_track = c->adj.n_obs = 0;
+        return MPM_OK;
+    }
+    if (!c || n_track < 0 || n_obs <= 0 || !ids || !steps || !z_obs)
         return fail(c, MPM_EINVAL, "mpm_set_observations: bad argument");
     const int64_t n = c->hp.n;
     if (n == 0) return fail(c, MPM_ESTATE, "mpm_set_observations: no particles loaded");
@@ -748,19 +780,112 @@ int mpm_set_observations(mpm_ctx *c, int n_track, const int64_t *ids, int n_obs,
     return MPM_OK;
 }
 
+int mpm_set_velocity_monitors(mpm_ctx *c, int n_mon, const double *boxes, int n_obs, const int *steps,
+                              const double *v_obs)
+{
+    if (c && n_mon == 0) {                        // clear the monitors
+        c->adj.n_mon = c->adj.n_mobs = 0;
+        return MPM_OK;
+    }
+    if (!c || n_mon < 0 || n_mon > kMaxMonitors || n_obs <= 0 || !boxes || !steps || !v_obs)
+        return fail(c, MPM_EINVAL, "mpm_set_velocity_monitors: bad argument");
+    const int d = c->grid.dim;
+    for (int l = 0; l < n_mon; ++l)
+        for (int a = 0; a < d; ++a) {
+            const double lo = boxes[(size_t)l * 2 * d + a], hi = boxes[(size_t)l * 2 * d + d + a];
+            if (!(lo <= hi) || !std::isfinite(lo) || !std::isfinite(hi))
+                return fail(c, MPM_EINVAL, "mpm_set_velocity_monitors: bad box");
+        }
+    for (int o = 0; o < n_obs; ++o)
+        if (steps[o] < 1 || (o > 0 && steps[o] <= steps[o - 1]))
+            return fail(c, MPM_EINVAL, "mpm_set_velocity_monitors: steps must be >= 1 and increasing");
+    AdjHost &a = c->adj;
+    dfree(a.d_mboxes); dfree(a.d_msums); dfree(a.d_mg);
+    int rc = dalloc(c, &a.d_mboxes, (size_t)n_mon * 2 * d, "monitor boxes");
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_msums, (size_t)n_obs * n_mon * (d + 1), "monitor sums");
+    if (rc == MPM_OK) rc = dalloc(c, &a.d_mg, (size_t)n_obs * n_mon * d, "monitor seeds");
+    if (rc != MPM_OK) return rc;
+    CK(cudaMemcpy(a.d_mboxes, boxes, sizeof(double) * n_mon * 2 * d, cudaMemcpyHostToDevice), "copy boxes");
+    a.n_mon = n_mon;
+    a.n_mobs = n_obs;
+    a.msteps.assign(steps, steps + n_obs);
+    a.mz.assign(v_obs, v_obs + (size_t)n_obs * n_mon * d);
+    return MPM_OK;
+}
+
+int mpm_monitor_means(mpm_ctx *c, int n_mon, const double *boxes, double *out)
+{
+    if (!c || n_mon < 1 || n_mon > kMaxMonitors || !boxes || !out)
+        return fail(c, MPM_EINVAL, "mpm_monitor_means: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_monitor_means: no particles loaded");
+    if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_monitor_means: batch must be 1");
+    const HostParams &h = c->hp;
+    DevState &ds = c->ds;
+    const int d = h.dim;
+    double *dev = nullptr;
+    int rc = dalloc(c, &dev, (size_t)n_mon * (3 * d + 1), "monitor scratch");
+    if (rc != MPM_OK) return rc;
+    double *dboxes = dev + (size_t)n_mon * (d + 1);
+    cudaError_t e = cudaMemcpyAsync(dboxes, boxes, sizeof(double) * n_mon * 2 * d, cudaMemcpyHostToDevice, ds.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, sizeof(double) * n_mon * (d + 1), ds.stream);
+    if (e == cudaSuccess) {
+        const size_t rsz = h.precision == MPM_FP64 ? 8 : 4, rs = rsz * (size_t)h.npad;
+        c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, h.npad, n_mon, dboxes,
+                             dev);
+        e = cudaMemcpyAsync(out, dev, sizeof(double) * n_mon * (d + 1), cudaMemcpyDeviceToHost, ds.stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ds.stream);
+    dfree(dev);
+    if (e != cudaSuccess) return fail(c, MPM_ECUDA, "mpm_monitor_means: device error");
+    for (int l = 0; l < n_mon; ++l) {
+        double *o = out + (size_t)l * (d + 1);
+        if (o[d] > 0.0)
+            for (int a = 0; a < d; ++a) o[a] /= o[d];
+    }
+    return MPM_OK;
+}
+
+int mpm_get_initial_adjoint(mpm_ctx *c, int field, double *out)
+{
+    if (!c || !out) return fail(c, MPM_EINVAL, "mpm_get_initial_adjoint: bad argument");
+    AdjHost &a = c->adj;
+    if (a.lam0 < 0) return fail(c, MPM_ESTATE, "mpm_get_initial_adjoint: no adjoint computed");
+    const int d = c->grid.dim;
+    int w = 0, off = 0;
+    switch (field) {
+    case MPM_FIELD_X: w = d; off = 0; break;
+    case MPM_FIELD_V: w = d; off = d; break;
+    case MPM_FIELD_C: w = d * d; off = 2 * d; break;
+    case MPM_FIELD_RHO: w = 1; off = 2 * d + d * d; break;
+    default: return fail(c, MPM_EINVAL, "mpm_get_initial_adjoint: field has no adjoint");
+    }
+    const int64_t n = c->hp.n;
+    double *dev = nullptr;
+    int rc = dalloc(c, &dev, (size_t)n * w, "initial adjoint");
+    if (rc != MPM_OK) return rc;
+    c->aops->gather(c->hp, c->ds, w, off, a.lam_id, a.lam[a.lam0], dev);
+    cudaError_t e = cudaMemcpyAsync(out, dev, sizeof(double) * n * w, cudaMemcpyDeviceToHost, c->ds.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->ds.stream);
+    dfree(dev);
+    if (e != cudaSuccess) return fail(c, MPM_ECUDA, "mpm_get_initial_adjoint: copy failed");
+    return MPM_OK;
+}
+
 int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, double *loss_out, double *dL_dmu_out)
 {
-    if (!c || n_steps < 1 || checkpoint_every < 1 || !loss_out || !dL_dmu_out)
+    if (!c || n_steps < 1 || checkpoint_every < 1 || !loss_out || (wall >= 0 && !dL_dmu_out))
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: bad argument");
     if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no particles loaded");
     if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_step_adjoint: batch must be 1");
     if (c->grid.transfer != MPM_TRANSFER_APIC)
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: the adjoint follows the APIC transfer");
-    if (wall < 0 || wall >= 2 * c->grid.dim || c->ds.mu_dev[wall] == nullptr)
+    if (wall < -1 || wall >= 2 * c->grid.dim || (wall >= 0 && c->ds.mu_dev[wall] == nullptr))
         return fail(c, MPM_EINVAL, "mpm_step_adjoint: the wall has no friction field");
     AdjHost &a = c->adj;
-    if (a.n_obs == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no observations set");
-    if (a.steps.back() > n_steps) return fail(c, MPM_EINVAL, "mpm_step_adjoint: observation beyond the horizon");
+    if (a.n_obs == 0 && a.n_mobs == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint: no observations set");
+    if ((a.n_obs > 0 && a.steps.back() > n_steps) || (a.n_mobs > 0 && a.msteps.back() > n_steps))
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint: observation beyond the horizon");
+    a.lam0 = -1;
     const HostParams &h = c->hp;
     DevState &ds = c->ds;
     const int d = h.dim;
@@ -786,7 +911,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         a.seg_cap = K;
     }
     const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
-    const size_t fbytes = ((size_t)h.node_tiles_per_sim * sizeof(uint32_t) + 255) / 256 * 256;
+    const size_t fbytes = ((size_t)(h.node_tiles_per_sim + 1) * sizeof(int32_t) + 255) / 256 * 256;
     if (a.seg_grid_cap < K) {
         dfree(a.seg_grid);
         int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * K, "segment grids");
@@ -821,42 +946,45 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         CK(cudaMemsetAsync(a.d_mubar[w], 0, sizeof(double) * cnt, ds.stream), "zero dL/dmu");
         mub.w[w] = a.d_mubar[w];
     }
-    std::vector<int> obs_of_step(n_steps + 1, -1);
+    std::vector<int> obs_of_step(n_steps + 1, -1), mobs_of_step(n_steps + 1, -1);
     for (int o = 0; o < a.n_obs; ++o) obs_of_step[a.steps[o]] = o;
+    for (int o = 0; o < a.n_mobs; ++o) mobs_of_step[a.msteps[o]] = o;
+    const size_t msum_stride = (size_t)a.n_mon * (d + 1), mg_stride = (size_t)a.n_mon * d;
+    if (a.n_mobs > 0)
+        CK(cudaMemsetAsync(a.d_msums, 0, sizeof(double) * a.n_mobs * msum_stride, ds.stream), "zero monitor sums");
     auto ckpt_ptr = [&](int64_t k) { return (void *)((char *)a.ckpt + k * st_bytes); };
     auto seg_ptr = [&](int64_t j) { return (void *)((char *)a.seg + j * st_bytes); };
     auto gridA_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + 2 * j * gbytes); };
     auto gridV_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + (2 * j + 1) * gbytes); };
-    auto gridF_ptr = [&](int64_t j) { return (uint32_t *)((char *)a.seg_grid + 2 * K * gbytes + j * fbytes); };
-    auto seg_id_ptr = [&](int64_t j) { return a.seg_id + j * n; };
+    auto gridL_ptr = [&](int64_t j) { return (int32_t *)((char *)a.seg_grid + 2 * K * gbytes + j * fbytes); };
     std::vector<int64_t> seg_gen(K);
-    // state j of a segment: saved (with its order) after the step's sort, and the
-    // step saves its grid
-    if (!c->aux) {
-        CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "adjoint stream");
-        CK(cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming), "adjoint event");
-        CK(cudaEventCreateWithFlags(&c->ev_saved, cudaEventDisableTiming), "adjoint event");
-    }
+    std::vector<int> seg_ids(K);                // which slot of seg_id holds the order of state j
+    auto seg_id_ptr = [&](int64_t j) { return a.seg_id + (int64_t)seg_ids[j] * n; };
+    // state j of a segment: after the step's sort, P2G copies the state it reads and
+    // the grid update saves its grid; the order's ids are copied once per sort
     auto keep_state = [&](int j) -> int {
         if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
             int rc = do_sort(c);
             if (rc != MPM_OK) return rc;
         }
-        // the copy overlaps the step's P2G and grid update; its G2P waits for it
-        if (cudaEventRecord(c->ev_sorted, ds.stream) != cudaSuccess ||
-            cudaStreamWaitEvent(c->aux, c->ev_sorted, 0) != cudaSuccess)
-            return fail(c, MPM_ECUDA, "adjoint stream ordering");
-        c->aops->save_slots(h, ds, c->aux, seg_ptr(j), seg_id_ptr(j));
-        if (cudaEventRecord(c->ev_saved, c->aux) != cudaSuccess) return fail(c, MPM_ECUDA, "adjoint stream ordering");
-        c->g2p_wait = c->ev_saved;
         seg_gen[j] = c->sorts;
+        if (j > 0 && seg_gen[j] == seg_gen[j - 1]) {
+            seg_ids[j] = seg_ids[j - 1];
+        } else {
+            seg_ids[j] = j;
+            CK(cudaMemcpyAsync(a.seg_id + (int64_t)j * n, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                               ds.stream), "segment order");
+        }
+        ds.save_S = seg_ptr(j);
         ds.save_A = gridA_ptr(j);
         ds.save_V = gridV_ptr(j);
-        ds.save_F = gridF_ptr(j);
-        CK(cudaMemsetAsync(ds.save_F, 0, sizeof(uint32_t) * h.node_tiles_per_sim, ds.stream), "tile flags");
+        ds.save_L = gridL_ptr(j);
         return MPM_OK;
     };
-    auto stop_keeping = [&]() { ds.save_A = ds.save_V = ds.save_F = nullptr; };
+    auto stop_keeping = [&]() {
+        ds.save_S = ds.save_A = ds.save_V = nullptr;
+        ds.save_L = nullptr;
+    };
     CK(cudaMemsetAsync(a.grid.GVB, 0, gbytes, ds.stream), "zero grid adjoint");
     const size_t obs_stride = (size_t)a.n_track * d;
     // forward pass with checkpoints and observations; the last segment's states
@@ -872,6 +1000,11 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         stop_keeping();
         if (rc != MPM_OK) return rc;
         if (obs_of_step[t] >= 0) c->aops->track(h, ds, a.d_track_of_id, a.d_xobs + obs_of_step[t] * obs_stride);
+        if (mobs_of_step[t] >= 0) {
+            const size_t rs = rsz * (size_t)h.npad;
+            c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, h.npad, a.n_mon,
+                                 a.d_mboxes, a.d_msums + mobs_of_step[t] * msum_stride);
+        }
         if (t % K == 0 && t < n_steps) c->aops->save(h, ds, ckpt_ptr(t / K));
     }
     CK(cudaMemcpyAsync(a.final_S, ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, cudaMemcpyDeviceToDevice, ds.stream),
@@ -890,6 +1023,24 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         const double e = xobs[i] - a.z[i];
         loss += e * e;
     }
+    // monitor loss sum_obs sum_l |Q_l - z_l|^2 over non-empty monitors, and its seeds
+    // g_l = 2 (Q_l - z_l) / |P_l|
+    if (a.n_mobs > 0) {
+        std::vector<double> ms(a.n_mobs * msum_stride), mg(a.n_mobs * mg_stride, 0.0);
+        CK(cudaMemcpy(ms.data(), a.d_msums, sizeof(double) * ms.size(), cudaMemcpyDeviceToHost), "monitor sums");
+        for (int o = 0; o < a.n_mobs; ++o)
+            for (int l = 0; l < a.n_mon; ++l) {
+                const double *sm = &ms[o * msum_stride + (size_t)l * (d + 1)];
+                const double cnt = sm[d];
+                if (!(cnt > 0.0)) continue;
+                for (int b = 0; b < d; ++b) {
+                    const double e = sm[b] / cnt - a.mz[o * mg_stride + (size_t)l * d + b];
+                    loss += e * e;
+                    mg[o * mg_stride + (size_t)l * d + b] = 2.0 * e / cnt;
+                }
+            }
+        CK(cudaMemcpy(a.d_mg, mg.data(), sizeof(double) * mg.size(), cudaMemcpyHostToDevice), "monitor seeds");
+    }
     // Reverse sweep, one segment at a time (recomputed from its checkpoint).  States
     // are saved in the particle order the context holds at the time (a contiguous
     // copy); the adjoint state follows the order of the state it belongs to and is
@@ -902,6 +1053,11 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         const int o = obs_of_step[n_steps];
         c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride, a.d_z + o * obs_stride,
                             a.lam[cur]);
+    }
+    if (mobs_of_step[n_steps] >= 0) {               // the final state's positions, in the order of lam
+        const size_t rs = rsz * (size_t)h.npad;
+        c->aops->monitor_seed(h, ds, (char *)ds.S + rs * h.off_x, h.npad, a.n_mon, a.d_mboxes,
+                              a.d_mg + mobs_of_step[n_steps] * mg_stride, a.lam[cur]);
     }
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
@@ -924,7 +1080,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                                    ds.stream), "adjoint order");
                 lam_gen = seg_gen[j];
             }
-            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridF_ptr(j), a.lam[cur],
+            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
                           a.lam[cur ^ 1], mub);
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
@@ -932,6 +1088,9 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                 c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride,
                                     a.d_z + o * obs_stride, a.lam[cur]);
             }
+            if (t >= 1 && mobs_of_step[t] >= 0)     // S^t is the state kept for step j, in the order of lam
+                c->aops->monitor_seed(h, ds, seg_ptr(j), n, a.n_mon, a.d_mboxes,
+                                      a.d_mg + mobs_of_step[t] * mg_stride, a.lam[cur]);
         }
         int rc = check_launch(c, "mpm_step_adjoint");
         if (rc != MPM_OK) return rc;
@@ -943,9 +1102,12 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     CK(cudaMemcpyAsync(ds.sim, a.final_sim, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream),
        "restore sims");
     c->need_sort = true;
-    const int64_t cnt = (int64_t)ds.n_seg[wall][0] * ds.n_seg[wall][1];
-    CK(cudaMemcpyAsync(dL_dmu_out, a.d_mubar[wall], sizeof(double) * cnt, cudaMemcpyDeviceToHost, ds.stream),
-       "copy dL/dmu");
+    a.lam0 = cur;
+    if (wall >= 0) {
+        const int64_t cnt = (int64_t)ds.n_seg[wall][0] * ds.n_seg[wall][1];
+        CK(cudaMemcpyAsync(dL_dmu_out, a.d_mubar[wall], sizeof(double) * cnt, cudaMemcpyDeviceToHost, ds.stream),
+           "copy dL/dmu");
+    }
     int rc = read_status(c);
     if (rc != MPM_OK) return rc;
     *loss_out = loss;

@@ -19,6 +19,16 @@
 namespace mpm {
 
 constexpr int kMaxWalls = 6;
+constexpr int kMaxObstacles = 8;
+
+// Stationary box obstacles in node units: a node with integer coordinate c
+// (position c dx) is inside when lo[a] <= c[a] <= hi[a] on every axis; bit 2a
+// (2a + 1) of faces is set when the low (high) face of axis a is a contact face.
+struct Obstacles {
+    int n;
+    int lo[kMaxObstacles][3], hi[kMaxObstacles][3];
+    int faces[kMaxObstacles];
+};
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
@@ -65,6 +75,7 @@ struct HostParams {
     int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
     int64_t n, npad;
     int ncomp, off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
+    Obstacles obs;
 };
 
 template <class R>
@@ -75,6 +86,7 @@ struct Params {
     R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef;
     int material, dp_literal, gamma_int, transfer, no_force;
     R flip_alpha;
+    R *save_S;                    // P2G: copy of its inputs in slot order (nullptr = none)
     uint32_t *flags;              // node tile flags, the touched-tile list and its length
     int32_t *node_list, *list_count;
     int n_tiles[3], G_nodes[3], node_tiles[3];
@@ -82,6 +94,7 @@ struct Params {
     int64_t n, npad;
     int off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
     WallDev wall[kMaxWalls];
+    Obstacles obs;
 };
 
 template <class R> struct R4 { R x, y, z, w; };
@@ -116,7 +129,9 @@ struct DevState {
     void *A2 = nullptr, *V2 = nullptr;   // FLIP: (m, q) without forces and the pre-update grid velocity
     void *save_A = nullptr;       // when set, the grid update also copies (m, q + dt f) ...
     void *save_V = nullptr;       // ... and the post-wall velocity of every node it updates here,
-    void *save_F = nullptr;       // ... and which node tiles it updated (one word per tile)
+    int32_t *save_L = nullptr;    // ... and the list of node tiles it updated ([0] count, then the tiles)
+    void *save_S = nullptr;       // when set, P2G copies the components it reads (x, v, C, rho [, sigma])
+                                  // of every particle here, in slot order (save_S[c n + slot])
     CUtensorMap tmap_V;           // TMA descriptor of V: (4, G_x, G_y, [G_z], batch)
     void *mu_dev[kMaxWalls];
     int n_seg[kMaxWalls][2];
@@ -149,14 +164,21 @@ struct AdjOps {
     void (*seed)(const HostParams &, DevState &, int n_track, const int64_t *ids, const double *x_obs,
                  const double *z_obs, void *lam);
     void (*step)(const HostParams &, DevState &, const AdjDev &, const void *st, const void *GA, const void *GV,
-                 const uint32_t *GF, const void *lam_in, void *lam_out, MuBar mub);
+                 const int32_t *GL, const void *lam_in, void *lam_out, MuBar mub);
     void (*zero)(const HostParams &, DevState &, void *p, int64_t count);
-    void (*save_slots)(const HostParams &, DevState &, cudaStream_t stream, void *dst, int32_t *dst_id);
     void (*reorder)(const HostParams &, DevState &, int nc, const int32_t *id_old, int32_t *pos_scratch,
                     const int32_t *id_new, const void *in, void *out);
     void (*seed_slots)(const HostParams &, DevState &, const int32_t *id, const int32_t *track_of_id,
                        const double *x_obs, const double *z_obs, void *lam);
+    // velocity monitors: sums of v and counts per box; the adjoint seed of their loss
+    void (*monitor_sum)(const HostParams &, DevState &, const void *x, const void *v, int64_t ld, int n_mon,
+                        const double *boxes, double *sums);
+    void (*monitor_seed)(const HostParams &, DevState &, const void *x, int64_t ld, int n_mon,
+                         const double *boxes, const double *g, void *lam);
+    // out[id[s] w + k] = lam[(off + k) n + s]
+    void (*gather)(const HostParams &, DevState &, int w, int off, const int32_t *id, const void *lam, double *out);
 };
+constexpr int kMaxMonitors = 64;
 extern const AdjOps adj_ops_f32;
 extern const AdjOps adj_ops_f64;
 

@@ -227,7 +227,8 @@ template <int D> __host__ __device__ __forceinline__ constexpr int p2g_ncomp(int
 }
 
 // P2G factors of one particle from its raw components raw(j) (staging order).
-template <class R, int D, class Raw>
+// MAT = 0 (fluid) or 1 (Drucker-Prager) fixes the material at compile time; -1 reads it from P.
+template <class R, int D, int MAT = -1, class Raw>
 __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFactors<R, D> &f)
 {
     constexpr int J_RHO = 2 * D + D * D;
@@ -241,7 +242,7 @@ __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFact
     for (int q = 0; q < D * D; ++q) C[q] = raw(2 * D + q);
     const R rho = raw(J_RHO);
     const R Vp = P.mass / rho;
-    if (P.material == 0) {
+    if (MAT >= 0 ? MAT == 0 : P.material == 0) {
         const R c = P.dt * Vp * tait(P, rho);          // -dt V (-p I)
 #pragma unroll
         for (int q = 0; q < D * D; ++q) Fm[q] = (q % (D + 1) == 0) ? c : R(0);
@@ -352,9 +353,15 @@ template <class R, int D> __host__ __device__ constexpr size_t p2g_stage_offset(
 {
     return ((size_t)(D + 1) * Geo<D>::WN * sizeof(R) + (Geo<D>::TN + 1) * sizeof(int32_t) + 15) & ~size_t(15);
 }
+// Particles in flight per P2G thread (cp.async stages of its staging slots; 3
+// measured slower than 2 on the 3D collapse).
+#ifndef MPM_P2G_STAGES
+#define MPM_P2G_STAGES 2
+#endif
+
 template <class R, int D, int NT> __host__ __device__ constexpr size_t p2g_smem_bytes()
 {
-    return p2g_stage_offset<R, D>() + (size_t)2 * p2g_ncomp<D>(1) * NT * sizeof(R);
+    return p2g_stage_offset<R, D>() + (size_t)MPM_P2G_STAGES * p2g_ncomp<D>(1) * NT * sizeof(R);
 }
 
 template <int D> __device__ __forceinline__ int win_index(const int l[D], int k0, int k1, int k2)
@@ -432,6 +439,9 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 
 // Walks one thread's particles of a tile: cells c = threadIdx.x, +NT, ... and
 // the slots q of each cell (cell_off ranges); next() moves to the next particle.
+// (Rotating the cell of each round across the tile's columns, which balances
+// tiles cut by the body's edge, measured slower: the warps' cells then straddle
+// two layer groups.)
 template <int TN, int NT> struct CellCursor {
     int c, q, q1;
     __device__ __forceinline__ void start() { c = (int)threadIdx.x - NT; q = 0; q1 = 0; }
@@ -462,7 +472,7 @@ template <int D> constexpr int kP2GStageComps = p2g_ncomp<D>(1);
 // the grid if it has also left the window.  The window is added to the grid with
 // one vector atomic per touched node.  Without REG (FP64 in 3D) every particle
 // is scattered on its own.
-template <class R, int D, bool REG, int NT>
+template <class R, int D, bool REG, int NT, int MAT>
 __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     k_p2g(const Params<R> P, const R *__restrict__ S, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
           const int32_t *__restrict__ posmap, const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A,
@@ -471,6 +481,8 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     using Gm = Geo<D>;
     constexpr int NCM = kP2GStageComps<D>;
     constexpr int NXC = 2 * D + D * D;                // x, v, C: consecutive in the state
+    constexpr int NC = p2g_ncomp<D>(MAT);             // components this material stages
+    constexpr int OFF_RHO = 2 * D + 2 * D * D;        // rho (then sigma) follow x, v, C, F
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     int32_t *off = reinterpret_cast<int32_t *>(sm + (D + 1) * Gm::WN);
@@ -478,8 +490,8 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     __shared__ uint32_t tile_mask;
     __shared__ int s_slot;
     const int n_tiles = counters[1];
-    const int nc = p2g_ncomp<D>(P.material);
     const int tid = threadIdx.x;
+    const int64_t npad = P.npad;
     for (;;) {
         const int k = next_tile(&counters[2], n_tiles, &s_slot);
         if (k < 0) break;
@@ -502,25 +514,27 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
         const R *St = S + t.y;
         bool any_escape = false;
 
+        R *const Sv = P.save_S == nullptr ? nullptr : P.save_S + t.y;
         auto issue = [&](int stage, int32_t pos) {
             R *dst = stg + stage * NCM * NT + tid;
             const R *src = St + pos;
-            for (int j = 0; j < nc; ++j) {
-                const int comp = j < NXC ? j : P.off_rho + (j - NXC);
-                cp_async_elem(dst + j * NT, src + (int64_t)comp * P.npad);
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
+                cp_async_elem(dst + j * NT, src + comp * npad);
             }
         };
-        // producer: two particles ahead of the consumer, its next slot's position prefetched
+        // producer: MPM_P2G_STAGES particles ahead of the consumer, its next slot's position prefetched
         CellCursor<Gm::TN, NT> pc, cc;
         pc.start();
         cc.start();
         bool hp = pc.next(off);
-        if (hp) issue(0, pmap[pc.q]);
-        cp_async_commit();
-        hp = hp && pc.next(off);
-        if (hp) issue(1, pmap[pc.q]);
-        cp_async_commit();
-        hp = hp && pc.next(off);
+#pragma unroll
+        for (int s0 = 0; s0 < MPM_P2G_STAGES; ++s0) {
+            if (hp) issue(s0, pmap[pc.q]);
+            cp_async_commit();
+            hp = hp && pc.next(off);
+        }
         int32_t ppos = hp ? pmap[pc.q] : 0;
 
         bool hc = cc.next(off);
@@ -546,11 +560,16 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
                         for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
                 }
             }
-            cp_async_wait<1>();
+            cp_async_wait<MPM_P2G_STAGES - 1>();
             P2GFactors<R, D> f;
             {
                 const R *src = stg + stage * NCM * NT + tid;
-                p2g_factors<R, D>(P, [&](int j) { return src[j * NT]; }, f);
+                if (Sv != nullptr) {                   // the adjoint's copy of this step's state
+                    R *d = Sv + pmap[cc.q];
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
+                }
+                p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
             }
             if (hp) issue(stage, ppos);
             cp_async_commit();
@@ -566,7 +585,7 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
                 p2g_scatter<R, D>(P, f, org, sm, Asim, fsim, esc);
                 any_escape |= esc;
             }
-            stage ^= 1;
+            stage = stage + 1 == MPM_P2G_STAGES ? 0 : stage + 1;
             hc = cc.next(off);
             if constexpr (REG) {
                 if (!hc || cc.c != cur) {
@@ -617,6 +636,42 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
 
 // ------------------------------------------------------------------ grid update
 
+// Frictionless contact with the stationary obstacles (Sec. 4.1): a node inside a
+// box takes the outward normal n of the nearest contact face and, moving into the
+// box (v . n < 0), loses its normal component.  The normals are axis-aligned, so
+// that component is one coordinate.  Returns the axes it zeroed (bit a).
+template <class R, int D>
+__device__ __forceinline__ unsigned obstacle_contact(const Params<R> &P, const int a3[3], R vel[3])
+{
+    unsigned removed = 0u;
+    for (int o = 0; o < P.obs.n; ++o) {
+        int c[3] = {0, 0, 0};
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            c[a] = a3[a] - 2;
+            in = in && c[a] >= P.obs.lo[o][a] && c[a] <= P.obs.hi[o][a];
+        }
+        if (!in) continue;
+        const int faces = P.obs.faces[o];
+        int best = -1, bd = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int dl = c[a] - P.obs.lo[o][a], dh = P.obs.hi[o][a] - c[a];
+            if (((faces >> (2 * a)) & 1) && (best < 0 || dl < bd)) { best = 2 * a; bd = dl; }
+            if (((faces >> (2 * a + 1)) & 1) && (best < 0 || dh < bd)) { best = 2 * a + 1; bd = dh; }
+        }
+        if (best < 0) continue;
+        const int ax = best >> 1;
+        const bool into = (best & 1) ? vel[ax] < R(0) : vel[ax] > R(0);
+        if (into) {
+            vel[ax] = R(0);
+            removed |= 1u << ax;
+        }
+    }
+    return removed;
+}
+
 // Blocks walk the list of node tiles the last P2G touched.
 // Reads (m, q + dt f), writes the contact-corrected velocity and clears the
 // accumulator for the next step.
@@ -624,15 +679,16 @@ template <class R, int D>
 __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restrict__ A,
                                               R4<R> *__restrict__ V, uint32_t *__restrict__ flags,
                                               R4<R> *__restrict__ saveA, R4<R> *__restrict__ saveV,
-                                              uint32_t *__restrict__ saveF, R4<R> *__restrict__ A2,
+                                              int32_t *__restrict__ saveL, R4<R> *__restrict__ A2,
                                               R4<R> *__restrict__ V2, const int32_t *__restrict__ list,
                                               const int32_t *__restrict__ count)
 {
     using Gm = Geo<D>;
     const int n_list = *count;
+    if (saveL != nullptr && blockIdx.x == 0 && threadIdx.x == 0) saveL[0] = n_list;
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
     const int64_t ut = list[li];
-    if (saveF != nullptr && threadIdx.x == 0) saveF[ut] = 1u;
+    if (saveL != nullptr && threadIdx.x == 0) saveL[1 + li] = (int32_t)ut;
     const int sim = (int)(ut / P.node_tiles_per_sim);
     int64_t r = ut - (int64_t)sim * P.node_tiles_per_sim;
     int u[3] = {0, 0, 0};
@@ -666,6 +722,7 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
             vel[1] = acc.z * inv_m + P.dt * P.gravity[1];
             if (D == 3) vel[2] = acc.w * inv_m + P.dt * P.gravity[2];
         }
+        obstacle_contact<R, D>(P, a3, vel);
         // walls x-, x+, y-, y+, (z-, z+), floor last
 #pragma unroll
         for (int q = 0; q < 2 * D; ++q) {
@@ -1279,6 +1336,7 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.transfer = h.transfer;
     P.flip_alpha = (R)h.flip_alpha;
     P.no_force = 0;
+    P.save_S = (R *)ds.save_S;
     P.flags = ds.flags;
     P.node_list = ds.node_list;
     P.list_count = ds.counters + 4;
@@ -1289,6 +1347,7 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.npad = h.npad;
     P.off_x = h.off_x; P.off_v = h.off_v; P.off_C = h.off_C; P.off_F = h.off_F;
     P.off_rho = h.off_rho; P.off_sig = h.off_sig; P.off_eps = h.off_eps;
+    P.obs = h.obs;
     for (int w = 0; w < kMaxWalls; ++w) {
         P.wall[w].mu = ds.mu_dev[w];
         P.wall[w].n_seg[0] = ds.n_seg[w][0];
@@ -1330,13 +1389,14 @@ template <class R, int D> struct Launch {
     static constexpr bool kReg = (sizeof(R) == 4) || (D == 2);
     static constexpr int kP2GThreads = (D == 3 && kReg) ? 128 : 256;
     static size_t p2g_smem() { return p2g_smem_bytes<R, D, kP2GThreads>(); }
-    static void p2g(const HostParams &h, DevState &ds)
+    // one instantiation per material (the staged component count is a compile-time constant)
+    template <int MAT> static void p2g_launch(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
         const size_t smem = p2g_smem();
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_p2g<R, D, kReg, kP2GThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_p2g<R, D, kReg, kP2GThreads, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
             attr = true;
         }
@@ -1344,16 +1404,22 @@ template <class R, int D> struct Launch {
         const int64_t cap = (int64_t)ds.num_sms * (kP2GThreads == 128 ? MPM_P2G_MINB : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
+        k_p2g<R, D, kReg, kP2GThreads, MAT><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
             P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
         if (h.transfer == 3) {                       // FLIP: the momenta without forces, for v_i^n
             auto P2 = P;
             P2.no_force = 1;
+            P2.save_S = nullptr;
             cudaMemsetAsync(ds.counters + 2, 0, sizeof(int32_t), ds.stream);
-            k_p2g<R, D, kReg, kP2GThreads><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
+            k_p2g<R, D, kReg, kP2GThreads, MAT><<<(int)nb, kP2GThreads, smem, ds.stream>>>(
                 P2, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap, ds.cell_off, (R4<R> *)ds.A2, ds.flags,
                 ds.escaped);
         }
+    }
+    static void p2g(const HostParams &h, DevState &ds)
+    {
+        if (h.material == 1) p2g_launch<1>(h, ds);
+        else p2g_launch<0>(h, ds);
     }
     static void grid(const HostParams &h, DevState &ds)
     {
@@ -1362,7 +1428,7 @@ template <class R, int D> struct Launch {
         if (nb > (int64_t)ds.num_sms * 8) nb = (int64_t)ds.num_sms * 8;
         k_grid<R, D><<<(unsigned)nb, 256, 0, ds.stream>>>(P, (R4<R> *)ds.A, (R4<R> *)ds.V, ds.flags,
                                                            (R4<R> *)ds.save_A, (R4<R> *)ds.save_V,
-                                                           (uint32_t *)ds.save_F, (R4<R> *)ds.A2, (R4<R> *)ds.V2,
+                                                           ds.save_L, (R4<R> *)ds.A2, (R4<R> *)ds.V2,
                                                            ds.node_list, ds.counters + 4);
     }
     // the APIC transfer has its own instantiation; the others (TPIC, PIC, FLIP) share one

@@ -12,7 +12,8 @@ const Ops ops_f32 = {
 const AdjOps adj_ops_f32 = {
     AdjDispatch<float>::save, AdjDispatch<float>::restore, AdjDispatch<float>::track,
     AdjDispatch<float>::seed, AdjDispatch<float>::step,    AdjDispatch<float>::zero,
-    AdjDispatch<float>::save_slots, AdjDispatch<float>::reorder, AdjDispatch<float>::seed_slots,
+    AdjDispatch<float>::reorder, AdjDispatch<float>::seed_slots, AdjDispatch<float>::monitor_sum,
+    AdjDispatch<float>::monitor_seed, AdjDispatch<float>::gather,
 };
 
 }  // namespace mpm

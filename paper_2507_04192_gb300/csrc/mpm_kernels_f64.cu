@@ -12,7 +12,8 @@ const Ops ops_f64 = {
 const AdjOps adj_ops_f64 = {
     AdjDispatch<double>::save, AdjDispatch<double>::restore, AdjDispatch<double>::track,
     AdjDispatch<double>::seed, AdjDispatch<double>::step,    AdjDispatch<double>::zero,
-    AdjDispatch<double>::save_slots, AdjDispatch<double>::reorder, AdjDispatch<double>::seed_slots,
+    AdjDispatch<double>::reorder, AdjDispatch<double>::seed_slots, AdjDispatch<double>::monitor_sum,
+    AdjDispatch<double>::monitor_seed, AdjDispatch<double>::gather,
 };
 
 }  // namespace mpm

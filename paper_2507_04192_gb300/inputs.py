@@ -83,6 +83,8 @@ class Workload:
     """(wall, (n_seg0, n_seg1), mu[n_seg1 * n_seg0]) triples; walls not listed are slip walls."""
     v: Optional[np.ndarray] = None     # (n, dim) initial velocities, None = at rest
     extras: Dict[str, object] = field(default_factory=dict)
+    obstacles: List[Tuple[Tuple[float, ...], Tuple[float, ...]]] = field(default_factory=list)
+    """Stationary rigid boxes (low corner, high corner) with frictionless contact."""
 
     @property
     def n(self) -> int:
@@ -175,7 +177,7 @@ def dam_break_2d(n_cells: int = 64, width: float = 0.25, height: float = 0.5,
 def granular_cylinder_3d(n_cells: Tuple[int, int, int] = (256, 256, 128), radius_cells: float = 38,
                          height_cells: float = 76, ppc_axis: int = 2, seed: int = 0,
                          dt: float = 1.0e-5, floor_mu: float = 0.4, steps: int = 1000,
-                         sort_every: int = 16, dx: float = 1.0 / 256.0) -> Workload:
+                         sort_every: int = 32, dx: float = 1.0 / 256.0) -> Workload:
     """Drucker-Prager sand cylinder on the floor at the domain centre (dx = 1/256 m).
 
     Radius 38 dx and height 76 dx at 2 points per cell and axis give 2,761,536
@@ -229,6 +231,81 @@ def shallow_dam_break_2d(dx: float = 0.004, length: float = 1.0, height: float =
                     sort_every=sort_every, extras=dict(body_lo=(0.0, 0.0), body_hi=(length, height), seed=seed))
 
 
+def dam_break_3d(n_cells: Tuple[int, int, int] = (200, 100, 80), dx: float = 0.005, length: float = 0.3,
+                 width: float = 0.5, height: float = 0.2, sound_speed: float = 35.0, ppc_axis: int = 2,
+                 seed: int = 0, dt: float = 1.0e-5, steps: int = 1000, sort_every: int = 32,
+                 obstacles: bool = True) -> Workload:
+    """The 3D dam break with two rigid square columns of Sec. 4.1.
+
+    Domain 1.0 x 0.5 x 0.4 m at dx = 1/200; a water column ``length`` x ``width``
+    x ``height`` at the x- wall; 8 particles per cell (2 per axis) give
+    60 x 100 x 40 cells x 8 = 1,920,000 particles.  Water with the paper's
+    linear equation of state (Tait with gamma = 1, K = rho0 c^2, c = 35 m/s).
+    Columns of side 0.04 m and 0.06 m stand on the floor with their base centres
+    at (0.5, 0.3) and (0.6, 0.1) m and reach the ceiling.
+    """
+    dom = tuple(c * dx for c in n_cells)
+    x = lattice_particles(tuple(n_cells), dx, ppc_axis,
+                          lambda p: (p[:, 0] < length) & (p[:, 1] < width) & (p[:, 2] < height),
+                          (0.0, 0.0, 0.0), (length, width, height), seed)
+    mat = dict(FLUID_WATER, bulk_K=1000.0 * sound_speed ** 2, gamma=1.0)
+    obs = []
+    if obstacles:
+        for (cx, cy), side in (((0.5, 0.3), 0.04), ((0.6, 0.1), 0.06)):
+            obs.append(((cx - side / 2, cy - side / 2, 0.0), (cx + side / 2, cy + side / 2, dom[2])))
+    return Workload(name=f"dam_break_3d_{n_cells[0]}x{n_cells[1]}x{n_cells[2]}", dim=3, n_cells=tuple(n_cells),
+                    dx=dx, dt=dt, gravity=(0.0, 0.0, -9.81), material=mat, x=x,
+                    particle_volume=dx ** 3 / ppc_axis ** 3, steps=steps, sort_every=sort_every,
+                    extras=dict(body_lo=(0.0, 0.0, 0.0), body_hi=(length, width, height), seed=seed),
+                    obstacles=obs)
+
+
+def dam_break_velocity_inverse(dx: float = 0.01, column: float = 0.5, domain: Tuple[float, float] = (1.5, 0.6),
+                               sound_speed: float = 50.0, dt: float = 3.0e-5, steps: int = 10_000,
+                               n_frames: int = 100, frame_every: int = 10, n_track: int = 100,
+                               alpha_true: float = 2.0, seed: int = 0, sort_every: int = 16,
+                               checkpoint_every: int = 100) -> Workload:
+    """Dam break whose initial horizontal velocity is unknown (Sec. 5.2).
+
+    Water column H0 = L0 = ``column`` at the left wall of a ``domain`` box, 4
+    particles per cell (2 per axis), inviscid, linear EOS with sound speed
+    ``sound_speed`` (Tait gamma = 1, K = rho0 c^2).  True initial velocity
+    v_x = alpha (H0 - y), v_y = 0.  Observations: the last n_frames x
+    frame_every steps, every frame_every steps; tracked particles (n_track seeded,
+    or every particle when n_track = 0) and nine velocity monitors, squares of
+    half-side 0.01 m centred on {0.2, 0.3, 0.4} x {0.1, 0.2, 0.3} m.  At dx = 0.01
+    this is 10,000 particles on a 150 x 60 grid; at dx = 0.005, 40,000 on 300 x 120.
+    """
+    n_cells = (int(round(domain[0] / dx)), int(round(domain[1] / dx)))
+    x = lattice_particles(n_cells, dx, 2, lambda p: (p[:, 0] < column) & (p[:, 1] < column),
+                          (0.0, 0.0), (column, column), seed)
+    mat = dict(FLUID_WATER, bulk_K=1000.0 * sound_speed ** 2, gamma=1.0)
+    w = Workload(name=f"dam_break_velocity_inverse_{n_cells[0]}x{n_cells[1]}", dim=2, n_cells=n_cells, dx=dx,
+                 dt=dt, gravity=(0.0, -9.81), material=mat, x=x, particle_volume=dx * dx / 4, steps=steps,
+                 sort_every=sort_every,
+                 extras=dict(body_lo=(0.0, 0.0), body_hi=(column, column), seed=seed))
+    w.v = velocity_profile_linear(x, alpha_true, column)
+    obs_steps = [steps - (n_frames - 1 - k) * frame_every for k in range(n_frames)]
+    ids = (np.arange(w.n, dtype=np.int64) if n_track == 0 else
+           tracked_particles(x, n_track, seed, np.array((0.0, 0.0)), np.array((column, column))))
+    monitors = [((cx - 0.01, cy - 0.01), (cx + 0.01, cy + 0.01)) for cy in (0.1, 0.2, 0.3) for cx in (0.2, 0.3, 0.4)]
+    w.extras.update(H0=column, alpha_true=alpha_true, obs_steps=obs_steps, track_ids=ids, monitors=monitors,
+                    checkpoint_every=checkpoint_every)
+    return w
+
+
+def velocity_profile_linear(x: np.ndarray, alpha: float, H0: float) -> np.ndarray:
+    """v_x = alpha (H0 - y), v_y = 0 (Sec. 5.2)."""
+    v = np.zeros_like(x)
+    v[:, 0] = alpha * (H0 - x[:, 1])
+    return v
+
+
+def velocity_profile_field(y: np.ndarray, H0: float) -> np.ndarray:
+    """The reference field of Sec. 5.2: 2 (1 - (y/H0)^2) + 0.2 sin(4 pi y / H0)."""
+    return 2.0 * (1.0 - (y / H0) ** 2) + 0.2 * np.sin(4.0 * np.pi * y / H0)
+
+
 def granular_inverse_3d(n_cells: Tuple[int, int, int] = (192, 192, 96), radius_cells: float = 30,
                         height_cells: float = 60, patches: Tuple[int, int] = (16, 16), n_track: int = 128,
                         n_obs: int = 10, steps: int = 600, seed: int = 0, checkpoint_every: int = 60,
@@ -256,4 +333,6 @@ WORKLOADS = {
     "dam_break_inverse_2d_128": lambda: dam_break_inverse_2d(128),
     "granular_cylinder_3d_192x192x96": lambda: granular_cylinder_3d((192, 192, 96), 30, 60, steps=600),
     "granular_inverse_3d_192x192x96": lambda: granular_inverse_3d(),
+    "dam_break_3d_200x100x80": lambda: dam_break_3d(),
+    "dam_break_velocity_inverse_150x60": lambda: dam_break_velocity_inverse(),
 }

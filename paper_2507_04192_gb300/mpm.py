@@ -77,6 +77,10 @@ def load_library(build_if_missing: bool = True):
             "mpm_load_particles": (I, [P, L, P, P, D, P]),
             "mpm_set_particle_field": (I, [P, I, P]),
             "mpm_set_friction_field": (I, [P, I, P, P]),
+            "mpm_set_obstacles": (I, [P, I, P]),
+            "mpm_set_velocity_monitors": (I, [P, I, P, I, P, P]),
+            "mpm_get_initial_adjoint": (I, [P, I, P]),
+            "mpm_monitor_means": (I, [P, I, P, P]),
             "mpm_step": (I, [P, I]),
             "mpm_synchronize": (I, [P]),
             "mpm_get_particles": (I, [P, I, P]),
@@ -158,6 +162,12 @@ def mpm_set_friction_field(ctx, wall: int, n_seg: Sequence[int], mu: np.ndarray)
     _check(ctx, load_library().mpm_set_friction_field(ctx, int(wall), ns, _dptr(m)))
 
 
+def mpm_set_obstacles(ctx, boxes):
+    """Stationary rigid boxes [(lo, hi), ...] with frictionless contact."""
+    b = np.ascontiguousarray(np.asarray([list(lo) + list(hi) for lo, hi in boxes], dtype=np.float64).reshape(-1))
+    _check(ctx, load_library().mpm_set_obstacles(ctx, len(boxes), _dptr(b) if len(boxes) else None))
+
+
 def mpm_step(ctx, n_steps: int):
     _check(ctx, load_library().mpm_step(ctx, int(n_steps)))
 
@@ -235,12 +245,51 @@ def mpm_set_observations(ctx, ids: np.ndarray, steps: Sequence[int], z_obs: np.n
     _check(ctx, load_library().mpm_set_observations(ctx, len(ids), _dptr(ids), len(st), _dptr(st), _dptr(z)))
 
 
+def mpm_clear_observations(ctx):
+    _check(ctx, load_library().mpm_set_observations(ctx, 0, None, 0, None, None))
+
+
+def mpm_set_velocity_monitors(ctx, boxes, steps: Sequence[int], v_obs: np.ndarray):
+    """Eulerian velocity monitors: boxes [(lo, hi), ...], observation steps and the
+    observed mean velocities (n_obs x n_mon x dim)."""
+    b = np.ascontiguousarray(np.asarray([list(lo) + list(hi) for lo, hi in boxes], dtype=np.float64).reshape(-1))
+    st = np.ascontiguousarray(steps, dtype=np.int32)
+    z = np.ascontiguousarray(v_obs, dtype=np.float64)
+    assert z.shape[:2] == (len(st), len(boxes))
+    _check(ctx, load_library().mpm_set_velocity_monitors(ctx, len(boxes), _dptr(b), len(st), _dptr(st), _dptr(z)))
+
+
+def mpm_monitor_means(ctx, boxes):
+    """Mean velocity (n_mon x dim) and particle count (n_mon) of each monitor box on the current state."""
+    b = np.ascontiguousarray(np.asarray([list(lo) + list(hi) for lo, hi in boxes], dtype=np.float64).reshape(-1))
+    dim = len(boxes[0][0])
+    out = np.zeros((len(boxes), dim + 1), dtype=np.float64)
+    _check(ctx, load_library().mpm_monitor_means(ctx, len(boxes), _dptr(b), _dptr(out)))
+    return out[:, :dim].copy(), out[:, dim].astype(np.int64)
+
+
+def mpm_clear_velocity_monitors(ctx):
+    _check(ctx, load_library().mpm_set_velocity_monitors(ctx, 0, None, 0, None, None))
+
+
 def mpm_step_adjoint(ctx, n_steps: int, checkpoint_every: int, wall: int, n_mu: int):
+    """Loss and dL/dmu of one wall (wall = -1: no friction gradient, returns an empty array)."""
     loss = C.c_double()
-    g = np.zeros(n_mu, dtype=np.float64)
+    g = np.zeros(max(n_mu, 0), dtype=np.float64)
     _check(ctx, load_library().mpm_step_adjoint(ctx, int(n_steps), int(checkpoint_every), int(wall),
-                                                C.byref(loss), _dptr(g)))
+                                                C.byref(loss), _dptr(g) if wall >= 0 else None))
     return loss.value, g
+
+
+def mpm_get_initial_adjoint(ctx, field: str) -> np.ndarray:
+    """dL/d(field of the initial state) of the last adjoint, load order, (n, width)."""
+    n = mpm_num_particles(ctx)
+    w = {"x": None, "v": None, "C": None, "rho": 1}[field]
+    dim = mpm_field_width(ctx, "x")
+    w = w if w is not None else (dim * dim if field == "C" else dim)
+    out = np.zeros((n, w), dtype=np.float64)
+    _check(ctx, load_library().mpm_get_initial_adjoint(ctx, FIELDS[field], _dptr(out)))
+    return out
 
 
 def mpm_step_noalloc(grid: GridDesc, material: Material, n: int, particle_volume: float, state_in: StatePtrs,
@@ -370,6 +419,8 @@ class Simulation:
             sim.load(w.x, w.v, w.particle_volume)
             for wall, nseg, mu in w.friction:
                 sim.set_friction(wall, nseg, np.tile(np.asarray(mu, dtype=np.float64).reshape(-1), batch))
+            if getattr(w, "obstacles", None):
+                sim.set_obstacles(w.obstacles)
         return sim
 
     def close(self):
@@ -391,6 +442,9 @@ class Simulation:
 
     def set_friction(self, wall, n_seg, mu):
         mpm_set_friction_field(self.ctx, wall, n_seg, mu)
+
+    def set_obstacles(self, boxes):
+        mpm_set_obstacles(self.ctx, boxes)
 
     def step(self, n=1):
         mpm_step(self.ctx, n)
