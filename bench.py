@@ -349,9 +349,21 @@ def secondary_measurements(stream, dev):
     inf = _event_ms(stream, lambda: [net.infer(xs) for _ in range(reps)]) / reps
     net.close()
     fl_fwd = 2 * 256 * sum(W[i] * W[i + 1] for i in range(3))
-    # the tensor-core GEMM itself on a shape large enough to fill the GPU
+    out["mlp"] = {"widths": W, "batch": 256, "train_step_ms": tr, "infer_ms": inf,
+                  "train_tflops": 3 * fl_fwd / (tr * 1e-3) / 1e12,
+                  "note": "host-synchronous calls incl. host<->device copies of x, targets and loss",
+                  "gemm": gemm_measurement(stream)}
+    return out
+
+
+def gemm_measurement(stream, shape=(8192, 2048, 2048), reps=10):
+    """The tensor-core GEMM itself (C = A B^T, bf16 in, fp32 out) on a shape large
+    enough to fill the GPU, against the measured cuBLAS bf16 burst peak."""
     import torch
-    gM, gN, gK = 8192, 2048, 2048
+
+    from paper_2507_04192_gb300 import mpm
+
+    gM, gN, gK = shape
     ga = torch.randn(gM, gK, device="cuda").to(torch.bfloat16)
     gb = torch.randn(gN, gK, device="cuda").to(torch.bfloat16)
     gc = torch.empty(gM, gN, device="cuda")
@@ -360,15 +372,12 @@ def secondary_measurements(stream, dev):
                                     gst.data_ptr(), stream.cuda_stream)
     for _ in range(3):
         run()
-    gms = _event_ms(stream, lambda: [run() for _ in range(10)]) / 10
+    gms = _event_ms(stream, lambda: [run() for _ in range(reps)]) / reps
+    assert int(gst.item()) == 0
     peak_tf = load_peaks_bf16()
     gemm_tf = 2.0 * gM * gN * gK / (gms * 1e-3) / 1e12
-    out["mlp"] = {"widths": W, "batch": 256, "train_step_ms": tr, "infer_ms": inf,
-                  "train_tflops": 3 * fl_fwd / (tr * 1e-3) / 1e12,
-                  "note": "host-synchronous calls incl. host<->device copies of x, targets and loss",
-                  "gemm": {"shape": [gM, gN, gK], "ms": gms, "tflops": gemm_tf, "peak": peak_tf,
-                           "frac": gemm_tf / peak_tf, "peak_source": "measured bf16_tflops (cuBLAS burst)"}}
-    return out
+    return {"shape": [gM, gN, gK], "ms": gms, "tflops": gemm_tf, "peak": peak_tf, "frac": gemm_tf / peak_tf,
+            "peak_source": "measured bf16_tflops (cuBLAS burst)"}
 
 
 def bench_ours(args):
@@ -511,11 +520,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--headline-only", action="store_true", help="skip the adjoint, batched and network lines")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 line")
+    ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM line (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         bench_reference(args)
+    elif args.gemm_only:
+        import torch
+        stream = torch.cuda.Stream()
+        print(json.dumps({"mlp_gemm": gemm_measurement(stream)}), flush=True)
     else:
         bench_ours(args)
 

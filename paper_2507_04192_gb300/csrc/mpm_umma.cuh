@@ -39,14 +39,25 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
 
 // Pipeline: the operand tiles are brought in by TMA (cp.async.bulk.tensor,
 // 128-byte swizzle: a K-chunk of 64 bf16 is one 128-byte swizzle row per M/N
-// row) through a ring of kUmmaStages shared-memory stages.  Thread 0 produces
+// row) through a ring of shared-memory stages.  Thread 0 produces
 // (waits for a free stage, arms its mbarrier with the byte count, issues the
 // two tile loads); thread 32 consumes (waits for a full stage, issues the four
 // K = 16 MMAs, commits them to the stage's "empty" mbarrier so the producer can
 // refill it).  A final commit signals the epilogue, which reads TMEM and either
 // stores C or applies bias + GELU (bf16 copy for the next layer) or bias +
 // scaled sigmoid.  All waits are bounded.
-constexpr int kUmmaStages = 4;
+// Tile choice: 128 x 128 tiles through a ring of MPM_UMMA_STAGES stages; when N
+// >= 256 and the 128 x 256 tiles alone fill every SM (MPM_UMMA_WIDE), 128 x 256
+// tiles through MPM_UMMA_WIDE_STAGES stages (half the operand traffic per FLOP).
+#ifndef MPM_UMMA_STAGES
+#define MPM_UMMA_STAGES 4
+#endif
+#ifndef MPM_UMMA_WIDE
+#define MPM_UMMA_WIDE 1
+#endif
+#ifndef MPM_UMMA_WIDE_STAGES
+#define MPM_UMMA_WIDE_STAGES 4
+#endif
 enum UmmaEpilogue { kEpiStore = 0, kEpiBiasGelu = 1, kEpiBiasSigmoid = 2 };
 
 struct UmmaEpi {
@@ -87,7 +98,7 @@ __device__ __forceinline__ bool umma_wait_parity(uint64_t *bar, uint32_t parity)
 
 __device__ __forceinline__ float umma_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
-template <int NT>
+template <int NT, int STAGES>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_gemm_tma(int M, int N, int K, const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB, float *__restrict__ Cout, int ldc, UmmaEpi epi,
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                              ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[kUmmaStages], empty[kUmmaStages], done;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
     __shared__ uint32_t tmem_base;
     __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kUmmaStages; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&empty[s])) : "memory");
         }
@@ -130,8 +141,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 
     if (tid == 0) {                                        // producer
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kUmmaStages;
-            const uint32_t ph = (uint32_t)(kc / kUmmaStages) & 1u;
+            const int s = kc % STAGES;
+            const uint32_t ph = (uint32_t)(kc / STAGES) & 1u;
             if (!umma_wait_parity(&empty[s], ph ^ 1u)) {
                 failed = 1;
                 break;
@@ -155,8 +166,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         const uint32_t idesc = umma_idesc_bf16(kUmmaM, NT);
         bool ok = true;
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kUmmaStages;
-            const uint32_t ph = (uint32_t)(kc / kUmmaStages) & 1u;
+            const int s = kc % STAGES;
+            const uint32_t ph = (uint32_t)(kc / STAGES) & 1u;
             if (!umma_wait_parity(&full[s], ph)) {
                 ok = false;
                 break;
@@ -220,9 +231,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                      : "memory");
 }
 
-template <int NT> constexpr size_t umma_tma_smem_bytes()
+template <int NT, int STAGES> constexpr size_t umma_tma_smem_bytes()
 {
-    return (size_t)kUmmaStages * (kUmmaM + NT) * kUmmaKC * 2 + 1024;
+    return (size_t)STAGES * (kUmmaM + NT) * kUmmaKC * 2 + 1024;
 }
 
 // 2D tensor map of a row-major bf16 matrix (rows x cols, leading dimension ld
@@ -247,25 +258,41 @@ inline bool umma_tensor_map(CUtensorMap *tm, const __nv_bfloat16 *ptr, int rows,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int NT, int STAGES>
+inline cudaError_t umma_launch(int M, int N, int K, const CUtensorMap &tmA, const CUtensorMap &tmB, float *C, int ldc,
+                               const UmmaEpi &epi, int32_t *status, cudaStream_t stream)
+{
+    constexpr size_t smem = umma_tma_smem_bytes<NT, STAGES>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_umma_gemm_tma<NT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    dim3 g((M + kUmmaM - 1) / kUmmaM, (N + NT - 1) / NT);
+    k_umma_gemm_tma<NT, STAGES><<<g, kUmmaThreads, smem, stream>>>(M, N, K, tmA, tmB, C, ldc, epi, status);
+    return cudaGetLastError();
+}
+
 // C = A B^T through the pipelined TMA kernel, with an optional fused epilogue.
 inline cudaError_t umma_gemm_tma(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
                                  int ldb, float *C, int ldc, const UmmaEpi &epi, int32_t *status, cudaStream_t stream)
 {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    }
+    const int NT = N <= 32 ? 32
+                   : (MPM_UMMA_WIDE && N >= 256 && (int64_t)((M + kUmmaM - 1) / kUmmaM) * ((N + 255) / 256) >= sms)
+                       ? 256
+                       : 128;
     CUtensorMap tmA, tmB;
-    const int NT = N <= 32 ? 32 : 128;
     if (!umma_tensor_map(&tmA, A, M, K, lda, kUmmaM) || !umma_tensor_map(&tmB, B, N, K, ldb, NT))
         return cudaErrorInvalidValue;
-    dim3 g((M + kUmmaM - 1) / kUmmaM, (N + NT - 1) / NT);
-    if (NT == 32) {
-        static bool a = false;
-        if (!a) { cudaFuncSetAttribute(k_umma_gemm_tma<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_tma_smem_bytes<32>()); a = true; }
-        k_umma_gemm_tma<32><<<g, kUmmaThreads, umma_tma_smem_bytes<32>(), stream>>>(M, N, K, tmA, tmB, C, ldc, epi, status);
-    } else {
-        static bool a = false;
-        if (!a) { cudaFuncSetAttribute(k_umma_gemm_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_tma_smem_bytes<128>()); a = true; }
-        k_umma_gemm_tma<128><<<g, kUmmaThreads, umma_tma_smem_bytes<128>(), stream>>>(M, N, K, tmA, tmB, C, ldc, epi, status);
-    }
-    return cudaGetLastError();
+    if (NT == 32) return umma_launch<32, 4>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
+    if (NT == 256) return umma_launch<256, MPM_UMMA_WIDE_STAGES>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
+    return umma_launch<128, MPM_UMMA_STAGES>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
 }
 
 

@@ -36,7 +36,9 @@ def _gemm(M, N, K, lda=None, ldb=None, ldc=None, seed=0):
 
 
 @pytest.mark.parametrize("M,N,K", [(256, 256, 640), (256, 256, 256), (256, 32, 256), (32, 256, 256),
-                                   (256, 640, 256), (130, 40, 72), (1, 8, 8), (300, 136, 1000)])
+                                   (256, 640, 256), (130, 40, 72), (1, 8, 8), (300, 136, 1000),
+                                   # 128 x 256 tiles (enough of them to fill every SM), full and ragged
+                                   (4864, 1024, 256), (5000, 1000, 200)])
 def test_gemm_bf16_matches_fp64_product(M, N, K):
     C, ref, mag = _gemm(M, N, K)
     assert np.isfinite(C[:, :N]).all()
