@@ -634,6 +634,189 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
 }
 
+// A particle that left its sort cell, scattered on its own to the grid (27 vector
+// atomics) with its node tiles marked.  Kept out of line: the path is rare and
+// its registers would otherwise count against the accumulating loop.
+template <class R>
+__device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> &f, R mass, R4<R> *Asim, int Gx, int Gy,
+                                         uint32_t *fsim, int32_t *list, int32_t *count, int ntx, int nty)
+{
+    for (int kk = 0; kk < 27; ++kk) {
+        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
+        R m, mom[3];
+        p2g_node<R, 3>(f, mass, k0, k1, k2, m, mom);
+        const int a0 = f.b[0] + 2 + k0, a1 = f.b[1] + 2 + k1, a2 = f.b[2] + 2 + k2;
+        red_add4(&Asim[((int64_t)a2 * Gy + a1) * Gx + a0], m, mom[0], mom[1], mom[2]);
+        const int u0 = a0 / Geo<3>::T, u1 = a1 / Geo<3>::T, u2 = a2 / Geo<3>::T;
+        mark_node_tile(fsim, list, count, ((int64_t)u2 * nty + u1) * ntx + u0);
+    }
+}
+
+// P2G without a shared-memory window (3D, register accumulation).  Warps claim
+// work items of 128 cells (two layer groups of a tile) from a global cursor and
+// never synchronise with each other: lane l walks cells base + l, + 32, + 64,
+// + 96 through the same two-stage cp.async pipeline as k_p2g, sums the
+// particles still in their cell in registers and adds the 27 node sums of a
+// cell straight to the grid with vector atomics (27 per cell instead of 108
+// shared-memory atomics plus the window pass); particles that left their cell
+// are scattered on their own to the grid.  The warp marks the node tiles its
+// cells reach.
+#ifndef MPM_P2G_DIRECT
+#define MPM_P2G_DIRECT 1
+#endif
+template <class R, int NT, int MAT>
+__global__ void __launch_bounds__(NT, MPM_P2G_MINB)
+    k_p2g_direct(const Params<R> P, const R *__restrict__ S, const int4 *__restrict__ tiles,
+                 int32_t *__restrict__ counters, const int32_t *__restrict__ posmap,
+                 const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A, uint32_t *__restrict__ flags,
+                 unsigned long long *__restrict__ escaped_count)
+{
+    constexpr int D = 3;
+    using Gm = Geo<D>;
+    constexpr int NCM = kP2GStageComps<D>;
+    constexpr int NXC = 2 * D + D * D;
+    constexpr int NC = p2g_ncomp<D>(MAT);
+    constexpr int OFF_RHO = 2 * D + 2 * D * D;
+    constexpr int CELLS = 128;                       // cells per work item
+    constexpr int ITEMS = Gm::TN / CELLS;            // work items per tile
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *stg = reinterpret_cast<R *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int n_items = counters[1] * ITEMS;
+    const int64_t npad = P.npad;
+    bool any_escape = false;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&counters[2], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int k = item / ITEMS;
+        const int cbase = (item - k * ITEMS) * CELLS;
+        const int4 t = tiles[k];
+        const int sim = (int)(t.x / P.tiles_per_sim);
+        int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
+        int org[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
+            tl /= P.n_tiles[a];
+        }
+        R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
+        uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
+        const int32_t *pmap = posmap + t.y;
+        const int32_t *off = cell_off + (int64_t)k * (Gm::TN + 1);
+        const R *St = S + t.y;
+        R *const Sv = P.save_S == nullptr ? nullptr : P.save_S + t.y;
+        auto issue = [&](int stage, int32_t pos) {
+            R *dst = stg + stage * NCM * NT + tid;
+            const R *src = St + pos;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
+                cp_async_elem(dst + j * NT, src + comp * npad);
+            }
+        };
+        // cursors over this lane's cells cbase + lane + 32 r and their slots
+        struct Cur {
+            int c, q, q1, end;
+            __device__ __forceinline__ bool next(const int32_t *o)
+            {
+                ++q;
+                while (q >= q1) {
+                    c += 32;
+                    if (c >= end) return false;
+                    q = o[c];
+                    q1 = o[c + 1];
+                }
+                return true;
+            }
+        };
+        Cur pc{cbase + lane - 32, 0, 0, cbase + CELLS}, cc = pc;
+        bool hp = pc.next(off);
+#pragma unroll
+        for (int s0 = 0; s0 < 2; ++s0) {
+            if (hp) issue(s0, pmap[pc.q]);
+            cp_async_commit();
+            hp = hp && pc.next(off);
+        }
+        int32_t ppos = hp ? pmap[pc.q] : 0;
+        bool hc = cc.next(off);
+        int stage = 0, cur = -1;
+        int bown[D], nb[D];
+        unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
+        R acc[Gm::STENCIL][D + 1];
+        while (hc) {
+            if (cc.c != cur) {
+                cur = cc.c;
+                int r = cur;
+                unsigned hi = 0u;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const int ci = r % Gm::T;
+                    r /= Gm::T;
+                    bown[a] = org[a] + ci - 1;         // base cell index of the cell's particles
+                    nb[a] = org[a] + ci + 1;           // its first stencil node
+                    hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if ((m & ~hi & 7u) == 0u) reach |= 1u << m;
+#pragma unroll
+                for (int kk = 0; kk < Gm::STENCIL; ++kk)
+#pragma unroll
+                    for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
+            }
+            cp_async_wait<1>();
+            P2GFactors<R, D> f;
+            {
+                const R *src = stg + stage * NCM * NT + tid;
+                if (Sv != nullptr) {                   // the adjoint's copy of this step's state
+                    R *d = Sv + pmap[cc.q];
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
+                }
+                p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
+            }
+            if (hp) issue(stage, ppos);
+            cp_async_commit();
+            hp = hp && pc.next(off);
+            if (hp) ppos = pmap[pc.q];
+            bool own = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
+            if (own) {
+                p2g_accumulate<R, D>(f, P.mass, acc);
+            } else {                                   // left its cell since the sort: on its own
+                any_escape = true;
+                p2g_escape3<R>(f, P.mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
+                               P.node_tiles[0], P.node_tiles[1]);
+            }
+            stage ^= 1;
+            hc = cc.next(off);
+            if (!hc || cc.c != cur) {                  // the cell is done: its 27 node sums to the grid
+                const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
+                R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];
+#pragma unroll
+                for (int kk = 0; kk < Gm::STENCIL; ++kk)
+                    red_add4(base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy, acc[kk][0], acc[kk][1],
+                             acc[kk][2], acc[kk][3]);
+            }
+        }
+        cp_async_wait<0>();
+        // node tiles reached by the warp's cells (those holding particles)
+        const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
+        if (lane < 8 && ((wreach >> lane) & 1u)) {
+            int u[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
+            mark_node_tile(flags, P.node_list, P.list_count, (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
+        }
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
+    if (ball && lane == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
+    if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
+}
+
 // ------------------------------------------------------------------ grid update
 
 // Frictionless contact with the stationary obstacles (Sec. 4.1): a node inside a
@@ -1393,6 +1576,23 @@ template <class R, int D> struct Launch {
     template <int MAT> static void p2g_launch(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
+        if constexpr (D == 3 && sizeof(R) == 4 && MPM_P2G_DIRECT) {
+            constexpr int NT = kP2GThreads;
+            const size_t smem = (size_t)2 * kP2GStageComps<3> * NT * sizeof(R);
+            const int nb = ds.num_sms * MPM_P2G_MINB;
+            k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap,
+                                                                  ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
+            if (h.transfer == 3) {                   // FLIP: the momenta without forces, for v_i^n
+                auto P2 = P;
+                P2.no_force = 1;
+                P2.save_S = nullptr;
+                cudaMemsetAsync(ds.counters + 2, 0, sizeof(int32_t), ds.stream);
+                k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P2, (const R *)ds.S, ds.tiles, ds.counters,
+                                                                      ds.posmap, ds.cell_off, (R4<R> *)ds.A2,
+                                                                      ds.flags, ds.escaped);
+            }
+            return;
+        }
         const size_t smem = p2g_smem();
         static bool attr = false;
         if (!attr) {
