@@ -249,10 +249,25 @@ int mpm_monitor_means(mpm_ctx *ctx, int n_mon, const double *boxes, double *out)
  * rho, sigma) for Drucker-Prager; the zone and contact branches of the forward
  * step are held fixed), batch 1.  Device memory: checkpoints of
  * (2 dim + dim^2 + 1) reals per particle each (+ 6 for Drucker-Prager), plus
- * checkpoint_every states.
+ * checkpoint_every states with their grids (more with mpm_set_adjoint_memory),
+ * plus in 3D single precision 21 reals per particle of scatter coefficients and
+ * the sort tables of each sort generation the kept states span.
  */
 int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, double *loss_out,
                      double *dL_dmu_out);
+
+/*
+ * Device memory (bytes) mpm_step_adjoint may use, beyond what one segment of
+ * checkpoint_every states needs, to keep more segments of the first forward
+ * pass: the last 1 + bytes / (one segment's size) segments are then reversed
+ * without recomputation (Sec. 3.3.2 trades memory for recomputation; a GPU with
+ * memory to spare can keep the whole horizon).  Default 0: only the last
+ * segment is kept and every other one is recomputed from its checkpoint.  A
+ * segment of K states takes K x ((2 dim + dim^2 + 1 [+ 6]) reals per particle
+ * + two grids of 4 reals per node + 4 bytes per particle) plus the sort tables
+ * of its sort generations.  The result does not depend on the setting.
+ */
+int mpm_set_adjoint_memory(mpm_ctx *ctx, int64_t bytes);
 
 /*
  * dL/d(field of the initial state) of the last mpm_step_adjoint (the adjoint

@@ -649,9 +649,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA,
                                                       R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB,
-                                                      const int32_t *__restrict__ GL, MuBar mu_bar)
+                                                      const int32_t *__restrict__ GL, MuBar mu_bar,
+                                                      int32_t *__restrict__ scatter_cursor)
 {
     using Gm = Geo<D>;
+    if (scatter_cursor != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *scatter_cursor = 0;
     const int n_list = GL[0];
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
     const int64_t ut = GL[1 + li];
@@ -976,10 +978,11 @@ __device__ __forceinline__ int hidx3(int b, int a)
 // 3D adjoint of G2P (same outputs as k_adj_g2p_bwd): the forward velocity
 // moments and the x-derivatives of the weights enter through stencil moments of
 // the node velocities; only the scatter of v_bar runs node by node.
-template <class R>
+template <class R, bool SPLIT>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
     k_adj_g2p_bwd3(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GV,
-                   const R *__restrict__ lam_in, R *__restrict__ lam_out, R4<R> *__restrict__ GVB)
+                   const R *__restrict__ lam_in, R *__restrict__ lam_out, R4<R> *__restrict__ GVB,
+                   R *__restrict__ coef)
 {
     constexpr int D = 3, JC = 2 * D, JR = 2 * D + D * D;
     const int64_t n = P.n;
@@ -1061,7 +1064,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
             }
             xb[b] += acc;
         }
-        // v_bar scatter: v_bar_k = w_k (vbt + cscale Cb (k - fx)) + Lb grad w_k
+        // v_bar scatter: v_bar_k = w_k (vbt + cscale Cb (k - fx)) + Lb grad w_k; with SPLIT
+        // the coefficients (vbt, Cb, Lb) go to coef for the cell-ordered scatter pass
+        if constexpr (SPLIT) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) coef[a * n + p] = vbt[a];
+#pragma unroll
+            for (int q = 0; q < D * D; ++q) {
+                coef[(3 + q) * n + p] = Cb[q];
+                coef[(12 + q) * n + p] = Lb[q];
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < 27; ++k) {
             const int kk[3] = {k % 3, (k / 3) % 3, k / 9};
@@ -1081,6 +1094,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
             }
             const int a3[3] = {s.b[0] + 2 + kk[0], s.b[1] + 2 + kk[1], s.b[2] + 2 + kk[2]};
             red_add4(&GVB[lin3<D>(a3, P.G_nodes)], vb[0], vb[1], vb[2], R(0));
+        }
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) lam_out[a * n + p] = xb[a];
@@ -1193,6 +1207,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
 
 struct AdjDev {
     void *GVB, *GAB;                    // adjoint grid buffers (R4 per node)
+    // 3D single precision: the v_bar scatter runs as a cell-ordered pass (k_p2g_direct,
+    // MAT 2) when the sort tables of the state's generation are given
+    void *coef = nullptr;               // 21 x n scatter coefficients
+    int32_t *cursor = nullptr;          // its work-item cursor (zero between steps)
+    const int4 *tiles = nullptr;        // sort tables of the state's generation
+    const int32_t *n_tiles = nullptr, *posmap = nullptr, *cell_off = nullptr;
 };
 
 template <class R, int D> struct AdjLaunch {
@@ -1256,17 +1276,35 @@ template <class R, int D> struct AdjLaunch {
                      const void *GV, const int32_t *GL, const void *lam_in, void *lam_out, MuBar mub)
     {
         auto P = make_params<R>(h, ds);
-        if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
-            k_adj_g2p_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
-                                                                   (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB);
-        else
+        bool split = false;
+        if constexpr (D == 3 && MPM_ADJ_SEPARABLE) {
+            if constexpr (sizeof(R) == 4 && MPM_P2G_DIRECT) split = a.coef != nullptr && a.tiles != nullptr;
+            if (split) {
+                if constexpr (sizeof(R) == 4 && MPM_P2G_DIRECT) {
+                    k_adj_g2p_bwd3<R, true><<<pblocks(h, ds), 256, 0, ds.stream>>>(
+                        P, (const R *)st, (const R4<R> *)GV, (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB,
+                        (R *)a.coef);
+                    constexpr int NT = 128;
+                    const size_t smem = (size_t)2 * direct_stage_comps<2>() * NT * sizeof(R);
+                    P2GIO<R> io{(const R *)st, (const R *)a.coef, h.n, a.tiles, a.n_tiles, a.cursor, a.posmap,
+                                a.cell_off, (R4<R> *)a.GVB, nullptr};
+                    k_p2g_direct<R, NT, 2><<<ds.num_sms * MPM_P2G_MINB, NT, smem, ds.stream>>>(P, io, nullptr,
+                                                                                               nullptr);
+                }
+            } else {
+                k_adj_g2p_bwd3<R, false><<<pblocks(h, ds), 256, 0, ds.stream>>>(
+                    P, (const R *)st, (const R4<R> *)GV, (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB, nullptr);
+            }
+        } else {
             k_adj_g2p_bwd<R, D><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)GV,
                                                                          (const R *)lam_in, (R *)lam_out,
                                                                          (R4<R> *)a.GVB);
+        }
         int64_t nbg = h.node_tiles_per_sim;             // blocks stride the saved tile list
         if (nbg > (int64_t)ds.num_sms * 8) nbg = (int64_t)ds.num_sms * 8;
         k_adj_grid_bwd<R, D><<<(unsigned)nbg, 256, 0, ds.stream>>>(P, (const R4<R> *)GA, (R4<R> *)a.GVB,
-                                                                   (R4<R> *)a.GAB, GL, mub);
+                                                                   (R4<R> *)a.GAB, GL, mub,
+                                                                   split ? a.cursor : nullptr);
         if constexpr (D == 3 && MPM_ADJ_SEPARABLE)
             k_adj_p2g_bwd3<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(P, (const R *)st, (const R4<R> *)a.GAB,
                                                                    (R *)lam_out);

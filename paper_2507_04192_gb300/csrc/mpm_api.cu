@@ -50,6 +50,12 @@ struct AdjHost {
     double *d_mboxes = nullptr, *d_msums = nullptr, *d_mg = nullptr;
     // after mpm_step_adjoint: lam[lam0] is the adjoint of the initial state, in order lam_id
     int lam0 = -1;
+    // 3D single precision: scatter coefficients and, per sort generation of the segment
+    // being reversed, its sort tables (tiles, count, position map, cell offsets)
+    void *coef = nullptr;
+    int gen_cap = 0;
+    int4 *gen_tiles = nullptr;
+    int32_t *gen_ntiles = nullptr, *gen_posmap = nullptr, *gen_celloff = nullptr;
 };
 
 // One saved copy of the particle state on the device.
@@ -81,6 +87,7 @@ struct mpm_ctx {
     AdjHost adj;
     const AdjOps *aops = nullptr;
     StateSlot slots[kMaxSlots];
+    int64_t adj_budget = 0;            // device bytes the adjoint may use to keep more than one segment
 };
 
 namespace {
@@ -139,6 +146,8 @@ void free_adjoint(mpm_ctx *c)
     for (int w = 0; w < kMaxWalls; ++w) dfree(a.d_mubar[w]);
     dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
     dfree(a.d_mboxes); dfree(a.d_msums); dfree(a.d_mg);
+    dfree(a.coef); dfree(a.gen_tiles); dfree(a.gen_ntiles); dfree(a.gen_posmap); dfree(a.gen_celloff);
+    a.gen_cap = 0;
     a.ckpt_cap = a.seg_cap = 0;
     a.allocated = false;
     a.n_track = a.n_obs = 0;
@@ -845,6 +854,13 @@ int mpm_monitor_means(mpm_ctx *c, int n_mon, const double *boxes, double *out)
     return MPM_OK;
 }
 
+int mpm_set_adjoint_memory(mpm_ctx *c, int64_t bytes)
+{
+    if (!c || bytes < 0) return fail(c, MPM_EINVAL, "mpm_set_adjoint_memory: bad argument");
+    c->adj_budget = bytes;
+    return MPM_OK;
+}
+
 int mpm_get_initial_adjoint(mpm_ctx *c, int field, double *out)
 {
     if (!c || !out) return fail(c, MPM_EINVAL, "mpm_get_initial_adjoint: bad argument");
@@ -895,6 +911,21 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     const int64_t n = h.n;
     const size_t st_bytes = (size_t)NA * n * rsz;
     const int64_t n_ckpt = (n_steps + K - 1) / K;
+    const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+    const size_t fbytes = ((size_t)(h.node_tiles_per_sim + 1) * sizeof(int32_t) + 255) / 256 * 256;
+    // cell-ordered v_bar scatter (3D single precision): coefficients and sort tables
+    // for every sort generation a segment can hold
+    const bool split = d == 3 && h.precision == MPM_FP32;
+    const int gens_seg = std::min(K, K / std::max(1, c->grid.sort_every) + 2);
+    const int64_t TNc = 512 + 1;
+    const size_t gen_bytes = split ? (size_t)ds.max_tiles * (sizeof(int4) + TNc * 4) + (size_t)n * 4 + 4 : 0;
+    // segments kept from the first pass: the last one always; more while the budget
+    // set by mpm_set_adjoint_memory allows (those need no recomputation)
+    const size_t seg_bytes = (size_t)K * (st_bytes + 2 * gbytes + fbytes + (size_t)n * 4) + gens_seg * gen_bytes;
+    int64_t m_keep = 1 + (int64_t)(c->adj_budget > 0 ? c->adj_budget / (int64_t)seg_bytes : 0);
+    if (m_keep > n_ckpt) m_keep = n_ckpt;
+    const int64_t KS = m_keep * K;                 // kept-state slots
+    const int gens = split ? (int)(m_keep * gens_seg) : 0;
     // buffers
     if (a.ckpt_cap < n_ckpt) {
         dfree(a.ckpt);
@@ -902,23 +933,31 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         if (rc != MPM_OK) return rc;
         a.ckpt_cap = n_ckpt;
     }
-    if (a.seg_cap < K) {
+    if (a.seg_cap < KS) {
         dfree(a.seg);
         dfree(a.seg_id);
-        int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * K, "segment states");
-        if (rc == MPM_OK) rc = dalloc(c, &a.seg_id, (size_t)n * K, "segment orders");
+        int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * KS, "segment states");
+        if (rc == MPM_OK) rc = dalloc(c, &a.seg_id, (size_t)n * KS, "segment orders");
         if (rc != MPM_OK) return rc;
-        a.seg_cap = K;
+        a.seg_cap = KS;
     }
-    const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
-    const size_t fbytes = ((size_t)(h.node_tiles_per_sim + 1) * sizeof(int32_t) + 255) / 256 * 256;
-    if (a.seg_grid_cap < K) {
+    if (a.seg_grid_cap < KS) {
         dfree(a.seg_grid);
-        int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * K, "segment grids");
+        int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * KS, "segment grids");
         if (rc != MPM_OK) return rc;
         // nodes a step does not touch keep finite values from earlier steps (never read)
-        CK(cudaMemsetAsync(a.seg_grid, 0, (2 * gbytes + fbytes) * K, ds.stream), "zero segment grids");
-        a.seg_grid_cap = K;
+        CK(cudaMemsetAsync(a.seg_grid, 0, (2 * gbytes + fbytes) * KS, ds.stream), "zero segment grids");
+        a.seg_grid_cap = KS;
+    }
+    if (split && a.gen_cap < gens) {
+        dfree(a.coef); dfree(a.gen_tiles); dfree(a.gen_ntiles); dfree(a.gen_posmap); dfree(a.gen_celloff);
+        int rc = dalloc(c, (unsigned char **)&a.coef, (size_t)21 * n * rsz, "scatter coefficients");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_tiles, (size_t)gens * ds.max_tiles, "generation tiles");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_ntiles, (size_t)gens, "generation tile counts");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_posmap, (size_t)gens * n, "generation position maps");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_celloff, (size_t)gens * ds.max_tiles * TNc, "generation offsets");
+        if (rc != MPM_OK) return rc;
+        a.gen_cap = gens;
     }
     if (!a.allocated) {
         int rc = MPM_OK;
@@ -956,9 +995,13 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     auto seg_ptr = [&](int64_t j) { return (void *)((char *)a.seg + j * st_bytes); };
     auto gridA_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + 2 * j * gbytes); };
     auto gridV_ptr = [&](int64_t j) { return (void *)((char *)a.seg_grid + (2 * j + 1) * gbytes); };
-    auto gridL_ptr = [&](int64_t j) { return (int32_t *)((char *)a.seg_grid + 2 * K * gbytes + j * fbytes); };
-    std::vector<int64_t> seg_gen(K);
-    std::vector<int> seg_ids(K);                // which slot of seg_id holds the order of state j
+    auto gridL_ptr = [&](int64_t j) { return (int32_t *)((char *)a.seg_grid + 2 * KS * gbytes + j * fbytes); };
+    // kept states live in slots: the last m_keep segments of the first pass in blocks
+    // of K (segment n_ckpt - m_keep + b in block b), recomputed segments in block 0
+    std::vector<int64_t> seg_gen(KS);
+    std::vector<int> seg_ids(KS);               // which slot of seg_id holds the order of state j
+    std::vector<int> seg_tab(KS, -1);           // which generation slot holds the sort tables of state j
+    int next_gen = 0;
     auto seg_id_ptr = [&](int64_t j) { return a.seg_id + (int64_t)seg_ids[j] * n; };
     // state j of a segment: after the step's sort, P2G copies the state it reads and
     // the grid update saves its grid; the order's ids are copied once per sort
@@ -970,10 +1013,26 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         seg_gen[j] = c->sorts;
         if (j > 0 && seg_gen[j] == seg_gen[j - 1]) {
             seg_ids[j] = seg_ids[j - 1];
+            seg_tab[j] = seg_tab[j - 1];
         } else {
             seg_ids[j] = j;
             CK(cudaMemcpyAsync(a.seg_id + (int64_t)j * n, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
                                ds.stream), "segment order");
+            if (j == 0) next_gen = 0;
+            seg_tab[j] = -1;
+            if (split && next_gen < a.gen_cap) {       // the sort tables of this generation
+                const int g = next_gen++;
+                seg_tab[j] = g;
+                CK(cudaMemcpyAsync(a.gen_tiles + (int64_t)g * ds.max_tiles, ds.tiles, sizeof(int4) * ds.max_tiles,
+                                   cudaMemcpyDeviceToDevice, ds.stream), "generation tiles");
+                CK(cudaMemcpyAsync(a.gen_ntiles + g, ds.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                   ds.stream), "generation tile count");
+                CK(cudaMemcpyAsync(a.gen_posmap + (int64_t)g * n, ds.posmap, sizeof(int32_t) * n,
+                                   cudaMemcpyDeviceToDevice, ds.stream), "generation position map");
+                CK(cudaMemcpyAsync(a.gen_celloff + (int64_t)g * ds.max_tiles * TNc, ds.cell_off,
+                                   sizeof(int32_t) * ds.max_tiles * TNc, cudaMemcpyDeviceToDevice, ds.stream),
+                   "generation offsets");
+            }
         }
         ds.save_S = seg_ptr(j);
         ds.save_A = gridA_ptr(j);
@@ -989,7 +1048,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     const size_t obs_stride = (size_t)a.n_track * d;
     // forward pass with checkpoints and observations; the last segment's states
     // and grids are kept on the way (its reverse needs no recompute)
-    const int64_t last_t0 = (n_ckpt - 1) * K;
+    const int64_t first_kept = n_ckpt - m_keep;         // segments from here on are kept by the first pass
+    const int64_t last_t0 = first_kept * K;
     c->aops->save(h, ds, ckpt_ptr(0));
     for (int t = 1; t <= n_steps; ++t) {
         if (t - 1 >= last_t0) {
@@ -1005,7 +1065,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
             c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, h.npad, a.n_mon,
                                  a.d_mboxes, a.d_msums + mobs_of_step[t] * msum_stride);
         }
-        if (t % K == 0 && t < n_steps) c->aops->save(h, ds, ckpt_ptr(t / K));
+        if (t % K == 0 && t / K < first_kept) c->aops->save(h, ds, ckpt_ptr(t / K));   // recomputed later
     }
     CK(cudaMemcpyAsync(a.final_S, ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, cudaMemcpyDeviceToDevice, ds.stream),
        "save final state");
@@ -1061,7 +1121,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     }
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
-        if (k < n_ckpt - 1) {                          // recompute the segment from its checkpoint
+        const int base = k >= first_kept ? (int)((k - first_kept) * K) : 0;
+        if (k < first_kept) {                          // recompute the segment from its checkpoint
             c->aops->restore(h, ds, ckpt_ptr(k));
             c->need_sort = true;
             for (int j = 0; j < t1 - t0; ++j) {
@@ -1072,7 +1133,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
             }
         }
         for (int t = t1 - 1; t >= t0; --t) {
-            const int j = t - t0;
+            const int j = base + t - t0;               // the kept state's slot
             if (seg_gen[j] != lam_gen) {             // a sort between the two states: re-order
                 c->aops->reorder(h, ds, NA, a.lam_id, a.lam_pos, seg_id_ptr(j), a.lam[cur], a.lam[cur ^ 1]);
                 cur ^= 1;
@@ -1080,7 +1141,17 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                                    ds.stream), "adjoint order");
                 lam_gen = seg_gen[j];
             }
-            c->aops->step(h, ds, a.grid, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
+            AdjDev ad = a.grid;
+            if (seg_tab[j] >= 0) {
+                const int g = seg_tab[j];
+                ad.coef = a.coef;
+                ad.cursor = ds.counters + 5;
+                ad.tiles = a.gen_tiles + (int64_t)g * ds.max_tiles;
+                ad.n_tiles = a.gen_ntiles + g;
+                ad.posmap = a.gen_posmap + (int64_t)g * n;
+                ad.cell_off = a.gen_celloff + (int64_t)g * ds.max_tiles * TNc;
+            }
+            c->aops->step(h, ds, ad, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
                           a.lam[cur ^ 1], mub);
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {

@@ -634,9 +634,67 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
 }
 
+// Where k_p2g_direct takes its particles and writes its sums.  Forward P2G (MAT
+// = 0 fluid, 1 Drucker-Prager): the state S (stride ld = npad), the current sort
+// tables and cursor counters[2], sums into A, node tiles marked.  The adjoint's
+// v_bar scatter (MAT = 2): positions from a kept state (stride ld = n) and the
+// 21 scatter coefficients per particle from src2 (v_bar_t, C_bar, L_bar), the
+// sort tables of that state's generation and its own cursor, sums into the grid
+// adjoint, no marks.
+template <class R> struct P2GIO {
+    const R *S;                       // x (and for P2G the other inputs): component c at S[c ld + slot]
+    const R *src2;                    // MAT 2: 21 coefficients, component c at src2[c ld + slot]
+    int64_t ld;
+    const int4 *tiles;                // compact tiles in key order
+    const int32_t *n_tiles;           // their count
+    int32_t *cursor;                  // work-item cursor (zero at launch)
+    const int32_t *posmap, *cell_off;
+    R4<R> *A;                         // sums (per simulation: A + sim * nodes_per_sim)
+    uint32_t *flags;                  // node tile flags (MAT 0, 1)
+};
+
+// P2G factors of one particle of the adjoint's v_bar scatter (Eq. dzda reversed
+// through G2P): the node value v_bar_k = w_k (v_bar_t + (4 / dx) C_bar (k - fx))
+// + L_bar grad w_k is P2G's momentum with mass 1, velocity v_bar_t, affine
+// matrix (4 / dx^2) C_bar and stress coefficient L_bar.
+template <class R, class Raw>
+__device__ __forceinline__ void adj_scatter_factors(const Params<R> &P, Raw raw, P2GFactors<R, 3> &f)
+{
+    constexpr int D = 3;
+    R x[D], fx[D], dw[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = raw(a);
+        f.b[a] = base_cell(x[a], P.inv_dx, P.n_cells[a]);
+        fx[a] = x[a] * P.inv_dx - R(f.b[a]);
+        bspline(fx[a], P.inv_dx, f.w[a], dw[a]);
+    }
+    const R cs = R(4) * P.inv_dx;                 // C_bar (k - fx) enters as (4 / dx) C_bar (k - fx)
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R u0 = raw(3 + a);
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) u0 -= cs * raw(6 + a * D + c2) * fx[c2];
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) {
+            const R mc = cs * raw(6 + a * D + b2);
+            const R lb = raw(15 + a * D + b2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                R e = mc * R(j) * f.w[b2][j] + lb * dw[b2][j];
+                if (b2 == 0) e += u0 * f.w[0][j];
+                f.E[a][b2][j] = e;
+            }
+        }
+    }
+}
+
 // A particle that left its sort cell, scattered on its own to the grid (27 vector
-// atomics) with its node tiles marked.  Kept out of line: the path is rare and
-// its registers would otherwise count against the accumulating loop.
+// atomics), with its node tiles marked when fsim is set.  Kept out of line: the
+// path is rare and its registers would otherwise count against the accumulating
+// loop.
+// Node values are stored (m, q) for P2G; with fsim == nullptr (the adjoint's v_bar
+// scatter, no mass channel) as (q, 0), the grid adjoint's layout.
 template <class R>
 __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> &f, R mass, R4<R> *Asim, int Gx, int Gy,
                                          uint32_t *fsim, int32_t *list, int32_t *count, int ntx, int nty)
@@ -646,53 +704,60 @@ __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> &f, R mass, R4<R
         R m, mom[3];
         p2g_node<R, 3>(f, mass, k0, k1, k2, m, mom);
         const int a0 = f.b[0] + 2 + k0, a1 = f.b[1] + 2 + k1, a2 = f.b[2] + 2 + k2;
-        red_add4(&Asim[((int64_t)a2 * Gy + a1) * Gx + a0], m, mom[0], mom[1], mom[2]);
-        const int u0 = a0 / Geo<3>::T, u1 = a1 / Geo<3>::T, u2 = a2 / Geo<3>::T;
-        mark_node_tile(fsim, list, count, ((int64_t)u2 * nty + u1) * ntx + u0);
+        R4<R> *node = &Asim[((int64_t)a2 * Gy + a1) * Gx + a0];
+        if (fsim != nullptr) red_add4(node, m, mom[0], mom[1], mom[2]);
+        else red_add4(node, mom[0], mom[1], mom[2], R(0));
+        if (fsim != nullptr) {
+            const int u0 = a0 / Geo<3>::T, u1 = a1 / Geo<3>::T, u2 = a2 / Geo<3>::T;
+            mark_node_tile(fsim, list, count, ((int64_t)u2 * nty + u1) * ntx + u0);
+        }
     }
 }
+
+// Components staged per particle by k_p2g_direct: P2G's inputs (MAT 0, 1), or x
+// and the 21 scatter coefficients (MAT 2).
+template <int MAT> __host__ __device__ constexpr int direct_stage_comps() { return MAT == 2 ? 24 : kP2GStageComps<3>; }
 
 // P2G without a shared-memory window (3D, register accumulation).  Warps claim
 // work items of 128 cells (two layer groups of a tile) from a global cursor and
 // never synchronise with each other: lane l walks cells base + l, + 32, + 64,
-// + 96 through the same two-stage cp.async pipeline as k_p2g, sums the
-// particles still in their cell in registers and adds the 27 node sums of a
-// cell straight to the grid with vector atomics (27 per cell instead of 108
-// shared-memory atomics plus the window pass); particles that left their cell
-// are scattered on their own to the grid.  The warp marks the node tiles its
-// cells reach.
+// + 96 through a two-stage cp.async pipeline, sums the particles still in their
+// cell in registers and adds the 27 node sums of a cell straight to the grid
+// with vector atomics (27 per cell instead of 108 shared-memory atomics plus the
+// window pass); particles that left their cell are scattered on their own.  The
+// warp marks the node tiles its cells reach.
 #ifndef MPM_P2G_DIRECT
 #define MPM_P2G_DIRECT 1
 #endif
 template <class R, int NT, int MAT>
 __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
-    k_p2g_direct(const Params<R> P, const R *__restrict__ S, const int4 *__restrict__ tiles,
-                 int32_t *__restrict__ counters, const int32_t *__restrict__ posmap,
-                 const int32_t *__restrict__ cell_off, R4<R> *__restrict__ A, uint32_t *__restrict__ flags,
-                 unsigned long long *__restrict__ escaped_count)
+    k_p2g_direct(const Params<R> P, const P2GIO<R> io, unsigned long long *__restrict__ escaped_count,
+                 int32_t *__restrict__ g2p_cursor)
 {
     constexpr int D = 3;
     using Gm = Geo<D>;
-    constexpr int NCM = kP2GStageComps<D>;
+    constexpr bool ADJ = MAT == 2;
+    constexpr int NCM = direct_stage_comps<MAT>();
     constexpr int NXC = 2 * D + D * D;
-    constexpr int NC = p2g_ncomp<D>(MAT);
+    constexpr int NC = ADJ ? 24 : p2g_ncomp<D>(MAT);
     constexpr int OFF_RHO = 2 * D + 2 * D * D;
     constexpr int CELLS = 128;                       // cells per work item
     constexpr int ITEMS = Gm::TN / CELLS;            // work items per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *stg = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int n_items = counters[1] * ITEMS;
-    const int64_t npad = P.npad;
+    const int n_items = *io.n_tiles * ITEMS;
+    const int64_t ld = io.ld;
+    const R mass = ADJ ? R(0) : P.mass;
     bool any_escape = false;
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(&counters[2], 1);
+        if (lane == 0) item = atomicAdd(io.cursor, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int k = item / ITEMS;
         const int cbase = (item - k * ITEMS) * CELLS;
-        const int4 t = tiles[k];
+        const int4 t = io.tiles[k];
         const int sim = (int)(t.x / P.tiles_per_sim);
         int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
         int org[3];
@@ -701,19 +766,27 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
             org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
             tl /= P.n_tiles[a];
         }
-        R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
-        uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
-        const int32_t *pmap = posmap + t.y;
-        const int32_t *off = cell_off + (int64_t)k * (Gm::TN + 1);
-        const R *St = S + t.y;
-        R *const Sv = P.save_S == nullptr ? nullptr : P.save_S + t.y;
+        R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
+        uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
+        const int32_t *pmap = io.posmap + t.y;
+        const int32_t *off = io.cell_off + (int64_t)k * (Gm::TN + 1);
+        const R *St = io.S + t.y;
+        const R *S2 = ADJ ? io.src2 + t.y : nullptr;
+        R *const Sv = (ADJ || P.save_S == nullptr) ? nullptr : P.save_S + t.y;
         auto issue = [&](int stage, int32_t pos) {
             R *dst = stg + stage * NCM * NT + tid;
-            const R *src = St + pos;
+            if constexpr (ADJ) {
 #pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
-                cp_async_elem(dst + j * NT, src + comp * npad);
+                for (int j = 0; j < 3; ++j) cp_async_elem(dst + j * NT, St + pos + j * ld);
+#pragma unroll
+                for (int j = 0; j < 21; ++j) cp_async_elem(dst + (3 + j) * NT, S2 + pos + j * ld);
+            } else {
+                const R *src = St + pos;
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
+                    cp_async_elem(dst + j * NT, src + comp * ld);
+                }
             }
         };
         // cursors over this lane's cells cbase + lane + 32 r and their slots
@@ -770,12 +843,16 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
             P2GFactors<R, D> f;
             {
                 const R *src = stg + stage * NCM * NT + tid;
-                if (Sv != nullptr) {                   // the adjoint's copy of this step's state
-                    R *d = Sv + pmap[cc.q];
+                if constexpr (ADJ) {
+                    adj_scatter_factors<R>(P, [&](int j) { return src[j * NT]; }, f);
+                } else {
+                    if (Sv != nullptr) {               // the adjoint's copy of this step's state
+                        R *d = Sv + pmap[cc.q];
 #pragma unroll
-                    for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
+                        for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
+                    }
+                    p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
                 }
-                p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
             }
             if (hp) issue(stage, ppos);
             cp_async_commit();
@@ -785,10 +862,10 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
 #pragma unroll
             for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
             if (own) {
-                p2g_accumulate<R, D>(f, P.mass, acc);
+                p2g_accumulate<R, D>(f, mass, acc);
             } else {                                   // left its cell since the sort: on its own
                 any_escape = true;
-                p2g_escape3<R>(f, P.mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
+                p2g_escape3<R>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
                                P.node_tiles[0], P.node_tiles[1]);
             }
             stage ^= 1;
@@ -797,24 +874,30 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
                 const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
                 R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];
 #pragma unroll
-                for (int kk = 0; kk < Gm::STENCIL; ++kk)
-                    red_add4(base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy, acc[kk][0], acc[kk][1],
-                             acc[kk][2], acc[kk][3]);
+                for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+                    R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
+                    if constexpr (ADJ) red_add4(node, acc[kk][1], acc[kk][2], acc[kk][3], R(0));   // (v_bar, 0)
+                    else red_add4(node, acc[kk][0], acc[kk][1], acc[kk][2], acc[kk][3]);          // (m, q)
+                }
             }
         }
         cp_async_wait<0>();
-        // node tiles reached by the warp's cells (those holding particles)
-        const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
-        if (lane < 8 && ((wreach >> lane) & 1u)) {
-            int u[3];
+        if constexpr (!ADJ) {                          // node tiles reached by the warp's cells
+            const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
+            if (lane < 8 && ((wreach >> lane) & 1u)) {
+                int u[3];
 #pragma unroll
-            for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
-            mark_node_tile(flags, P.node_list, P.list_count, (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
+                for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
+                mark_node_tile(io.flags, P.node_list, P.list_count,
+                               (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
+            }
         }
     }
-    const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
-    if (ball && lane == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
-    if (threadIdx.x == 0) counters[3] = 0;         // G2P cursor for the next kernel (G2P follows)
+    if (escaped_count != nullptr) {
+        const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
+        if (ball && lane == 0) atomicAdd(escaped_count, (unsigned long long)__popc(ball));
+    }
+    if (g2p_cursor != nullptr && threadIdx.x == 0) *g2p_cursor = 0;   // G2P cursor for the next kernel
 }
 
 // ------------------------------------------------------------------ grid update
@@ -1578,18 +1661,18 @@ template <class R, int D> struct Launch {
         auto P = make_params<R>(h, ds);
         if constexpr (D == 3 && sizeof(R) == 4 && MPM_P2G_DIRECT) {
             constexpr int NT = kP2GThreads;
-            const size_t smem = (size_t)2 * kP2GStageComps<3> * NT * sizeof(R);
+            const size_t smem = (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R);
             const int nb = ds.num_sms * MPM_P2G_MINB;
-            k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, (const R *)ds.S, ds.tiles, ds.counters, ds.posmap,
-                                                                  ds.cell_off, (R4<R> *)ds.A, ds.flags, ds.escaped);
+            P2GIO<R> io{(const R *)ds.S, nullptr, h.npad, ds.tiles, ds.counters + 1, ds.counters + 2,
+                        ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags};
+            k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, io, ds.escaped, ds.counters + 3);
             if (h.transfer == 3) {                   // FLIP: the momenta without forces, for v_i^n
                 auto P2 = P;
                 P2.no_force = 1;
                 P2.save_S = nullptr;
                 cudaMemsetAsync(ds.counters + 2, 0, sizeof(int32_t), ds.stream);
-                k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P2, (const R *)ds.S, ds.tiles, ds.counters,
-                                                                      ds.posmap, ds.cell_off, (R4<R> *)ds.A2,
-                                                                      ds.flags, ds.escaped);
+                io.A = (R4<R> *)ds.A2;
+                k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P2, io, ds.escaped, ds.counters + 3);
             }
             return;
         }

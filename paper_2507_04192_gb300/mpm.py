@@ -81,6 +81,7 @@ def load_library(build_if_missing: bool = True):
             "mpm_set_velocity_monitors": (I, [P, I, P, I, P, P]),
             "mpm_get_initial_adjoint": (I, [P, I, P]),
             "mpm_monitor_means": (I, [P, I, P, P]),
+            "mpm_set_adjoint_memory": (I, [P, C.c_int64]),
             "mpm_step": (I, [P, I]),
             "mpm_synchronize": (I, [P]),
             "mpm_get_particles": (I, [P, I, P]),
@@ -279,6 +280,11 @@ def mpm_step_adjoint(ctx, n_steps: int, checkpoint_every: int, wall: int, n_mu: 
     _check(ctx, load_library().mpm_step_adjoint(ctx, int(n_steps), int(checkpoint_every), int(wall),
                                                 C.byref(loss), _dptr(g) if wall >= 0 else None))
     return loss.value, g
+
+
+def mpm_set_adjoint_memory(ctx, nbytes: int):
+    """Device bytes the adjoint may spend keeping more first-pass segments (0: recompute all but the last)."""
+    _check(ctx, load_library().mpm_set_adjoint_memory(ctx, int(nbytes)))
 
 
 def mpm_get_initial_adjoint(ctx, field: str) -> np.ndarray:

@@ -67,9 +67,10 @@ def oracle_grad(c, mu, z):
     return loss, grad
 
 
-def gpu_grad(c, mu, z, precision=mpm.MPM_FP64, K=50, sort_every=8):
+def gpu_grad(c, mu, z, precision=mpm.MPM_FP64, K=50, sort_every=8, keep_bytes=0):
     sim = mpm.Simulation(c["dim"], c["cells"], c["dx"], c["dt"], c["g"], dict(inputs.SAND_DP), precision, sort_every)
     sim.load(c["x"], None, c["vol"])
+    mpm.mpm_set_adjoint_memory(sim.ctx, keep_bytes)
     sim.set_friction(c["wall"], c["nseg"], mu)
     mpm.mpm_set_observations(sim.ctx, c["ids"], c["obs"], z)
     loss, grad = mpm.mpm_step_adjoint(sim.ctx, max(c["obs"]), K, c["wall"], len(mu))
@@ -122,3 +123,32 @@ def test_sand_checkpoint_interval_does_not_change_the_gradient(problem):
         loss, grad = gpu_grad(c, mu, z, K=K, sort_every=se)
         assert loss == pytest.approx(ref[0], rel=1e-11)
         np.testing.assert_allclose(grad, ref[1], rtol=0, atol=1e-9 * np.abs(ref[1]).max())
+
+
+@pytest.mark.parametrize("K,se", [(50, 8), (7, 3), (1, 1)])
+def test_sand_3d_fp32_adjoint_matches_fp64_on_a_short_horizon(K, se):
+    # Single precision runs the v_bar scatter as a cell-ordered pass over the sort
+    # tables of each kept state's generation; on a short horizon it must follow the
+    # double-precision gradient to FP32 rounding, whatever the checkpoint and sort
+    # intervals (which change the generations a segment holds).
+    c = column_3d(steps=60)
+    z = truth(c) + 2e-3                       # residuals well above FP32 position rounding
+    mu = np.full(4, 0.35)
+    l64, g64 = gpu_grad(c, mu, z)
+    l32, g32 = gpu_grad(c, mu, z, mpm.MPM_FP32, K=K, sort_every=se)
+    assert np.abs(g64).max() > 0
+    assert l32 == pytest.approx(l64, rel=1e-3)
+    assert np.linalg.norm(g32 - g64) <= 1e-3 * np.linalg.norm(g64)
+
+
+@pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_FP32])
+def test_kept_segments_give_the_recomputed_gradient(problem, precision):
+    # with memory to keep every segment of the first pass nothing is recomputed;
+    # the gradient is the one of the checkpoint-and-recompute sweep
+    c, z, mu, _ = problem
+    ref = gpu_grad(c, mu, z, precision, K=50)
+    for keep in (1 << 20, 1 << 40):                  # a few segments / all of them
+        loss, grad = gpu_grad(c, mu, z, precision, K=50, keep_bytes=keep)
+        tol = 1e-9 if precision == mpm.MPM_FP64 else 1e-4
+        assert loss == pytest.approx(ref[0], rel=tol)
+        assert np.linalg.norm(grad - ref[1]) <= tol * np.linalg.norm(ref[1])
