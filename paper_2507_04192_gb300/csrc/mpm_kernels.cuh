@@ -692,11 +692,13 @@ __device__ __forceinline__ void adj_scatter_factors(const Params<R> &P, Raw raw,
 // A particle that left its sort cell, scattered on its own to the grid (27 vector
 // atomics), with its node tiles marked when fsim is set.  Kept out of line: the
 // path is rare and its registers would otherwise count against the accumulating
-// loop.
+// loop.  The factors go by value: a reference kept them in local memory for every
+// particle (P2G 0.166 -> 0.145 ms on the 2.76M-particle collapse by value; having
+// the callee recompute them from the staged slots measured 0.188 ms).
 // Node values are stored (m, q) for P2G; with fsim == nullptr (the adjoint's v_bar
 // scatter, no mass channel) as (q, 0), the grid adjoint's layout.
 template <class R>
-__device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> &f, R mass, R4<R> *Asim, int Gx, int Gy,
+__device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R> *Asim, int Gx, int Gy,
                                          uint32_t *fsim, int32_t *list, int32_t *count, int ntx, int nty)
 {
     for (int kk = 0; kk < 27; ++kk) {
