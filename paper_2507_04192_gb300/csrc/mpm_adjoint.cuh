@@ -35,6 +35,10 @@
 #ifndef MPM_ADJ3_MINB
 #define MPM_ADJ3_MINB 2
 #endif
+// Resident blocks per SM of the 3D P2G adjoint in single precision.
+#ifndef MPM_ADJ3P_MINB
+#define MPM_ADJ3P_MINB 2
+#endif
 
 namespace mpm {
 
@@ -1105,7 +1109,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
 // 3D adjoint of P2G (same outputs as k_adj_p2g_bwd) from stencil moments of the
 // grid adjoint (P_bar as the three-component field, m_bar as the scalar one).
 template <class R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3P_MINB : 1)
     k_adj_p2g_bwd3(const Params<R> P, const R *__restrict__ st, const R4<R> *__restrict__ GAB,
                    R *__restrict__ lam_out)
 {
