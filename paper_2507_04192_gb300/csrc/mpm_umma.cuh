@@ -58,6 +58,10 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
 #ifndef MPM_UMMA_WIDE_STAGES
 #define MPM_UMMA_WIDE_STAGES 4
 #endif
+// The 128 x 256 path as a persistent kernel with a double-buffered accumulator.
+#ifndef MPM_UMMA_PERSIST
+#define MPM_UMMA_PERSIST 1
+#endif
 enum UmmaEpilogue { kEpiStore = 0, kEpiBiasGelu = 1, kEpiBiasSigmoid = 2 };
 
 struct UmmaEpi {
@@ -231,6 +235,212 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                      : "memory");
 }
 
+// Epilogue of one 8-column chunk of a row: C (and the fused GELU / sigmoid outputs).
+__device__ __forceinline__ void umma_store8(const uint32_t r[8], int row, int col0, int N, float *Cout, int ldc,
+                                            const UmmaEpi &epi)
+{
+    const int64_t o0 = (int64_t)row * ldc + col0;
+    if (epi.mode == kEpiStore && col0 + 8 <= N && (ldc & 3) == 0) {     // two 16-byte stores
+        float4 *d = reinterpret_cast<float4 *>(Cout + o0);
+        d[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+        d[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int col = col0 + e;
+        if (col >= N) continue;
+        float z = __uint_as_float(r[e]);
+        const int64_t o = o0 + e;
+        if (epi.mode != kEpiStore) z += epi.bias[col];
+        Cout[o] = z;
+        if (epi.mode == kEpiBiasGelu) epi.xnext[o] = __float2bfloat16_rn(umma_gelu(z));
+        else if (epi.mode == kEpiBiasSigmoid) epi.y[o] = epi.lo + (epi.hi - epi.lo) / (1.0f + expf(-z));
+    }
+}
+
+// Persistent, warp-specialised form for large problems: one CTA per SM walks the
+// 128 x 256 tiles (M fastest within bands of 8 N-tiles, so that consecutive
+// tiles of the SMs share their B tiles in L2).  Warp 0 produces (TMA into the
+// ring of stages), warp 1 issues the MMAs, warps 2-5 run the epilogue; the fp32
+// accumulator is double-buffered in TMEM (2 x 256 of the 512 columns), so the
+// epilogue of one tile overlaps the main loop of the next.  Every wait is
+// bounded; a timeout sets the status word and every role leaves.
+constexpr int kUmmaPersistThreads = 192;
+template <int STAGES>
+__global__ void __launch_bounds__(kUmmaPersistThreads, 1)
+    k_umma_gemm_persist(int M, int N, int K, const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, float *__restrict__ Cout, int ldc, UmmaEpi epi,
+                        int32_t *__restrict__ status)
+{
+    constexpr int NT = 256;
+    constexpr uint32_t A_BYTES = kUmmaM * kUmmaKC * 2, B_BYTES = NT * kUmmaKC * 2;
+    constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *sbase = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                             ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nk = (K + kUmmaKC - 1) / kUmmaKC;
+    const int tm = (M + kUmmaM - 1) / kUmmaM, tn = (N + NT - 1) / NT;
+    const int n_tiles = tm * tn;
+    constexpr int BAND = 8;                              // N-tiles per band
+    auto tile_coords = [&](int t, int &m0, int &n0) {
+        const int band = t / (BAND * tm);
+        const int r = t - band * BAND * tm;
+        const int bw = min(BAND, tn - band * BAND);
+        m0 = (r / bw) * kUmmaM;
+        n0 = (band * BAND + r % bw) * NT;
+    };
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         umma_smem_u32(&tmem_base)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&empty[s])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&acc_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(umma_smem_u32(&acc_empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma_smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {                                     // producer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < n_tiles && !failed; t += gridDim.x) {
+                int m0, n0;
+                tile_coords(t, m0, n0);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!umma_wait_parity(&empty[s], ph ^ 1u)) {
+                        failed = 1;
+                        break;
+                    }
+                    const uint32_t sa = umma_smem_u32(sbase + s * STAGE), sb = sa + A_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     umma_smem_u32(&full[s])),
+                                 "r"(STAGE)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3}], [%4];" ::"r"(sa),
+                                 "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kc * kUmmaKC), "r"(m0),
+                                 "r"(umma_smem_u32(&full[s]))
+                                 : "memory");
+                    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3}], [%4];" ::"r"(sb),
+                                 "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kc * kUmmaKC), "r"(n0),
+                                 "r"(umma_smem_u32(&full[s]))
+                                 : "memory");
+                }
+            }
+        }
+    } else if (warp == 1) {                              // MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16(kUmmaM, NT);
+            int it = 0, lt = 0;
+            for (int t = blockIdx.x; t < n_tiles && !failed; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (!umma_wait_parity(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u)) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_addr = tmem + (uint32_t)(b * NT);
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!umma_wait_parity(&full[s], ph)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = umma_smem_u32(sbase + s * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < kUmmaKC / 16; ++kk) {
+                        const uint64_t da = umma_desc_sw128(sa + kk * 32), db = umma_desc_sw128(sb + kk * 32);
+                        const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+                                     "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                                     : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     umma_smem_u32(&empty[s]))
+                                 : "memory");
+                }
+                if (!ok) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 umma_smem_u32(&acc_full[b]))
+                             : "memory");
+            }
+            // every MMA this thread issued has completed before TMEM is released
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             umma_smem_u32(&done))
+                         : "memory");
+            if (!umma_wait_parity(&done, 0u)) failed = 1;
+        }
+    } else {                                             // epilogue: warps 2-5, TMEM lane quarter warp % 4
+        const int q = warp & 3;
+        int lt = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            bool ok = false;
+            if (lane == 0) ok = umma_wait_parity(&acc_full[b], (uint32_t)(lt >> 1) & 1u);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) failed = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int m0, n0;
+            tile_coords(t, m0, n0);
+            const int row = m0 + q * 32 + lane;
+            for (int c0 = 0; c0 < NT; c0 += 8) {
+                uint32_t r[8];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                               "=r"(r[6]), "=r"(r[7])
+                             : "r"(taddr)
+                             : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M && n0 + c0 < N) umma_store8(r, row, n0 + c0, N, Cout, ldc, epi);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)                               // this quarter of the accumulator is free again
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma_smem_u32(&acc_empty[b]))
+                             : "memory");
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (failed && tid == 0) atomicOr(status, (int32_t)kStatusTimeout);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
 template <int NT, int STAGES> constexpr size_t umma_tma_smem_bytes()
 {
     return (size_t)STAGES * (kUmmaM + NT) * kUmmaKC * 2 + 1024;
@@ -291,6 +501,19 @@ inline cudaError_t umma_gemm_tma(int M, int N, int K, const __nv_bfloat16 *A, in
     if (!umma_tensor_map(&tmA, A, M, K, lda, kUmmaM) || !umma_tensor_map(&tmB, B, N, K, ldb, NT))
         return cudaErrorInvalidValue;
     if (NT == 32) return umma_launch<32, 4>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
+    if (NT == 256 && MPM_UMMA_PERSIST) {
+        constexpr size_t smem = umma_tma_smem_bytes<256, MPM_UMMA_WIDE_STAGES>();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_umma_gemm_persist<MPM_UMMA_WIDE_STAGES>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        const int tiles = ((M + kUmmaM - 1) / kUmmaM) * ((N + 255) / 256);
+        k_umma_gemm_persist<MPM_UMMA_WIDE_STAGES><<<std::min(sms, tiles), kUmmaPersistThreads, smem, stream>>>(
+            M, N, K, tmA, tmB, C, ldc, epi, status);
+        return cudaGetLastError();
+    }
     if (NT == 256) return umma_launch<256, MPM_UMMA_WIDE_STAGES>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
     return umma_launch<128, MPM_UMMA_STAGES>(M, N, K, tmA, tmB, C, ldc, epi, status, stream);
 }
