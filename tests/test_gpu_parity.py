@@ -213,3 +213,22 @@ def test_full_size_granular_cylinder_two_steps(precision):
     assert np.abs(gpu["x"] - ref["x"]).max() <= tol * L
     rs = scale(ref["sigma"])
     assert np.abs(gpu["sigma"].reshape(-1, 3, 3) - ref["sigma"]).max() <= (1e-8 if precision else 1e-3) * rs
+
+
+def test_batched_3d_sand_fp32_matches_oracle_per_simulation():
+    # several simulations in one context take the window-free P2G's per-simulation
+    # grid offsets; each must follow its own oracle run
+    base = inputs.granular_cylinder_3d((16, 16, 16), 4, 8, dt=2e-4, dx=1 / 16, floor_mu=0.0, steps=30)
+    mus = [0.1, 0.4, 0.8]
+    B = len(mus)
+    sim = mpm.Simulation(3, base.n_cells, base.dx, base.dt, base.gravity, base.material, mpm.MPM_FP32, 8, batch=B)
+    sim.load(np.concatenate([base.x] * B), None, base.particle_volume,
+             np.repeat(np.arange(B, dtype=np.int32), base.n))
+    sim.set_friction(4, (1, 1), np.array(mus))
+    sim.step(30)
+    xb = sim.get("x").reshape(B, base.n, 3)
+    sim.close()
+    for b, mu in enumerate(mus):
+        w = inputs.granular_cylinder_3d((16, 16, 16), 4, 8, dt=2e-4, dx=1 / 16, floor_mu=mu, steps=30)
+        ref = run_oracle(w, 30)
+        assert np.abs(xb[b] - ref["x"]).max() <= 1e-4
