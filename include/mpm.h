@@ -337,8 +337,8 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  * at most 131072 grid nodes (4 MiB, kept by every GPU that loads the library
  * until the process exits).  Supports dim 2 or 3, MPM_FP64, batch 1, the APIC
  * transfer, slip walls
- * (no friction fields), no sorting; gravity, Tait fluid and Drucker-Prager as
- * in mpm_step.  `out` may alias `in` particle by particle.
+ * (no friction fields, no obstacles), no sorting; gravity, Tait fluid and
+ * Drucker-Prager as in mpm_step.  `out` may alias `in` particle by particle.
  *
  * Rules: the call queues its kernels on cuda_stream (NULL = the legacy default
  * stream) and returns without waiting.  The first call on each device resolves

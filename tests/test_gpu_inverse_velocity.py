@@ -80,3 +80,28 @@ def test_velocity_constant_recovered_from_monitors():
     res = velocity_inverse.invert_alpha(prob, alpha0=0.1, alpha_true=2.0, tol=0.02, max_iters=80)
     prob.close()
     assert res.converged, res.history[-3:]
+
+
+def test_3d_monitors_and_initial_adjoint_match_oracle():
+    # the 3D forms of the monitor kernels and of the initial-state adjoint
+    w = inputs.dam_break_3d((16, 8, 8), dx=1 / 16, dt=2e-4, steps=0, obstacles=False)
+    w.v = np.tile([0.6, 0.1, 0.0], (w.n, 1)) * (1.0 - w.x[:, 2:3] / 0.2)
+    boxes = [((0.05, 0.1, 0.02), (0.2, 0.3, 0.12)), ((0.2, 0.2, 0.0), (0.35, 0.45, 0.1))]
+    obs_steps = [20, 40]
+    w.extras.update(obs_steps=obs_steps, monitors=boxes, track_ids=np.arange(0, w.n, 97, dtype=np.int64))
+    zx, zv = observe(w, w.v * 0.8)
+    ref_loss, ref_g = loss_and_v0_adjoint(w, w.v, zx=zx, zv=zv)
+    loss, g = gpu_loss_and_v0(w, w.v, zx=zx, zv=zv, K=15)
+    assert ref_loss > 0 and np.abs(ref_g).max() > 0
+    assert loss == pytest.approx(ref_loss, rel=1e-9)
+    np.testing.assert_allclose(g, ref_g, rtol=0, atol=1e-6 * np.abs(ref_g).max())
+    sim = mpm.Simulation(3, w.n_cells, w.dx, w.dt, w.gravity, w.material, mpm.MPM_FP64, w.sort_every)
+    sim.load(w.x, w.v, w.particle_volume)
+    sim.step(30)
+    Q, cnt = mpm.mpm_monitor_means(sim.ctx, boxes)
+    x, v = sim.get("x"), sim.get("v")
+    sim.close()
+    Qr, cr = oracle.monitor_means(x, v, boxes)
+    np.testing.assert_array_equal(cnt, cr)
+    assert cnt.min() > 0
+    np.testing.assert_allclose(Q, Qr, rtol=0, atol=1e-12 * max(1.0, np.abs(Qr).max()))

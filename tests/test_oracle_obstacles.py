@@ -161,3 +161,21 @@ def test_one_step_vjp_with_obstacle_contact_matches_central_differences():
     fd = (J(eps) - J(-eps)) / (2 * eps)
     an = sum(float((a * b).sum()) for a, b in zip([xb, vb, Bb, rb], dirs))
     assert an == pytest.approx(fd, rel=1e-5)
+
+
+def test_box_beyond_a_plane_is_a_slip_wall_3d():
+    # the 3D form of the pin above, with the plane normal to y and a z-column box
+    dx = 1.0 / 16
+    def run(n_cells, obstacles):
+        x = inputs.lattice_particles(n_cells, dx, 2, lambda p: (np.abs(p[:, 1] - 5.5 * dx) < 2 * dx)
+                                     & (np.abs(p[:, 0] - 4 * dx) < 2 * dx) & (p[:, 2] < 4 * dx),
+                                     (2 * dx, 3.5 * dx, 0.0), (6 * dx, 7.5 * dx, 4 * dx), 0)
+        orc = oracle.Oracle(3, n_cells, dx, 2e-4, (0.0, 0.0, -9.81), WATER, dx ** 3 / 8, obstacles=obstacles)
+        st = orc.initial_state(x, np.tile([0.0, 1.0, 0.0], (len(x), 1)))
+        orc.step(st, 25)
+        return st
+    a = run((8, 12, 8), [((-1.0, 8 * dx, -1.0), (2.0, 2.0, 2.0))])
+    b = run((8, 8, 8), [])
+    assert a.x[:, 1].max() < 8 * dx and np.abs(b.v[:, 1]).max() > 0.0
+    for f in ("x", "v", "B", "F", "rho"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
