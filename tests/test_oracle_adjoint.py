@@ -75,6 +75,38 @@ def test_one_step_vjp_matches_central_differences_in_the_state():
         assert pair([xb, vb, Bb, rb], sub) == pytest.approx(fdb, rel=1e-5, abs=1e-9 * abs(fd)), f"block {blk}"
 
 
+def test_one_step_vjp_through_the_position_clamp():
+    """Two particles driven through the floor within one step end on it: their
+    new heights no longer depend on the state, and the adjoint must agree with
+    central differences there as well as for the free particles."""
+    N = 16
+    dx = 1.0 / N
+    orc = oracle.Oracle(2, (N, N), dx, 2e-3, (0.0, -9.81), dict(inputs.FLUID_WATER), dx * dx / 4)
+    x = np.array([[0.30, 1e-4], [0.33, 1e-4], [0.50, 0.40], [0.52, 0.41], [0.49, 0.43]])
+    st = orc.initial_state(x, np.array([[0.2, -1.0], [0.1, -1.0], [0.3, 0.1], [-0.2, 0.0], [0.1, -0.1]]))
+    assert (forward(orc, st).x[:2, 1] == 0.0).all()
+    rng = np.random.default_rng(9)
+    n = st.n
+    lam = [rng.normal(size=(n, 2)), rng.normal(size=(n, 2)), rng.normal(size=(n, 2, 2)) / dx ** 2,
+           rng.normal(size=n) * 1e-3]
+    (xb, vb, Bb, rb), _ = orc.step_vjp(st, *lam)
+    dirs = [rng.normal(size=(n, 2)) * dx * 0.01, rng.normal(size=(n, 2)) * 0.01, rng.normal(size=(n, 2, 2)) * dx * dx,
+            rng.normal(size=n) * 0.1]
+    eps = 1e-5
+    for blk in range(4):
+        sub = [d if k == blk else np.zeros_like(d) for k, d in enumerate(dirs)]
+
+        def J(scale):
+            s = st.copy()
+            s.x += scale * sub[0]; s.v += scale * sub[1]; s.B += scale * sub[2]; s.rho += scale * sub[3]
+            for p in range(n):
+                s.sigma[p] = -orc.tait_pressure(s.rho[p]) * np.eye(3)
+            s2 = forward(orc, s)
+            return pair(lam, [s2.x, s2.v, s2.B, s2.rho])
+        fd = (J(eps) - J(-eps)) / (2 * eps)
+        assert pair([xb, vb, Bb, rb], sub) == pytest.approx(fd, rel=1e-5, abs=1e-12), f"block {blk}"
+
+
 def test_one_step_vjp_matches_central_differences_in_mu():
     orc, st, mu, rng = setup(1)
     n = st.n

@@ -8,6 +8,7 @@ import oracle
 from paper_2507_04192_gb300 import inputs
 
 COHESIVE = dict(inputs.SAND_DP, cohesion=2.0e3, sigma_t=500.0)
+DILATANT = dict(COHESIVE, psi_deg=10.0)           # q_psi > 0: the return also moves the mean stress
 
 
 def make(material, dim=2, N=16, dt=2e-4, mu=None, n_seg=4):
@@ -47,7 +48,8 @@ def dp_case(orc, zone, rng):
 
 
 @pytest.mark.parametrize("material,zone", [(inputs.SAND_DP, 1), (inputs.SAND_DP, 2), (inputs.SAND_DP, 4),
-                                           (COHESIVE, 1), (COHESIVE, 2), (COHESIVE, 3), (COHESIVE, 4)])
+                                           (COHESIVE, 1), (COHESIVE, 2), (COHESIVE, 3), (COHESIVE, 4),
+                                           (DILATANT, 2), (DILATANT, 4)])
 def test_dp_vjp_matches_central_differences(material, zone):
     rng = np.random.default_rng(zone)
     orc = make(material)

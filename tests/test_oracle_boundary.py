@@ -1,5 +1,7 @@
 """Pins of the oracle's wall contact (Eq. coulomb_friction, Sec. 5.3) and grid
-update (Sec. 2.2) against the Coulomb law and a sliding-block solution."""
+update (Sec. 2.2) against the Coulomb law, hand-worked nodes (segments, the wall
+order at an edge) and a sliding-block solution, and of the position clamp of
+G2P."""
 import numpy as np
 import pytest
 
@@ -63,6 +65,39 @@ def test_grid_update_walls_and_segments():
             if m > 0:
                 out[0] = 0.0 if vt <= m * vn else np.sign(out[0]) * (vt - m * vn)
         np.testing.assert_allclose(gv[idx], out, atol=1e-15, err_msg=f"node {jx},{jy}")
+
+
+def test_floor_acts_last_at_a_3d_edge_node():
+    """On the edge shared by the x- wall (slip) and the floor (friction mu) the
+    walls act one after the other, the floor last.  For v = (-0.5, 0.8, -0.4)
+    and mu = 0.3, by hand: the x- wall removes v_x, leaving (0, 0.8, -0.4); the
+    floor then sees v_n = 0.4 and |v_t| = 0.8 > mu v_n = 0.12, so the node slides
+    at 0.8 - 0.12 = 0.68.  (The floor first would leave 0.8 (1 - 0.12 / |(-0.5, 0.8)|)
+    = 0.698...)."""
+    N, dx = 4, 0.25
+    orc = oracle.Oracle(3, (N, N, N), dx, 1e-3, (0.0, 0.0, 0.0), dict(inputs.FLUID_WATER), dx ** 3,
+                        friction=[(4, (1, 1), [0.3])])
+    G = orc.num_nodes
+    nx, ny, _ = orc.node_shape
+    gm, gq = np.zeros(G), np.zeros((G, 3))
+    idx = 1 + nx * (2 + ny * 1)                         # node (x, y, z) = (0, dx, 0)
+    gm[idx] = 1.0
+    gq[idx] = [-0.5, 0.8, -0.4]
+    gv = orc.grid_update(gm, gq, np.zeros((G, 3)))
+    np.testing.assert_allclose(gv[idx], [0.0, 0.68, 0.0], rtol=0, atol=1e-15)
+
+
+def test_positions_are_clamped_to_the_domain():
+    """Particles driven through the floor and the ceiling within one step end on
+    them (x_p is clamped to [0, L] after the advection of Sec. 2.2)."""
+    N = 16
+    dx = 1.0 / N
+    orc = oracle.Oracle(2, (N, N), dx, 2e-3, (0.0, 0.0), dict(inputs.FLUID_WATER), dx * dx / 4)
+    x = np.array([[0.30, 1e-4], [0.33, 1e-4], [0.60, 1.0 - 1e-4], [0.63, 1.0 - 1e-4], [0.5, 0.5]])
+    st = orc.initial_state(x, np.array([[0.2, -1.0], [0.1, -1.0], [0.0, 1.0], [0.1, 1.0], [0.0, 0.0]]))
+    orc.step(st, 1)
+    assert (st.x[:2, 1] == 0.0).all() and (st.x[2:4, 1] == 1.0).all()
+    assert st.x[4, 1] == 0.5 and (st.x[:4, 0] > 0.25).all() and (st.x[:4, 0] < 0.75).all()
 
 
 def test_mass_threshold_and_acceleration():

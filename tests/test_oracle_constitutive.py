@@ -42,6 +42,24 @@ def test_dp_constants_at_30_degrees():
     assert c["alpha_P"] == pytest.approx(np.sqrt(1 + c["q_phi"] ** 2) - c["q_phi"])
 
 
+def test_dp_constants_with_cohesion_and_a_tension_cutoff():
+    # phi = 30 deg: sin = 1/2 and cos = sqrt(3)/2, so q_phi = 2 sqrt(3)/7 and k_phi = 6 c / 7;
+    # the cone's apex sits at the mean stress k_phi / q_phi = sqrt(3) c
+    q = 2.0 * np.sqrt(3.0) / 7.0
+    c = dp_oracle(cohesion=700.0, sigma_t=100.0).dp_constants()
+    assert c["q_phi"] == pytest.approx(q, rel=1e-14)
+    assert c["k_phi"] == pytest.approx(600.0, rel=1e-14)
+    assert c["sigma_t"] == 100.0
+    assert c["tau_P"] == pytest.approx(600.0 - 100.0 * q, rel=1e-14)
+    assert c["alpha_P"] == pytest.approx(np.sqrt(1.0 + q * q) - q, rel=1e-14)
+    # dilatancy: q_psi follows the same form in psi (psi = 90 deg: 6 / (4 sqrt(3)))
+    assert dp_oracle(psi_deg=90.0).dp_constants()["q_psi"] == pytest.approx(1.5 / np.sqrt(3.0), rel=1e-14)
+    # a tension cutoff beyond the apex is brought back to it, where tau_P vanishes
+    c = dp_oracle(cohesion=700.0, sigma_t=5000.0).dp_constants()
+    assert c["sigma_t"] == pytest.approx(np.sqrt(3.0) * 700.0, rel=1e-14)
+    assert abs(c["tau_P"]) < 1e-10
+
+
 def test_dp_elastic_oedometric_step():
     """Uniaxial strain increment under confinement: textbook oedometric response."""
     orc = dp_oracle()

@@ -3,7 +3,9 @@
 The rounding helper against torch's bfloat16 cast (round to nearest even) and
 hand-worked ties; GELU against torch's exact-erf GELU and its odd-part identity;
 the loss gradient against central finite differences with rounding off; a
-one-layer network against its closed form.
+one-layer network against its closed form; with rounding on, the loss and every
+gradient depend on the weights only through their bfloat16 values (the values
+the tensor cores are fed), in the forward and the backward products.
 """
 import numpy as np
 import pytest
@@ -80,3 +82,21 @@ def test_bf16_rounding_points_change_little():
     l1, g1 = mlp.loss_and_grad(p, widths, x, t, bf16_round=True)
     assert l1 == pytest.approx(l0, rel=2e-2)
     assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0)
+
+
+def test_values_depend_on_the_weights_only_through_their_bf16_roundings():
+    rng = np.random.default_rng(4)
+    widths = [16, 24, 24, 8]
+    n_par = sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+    p = rng.standard_normal(n_par) * 0.3
+    x = rng.standard_normal((12, 16))
+    t = rng.uniform(0.1, 0.6, (12, 8))
+    layers = mlp.unpack(p, widths)
+    # bf16-exact weights, then the same weights moved by a quarter of a bf16 unit in the last place
+    exact = mlp.pack([(mlp.bf16(W), b) for W, b in layers])
+    moved = mlp.pack([(mlp.bf16(W) * (1.0 + 2.0 ** -10), b) for W, b in layers])
+    assert (mlp.bf16(moved) == moved).sum() < 0.5 * n_par
+    l0, g0 = mlp.loss_and_grad(exact, widths, x, t)
+    l1, g1 = mlp.loss_and_grad(moved, widths, x, t)
+    assert l1 == l0
+    np.testing.assert_array_equal(g1, g0)

@@ -60,6 +60,12 @@ def test_faces_outside_the_domain_are_not_contact_faces():
     for c1 in range(0, 11):
         assert tuple(np.round(orc.obstacle_normal(0, (4 + 1, c1 + 1))[:2]).astype(int)) == (-1, 0)
         assert tuple(np.round(orc.obstacle_normal(0, (6 + 1, c1 + 1))[:2]).astype(int)) == (1, 0)
+    # a box standing on the floor: its y- face lies on the domain wall, so a node on
+    # the floor inside it takes the nearest of the other faces (x- 3, x+ 3, y+ 5: x- first)
+    orc = oracle.Oracle(2, (10, 10), dx, 1e-4, (0.0, 0.0), WATER, dx * dx / 4,
+                        obstacles=[((0.2, 0.0), (0.8, 0.5))])
+    assert tuple(np.round(orc.obstacle_normal(0, (5 + 1, 0 + 1))[:2]).astype(int)) == (-1, 0)
+    assert tuple(np.round(orc.obstacle_normal(0, (5 + 1, 4 + 1))[:2]).astype(int)) == (0, 1)
     # a box covering the whole domain has no contact face
     orc = oracle.Oracle(2, (10, 10), dx, 1e-4, (0.0, 0.0), WATER, dx * dx / 4,
                         obstacles=[((-1.0, -1.0), (2.0, 2.0))])

@@ -6,6 +6,10 @@ APIC keeps the affine matrix, TPIC the particle velocity gradient, PIC nothing.
   with its gradient as the particle matrix reproduces it on the grid, and G2P
   returns it), while PIC loses the A x part on the grid;
 - the TPIC particle matrix after a step equals the velocity gradient L_p;
+- in the same affine field L_p = A at every particle, so one step gives
+  F <- (I + dt A) F, rho <- rho / (1 + dt tr A) and, for a viscous fluid, the
+  stress of Sec. 2.3 with the rate of deformation D = sym(A):
+  -p(rho) I - (2/3) mu tr(D) I + 2 mu D;
 - PIC conserves linear momentum but not angular momentum of a spinning disc,
   which APIC and TPIC conserve (linear grid interpolation of a rigid rotation).
 """
@@ -39,6 +43,30 @@ def test_affine_field_carried_exactly(transfer):
     orc.step(st, 1)
     np.testing.assert_allclose(st.v, v0 + (x0 - 0.5) @ A.T, rtol=0, atol=1e-12)
     np.testing.assert_allclose(orc.affine_C(st), np.broadcast_to(A, st.B.shape), rtol=0, atol=1e-10)
+
+
+def test_affine_field_gives_F_rho_and_the_viscous_stress():
+    N = 16
+    dx = 1.0 / N
+    x = inputs.lattice_particles((N, N), dx, 2, lambda p: (np.abs(p[:, 0] - 0.5) < 0.2) & (np.abs(p[:, 1] - 0.5) < 0.2),
+                                 (0.3, 0.3), (0.7, 0.7), 0)
+    mu = 0.7
+    dt = 1e-3
+    orc = oracle.Oracle(2, (N, N), dx, dt, (0.0, 0.0), dict(inputs.FLUID_WATER, viscosity=mu), dx * dx / 4)
+    A = np.array([[0.3, -0.8], [0.5, 0.4]])
+    st = orc.initial_state(x, np.array([0.2, -0.1]) + (x - 0.5) @ A.T)
+    st.B[:] = A * dx * dx / 4.0
+    rng = np.random.default_rng(7)
+    F0 = np.eye(2) + 0.3 * rng.normal(size=(st.n, 2, 2))
+    st.F[:] = F0
+    orc.step(st, 1)
+    np.testing.assert_allclose(st.F, np.einsum("ab,pbc->pac", np.eye(2) + dt * A, F0), rtol=0, atol=1e-12)
+    rho1 = 1000.0 / (1.0 + dt * np.trace(A))
+    np.testing.assert_allclose(st.rho, rho1, rtol=1e-13)
+    D = np.zeros((3, 3))
+    D[:2, :2] = 0.5 * (A + A.T)
+    sig = -orc.tait_pressure(rho1) * np.eye(3) - 2.0 / 3.0 * mu * np.trace(D) * np.eye(3) + 2.0 * mu * D
+    np.testing.assert_allclose(st.sigma, np.broadcast_to(sig, st.sigma.shape), rtol=0, atol=1e-9 * np.abs(sig).max())
 
 
 def test_pic_loses_the_affine_part():
