@@ -37,6 +37,9 @@ MLP_PINS = ["test_oracle_mlp.py"]
 MONITOR_PINS = ["test_oracle_inverse_velocity.py"]
 
 C = "mpm_oracle.c"
+VI = "velocity_inverse_oracle.py"
+# where each mutated file lives
+HOME = {C: "oracle", "mlp.py": "oracle", "__init__.py": "oracle", VI: "tests"}
 # (name, file, text, replacement, occurrence of text to replace)
 MUTANTS = [
     # quadratic B-spline (Sec. 2.1)
@@ -228,11 +231,17 @@ MUTANTS = [
     ("monitor mean over all particles", "__init__.py", "Q[l] = v[inside].sum(axis=0) / cnt[l]",
      "Q[l] = v[inside].sum(axis=0) / len(x)", 0),
     ("monitor seed without the count", "__init__.py", "g[inside] += 2.0 * e / cnt[l]", "g[inside] += 2.0 * e", 0),
+    # reverse recursion of the initial-velocity problems (tests/velocity_inverse_oracle.py)
+    ("tracked seed without the 2", VI, "lam[0][ids] += 2.0 * e", "lam[0][ids] += e", 0),
+    ("step adjoint taken at the later state", VI, "lam, _ = orc.step_vjp(states[t - 1], *lam)",
+     "lam, _ = orc.step_vjp(states[t], *lam)", 0),
+    ("initial adjoint of the position returned", VI, "return loss, lam[1]", "return loss, lam[0]", 0),
+    ("monitor seed dropped", VI, "lam[1] += g", "lam[1] += 0.0 * g", 0),
 ]
 
 
 def _pins(fname):
-    return {"mpm_oracle.c": C_PINS, "mlp.py": MLP_PINS, "__init__.py": MONITOR_PINS}[fname]
+    return {C: C_PINS, "mlp.py": MLP_PINS, "__init__.py": MONITOR_PINS, VI: MONITOR_PINS}[fname]
 
 
 def _replace_nth(src: str, old: str, new: str, nth: int) -> str:
@@ -246,19 +255,19 @@ def _replace_nth(src: str, old: str, new: str, nth: int) -> str:
 
 def _tree(base: str, mutant=None) -> str:
     """A private copy of the oracle and its pin files under base, with one mistake planted."""
-    os.makedirs(os.path.join(base, "oracle"))
-    for f in ("__init__.py", "mlp.py", "mpm_oracle.c"):
-        with open(os.path.join(ROOT, "oracle", f)) as fh:
+    files = [("oracle", f) for f in ("__init__.py", "mlp.py", "mpm_oracle.c")]
+    files += [("tests", f) for f in sorted(os.listdir(TESTS))
+              if f.startswith("test_oracle_") and f.endswith(".py") and f != os.path.basename(__file__)
+              or f in ("conftest.py", VI)]
+    for d in ("oracle", "tests"):
+        os.makedirs(os.path.join(base, d))
+    for d, f in files:
+        with open(os.path.join(ROOT, d, f)) as fh:
             src = fh.read()
-        if mutant is not None and mutant[1] == f:
+        if mutant is not None and mutant[1] == f and HOME[f] == d:
             src = _replace_nth(src, mutant[2], mutant[3], mutant[4])
-        with open(os.path.join(base, "oracle", f), "w") as fh:
+        with open(os.path.join(base, d, f), "w") as fh:
             fh.write(src)
-    os.makedirs(os.path.join(base, "tests"))
-    for f in os.listdir(TESTS):
-        if f.startswith("test_oracle_") and f.endswith(".py") and f != os.path.basename(__file__) or \
-                f in ("conftest.py", "velocity_inverse_oracle.py"):
-            shutil.copy(os.path.join(TESTS, f), os.path.join(base, "tests", f))
     shutil.copytree(os.path.join(TESTS, "golden"), os.path.join(base, "tests", "golden"))
     os.symlink(os.path.join(ROOT, "paper_2507_04192_gb300"), os.path.join(base, "paper_2507_04192_gb300"))
     with open(os.path.join(base, "pytest.ini"), "w") as fh:
