@@ -107,6 +107,59 @@ def test_one_step_vjp_through_the_position_clamp():
         assert pair([xb, vb, Bb, rb], sub) == pytest.approx(fd, rel=1e-5, abs=1e-12), f"block {blk}"
 
 
+def test_one_step_vjp_at_a_3d_edge_with_two_friction_walls():
+    """Fluid driven into the edge of the x- wall (mu 0.2) and the floor (mu 0.4):
+    edge nodes go through both walls in turn, so the adjoint must take the walls
+    in the reverse order, each linearised about its own input; every state
+    block and both walls' friction against central differences."""
+    N = 8
+    dx = 1.0 / N
+    rng = np.random.default_rng(11)
+    x = inputs.lattice_particles((N, N, N), dx, 2, lambda p: (p[:, 0] < 2 * dx) & (p[:, 2] < 2 * dx),
+                                 (0.0, 2 * dx, 0.0), (2 * dx, 5 * dx, 2 * dx), 0)
+    n = len(x)
+    water = dict(inputs.FLUID_WATER)
+
+    def make(mx, mf):
+        return oracle.Oracle(3, (N, N, N), dx, 5e-4, (0.0, 0.0, -9.81), water, dx ** 3 / 8,
+                             friction=[(0, (1, 1), [mx]), (4, (1, 1), [mf])])
+    orc = make(0.2, 0.4)
+    st = orc.initial_state(x, np.array([-0.6, 0.3, -0.5]) + 0.1 * rng.normal(size=(n, 3)))
+    st.B[:] = rng.normal(size=(n, 3, 3)) * dx * dx
+    st.rho[:] = 1000.0 * rng.uniform(0.995, 1.005, n)
+    for p in range(n):
+        st.sigma[p] = -orc.tait_pressure(st.rho[p]) * np.eye(3)
+    lam = [rng.normal(size=(n, 3)), rng.normal(size=(n, 3)), rng.normal(size=(n, 3, 3)) / dx ** 2,
+           rng.normal(size=n) * 1e-3]
+    (xb, vb, Bb, rb), mub = orc.step_vjp(st, *lam)
+    dirs = [rng.normal(size=(n, 3)) * dx * 0.01, rng.normal(size=(n, 3)) * 0.01, rng.normal(size=(n, 3, 3)) * dx * dx,
+            rng.normal(size=n) * 0.1]
+    eps = 1e-5
+    for blk in range(4):
+        sub = [d if k == blk else np.zeros_like(d) for k, d in enumerate(dirs)]
+
+        def J(scale):
+            s = st.copy()
+            s.x += scale * sub[0]; s.v += scale * sub[1]; s.B += scale * sub[2]; s.rho += scale * sub[3]
+            for p in range(n):
+                s.sigma[p] = -orc.tait_pressure(s.rho[p]) * np.eye(3)
+            s2 = forward(orc, s)
+            return pair(lam, [s2.x, s2.v, s2.B, s2.rho])
+        fd = (J(eps) - J(-eps)) / (2 * eps)
+        assert pair([xb, vb, Bb, rb], sub) == pytest.approx(fd, rel=1e-5, abs=1e-12), f"block {blk}"
+    for w, k in ((0, 0), (4, 1)):
+        h = 1e-6
+        up, dn = [0.2, 0.4], [0.2, 0.4]
+        up[k] += h
+        dn[k] -= h
+        def Jm(m):
+            s2 = forward(make(*m), st)
+            return pair(lam, [s2.x, s2.v, s2.B, s2.rho])
+        fd = (Jm(up) - Jm(dn)) / (2 * h)
+        assert abs(fd) > 0
+        assert mub[w][0] == pytest.approx(fd, rel=1e-5), f"wall {w}"
+
+
 def test_one_step_vjp_matches_central_differences_in_mu():
     orc, st, mu, rng = setup(1)
     n = st.n

@@ -3,9 +3,11 @@
 The rounding helper against torch's bfloat16 cast (round to nearest even) and
 hand-worked ties; GELU against torch's exact-erf GELU and its odd-part identity;
 the loss gradient against central finite differences with rounding off; a
-one-layer network against its closed form; with rounding on, the loss and every
-gradient depend on the weights only through their bfloat16 values (the values
-the tensor cores are fed), in the forward and the backward products.
+one-layer network against its closed form; with rounding on, the values the
+tensor cores are fed are bfloat16: the loss and every gradient depend on the
+weights and on the input only through their bfloat16 values, the hidden
+activations are bfloat16 numbers, and the weight gradients depend on the output
+error only through its bfloat16 value.
 """
 import numpy as np
 import pytest
@@ -100,3 +102,36 @@ def test_values_depend_on_the_weights_only_through_their_bf16_roundings():
     l1, g1 = mlp.loss_and_grad(moved, widths, x, t)
     assert l1 == l0
     np.testing.assert_array_equal(g1, g0)
+
+
+def _net(seed):
+    rng = np.random.default_rng(seed)
+    widths = [16, 24, 24, 8]
+    n_par = sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+    return widths, rng.standard_normal(n_par) * 0.3, rng.standard_normal((12, 16)), rng.uniform(0.1, 0.6, (12, 8))
+
+
+def test_input_enters_only_through_its_bf16_value_and_activations_are_bf16():
+    widths, p, x, t = _net(5)
+    xe = mlp.bf16(x)
+    xm = xe * (1.0 + 2.0 ** -10)
+    assert (mlp.bf16(xm) == xm).sum() < 0.5 * xm.size
+    l0, g0 = mlp.loss_and_grad(p, widths, xe, t)
+    l1, g1 = mlp.loss_and_grad(p, widths, xm, t)
+    assert l1 == l0
+    np.testing.assert_array_equal(g1, g0)
+    _, xs, _ = mlp.forward(p, widths, x)
+    for a in xs:
+        np.testing.assert_array_equal(mlp.bf16(a), a)
+
+
+def test_weight_gradients_see_the_output_error_only_through_its_bf16_value():
+    # targets moved by 1e-12 relative change the output error far below a bf16 unit:
+    # every weight gradient and the hidden layers' bias gradients stay bit-identical,
+    # while the output bias gradient (a sum of the unrounded error) moves
+    widths, p, x, t = _net(6)
+    _, g0 = mlp.loss_and_grad(p, widths, x, t)
+    _, g1 = mlp.loss_and_grad(p, widths, x, t * (1.0 + 1e-12))
+    n_out_bias = widths[-1]
+    np.testing.assert_array_equal(g1[:-n_out_bias], g0[:-n_out_bias])
+    assert (g1[-n_out_bias:] != g0[-n_out_bias:]).any()

@@ -204,7 +204,42 @@ MUTANTS = [
     ("adjoint P2G volume sign", C, "rhob0[p] += Vb * (-mp / (rho[p] * rho[p]))", "rhob0[p] += Vb * (mp / (rho[p] * rho[p]))", 0),
     ("adjoint P2G mass term dropped", C, "double phib = mp * gmb[i], gradb[3] = {0, 0, 0};",
      "double phib = 0.0, gradb[3] = {0, 0, 0};", 0),
+    ("Hessian mixed term on the diagonal", C, "h *= na == 0 ? f[c] : (na == 1 ? df[c] : ddf[c]);",
+     "h *= na == 0 ? f[c] : df[c];", 0),
+    ("Hessian of the outer piece", C, "(ax < 1.5 ? 1.0 : 0.0)", "(ax < 1.5 ? -1.0 : 0.0)", 0),
+    ("wall adjoint without the tangential projection", C, "for (int a = 0; a < 3; ++a) obt[a] = ob[a] - obn * n[a];",
+     "for (int a = 0; a < 3; ++a) obt[a] = ob[a];", 0),
+    ("wall adjoint slide scale sign", C, "double s = 1.0 - mu * vn / vtn;", "double s = 1.0 + mu * vn / vtn;", 0),
+    ("wall adjoints in forward order", C, "for (int q = nw - 1; q >= 0; --q) {", "for (int q = 0; q < nw; ++q) {", 0),
+    ("wall adjoint linearised at the wall's output", C, "wall_vjp(chain[q], nrm, wall_mu(P, w, j), ob, ib, mub);",
+     "wall_vjp(chain[q + 1], nrm, wall_mu(P, w, j), ob, ib, mub);", 0),
+    ("adjoint grid momentum without the mass", C, "gqb[i * d + a] = ob[a] / gm[i];", "gqb[i * d + a] = ob[a];", 0),
+    ("adjoint P2G velocity without the weight", C, "vb0[p * d + a] += phi * mp * qb;", "vb0[p * d + a] += mp * qb;", 0),
+    ("adjoint P2G affine adjoint transposed", C, "Mb[a * d + b] += phi * mp * qb * r[b];",
+     "Mb[b * d + a] += phi * mp * qb * r[b];", 0),
+    ("adjoint P2G stress gradient index", C, "gradb[b] += -Vp * sp[a * 3 + b] * fb;",
+     "gradb[a] += -Vp * sp[a * 3 + b] * fb;", 0),
+    ("adjoint P2G sand volume sign", C, "Vb += -sp[a * 3 + b] * S.grad[k][b] * fb;",
+     "Vb += sp[a * 3 + b] * S.grad[k][b] * fb;", 0),
+    ("adjoint P2G fluid gradient sign", C, "gradb[a] += Vp * pr * fb;", "gradb[a] += -Vp * pr * fb;", 0),
+    ("adjoint P2G fluid volume dropped", C, "Vb += pr * fb * S.grad[k][a];", "Vb += 0.0 * pr * fb * S.grad[k][a];", 0),
+    ("adjoint G2P gradient adjoint transposed", C, "gradb[b] += Lb[a * d + b] * via;",
+     "gradb[b] += Lb[b * d + a] * via;", 0),
+    ("adjoint G2P velocity-gradient term transposed", C, "Lg += Lb[a * d + b] * S.grad[k][b];",
+     "Lg += Lb[b * d + a] * S.grad[k][b];", 0),
+    ("adjoint G2P weight term without B", C, "phib += vbt[a] * via + Br * via;", "phib += vbt[a] * via;", 0),
+    ("adjoint density carried without the update", C, "rhob0[p] = rhob1[p] / den;", "rhob0[p] = rhob1[p];", 0),
+    ("obstacle extent rounded down", C, "long lo = (long)ceil(P->obstacle[o][0][a] / P->dx - 1e-9);",
+     "long lo = (long)floor(P->obstacle[o][0][a] / P->dx);", 0),
+    ("obstacle high side open", C, "if (c < lo || c > hi) return 0;", "if (c < lo || c >= hi) return 0;", 0),
     # Drucker-Prager adjoint (Appendix A, reverse)
+    ("DP adjoint corner keeps the mean-stress path", C, "double sm_nb = corner ? 0.0 : trb;", "double sm_nb = trb;", 0),
+    ("DP adjoint corner keeps the tau path", C, "if (!corner) tau_nb = rb / tau;", "tau_nb = rb / tau;", 0),
+    ("DP adjoint cone slope sign", C, "sm_nb += -c.q_phi * tau_nb;", "sm_nb += c.q_phi * tau_nb;", 0),
+    ("DP adjoint zone III corner sign", C, "taub += -rb * c.tau_P / (tau * tau);", "taub += rb * c.tau_P / (tau * tau);", 0),
+    ("DP adjoint Jaumann stress index", C, "sb0[j * 3 + k] += g * dw[i * 3 + k];", "sb0[j * 3 + k] += g * dw[k * 3 + i];", 0),
+    ("DP adjoint mean without the third", C, "for (int a = 0; a < 3; ++a) stb[a * 4] += smb / 3.0;",
+     "for (int a = 0; a < 3; ++a) stb[a * 4] += smb;", 0),
     ("DP adjoint zone II mean-stress chain", C, "smb += sm_nb * (1.0 - c.K * c.q_psi * c.q_phi / A);",
      "smb += sm_nb;", 0),
     ("DP adjoint zone II tau chain sign", C, "taub += sm_nb * (-c.K * c.q_psi / A);", "taub += sm_nb * (c.K * c.q_psi / A);", 0),
@@ -223,6 +258,11 @@ MUTANTS = [
     ("bias gradient averaged", "mlp.py", "gb = dz.sum(axis=0)", "gb = dz.mean(axis=0)", 0),
     ("squared-error gradient without the 2", "mlp.py", "dz = 2.0 * e / n", "dz = e / n", 0),
     ("backward through unrounded weights", "mlp.py", "da = dzr @ r(W)", "da = dz @ W", 0),
+    ("hidden activations not rounded", "mlp.py", "xs.append(r(gelu(z)))", "xs.append(gelu(z))", 0),
+    ("network input not rounded", "mlp.py", "xs, zs = [r(x)], []", "xs, zs = [np.asarray(x, dtype=np.float64)], []", 0),
+    ("weight gradient from the unrounded error", "mlp.py", "gW = dzr.T @ xs[l]", "gW = dz.T @ xs[l]", 0),
+    ("output sigmoid derivative sign", "mlp.py", "dz = 2.0 * e / n * (hi - lo) * s * (1.0 - s)",
+     "dz = 2.0 * e / n * (hi - lo) * s * (1.0 + s)", 0),
     # velocity monitors (oracle/__init__.py)
     ("monitor box open at the top", "__init__.py", "inside = np.all((x >= np.asarray(lo, dtype=np.float64)) & "
      "(x <= np.asarray(hi, dtype=np.float64)), axis=1)\n        cnt[l]",
