@@ -147,7 +147,17 @@ void mpm_destroy(mpm_ctx *ctx);
 int mpm_load_particles(mpm_ctx *ctx, int64_t n, const double *x, const double *v,
                        double particle_volume, const int32_t *sim_id);
 
-/* Overwrite one particle field (host, load order, the field's width per particle). */
+/*
+ * Overwrite one particle field from a host array in load order, with
+ * mpm_field_width() values per particle (the caller keeps ownership; it is
+ * copied before the call returns).  Returns MPM_EINVAL for a NULL array, an
+ * unknown field, sigma or eps of a fluid (its stress follows from the density),
+ * or positions outside the domain or not finite; MPM_ESTATE before any
+ * particles are loaded.  Non-finite values of the other fields are accepted:
+ * those that feed the dynamics (v, C, rho, sigma) surface as MPM_ENAN at the
+ * synchronisation after the next step; F and eps do not feed back and are not
+ * checked.
+ */
 int mpm_set_particle_field(mpm_ctx *ctx, int field, const double *values);
 
 /*

@@ -560,6 +560,15 @@ int mpm_set_particle_field(mpm_ctx *c, int field, const double *values)
         return fail(c, MPM_EINVAL, "mpm_set_particle_field: fluid stress follows from the density");
     if (field == MPM_FIELD_EPS && c->mat.kind != MPM_DRUCKER_PRAGER)
         return fail(c, MPM_EINVAL, "mpm_set_particle_field: no plastic strain in a fluid");
+    if (field == MPM_FIELD_X) {
+        const int d = c->grid.dim;
+        for (int64_t p = 0; p < c->hp.n; ++p)
+            for (int a = 0; a < d; ++a) {
+                const double xa = values[p * d + a];
+                if (!(xa >= 0.0 && xa <= c->hp.n_cells[a] * c->hp.dx))
+                    return fail(c, MPM_EINVAL, "mpm_set_particle_field: position outside the domain or not finite");
+            }
+    }
     DevState &ds = c->ds;
     CK(cudaMemcpyAsync(ds.staging, values, sizeof(double) * c->hp.n * wdt, cudaMemcpyHostToDevice, ds.stream),
        "copy field");
