@@ -240,6 +240,8 @@ int mpm_set_velocity_monitors(mpm_ctx *ctx, int n_mon, const double *boxes, int 
  * mpm_set_velocity_monitors, batch 1): per monitor the mean velocity (dim
  * values, 0 when empty) and the particle count, out = n_mon x (dim + 1) doubles
  * (host); synchronises.  Used to record Eulerian observations of a run.
+ * MPM_EINVAL for n_mon outside 1..MPM_MAX_MONITORS, a box with lo > hi or a
+ * non-finite bound, or batch != 1; MPM_ESTATE before any particles are loaded.
  */
 int mpm_monitor_means(mpm_ctx *ctx, int n_mon, const double *boxes, double *out);
 

@@ -840,6 +840,12 @@ int mpm_monitor_means(mpm_ctx *c, int n_mon, const double *boxes, double *out)
     const HostParams &h = c->hp;
     DevState &ds = c->ds;
     const int d = h.dim;
+    for (int l = 0; l < n_mon; ++l)
+        for (int a = 0; a < d; ++a) {
+            const double lo = boxes[(size_t)l * 2 * d + a], hi = boxes[(size_t)l * 2 * d + d + a];
+            if (!(lo <= hi) || !std::isfinite(lo) || !std::isfinite(hi))
+                return fail(c, MPM_EINVAL, "mpm_monitor_means: bad box");
+        }
     double *dev = nullptr;
     int rc = dalloc(c, &dev, (size_t)n_mon * (3 * d + 1), "monitor scratch");
     if (rc != MPM_OK) return rc;
