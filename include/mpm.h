@@ -305,8 +305,11 @@ int mpm_restore_state(mpm_ctx *ctx, int slot);
  * Host blob of the particle state for checkpoint/resume across processes.
  * mpm_state_blob_size gives the bytes needed; mpm_export_state writes the blob
  * (header, all fields, ids, simulation ids, FNV-1a checksum of the payload);
- * mpm_import_state verifies it (MPM_ECORRUPT on a bad magic, truncation or
- * checksum mismatch; MPM_EINVAL if it does not match the loaded particles).
+ * mpm_import_state verifies it before anything reaches the device
+ * (MPM_ECORRUPT on a bad magic, a payload size other than the loaded particles'
+ * state, truncation, a checksum mismatch, particle ids that are not a
+ * permutation of 0..n-1 or simulation ids outside the batch; MPM_EINVAL if its
+ * header does not match the loaded particles).  The caller owns the blob.
  */
 int64_t mpm_state_blob_size(const mpm_ctx *ctx);
 int mpm_export_state(mpm_ctx *ctx, void *blob, int64_t size);

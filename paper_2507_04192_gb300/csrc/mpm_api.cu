@@ -1300,19 +1300,35 @@ int mpm_import_state(mpm_ctx *c, const void *blob, int64_t size)
     if (h.n == 0 || hd.n != (uint64_t)h.n || hd.ncomp != (uint64_t)h.ncomp || hd.precision != (uint64_t)h.precision ||
         hd.dim != (uint64_t)h.dim)
         return fail(c, MPM_EINVAL, "mpm_import_state: blob does not match the loaded particles");
+    const int64_t rs = h.precision == MPM_FP64 ? 8 : 4;
+    const uint64_t expect = (uint64_t)h.ncomp * h.n * rs + 2 * sizeof(int32_t) * (uint64_t)h.n;
+    if (hd.payload != expect) return fail(c, MPM_ECORRUPT, "mpm_import_state: payload size does not match");
     if ((int64_t)(sizeof(BlobHeader) + hd.payload) > size) return fail(c, MPM_ECORRUPT, "mpm_import_state: truncated");
     const unsigned char *in = (const unsigned char *)blob + sizeof(BlobHeader);
     if (fnv1a(in, hd.payload) != hd.checksum) return fail(c, MPM_ECORRUPT, "mpm_import_state: checksum mismatch");
+    // the ids index the load-order readback and the simulation ids the per-simulation
+    // grids: a blob whose ids are not a permutation of 0..n-1, or whose simulation ids
+    // leave the batch, is refused before anything reaches the device
+    std::vector<int32_t> ids(h.n), sims(h.n);
+    std::memcpy(ids.data(), in + (size_t)h.ncomp * h.n * rs, sizeof(int32_t) * h.n);
+    std::memcpy(sims.data(), in + (size_t)h.ncomp * h.n * rs + sizeof(int32_t) * h.n, sizeof(int32_t) * h.n);
+    {
+        std::vector<unsigned char> seen(h.n, 0);
+        for (int64_t p = 0; p < h.n; ++p) {
+            if (ids[p] < 0 || ids[p] >= h.n || seen[ids[p]])
+                return fail(c, MPM_ECORRUPT, "mpm_import_state: particle ids are not a permutation");
+            seen[ids[p]] = 1;
+            if (sims[p] < 0 || sims[p] >= c->grid.batch)
+                return fail(c, MPM_ECORRUPT, "mpm_import_state: simulation id out of range");
+        }
+    }
     DevState &ds = c->ds;
-    const int64_t rs = h.precision == MPM_FP64 ? 8 : 4;
     for (int comp = 0; comp < h.ncomp; ++comp)
         CK(cudaMemcpyAsync((char *)ds.S + (size_t)comp * h.npad * rs, in + (size_t)comp * h.n * rs, (size_t)h.n * rs,
                            cudaMemcpyHostToDevice, ds.stream),
            "import state");
-    const unsigned char *ids = in + (size_t)h.ncomp * h.n * rs;
-    CK(cudaMemcpyAsync(ds.id, ids, sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import ids");
-    CK(cudaMemcpyAsync(ds.sim, ids + sizeof(int32_t) * h.n, sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream),
-       "import sims");
+    CK(cudaMemcpyAsync(ds.id, ids.data(), sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import ids");
+    CK(cudaMemcpyAsync(ds.sim, sims.data(), sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import sims");
     CK(cudaStreamSynchronize(ds.stream), "import state");
     c->need_sort = true;
     return MPM_OK;
