@@ -116,6 +116,9 @@ typedef struct {
  *       the corner return when a return lands past the tension cutoff.
  *   rho0: reference density (fluid) or initial density (sand); particle mass
  *       is rho0 * particle_volume.
+ * mpm_create rejects (MPM_EINVAL) non-finite or non-positive rho0, bulk_K, gamma
+ * and E; nu outside (-1, 0.5); angles outside [0, 90) degrees; a negative or
+ * non-finite cohesion or sigma_t.
  */
 typedef struct {
     int kind;

@@ -325,13 +325,22 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
     for (int a = 0; a < g.dim; ++a)
         if (g.n_cells[a] < 1 || g.n_cells[a] > 4096) return MPM_EINVAL;
     if (!(g.dx > 0) || !(g.dt > 0) || g.sort_every < 1 || g.batch < 1) return MPM_EINVAL;
+    if (!std::isfinite(g.dx) || !std::isfinite(g.dt)) return MPM_EINVAL;
+    for (int a = 0; a < g.dim; ++a)
+        if (!std::isfinite(g.gravity[a])) return MPM_EINVAL;
     if (g.transfer < MPM_TRANSFER_APIC || g.transfer > MPM_TRANSFER_FLIP) return MPM_EINVAL;
     if (g.transfer == MPM_TRANSFER_FLIP && !(g.flip_alpha >= 0.0 && g.flip_alpha <= 1.0)) return MPM_EINVAL;
     if (g.precision != MPM_FP32 && g.precision != MPM_FP64) return MPM_EINVAL;
     if (m.kind != MPM_FLUID && m.kind != MPM_DRUCKER_PRAGER) return MPM_EINVAL;
-    if (!(m.rho0 > 0)) return MPM_EINVAL;
-    if (m.kind == MPM_FLUID && (!(m.bulk_K > 0) || !(m.gamma > 0) || m.viscosity != 0.0)) return MPM_EINVAL;
-    if (m.kind == MPM_DRUCKER_PRAGER && (!(m.E > 0) || !(m.nu > -1.0 && m.nu < 0.5))) return MPM_EINVAL;
+    if (!(m.rho0 > 0) || !std::isfinite(m.rho0)) return MPM_EINVAL;
+    if (m.kind == MPM_FLUID && (!(m.bulk_K > 0) || !(m.gamma > 0) || m.viscosity != 0.0 ||
+                                !std::isfinite(m.bulk_K) || !std::isfinite(m.gamma)))
+        return MPM_EINVAL;
+    if (m.kind == MPM_DRUCKER_PRAGER &&
+        (!(m.E > 0) || !std::isfinite(m.E) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.phi_deg >= 0.0 && m.phi_deg < 90.0) ||
+         !(m.psi_deg >= 0.0 && m.psi_deg < 90.0) || !(m.cohesion >= 0.0) || !std::isfinite(m.cohesion) ||
+         !(m.sigma_t >= 0.0) || !std::isfinite(m.sigma_t)))
+        return MPM_EINVAL;
 
     mpm_ctx *c = new mpm_ctx();
     c->grid = g;

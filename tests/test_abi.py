@@ -65,3 +65,19 @@ def test_invalid_descriptors_rejected_before_device_use():
     with pytest.raises(mpm.MPMError) as e:       # viscous fluid is not supported
         mpm.mpm_create(g, mpm.material_struct(dict(kind=0, rho0=1000, bulk_K=1e5, gamma=7, viscosity=1e-3)))
     assert e.value.code == mpm.MPM_EINVAL
+
+
+def test_non_finite_and_unphysical_parameters_rejected_before_device_use():
+    fluid = dict(kind=0, rho0=1000, bulk_K=1e5, gamma=7)
+    sand = dict(kind=1, rho0=2000, E=1e6, nu=0.3, phi_deg=30, psi_deg=0, cohesion=0, sigma_t=0)
+    good = dict(dim=2, n_cells=(8, 8), dx=0.1, dt=1e-4, gravity=(0, -9.81))
+    cases = [(dict(good, dx=float("inf")), fluid), (dict(good, dt=float("nan")), fluid),
+             (dict(good, gravity=(0, float("nan"))), fluid), (good, dict(fluid, bulk_K=float("inf"))),
+             (good, dict(sand, phi_deg=90.0)), (good, dict(sand, phi_deg=-5.0)), (good, dict(sand, psi_deg=95.0)),
+             (good, dict(sand, cohesion=-1.0)), (good, dict(sand, sigma_t=-1.0)),
+             (good, dict(sand, sigma_t=float("inf"))), (good, dict(sand, nu=0.5)), (good, dict(sand, E=float("nan")))]
+    for gd, mat in cases:
+        g = mpm.grid_struct(gd["dim"], gd["n_cells"], gd["dx"], gd["dt"], gd["gravity"])
+        with pytest.raises(mpm.MPMError) as e:
+            mpm.mpm_create(g, mpm.material_struct(mat))
+        assert e.value.code == mpm.MPM_EINVAL, (gd, mat)
