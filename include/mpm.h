@@ -364,8 +364,9 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  * first call before any stream capture.  Every call on a device shares the
  * scratch and clears it before use, so calls whose work overlaps on the GPU
  * race: serialise them.  A grid of more than 131072 nodes ((N_x + 3)(N_y + 3)
- * [(N_z + 3)]) is rejected with MPM_EINVAL.  On failure a one-line message is
- * written to err (when err_len > 0).
+ * [(N_z + 3)]) is rejected with MPM_EINVAL, and so are the parameters that
+ * mpm_create rejects; both checks come before any device use.  On failure a
+ * one-line message is written to err (when err_len > 0).
  */
 typedef struct {
     double *x, *v, *C, *F, *rho, *sigma, *eps;   /* device pointers; sigma/eps for Drucker-Prager only */

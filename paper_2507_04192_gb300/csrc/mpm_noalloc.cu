@@ -222,6 +222,17 @@ extern "C" int mpm_step_noalloc(const mpm_grid_desc *grid, const mpm_material *m
         set_msg(err, err_len, "mpm_step_noalloc: needs dim 2 or 3, MPM_FP64, batch 1, APIC and a valid material");
         return MPM_EINVAL;
     }
+    bool finite = std::isfinite(gd.dx) && std::isfinite(gd.dt) && std::isfinite(m.rho0);
+    for (int a = 0; a < gd.dim; ++a) finite = finite && std::isfinite(gd.gravity[a]);
+    if (m.kind == MPM_FLUID) finite = finite && std::isfinite(m.bulk_K) && std::isfinite(m.gamma);
+    else
+        finite = finite && m.E > 0.0 && std::isfinite(m.E) && m.nu > -1.0 && m.nu < 0.5 && m.phi_deg >= 0.0 &&
+                 m.phi_deg < 90.0 && m.psi_deg >= 0.0 && m.psi_deg < 90.0 && m.cohesion >= 0.0 &&
+                 std::isfinite(m.cohesion) && m.sigma_t >= 0.0 && std::isfinite(m.sigma_t);
+    if (!finite) {
+        set_msg(err, err_len, "mpm_step_noalloc: non-finite or out-of-range grid or material parameter");
+        return MPM_EINVAL;
+    }
     if (!in.x || !in.v || !in.C || !in.F || !in.rho || !out.x || !out.v || !out.C || !out.F || !out.rho ||
         (m.kind == MPM_DRUCKER_PRAGER && (!in.sigma || !in.eps || !out.sigma || !out.eps))) {
         set_msg(err, err_len, "mpm_step_noalloc: missing state buffer");

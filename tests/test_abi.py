@@ -81,3 +81,11 @@ def test_non_finite_and_unphysical_parameters_rejected_before_device_use():
         with pytest.raises(mpm.MPMError) as e:
             mpm.mpm_create(g, mpm.material_struct(mat))
         assert e.value.code == mpm.MPM_EINVAL, (gd, mat)
+    # the allocation-free step applies the same checks before it touches its buffers
+    ptrs = mpm.StatePtrs()
+    for gd, mat in cases[:4] + cases[-2:]:
+        g = mpm.grid_struct(gd["dim"], gd["n_cells"], gd["dx"], gd["dt"], gd["gravity"], precision=mpm.MPM_FP64)
+        with pytest.raises(mpm.MPMError) as e:
+            mpm.mpm_step_noalloc(g, mpm.material_struct(mat), 10, 1e-4, ptrs, ptrs)
+        assert e.value.code == mpm.MPM_EINVAL, (gd, mat)
+        assert "missing state buffer" not in str(e.value), (gd, mat)      # rejected by the parameter checks
