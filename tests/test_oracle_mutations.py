@@ -34,7 +34,7 @@ C_PINS = ["test_oracle_bspline.py", "test_oracle_transfers.py", "test_oracle_tra
           "test_oracle_adjoint.py", "test_oracle_adjoint_dp.py", "test_oracle_inverse_velocity.py",
           "test_oracle_hydrostatic.py"]
 MLP_PINS = ["test_oracle_mlp.py"]
-MONITOR_PINS = ["test_oracle_inverse_velocity.py"]
+MONITOR_PINS = ["test_oracle_inverse_velocity.py"]     # the reverse recursion of the velocity problems
 
 C = "mpm_oracle.c"
 VI = "velocity_inverse_oracle.py"
@@ -271,6 +271,13 @@ MUTANTS = [
     ("monitor mean over all particles", "__init__.py", "Q[l] = v[inside].sum(axis=0) / cnt[l]",
      "Q[l] = v[inside].sum(axis=0) / len(x)", 0),
     ("monitor seed without the count", "__init__.py", "g[inside] += 2.0 * e / cnt[l]", "g[inside] += 2.0 * e", 0),
+    # parameters handed to the C step (oracle/__init__.py)
+    ("segment counts swapped", "__init__.py", "P.n_seg[wall][0], P.n_seg[wall][1] = int(nseg[0]), int(nseg[1])",
+     "P.n_seg[wall][0], P.n_seg[wall][1] = int(nseg[1]), int(nseg[0])", 0),
+    ("obstacle corners swapped", "__init__.py", "P.obstacle[o][0][a] = float(lo[a])\n"
+     "                P.obstacle[o][1][a] = float(hi[a])", "P.obstacle[o][0][a] = float(hi[a])\n"
+     "                P.obstacle[o][1][a] = float(lo[a])", 0),
+    ("particle mass is the volume", C, "{ return P->rho0 * P->particle_volume; }", "{ return P->particle_volume; }", 0),
     # reverse recursion of the initial-velocity problems (tests/velocity_inverse_oracle.py)
     ("tracked seed without the 2", VI, "lam[0][ids] += 2.0 * e", "lam[0][ids] += e", 0),
     ("step adjoint taken at the later state", VI, "lam, _ = orc.step_vjp(states[t - 1], *lam)",
@@ -281,7 +288,7 @@ MUTANTS = [
 
 
 def _pins(fname):
-    return {C: C_PINS, "mlp.py": MLP_PINS, "__init__.py": MONITOR_PINS, VI: MONITOR_PINS}[fname]
+    return {C: C_PINS, "mlp.py": MLP_PINS, "__init__.py": C_PINS, VI: MONITOR_PINS}[fname]
 
 
 def _replace_nth(src: str, old: str, new: str, nth: int) -> str:
