@@ -1,9 +1,11 @@
 """bench.py's reference arm (the FP64 CPU oracle timed on the host cores) runs
 without a GPU: one short run prints one JSON line carrying the same metric,
 unit, direction and workload as the GPU arm, with its CPU sample described; a
-non-zero rank of a multi-process launch prints nothing and exits 0."""
+non-zero rank of a multi-process launch prints nothing and exits 0, and a
+two-process torchrun launch prints exactly one line."""
 import json
 import os
+import socket
 import subprocess
 import sys
 
@@ -39,3 +41,18 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
