@@ -1,8 +1,12 @@
 """The byte accounting behind bench.py's roofline figures, checked on the CPU:
 the active-node count against a brute-force set of stencil nodes, the
 algorithmic bytes per particle against the state components each kernel must
-move, and the DRAM traffic file's format."""
+move, the DRAM traffic file's format, and the parsing of the clock record
+taken during the timed region (median SM clock, maximum clock, throttle
+reasons that were active)."""
 import os
+import subprocess
+import tempfile
 
 import numpy as np
 
@@ -40,3 +44,21 @@ def test_traffic_file_lists_the_roofline_kernels():
     for k in ("p2g", "g2p"):
         v = bench.read_traffic(k)
         assert v is None or v > 0
+
+
+def test_clock_record_parsing():
+    rows = ["0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1995, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, [N/A], 2070, 1391.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2040, 2070, 1200.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as fh:
+        fh.write("\n".join(rows) + "\n")
+    cs = object.__new__(bench.ClockSampler)
+    cs.path, cs.gpu = path, 0
+    cs.fh = open(os.devnull, "w")
+    cs.proc = subprocess.Popen(["sleep", "30"])
+    out = cs.stop()
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 4}
+    assert not os.path.exists(path)
