@@ -62,3 +62,14 @@ def test_clock_record_parsing():
     out = cs.stop()
     assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 4}
     assert not os.path.exists(path)
+
+
+def test_clock_records_that_reject_a_number():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 50}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected(dict(ok, reasons=["sw_power_cap"], sm_mhz=1800.0))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))          # stuck low with no reason: a clock lock
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1900.0))
