@@ -76,15 +76,18 @@ def test_one_step_vjp_matches_central_differences_in_the_state():
 
 
 def test_one_step_vjp_through_the_position_clamp():
-    """Two particles driven through the floor within one step end on it: their
-    new heights no longer depend on the state, and the adjoint must agree with
-    central differences there as well as for the free particles."""
+    """Particles driven through the floor and the ceiling within one step end on
+    them: their new heights no longer depend on the state, and the adjoint must
+    agree with central differences there as well as for the free particles."""
     N = 16
     dx = 1.0 / N
     orc = oracle.Oracle(2, (N, N), dx, 2e-3, (0.0, -9.81), dict(inputs.FLUID_WATER), dx * dx / 4)
-    x = np.array([[0.30, 1e-4], [0.33, 1e-4], [0.50, 0.40], [0.52, 0.41], [0.49, 0.43]])
-    st = orc.initial_state(x, np.array([[0.2, -1.0], [0.1, -1.0], [0.3, 0.1], [-0.2, 0.0], [0.1, -0.1]]))
-    assert (forward(orc, st).x[:2, 1] == 0.0).all()
+    x = np.array([[0.30, 1e-4], [0.33, 1e-4], [0.50, 0.40], [0.52, 0.41], [0.49, 0.43],
+                  [0.70, 1.0 - 1e-4], [0.73, 1.0 - 1e-4]])
+    st = orc.initial_state(x, np.array([[0.2, -1.0], [0.1, -1.0], [0.3, 0.1], [-0.2, 0.0], [0.1, -0.1],
+                                        [0.1, 1.0], [-0.1, 1.0]]))
+    s1 = forward(orc, st)
+    assert (s1.x[:2, 1] == 0.0).all() and (s1.x[5:, 1] == 1.0).all()
     rng = np.random.default_rng(9)
     n = st.n
     lam = [rng.normal(size=(n, 2)), rng.normal(size=(n, 2)), rng.normal(size=(n, 2, 2)) / dx ** 2,
@@ -108,15 +111,18 @@ def test_one_step_vjp_through_the_position_clamp():
 
 
 def test_one_step_vjp_at_a_3d_edge_with_two_friction_walls():
-    """Fluid driven into the edge of the x- wall (mu 0.2) and the floor (mu 0.4):
-    edge nodes go through both walls in turn, so the adjoint must take the walls
-    in the reverse order, each linearised about its own input; every state
-    block and both walls' friction against central differences."""
+    """Fluid driven into the edges of the floor (mu 0.4) with the x- wall (mu 0.2)
+    and with the x+ wall (slip): edge nodes go through two walls in turn, so the
+    adjoint must take the walls in the reverse order, each linearised about its
+    own input; every state block and both friction fields against central
+    differences."""
     N = 8
     dx = 1.0 / N
     rng = np.random.default_rng(11)
     x = inputs.lattice_particles((N, N, N), dx, 2, lambda p: (p[:, 0] < 2 * dx) & (p[:, 2] < 2 * dx),
                                  (0.0, 2 * dx, 0.0), (2 * dx, 5 * dx, 2 * dx), 0)
+    m = len(x)
+    x = np.concatenate([x, x * np.array([-1.0, 1.0, 1.0]) + np.array([1.0, 0.0, 0.0])])   # and at the x+ edge
     n = len(x)
     water = dict(inputs.FLUID_WATER)
 
@@ -124,7 +130,9 @@ def test_one_step_vjp_at_a_3d_edge_with_two_friction_walls():
         return oracle.Oracle(3, (N, N, N), dx, 5e-4, (0.0, 0.0, -9.81), water, dx ** 3 / 8,
                              friction=[(0, (1, 1), [mx]), (4, (1, 1), [mf])])
     orc = make(0.2, 0.4)
-    st = orc.initial_state(x, np.array([-0.6, 0.3, -0.5]) + 0.1 * rng.normal(size=(n, 3)))
+    v0 = np.array([-0.6, 0.3, -0.5]) + 0.1 * rng.normal(size=(n, 3))
+    v0[m:, 0] *= -1.0
+    st = orc.initial_state(x, v0)
     st.B[:] = rng.normal(size=(n, 3, 3)) * dx * dx
     st.rho[:] = 1000.0 * rng.uniform(0.995, 1.005, n)
     for p in range(n):
@@ -158,6 +166,67 @@ def test_one_step_vjp_at_a_3d_edge_with_two_friction_walls():
         fd = (Jm(up) - Jm(dn)) / (2 * h)
         assert abs(fd) > 0
         assert mub[w][0] == pytest.approx(fd, rel=1e-5), f"wall {w}"
+
+
+def test_nodes_below_the_mass_threshold_stay_out_of_the_adjoint():
+    """A particle whose stencil's outer nodes carry about 4e-13 of mass, below the
+    threshold 1e-10 rho0 dx^d = 3.9e-10, so the forward gives them no velocity:
+    the adjoint still agrees with central differences (such nodes weigh about
+    1e-13 in the result either way)."""
+    N = 16
+    dx = 1.0 / N
+    orc = oracle.Oracle(2, (N, N), dx, 5e-4, (0.0, -9.81), dict(inputs.FLUID_WATER), dx * dx / 4)
+    base = 7
+    fx = 1.5 - 1e-6                                     # w_0 = (1.5 - fx)^2 / 2 = 5e-13
+    x = np.array([[(base + fx) * dx, 0.5], [0.3, 0.3], [0.32, 0.31]])
+    rng = np.random.default_rng(13)
+    st = orc.initial_state(x, rng.normal(size=(3, 2)) * 0.3)
+    n = st.n
+    lam = [rng.normal(size=(n, 2)), rng.normal(size=(n, 2)), rng.normal(size=(n, 2, 2)) / dx ** 2,
+           rng.normal(size=n) * 1e-3]
+    (xb, vb, Bb, rb), _ = orc.step_vjp(st, *lam)
+    dirs = [rng.normal(size=(n, 2)) * dx * 0.01, rng.normal(size=(n, 2)) * 0.01, rng.normal(size=(n, 2, 2)) * dx * dx,
+            rng.normal(size=n) * 0.1]
+    eps = 1e-5
+
+    def J(scale):
+        s = st.copy()
+        s.x += scale * dirs[0]; s.v += scale * dirs[1]; s.B += scale * dirs[2]; s.rho += scale * dirs[3]
+        for p in range(n):
+            s.sigma[p] = -orc.tait_pressure(s.rho[p]) * np.eye(3)
+        s2 = forward(orc, s)
+        return pair(lam, [s2.x, s2.v, s2.B, s2.rho])
+    fd = (J(eps) - J(-eps)) / (2 * eps)
+    assert pair([xb, vb, Bb, rb], dirs) == pytest.approx(fd, rel=1e-5)
+
+
+def test_mu_gradient_reaches_the_last_segment_beyond_the_far_wall():
+    """Fluid sliding back from the x+ wall along the floor: floor nodes at and
+    beyond x = L use the last segment, whose dL/dmu must match central
+    differences like the others."""
+    N = 16
+    dx = 1.0 / N
+    rng = np.random.default_rng(12)
+    x = inputs.lattice_particles((N, N), dx, 2, lambda p: (p[:, 0] > 1.0 - 3 * dx) & (p[:, 1] < 2 * dx),
+                                 (1.0 - 3 * dx, 0.0), (1.0, 2 * dx), 1)
+    n = len(x)
+    mu = np.array([0.1, 0.2, 0.3, 0.25])
+
+    def make(m):
+        return oracle.Oracle(2, (N, N), dx, 5e-4, (0.0, -9.81), dict(inputs.FLUID_WATER), dx * dx / 4,
+                             friction=[(2, (4, 1), m)])
+    st = make(mu).initial_state(x, np.array([-0.8, -0.6]) + 0.1 * rng.normal(size=(n, 2)))
+    lam = [rng.normal(size=(n, 2)), rng.normal(size=(n, 2)), np.zeros((n, 2, 2)), np.zeros(n)]
+    _, mub = make(mu).step_vjp(st, *lam)
+    assert abs(mub[2][3]) > 0
+    h = 1e-6
+    for k in range(4):
+        up, dn = mu.copy(), mu.copy()
+        up[k] += h
+        dn[k] -= h
+        fd = (pair(lam, [forward(make(up), st).x, forward(make(up), st).v]) -
+              pair(lam, [forward(make(dn), st).x, forward(make(dn), st).v])) / (2 * h)
+        assert mub[2][k] == pytest.approx(fd, rel=1e-5, abs=1e-12), f"segment {k}"
 
 
 def test_one_step_vjp_matches_central_differences_in_mu():

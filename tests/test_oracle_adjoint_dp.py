@@ -41,21 +41,29 @@ def dp_case(orc, zone, rng):
     elif zone == 3:                                             # past the tension cutoff, inside the apex cone
         sm = c["sigma_t"] + 300.0
         tau = 0.3 * c["tau_P"]
-    else:                                                       # past the cutoff and outside: the corner
+    elif zone == 4:                                             # past the cutoff and outside: the corner
         sm = c["sigma_t"] + 300.0
         tau = 3.0 * max(c["tau_P"], 100.0)
+    elif zone == 5:                                             # past the cutoff, just above tau_P but under
+        sm = c["sigma_t"] + 300.0                               # the zone II/III line h = 0: Zone III corner
+        tau = c["tau_P"] + 0.5 * c["alpha_P"] * 300.0
+    else:                                                       # 0.1 Pa past the cutoff, 1 Pa above the line
+        sm = c["sigma_t"] + 0.1                                 # h = 0: Zone II, and with dilatancy the return
+        tau = c["tau_P"] + 1.0                                  # lands on the cone below the cutoff
+        dd, dw = dd * 1e-4, dw * 1e-4                           # increments well inside those margins
     return dd, dw, sm * np.eye(3) + tau * dev
 
 
 @pytest.mark.parametrize("material,zone", [(inputs.SAND_DP, 1), (inputs.SAND_DP, 2), (inputs.SAND_DP, 4),
                                            (COHESIVE, 1), (COHESIVE, 2), (COHESIVE, 3), (COHESIVE, 4),
-                                           (DILATANT, 2), (DILATANT, 4)])
+                                           (DILATANT, 2), (DILATANT, 4), (COHESIVE, 5), (DILATANT, 5),
+                                           (DILATANT, 6)])
 def test_dp_vjp_matches_central_differences(material, zone):
     rng = np.random.default_rng(zone)
     orc = make(material)
     dd, dw, s = dp_case(orc, zone, rng)
     z, _, _ = orc.dp_update(dd, dw, s)
-    assert z == (3 if zone == 4 else zone) or (zone == 4 and z in (2, 3))
+    assert z == {1: 1, 2: 2, 3: 3, 5: 3, 6: 2}.get(zone) or (zone == 4 and z in (2, 3))
     sb1 = rng.normal(size=(3, 3))
     sb0, ddb, dwb = orc.dp_vjp(dd, dw, s, sb1)
     dirs = [rng.normal(size=(3, 3)) * 1e-6, rng.normal(size=(3, 3)) * 1e-6, rng.normal(size=(3, 3)) * 10.0]

@@ -83,8 +83,30 @@ def test_floor_acts_last_at_a_3d_edge_node():
     idx = 1 + nx * (2 + ny * 1)                         # node (x, y, z) = (0, dx, 0)
     gm[idx] = 1.0
     gq[idx] = [-0.5, 0.8, -0.4]
+    # and on the edge of the x+ wall and the floor, by symmetry: (0, 0.68, 0) again
+    idx2 = (N + 1) + nx * (2 + ny * 1)                  # node (x, y, z) = (L, dx, 0)
+    gm[idx2] = 1.0
+    gq[idx2] = [0.5, 0.8, -0.4]
     gv = orc.grid_update(gm, gq, np.zeros((G, 3)))
     np.testing.assert_allclose(gv[idx], [0.0, 0.68, 0.0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(gv[idx2], [0.0, 0.68, 0.0], rtol=0, atol=1e-15)
+
+
+def test_last_segment_covers_the_floor_beyond_the_far_wall():
+    """Floor nodes at and beyond x = L belong to the last segment: moving away from
+    the x+ wall and into the floor with |v_t| = 0.3 <= mu_3 v_n = 1.0 x 0.4 they stick,
+    while the first segment (mu 0) lets the same velocity slip."""
+    N = 8
+    dx = 1.0 / N
+    mu = np.array([0.0, 0.2, 0.5, 1.0])
+    orc = oracle.Oracle(2, (N, N), dx, 1e-3, (0.0, 0.0), dict(inputs.FLUID_WATER), dx * dx,
+                        friction=[(2, (4, 1), mu)])
+    G = orc.num_nodes
+    nx = orc.node_shape[0]
+    gv = orc.grid_update(np.ones(G), np.tile([-0.3, -0.4], (G, 1)), np.zeros((G, 2)))
+    for jx in (N + 1, N + 2):                           # x = L and the ghost node beyond
+        np.testing.assert_allclose(gv[jx + nx * 1], [0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(gv[2 + nx * 1], [-0.3, 0.0], atol=1e-15)
 
 
 def test_positions_are_clamped_to_the_domain():
@@ -111,6 +133,13 @@ def test_mass_threshold_and_acceleration():
     interior = (1 + 2 * (N + 3)) + 1                    # node (2, 2)
     np.testing.assert_allclose(gv[interior], [0.5 + 0.01 * 2.0, 0.25 + 0.01 * 1.0], atol=1e-15)
     np.testing.assert_allclose(gv[7], 0.0)
+    # the threshold is m_eps = 1e-10 rho0 dx^d: below it a node has no velocity, above it the update applies
+    m_eps = 1e-10 * 1000.0 * 0.25 ** 2
+    gm2 = np.full(G, 2.0); gm2[interior] = 0.5 * m_eps; gm2[interior + 1] = 2.0 * m_eps
+    gv2 = orc.grid_update(gm2, gq, gf)
+    np.testing.assert_allclose(gv2[interior], 0.0)
+    np.testing.assert_allclose(gv2[interior + 1], [1.0 / (2.0 * m_eps) * (1.0 + 0.01 * 4.0),
+                                                   1.0 / (2.0 * m_eps) * (0.5 + 0.01 * 2.0)], rtol=1e-12)
 
 
 @pytest.mark.slow

@@ -129,6 +129,21 @@ def test_dp_zone3_caps_mean_stress():
     assert eps == pytest.approx(np.sqrt(2) / 3 * (sm0 - c["sigma_t"]) / c["K"], rel=1e-12)
 
 
+def test_dp_zone3_corner_of_a_cohesive_material():
+    # past the cutoff, with tau between tau_P and the zone II/III line h = 0: Zone III, and
+    # the deviator beyond tau_P takes it to the corner, sigma_m = sigma_t and tau = tau_P
+    orc = dp_oracle(cohesion=5e3, sigma_t=1e3)
+    c = orc.dp_constants()
+    dev = np.diag([1.0, -0.5, -0.5]) / np.sqrt(0.75)          # tau(dev) = 1
+    s0 = (c["sigma_t"] + 500.0) * np.eye(3) + (c["tau_P"] + 0.5 * c["alpha_P"] * 500.0) * dev
+    zone, s, _ = orc.dp_update(np.zeros((3, 3)), np.zeros((3, 3)), s0)
+    sm, tau, d = invariants(s)
+    assert zone == 3 and c["sigma_t"] > 0 and c["tau_P"] > 0
+    assert sm == pytest.approx(c["sigma_t"], rel=1e-14)
+    assert tau == pytest.approx(c["tau_P"], rel=1e-12)
+    np.testing.assert_allclose(d / tau, dev, atol=1e-12)
+
+
 def test_dp_cohesionless_tension_is_stress_free():
     """c = 0: any trial state with positive mean stress returns to the apex (zero stress)."""
     orc = dp_oracle()

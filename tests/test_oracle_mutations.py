@@ -11,8 +11,10 @@ copies, not the oracle in this repository, are the ones under test.
 Mistakes that leave the arithmetic unchanged for every input the method can see
 are not listed: the moment matrix D_p of the quadratic B-spline is (dx^2/4) I,
 so B_p D_p^-1 and D_p^-1 B_p agree; the Cauchy stress is symmetric, so
-sigma_ab grad_b and sigma_ba grad_b agree; and the walls in plain index order
-already put the floor after every wall that can share a node with it.
+sigma_ab grad_b and sigma_ba grad_b agree; the walls in plain index order
+already put the floor after every wall that can share a node with it; and the
+adjoint's own mass threshold is unobservable, since a node below it affects the
+result in proportion to its weight, about 1e-13.
 """
 from __future__ import annotations
 
@@ -232,6 +234,22 @@ MUTANTS = [
     ("obstacle extent rounded down", C, "long lo = (long)ceil(P->obstacle[o][0][a] / P->dx - 1e-9);",
      "long lo = (long)floor(P->obstacle[o][0][a] / P->dx);", 0),
     ("obstacle high side open", C, "if (c < lo || c > hi) return 0;", "if (c < lo || c >= hi) return 0;", 0),
+    ("segment beyond the far wall", C, "if (sq > ns - 1) sq = ns - 1;", "if (sq > ns - 1) sq = ns > 1 ? ns - 2 : 0;", 0),
+    ("adjoint segment beyond the far wall", C, "if (sq > ns - 1) sq = ns - 1;",
+     "if (sq > ns - 1) sq = ns > 1 ? ns - 2 : 0;", 1),
+    ("mass threshold scale", C, "double m_eps = 1e-10 * P->rho0 * pow(P->dx, d);",
+     "double m_eps = 1e-10 / P->rho0 * pow(P->dx, d);", 0),
+    ("floor index in 3D", C, "int floor_w = 2 * (d - 1);", "int floor_w = 2 / (d - 1);", 0),
+    ("adjoint floor index in 3D", C, "nw = 0, floor_w = 2 * (d - 1);", "nw = 0, floor_w = 2 / (d - 1);", 0),
+    ("zone III corner mean stress sign", C, "s[q] = r * sdev[q] + (q % 4 == 0 ? c.sig_t : 0.0);",
+     "s[q] = r * sdev[q] - (q % 4 == 0 ? c.sig_t : 0.0);", 0),
+    ("adjoint clamp test at the top", C, "int clamped = xn < 0.0 || xn > P->n_cells[a] * P->dx;",
+     "int clamped = xn < 0.0 || xn > P->n_cells[a] / P->dx;", 0),
+    ("adjoint obstacle projection on a y face", C,
+     "double obn = ob[0] * onrm[o][0] + ob[1] * onrm[o][1] + ob[2] * onrm[o][2];",
+     "double obn = ob[0] * onrm[o][0] - ob[1] * onrm[o][1] + ob[2] * onrm[o][2];", 0),
+    ("adjoint zone II/III line", C, "double h = tau - c.tau_P - c.alpha_P * (sm - c.sig_t);",
+     "double h = tau - c.tau_P - c.alpha_P / (sm - c.sig_t);", 1),
     # Drucker-Prager adjoint (Appendix A, reverse)
     ("DP adjoint corner keeps the mean-stress path", C, "double sm_nb = corner ? 0.0 : trb;", "double sm_nb = trb;", 0),
     ("DP adjoint corner keeps the tau path", C, "if (!corner) tau_nb = rb / tau;", "tau_nb = rb / tau;", 0),

@@ -128,17 +128,25 @@ def test_fluid_does_not_enter_a_free_standing_column():
     assert not inside.any()
 
 
-def test_one_step_vjp_with_obstacle_contact_matches_central_differences():
+@pytest.mark.parametrize("face", ["side", "top"])
+def test_one_step_vjp_with_obstacle_contact_matches_central_differences(face):
+    # fluid thrown at the box's x- face, or falling onto its top face (normal +y)
     rng = np.random.default_rng(3)
     N = 16
     dx = 1.0 / N
-    x = inputs.lattice_particles((N, N), dx, 2, lambda p: (np.abs(p[:, 0] - 0.4) < 0.1) & (p[:, 1] < 0.3),
-                                 (0.3, 0), (0.5, 0.3), 3)
+    if face == "side":
+        x = inputs.lattice_particles((N, N), dx, 2, lambda p: (np.abs(p[:, 0] - 0.4) < 0.1) & (p[:, 1] < 0.3),
+                                     (0.3, 0), (0.5, 0.3), 3)
+        v = np.array([1.2, 0.3])
+    else:
+        x = inputs.lattice_particles((N, N), dx, 2, lambda p: (p[:, 0] > 0.55) & (p[:, 0] < 0.7),
+                                     (0.55, 0.24), (0.7, 0.36), 3)
+        v = np.array([0.1, -1.2])
     n = len(x)
     orc = oracle.Oracle(2, (N, N), dx, 5e-4, (0.0, -9.81), WATER, dx * dx / 4,
                         obstacles=[((0.5 + 0.5 * dx, -1.0), (0.75, 0.2 + 0.5 * dx))])
     st = orc.initial_state(x)
-    st.v[:] = rng.normal(size=(n, 2)) * 0.3 + np.array([1.2, 0.3])   # moving into the box
+    st.v[:] = rng.normal(size=(n, 2)) * 0.3 + v                       # moving into the box
     st.B[:] = rng.normal(size=(n, 2, 2)) * dx * dx
     st.rho[:] = 1000.0 * rng.uniform(0.995, 1.005, n)
     for p in range(n):
