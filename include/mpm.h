@@ -171,7 +171,9 @@ int mpm_set_particle_field(mpm_ctx *ctx, int field, const double *values);
  * axis order (n_seg[1] = 1 in 2D); mu holds batch * n_seg[1] * n_seg[0]
  * coefficients >= 0, row-major [sim][s1][s0].  A node at tangential coordinate
  * x_t belongs to segment floor(x_t / L_t * n_seg) clamped to [0, n_seg - 1].
- * Walls without a friction field are slip walls (mu = 0).
+ * Walls without a friction field are slip walls (mu = 0).  MPM_EINVAL for a
+ * wall out of range, a segment count outside 1..65536, or a negative or
+ * non-finite coefficient.
  */
 int mpm_set_friction_field(mpm_ctx *ctx, int wall, const int n_seg[2], const double *mu);
 
@@ -193,13 +195,19 @@ int mpm_set_friction_field(mpm_ctx *ctx, int wall, const int n_seg[2], const dou
 #define MPM_MAX_OBSTACLES 8
 int mpm_set_obstacles(mpm_ctx *ctx, int n_obstacles, const double *boxes);
 
-/* Queue n_steps explicit MPM steps on the context's stream (asynchronous). */
+/* Queue n_steps explicit MPM steps on the context's stream (asynchronous).
+ * MPM_EINVAL for n_steps < 0, MPM_ESTATE before any particles are loaded,
+ * MPM_ECUDA when a launch fails; a non-finite state or a bounded device wait
+ * that ran out is reported by the next synchronising call. */
 int mpm_step(mpm_ctx *ctx, int n_steps);
 
 /* Wait for queued work; returns MPM_ENAN if any particle state became non-finite. */
 int mpm_synchronize(mpm_ctx *ctx);
 
-/* Copy one particle field to host memory (load order, doubles); synchronises. */
+/* Copy one particle field to host memory (load order, doubles, the field's
+ * width per particle); synchronises.  MPM_EINVAL for a NULL buffer or an
+ * unknown field, MPM_ESTATE before any particles are loaded, and any status the
+ * queued steps recorded (MPM_ENAN, MPM_ETIMEOUT). */
 int mpm_get_particles(mpm_ctx *ctx, int field, double *out);
 
 /* Number of doubles per particle of a field (or a negative status). */
@@ -218,7 +226,9 @@ int mpm_last_error(const mpm_ctx *ctx, char *buf, int len);
  * at the start of mpm_step_adjoint) and the observed positions z_obs
  * (n_obs x n_track x dim, host).  The loss is
  *     L = sum_obs sum_l |x_{id_l}^{step} - z_obs|^2.
- * n_track = 0 clears them (the other arguments are then ignored).
+ * n_track = 0 clears them (the other arguments are then ignored).  MPM_EINVAL
+ * for an id out of range or repeated, or steps that are not >= 1 and
+ * increasing; MPM_ESTATE before any particles are loaded.
  */
 int mpm_set_observations(mpm_ctx *ctx, int n_track, const int64_t *ids, int n_obs, const int *steps,
                          const double *z_obs);
