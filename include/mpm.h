@@ -277,6 +277,11 @@ int mpm_monitor_means(mpm_ctx *ctx, int n_mon, const double *boxes, double *out)
  * checkpoint_every states with their grids (more with mpm_set_adjoint_memory),
  * plus in 3D single precision 21 reals per particle of scatter coefficients and
  * the sort tables of each sort generation the kept states span.
+ * MPM_EINVAL for n_steps or checkpoint_every < 1, a NULL loss_out (or a NULL
+ * dL_dmu_out with wall >= 0), a batch other than 1, a transfer other than APIC,
+ * a wall without a friction field, or an observation beyond n_steps;
+ * MPM_ESTATE before any particles or observations are set; MPM_ENOMEM when the
+ * checkpoints do not fit; and any status the steps recorded.
  */
 int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, double *loss_out,
                      double *dL_dmu_out);
@@ -309,7 +314,9 @@ int mpm_get_initial_adjoint(mpm_ctx *ctx, int field, double *out);
  * Device state slots (0..15): copy of the whole particle state (all fields, in
  * the current internal order).  mpm_restore_state puts it back; used to rerun
  * a trajectory from the same start (inversion loops).  Slots are freed with
- * the particles.
+ * the particles.  MPM_EINVAL for a slot out of range; MPM_ESTATE to save before
+ * any particles are loaded or to restore an empty slot (or one saved for
+ * another particle count).
  */
 int mpm_save_state(mpm_ctx *ctx, int slot);
 int mpm_restore_state(mpm_ctx *ctx, int slot);
