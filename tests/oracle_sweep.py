@@ -1,11 +1,12 @@
-"""Mechanical mutation sweeps of the C oracle (test infrastructure; not collected
+"""Mechanical mutation sweeps of the oracle (test infrastructure; not collected
 by pytest).  Each sweep changes one thing on every code line of
-oracle/mpm_oracle.c in a private copy, runs the oracle's pin suite on the copy
+oracle/mpm_oracle.c (or oracle/mlp.py) in a private copy, runs the oracle's pin suite on the copy
 and lists the copies that still pass:
 
     python tests/oracle_sweep.py ops      # swap the first binary +, -, * of a line
     python tests/oracle_sweep.py consts   # move the first literal 0.5 ... 9.0 of a line
     python tests/oracle_sweep.py index    # transpose the first index pair of a line
+    python tests/oracle_sweep.py mlp      # swap +, -, *, / or drop a .T in oracle/mlp.py
 
 Survivors are either equivalent (they cannot change any result) or a missing
 pin; tests/test_oracle_mutations.py keeps a representative copy of every
@@ -32,8 +33,21 @@ INDEX = (("[a * d + b]", "[b * d + a]"), ("[b * d + a]", "[a * d + b]"), ("[i * 
          ("[k * d + j]", "[j * d + k]"))
 
 
+MLP_OPS = ((" + ", " - "), (" - ", " + "), (" * ", " / "), (" / ", " * "), (".T", ""))
+
+
 def mutants(lines, kind):
     out = []
+    if kind == "mlp":
+        for i, line in enumerate(lines):
+            s = line.strip()
+            if not s or s.startswith(("#", '"""', "def ", "import", "from")):
+                continue
+            for old, new in MLP_OPS:
+                k = line.find(old)
+                if k >= 0:
+                    out.append((i, old, new, k))
+        return out
     for i, line in enumerate(lines):
         s = line.strip()
         if not s or s.startswith(("/*", "*", "//", "#")):
@@ -58,7 +72,9 @@ def mutants(lines, kind):
 
 
 def run(kind: str, workers: int = 8):
-    src = open(os.path.join(harness.ROOT, "oracle", "mpm_oracle.c")).read()
+    fname = "mlp.py" if kind == "mlp" else "mpm_oracle.c"
+    pins = harness.MLP_PINS if kind == "mlp" else harness.C_PINS
+    src = open(os.path.join(harness.ROOT, "oracle", fname)).read()
     lines = src.split("\n")
     muts = mutants(lines, kind)
 
@@ -68,10 +84,10 @@ def run(kind: str, workers: int = 8):
         mutated[i] = mutated[i][:k] + new + mutated[i][k + len(old):]
         with tempfile.TemporaryDirectory(prefix="oracle_sweep_") as tmp:
             base = harness._tree(os.path.join(tmp, "b"))
-            with open(os.path.join(base, "oracle", "mpm_oracle.c"), "w") as fh:
+            with open(os.path.join(base, "oracle", fname), "w") as fh:
                 fh.write("\n".join(mutated))
             try:
-                rc = harness._run(base, harness.C_PINS).returncode
+                rc = harness._run(base, pins).returncode
             except RuntimeError:
                 rc = "no build"
         return i, old, rc
