@@ -175,8 +175,29 @@ def run_oracle_steps(n_particles: int, steps: int, warmup: int = 0):
     return time.perf_counter() - t0
 
 
+def host_cpu() -> dict:
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline_full_step():
-    """The oracle on one full step of the whole 2.76M-particle workload."""
+    """The oracle on one full step of the whole 2.76M-particle workload: the serial
+    build as it stands, and its OpenMP build on every host core."""
     import oracle
     from paper_2507_04192_gb300 import inputs
     w = inputs.granular_cylinder_3d()
@@ -185,16 +206,32 @@ def cpu_baseline_full_step():
     t0 = time.perf_counter()
     orc.step(st, 1)
     dt = time.perf_counter() - t0
-    return {"value": w.n / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 full step of all {w.n} particles on the 256x256x128 grid, FP64, single thread, "
-                      f"{dt:.1f} s"}
+    host = host_cpu()
+    out = {"value": w.n / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"1 full step of all {w.n} particles on the 256x256x128 grid, FP64, single thread, "
+                     f"{dt:.1f} s", "host": host}
+    try:
+        threads = os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+        st = orc.initial_state(w.x)
+        t0 = time.perf_counter()
+        orc.step(st, 1, omp=True)
+        dto = time.perf_counter() - t0
+        out["openmp"] = {"value": w.n / dto, "unit": "particle-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "sample": f"the same step, OpenMP build of the oracle (particle-parallel transfers with "
+                                   f"atomic grid sums, node-parallel grid update), {dto:.2f} s"}
+    except Exception as e:          # no OpenMP runtime on the host: the serial figure stands alone
+        out["openmp"] = {"unavailable": str(e).splitlines()[0][:200]}
+    return out
 
 
 def workload_config(world: int) -> dict:
     """The headline workload (the same object on both arms)."""
     return {"workload": WORKLOAD, "particles": 2761536, "grid": "256x256x128", "precision": "fp32",
             "material": "drucker_prager", "sort_every": 32, "parallelism": f"replicas{world}",
-            "l2": "inputs larger than L2 (353 MB particle state per step)"}
+            "l2": "inputs larger than L2 (353 MB particle state per step)",
+            "sort": "the timed window starts with a sort (keys, radix passes, tiles, state permutation), "
+                    "so every window holds at least one"}
 
 
 def bench_reference(args):
@@ -216,7 +253,8 @@ def bench_reference(args):
             "config": workload_config(world),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: the first {n} particles of the 2.76M-particle cylinder "
-                                       f"(bottom layers) on a grid cropped around them, FP64, single thread"},
+                                       f"(bottom layers) on a grid cropped around them, FP64, single thread",
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -436,7 +474,11 @@ def bench_ours(args):
         torch.cuda.synchronize(dev)
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
-        l0 = sim.stats()["launches"]
+        st0 = sim.stats()
+        # the window starts with a sort: whatever --steps is, one sort (the full state
+        # permutation included) is amortised over the timed steps, at least its share
+        # 1/sort_every of a long run
+        mpm.mpm_request_sort(sim.ctx)
         start.record(stream)
         sim.step(steps)
         end.record(stream)
@@ -444,24 +486,26 @@ def bench_ours(args):
         barrier()
         ms = start.elapsed_time(end)
         sim.synchronize()
-        launches = sim.stats()["launches"] - l0
+        st1 = sim.stats()
+        launches = st1["launches"] - st0["launches"]
+        sorts = st1["sorts"] - st0["sorts"]
         ktimes = {k: mpm.mpm_get_timing(sim.ctx, k) for k in mpm.KERNELS} if timing else None
         sim.close()
-        return ms, launches, ktimes
+        return ms, launches, ktimes, sorts
 
     # FP32 headline (clean timed region), with clocks sampled during it
     sampler = ClockSampler(local)
-    ms32, launches, _ = timed_run(mpm.MPM_FP32, args.steps, args.warmup)
+    ms32, launches, _, sorts = timed_run(mpm.MPM_FP32, args.steps, args.warmup)
     clocks = sampler.stop()
     # a throttled or clock-locked region is measured once more (every rank takes the same decision)
     if max_over_ranks(1.0 if clocks_rejected(clocks) else 0.0, dev) > 0.0:
         sampler = ClockSampler(local)
-        ms32, launches, _ = timed_run(mpm.MPM_FP32, args.steps, args.warmup)
+        ms32, launches, _, sorts = timed_run(mpm.MPM_FP32, args.steps, args.warmup)
         clocks = sampler.stop()
         if clocks is not None:
             clocks["remeasured"] = True
     # per-kernel device times (library CUDA events on the launch stream), same workload
-    _, _, kt = timed_run(mpm.MPM_FP32, args.steps, 3, timing=True)
+    _, _, kt, _ = timed_run(mpm.MPM_FP32, args.steps, 3, timing=True)
     # FP64 mode, fewer steps
     steps64 = max(1, min(args.steps, 200))
     ms64 = timed_run(mpm.MPM_FP64, steps64, 3)[0] if not args.no_fp64 else float("nan")
@@ -532,6 +576,7 @@ def bench_ours(args):
                     "h2d_bytes_per_step": n * 3 * 8 / args.steps, "d2h_bytes_per_step": n * 3 * 8 / args.steps,
                     "note": "one mpm_load_particles from host, K steps, one mpm_get_particles to host"},
             "gpu_launches": launches,
+            "sorts_in_window": sorts,
             "clocks": clocks,
         }
         line.update(extra)

@@ -47,7 +47,7 @@ typedef enum {
     MPM_ECUDA = -3,      /* a CUDA runtime call failed */
     MPM_ENAN = -4,       /* a particle state became non-finite */
     MPM_EDOMAIN = -5,    /* a particle index left the grid (never expected: positions are clamped) */
-    MPM_ETIMEOUT = -6,   /* a bounded host wait ran out */
+    MPM_ETIMEOUT = -6,   /* a bounded device wait ran out */
     MPM_ECORRUPT = -7,   /* a state blob failed its checksum */
     MPM_ESTATE = -8      /* call not valid in the context's current state */
 } mpm_status;
@@ -200,6 +200,52 @@ int mpm_set_obstacles(mpm_ctx *ctx, int n_obstacles, const double *boxes);
  * MPM_ECUDA when a launch fails; a non-finite state or a bounded device wait
  * that ran out is reported by the next synchronising call. */
 int mpm_step(mpm_ctx *ctx, int n_steps);
+
+/*
+ * Sort the particles by cell at the start of the next step, whatever the sort
+ * interval says (the interval restarts there).  The sort is an internal
+ * reordering (not part of the paper's method, which scatters unsorted
+ * particles, Sec. 3.3.1): results depend on it only through the rounding of
+ * the summation order.  MPM_EINVAL for a NULL context.
+ */
+int mpm_request_sort(mpm_ctx *ctx);
+
+/*
+ * Conservation sums of the particle-to-grid transfer (Sec. 2.2: the grid mass
+ * m_i of Eq. update_m and the momentum q_i + dt f_i of Eq. semi before the grid
+ * update).  With enable != 0, every later step also sums, on the device and in
+ * double precision, the grid values the transfer produced and the particle
+ * state it read; mpm_get_diagnostics copies the sums of the last such step
+ * (synchronises) into out[0 .. n) (n <= MPM_DIAG_COUNT):
+ *   out[0]     sum_i m_i over every grid node (all simulations of a batch)
+ *   out[1..3]  sum_i (q_i + dt f_i), components beyond dim are 0
+ *   out[4]     sum_p m_p of the particles
+ *   out[5..7]  sum_p m_p v_p
+ *   out[8]     grid nodes with a non-finite mass or momentum value
+ *   out[9]     particles with a non-finite position or velocity
+ *   out[10]    sum_i of |q_i + dt f_i| summed over its components (the scale
+ *              of the rounding of out[1..3])
+ * The B-spline weights form a partition of unity with linear reproduction and
+ * sum_i grad w_ip = 0 (Sec. 2.1), so out[0] = out[4] and out[1..3] = out[5..7]
+ * up to rounding.  Enabling costs one extra kernel per step and a reduction in
+ * the grid update.  MPM_EINVAL for bad arguments, MPM_ENOMEM when the 88-byte
+ * device buffer cannot be allocated, MPM_ESTATE when no step has run with the
+ * sums enabled.
+ */
+#define MPM_DIAG_COUNT 11
+int mpm_set_diagnostics(mpm_ctx *ctx, int enable);
+int mpm_get_diagnostics(mpm_ctx *ctx, double *out, int n);
+
+/*
+ * Test hook of the error paths (not part of the method): flags =
+ * MPM_DEBUG_WITHHOLD_WINDOW_COPY makes the grid-to-particle kernel arm no copy
+ * for its shared-memory grid window, so that its bounded device wait (about one
+ * second) runs out with no copy in flight; the next synchronising call then
+ * returns MPM_ETIMEOUT and the particle state is left partly updated.  0 turns
+ * the hook off.  MPM_EINVAL for an unknown flag.
+ */
+#define MPM_DEBUG_WITHHOLD_WINDOW_COPY 1
+int mpm_set_debug(mpm_ctx *ctx, int flags);
 
 /* Wait for queued work; returns MPM_ENAN if any particle state became non-finite. */
 int mpm_synchronize(mpm_ctx *ctx);
@@ -363,9 +409,9 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  * One explicit step that allocates no memory (the paper has no counterpart:
  * this is a deployment entry point of this library).
  *
- * For callers that cannot call cudaMalloc: code running while a stream is
- * captured into a CUDA graph, plugins inside an application that owns all
- * device memory, real-time loops that must not enter the allocator.  The
+ * For callers that cannot call cudaMalloc: plugins inside an application that
+ * owns all device memory, and real-time loops that must not enter the
+ * allocator (cudaMalloc may synchronise the device and take unbounded time).  The
  * particle state comes in and goes out through caller-owned device buffers
  * (layouts as for mpm_get_particles, doubles, n particles); the only scratch,
  * the background grid, lives in a static device array of this library holding
@@ -377,8 +423,12 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  *
  * Rules: the call queues its kernels on cuda_stream (NULL = the legacy default
  * stream) and returns without waiting.  The first call on each device resolves
- * the device address of the static scratch (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call on a device shares the
+ * the device address of the static scratch (cudaGetSymbolAddress) and loads
+ * the four kernels (cudaFuncGetAttributes, so that lazy module loading takes no
+ * memory at a later launch); make that first call before any stream capture.
+ * The address is kept per device ordinal for the life of the process: it is
+ * valid in the device's primary context (the runtime's) only, and not after a
+ * cudaDeviceReset.  Every call on a device shares the
  * scratch and clears it before use, so calls whose work overlaps on the GPU
  * race: serialise them.  A grid of more than 131072 nodes ((N_x + 3)(N_y + 3)
  * [(N_z + 3)]) is rejected with MPM_EINVAL, and so are the parameters that

@@ -23,8 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libmpm_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libmpm_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 MAX_WALLS = 6
 MAX_OBSTACLES = 8
@@ -60,50 +62,65 @@ class Params(C.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into ``oracle/_build`` (idempotent)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build`` (idempotent).
+
+    omp=True builds the OpenMP variant of the same source (particle-parallel
+    transfers with atomic grid sums, node-parallel grid update): a timing
+    baseline only, whose sums vary in rounding with the thread schedule.  The
+    checks use the serial build."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            return out
         os.makedirs(_BUILD, exist_ok=True)
-        tmp = _LIB + f".{os.getpid()}.tmp"
+        tmp = out + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               _SRC, "-o", tmp, "-lm"]
+               *(["-fopenmp"] if omp else []), _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        os.replace(tmp, out)
+        return out
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = C.CDLL(build(omp=True))
+            _declare(_lib_omp)
+        return _lib_omp
     if _lib is None:
         _lib = C.CDLL(build())
-        d, p, i, l = C.c_double, C.c_void_p, C.c_int, C.c_long
-        P = C.POINTER(Params)
-        sig = {
-            "orc_phi_bar": (d, [d]),
-            "orc_dphi_bar": (d, [d]),
-            "orc_num_nodes": (l, [P]),
-            "orc_particle_mass": (d, [P]),
-            "orc_p2g": (None, [P, l, p, p, p, p, p, p, p, p]),
-            "orc_grid_update": (None, [P, p, p, p, p]),
-            "orc_g2p": (None, [P, l, p, p, p, p, p, p, p, p]),
-            "orc_step": (i, [P, l, p, p, p, p, p, p, p, i]),
-            "orc_friction": (None, [p, p, d, p]),
-            "orc_dp_update": (i, [P, p, p, p, p]),
-            "orc_dp_constants": (None, [P, p]),
-            "orc_tait_pressure": (d, [P, d]),
-            "orc_affine_C": (None, [P, l, p, p, p]),
-            "orc_step_vjp": (i, [P, l] + [p] * 16),
-            "orc_dp_vjp": (None, [P, p, p, p, p, p, p, p]),
-            "orc_obstacle_normal": (i, [P, i, p, p]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(_lib, name)
-            f.restype = res
-            f.argtypes = args
+        _declare(_lib)
     return _lib
+
+
+def _declare(lib_):
+    d, p, i, l = C.c_double, C.c_void_p, C.c_int, C.c_long
+    P = C.POINTER(Params)
+    sig = {
+        "orc_phi_bar": (d, [d]),
+        "orc_dphi_bar": (d, [d]),
+        "orc_num_nodes": (l, [P]),
+        "orc_particle_mass": (d, [P]),
+        "orc_p2g": (None, [P, l, p, p, p, p, p, p, p, p]),
+        "orc_grid_update": (None, [P, p, p, p, p]),
+        "orc_g2p": (None, [P, l, p, p, p, p, p, p, p, p]),
+        "orc_step": (i, [P, l, p, p, p, p, p, p, p, i]),
+        "orc_friction": (None, [p, p, d, p]),
+        "orc_dp_update": (i, [P, p, p, p, p]),
+        "orc_dp_constants": (None, [P, p]),
+        "orc_tait_pressure": (d, [P, d]),
+        "orc_affine_C": (None, [P, l, p, p, p]),
+        "orc_step_vjp": (i, [P, l] + [p] * 16),
+        "orc_dp_vjp": (None, [P, p, p, p, p, p, p, p]),
+        "orc_obstacle_normal": (i, [P, i, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib_, name)
+        f.restype = res
+        f.argtypes = args
 
 
 def _ptr(a: np.ndarray):
@@ -203,8 +220,8 @@ class Oracle:
         lib().orc_g2p(C.byref(self.P), st.n, _ptr(gv), _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.F),
                       _ptr(st.rho), _ptr(st.sigma), _ptr(st.eps))
 
-    def step(self, st: "State", n_steps: int = 1):
-        rc = lib().orc_step(C.byref(self.P), st.n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.F),
+    def step(self, st: "State", n_steps: int = 1, omp: bool = False):
+        rc = lib(omp).orc_step(C.byref(self.P), st.n, _ptr(st.x), _ptr(st.v), _ptr(st.B), _ptr(st.F),
                             _ptr(st.rho), _ptr(st.sigma), _ptr(st.eps), int(n_steps))
         if rc != 0:
             raise MemoryError("oracle grid allocation failed")

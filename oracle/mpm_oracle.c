@@ -203,8 +203,11 @@ void orc_p2g(const orc_params *P, long n, const double *x, const double *v, cons
 {
     int d = P->dim;
     double mp = orc_particle_mass(P);
-    stencil_t S;
+    /* The pragmas take effect only in the OpenMP build of this file (a timing
+       baseline); the build the checks use is serial and ignores them. */
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
+        stencil_t S;
         const double *xp = x + p * d;
         const double *vp = v + p * d;
         const double *Bp = B + p * d * d;
@@ -222,15 +225,18 @@ void orc_p2g(const orc_params *P, long n, const double *x, const double *v, cons
         for (int k = 0; k < S.count; ++k) {
             long i = S.node[k];
             double phi = S.phi[k];
+#pragma omp atomic
             gm[i] += mp * phi;                          /* Eq. update_m */
             for (int a = 0; a < d; ++a) {
                 double aff = 0.0;
                 for (int b = 0; b < d; ++b) aff += M[a * d + b] * (S.xi[k][b] - xp[b]);
+#pragma omp atomic
                 gq[i * d + a] += phi * mp * (vp[a] + aff);
             }
             for (int a = 0; a < d; ++a) {
                 double fint = 0.0;
                 for (int b = 0; b < d; ++b) fint += S.grad[k][b] * sp[b * 3 + a];
+#pragma omp atomic
                 gf[i * d + a] += -Vp * fint + phi * mp * P->gravity[a];
             }
         }
@@ -344,6 +350,7 @@ void orc_grid_update(const orc_params *P, const double *gm, const double *gq, co
     int floor_w = 2 * (d - 1);
     for (int w = 0; w < 2 * d; ++w) if (w != floor_w) order[nw++] = w;
     order[nw++] = floor_w;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < G; ++i) {
         int j[3] = {0, 0, 0};
         long r = i;
@@ -602,8 +609,9 @@ void orc_g2p(const orc_params *P, long n, const double *gv, double *x, double *v
 {
     int d = P->dim;
     double dt = P->dt;
-    stencil_t S;
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
+        stencil_t S;
         double *xp = x + p * d;
         build_stencil(P, xp, &S);
         double vp[3] = {0.0, 0.0, 0.0}, Bp[9] = {0.0}, L[9] = {0.0};

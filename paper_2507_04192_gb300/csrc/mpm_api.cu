@@ -14,6 +14,7 @@
 #include "mpm_adjoint.cuh"
 
 using namespace mpm;
+static_assert(MPM_DIAG_COUNT == kDiagCount, "diagnostics slots");
 
 struct PendingTiming {
     int kernel;
@@ -88,6 +89,8 @@ struct mpm_ctx {
     const AdjOps *aops = nullptr;
     StateSlot slots[kMaxSlots];
     int64_t adj_budget = 0;            // device bytes the adjoint may use to keep more than one segment
+    double *diag_buf = nullptr;        // conservation sums (allocated by mpm_set_diagnostics)
+    bool diag_valid = false;           // a step has run with the sums enabled
 };
 
 namespace {
@@ -478,7 +481,7 @@ void mpm_destroy(mpm_ctx *c)
     free_particles(c);
     dfree(d.A); dfree(d.V); dfree(d.A2); dfree(d.V2); dfree(d.flags); dfree(d.node_list);
     dfree(d.tile_start); dfree(d.tile_end);
-    dfree(d.counters); dfree(d.status); dfree(d.escaped);
+    dfree(d.counters); dfree(d.status); dfree(d.escaped); dfree(c->diag_buf);
     for (int w = 0; w < kMaxWalls; ++w) dfree(d.mu_dev[w]);
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
@@ -658,6 +661,12 @@ int step_many(mpm_ctx *c, int n_steps)
             int rc = do_sort(c);
             if (rc != MPM_OK) return rc;
         }
+        if (c->ds.diag != nullptr) {           // conservation sums of this step: cleared, then the particles
+            CK(cudaMemsetAsync(c->ds.diag, 0, sizeof(double) * kDiagCount, c->ds.stream), "diagnostics clear");
+            c->ops->diag_particles(c->hp, c->ds);
+            c->launches++;
+            c->diag_valid = true;
+        }
         {
             TimingScope ts(c, MPM_KERNEL_P2G);
             c->ops->p2g(c->hp, c->ds);
@@ -687,6 +696,48 @@ int mpm_step(mpm_ctx *c, int n_steps)
     if (!c || n_steps < 0) return fail(c, MPM_EINVAL, "mpm_step: bad argument");
     if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step: no particles loaded");
     return step_many(c, n_steps);
+}
+
+int mpm_request_sort(mpm_ctx *c)
+{
+    if (!c) return MPM_EINVAL;
+    c->need_sort = true;
+    return MPM_OK;
+}
+
+int mpm_set_diagnostics(mpm_ctx *c, int enable)
+{
+    if (!c) return MPM_EINVAL;
+    if (enable) {
+        if (c->diag_buf == nullptr) {
+            int rc = dalloc(c, &c->diag_buf, kDiagCount, "diagnostics");
+            if (rc != MPM_OK) return rc;
+            CK(cudaMemsetAsync(c->diag_buf, 0, sizeof(double) * kDiagCount, c->ds.stream), "diagnostics clear");
+        }
+        c->ds.diag = c->diag_buf;
+    } else {
+        c->ds.diag = nullptr;
+    }
+    return MPM_OK;
+}
+
+int mpm_get_diagnostics(mpm_ctx *c, double *out, int n)
+{
+    if (!c || !out || n < 0) return fail(c, MPM_EINVAL, "mpm_get_diagnostics: bad argument");
+    if (!c->diag_valid || c->diag_buf == nullptr)
+        return fail(c, MPM_ESTATE, "mpm_get_diagnostics: no step has run with the diagnostics enabled");
+    double h[kDiagCount];
+    CK(cudaMemcpyAsync(h, c->diag_buf, sizeof(h), cudaMemcpyDeviceToHost, c->ds.stream), "diagnostics read");
+    CK(cudaStreamSynchronize(c->ds.stream), "diagnostics read");
+    for (int i = 0; i < n && i < kDiagCount; ++i) out[i] = h[i];
+    return MPM_OK;
+}
+
+int mpm_set_debug(mpm_ctx *c, int flags)
+{
+    if (!c || (flags & ~kDebugWithholdWindowCopy) != 0) return fail(c, MPM_EINVAL, "mpm_set_debug: unknown flag");
+    c->hp.debug = flags;
+    return MPM_OK;
 }
 
 int mpm_synchronize(mpm_ctx *c)
@@ -984,6 +1035,9 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         a.gen_cap = gens;
     }
     if (!a.allocated) {
+        // a failed earlier attempt may have left some of these allocated
+        dfree(a.lam[0]); dfree(a.lam[1]); dfree(a.grid.GVB); dfree(a.grid.GAB);
+        dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim); dfree(a.lam_id); dfree(a.lam_pos);
         int rc = MPM_OK;
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[0], st_bytes, "adjoint state");
         if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[1], st_bytes, "adjoint state");

@@ -76,6 +76,7 @@ struct HostParams {
     int64_t n, npad;
     int ncomp, off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
     Obstacles obs;
+    int debug;                    // kDebug* bits (test hooks of the error paths)
 };
 
 template <class R>
@@ -95,6 +96,8 @@ struct Params {
     int off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
     WallDev wall[kMaxWalls];
     Obstacles obs;
+    double *diag;                 // conservation sums of the step (nullptr = off), see kDiag*
+    int debug;
 };
 
 template <class R> struct R4 { R x, y, z, w; };
@@ -132,6 +135,7 @@ struct DevState {
     int32_t *save_L = nullptr;    // ... and the list of node tiles it updated ([0] count, then the tiles)
     void *save_S = nullptr;       // when set, P2G copies the components it reads (x, v, C, rho [, sigma])
                                   // of every particle here, in slot order (save_S[c n + slot])
+    double *diag = nullptr;       // kDiagCount doubles: conservation sums of the last step (when enabled)
     CUtensorMap tmap_V;           // TMA descriptor of V: (4, G_x, G_y, [G_z], batch)
     void *mu_dev[kMaxWalls];
     int n_seg[kMaxWalls][2];
@@ -139,6 +143,18 @@ struct DevState {
 };
 
 enum StatusBits { kStatusNaN = 1, kStatusChunkOverflow = 2, kStatusTimeout = 4 };
+
+// Test hooks (HostParams::debug): kDebugWithholdWindowCopy makes G2P arm no copy
+// for its grid window, so that its bounded wait runs out with nothing in flight.
+enum DebugBits { kDebugWithholdWindowCopy = 1 };
+
+// Slots of the conservation sums (DevState::diag), all in double precision:
+// grid mass, grid momentum (3), particle mass, particle momentum (3), non-finite
+// grid values, non-finite particle values, sum of |momentum components| on the grid.
+enum DiagSlots {
+    kDiagGridMass = 0, kDiagGridMom = 1, kDiagPartMass = 4, kDiagPartMom = 5, kDiagGridNonFinite = 8,
+    kDiagPartNonFinite = 9, kDiagGridAbsMom = 10, kDiagCount = 11
+};
 
 // Launchers implemented per precision (mpm_kernels_f32.cu, mpm_kernels_f64.cu).
 struct Ops {
@@ -150,6 +166,7 @@ struct Ops {
     void (*g2p)(const HostParams &, DevState &);
     void (*get_field)(const HostParams &, DevState &, int field, double *out_dev);
     void (*set_field)(const HostParams &, DevState &, int field, const double *in_dev);
+    void (*diag_particles)(const HostParams &, DevState &);
 };
 extern const Ops ops_f32;
 extern const Ops ops_f64;

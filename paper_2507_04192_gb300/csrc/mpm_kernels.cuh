@@ -144,13 +144,50 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
                  : "memory");
     return ok != 0u;
 }
-// Bounded wait: false after kMaxWaitIters unsuccessful polls.
-constexpr int kMaxWaitIters = 1 << 20;
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false once about one second has passed (device global timer) or
+// after kMaxWaitIters unsuccessful polls, whichever comes first.  A copy that
+// completes normally takes microseconds.
+constexpr int kMaxWaitIters = 1 << 24;
+constexpr uint64_t kMaxWaitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
 {
-    for (int it = 0; it < kMaxWaitIters; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (int it = 1; it < kMaxWaitIters; ++it) {
         if (mbar_try_wait(bar, phase)) return true;
+        if ((it & 255) == 0 && globaltimer_ns() - t0 > kMaxWaitNs) return false;
+    }
     return false;
+}
+
+// Adds the block-wide sums of v[0..K) to out[slot[k]] (double atomics from one
+// thread).  Every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ void block_sum_add(double (&v)[K], double *out, const int (&slot)[K])
+{
+    __shared__ double red[32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0 && t != 0.0) atomicAdd(out + slot[k], t);
+        }
+    }
 }
 // TMA tiled load of the grid window of one tile: coordinates (component, node x, y, [z], sim).
 __device__ __forceinline__ void tma_load_window(void *dst, const CUtensorMap *map, const int org[3], int sim,
@@ -954,6 +991,8 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
     using Gm = Geo<D>;
     const int n_list = *count;
     if (saveL != nullptr && blockIdx.x == 0 && threadIdx.x == 0) saveL[0] = n_list;
+    // conservation sums (P.diag set): mass, momentum (q + dt f), non-finite values, sum of |q|
+    double dsum[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
     const int64_t ut = list[li];
     if (saveL != nullptr && threadIdx.x == 0) saveL[1 + li] = (int32_t)ut;
@@ -983,6 +1022,14 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
         const R4<R> acc = As[idx];
         if (acc.x == R(0) && acc.y == R(0) && acc.z == R(0) && acc.w == R(0)) continue;
         As[idx] = R4<R>{R(0), R(0), R(0), R(0)};
+        if (P.diag != nullptr) {
+            dsum[0] += (double)acc.x;
+            dsum[1] += (double)acc.y;
+            dsum[2] += (double)acc.z;
+            dsum[3] += (double)acc.w;
+            dsum[4] += (rfinite(acc.x) && rfinite(acc.y) && rfinite(acc.z) && rfinite(acc.w)) ? 0.0 : 1.0;
+            dsum[5] += fabs((double)acc.y) + fabs((double)acc.z) + fabs((double)acc.w);
+        }
         R vel[3] = {R(0), R(0), R(0)};
         if (acc.x > P.m_eps) {
             const R inv_m = R(1) / acc.x;
@@ -1028,6 +1075,34 @@ __global__ void __launch_bounds__(256) k_grid(const Params<R> P, R4<R> *__restri
     }
     if (threadIdx.x == 0) flags[ut] = 0u;
     }
+    if (P.diag != nullptr) {
+        constexpr int slots[6] = {kDiagGridMass, kDiagGridMom, kDiagGridMom + 1, kDiagGridMom + 2, kDiagGridNonFinite,
+                                  kDiagGridAbsMom};
+        block_sum_add<6>(dsum, P.diag, slots);
+    }
+}
+
+// Conservation sums of the particles the next P2G reads (P.diag set): total mass,
+// momentum sum m_p v_p and the count of particles with a non-finite x or v.
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_diag_particles(const Params<R> P, const R *__restrict__ S)
+{
+    double dsum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const double mp = (double)P.mass;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n; p += (int64_t)gridDim.x * blockDim.x) {
+        bool fin = true;
+        dsum[0] += mp;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R v = S[(int64_t)(P.off_v + a) * P.npad + p];
+            const R x = S[(int64_t)(P.off_x + a) * P.npad + p];
+            fin = fin && rfinite(v) && rfinite(x);
+            dsum[1 + a] += mp * (double)v;
+        }
+        dsum[4] += fin ? 0.0 : 1.0;
+    }
+    constexpr int slots[5] = {kDiagPartMass, kDiagPartMom, kDiagPartMom + 1, kDiagPartMom + 2, kDiagPartNonFinite};
+    block_sum_add<5>(dsum, P.diag, slots);
 }
 
 // ------------------------------------------------------------------ G2P
@@ -1370,7 +1445,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
             org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
             tl /= P.n_tiles[a];
         }
-        if (tid == 0) {
+        if (tid == 0 && !(P.debug & kDebugWithholdWindowCopy)) {
             fence_proxy_async_smem();
             mbar_expect_tx(&mbar[2], (uint32_t)(Gm::WN * sizeof(R4<R>)));
             tma_load_window(Vw, &tmapV, org, sim, D, &mbar[2]);
@@ -1616,6 +1691,8 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.off_x = h.off_x; P.off_v = h.off_v; P.off_C = h.off_C; P.off_F = h.off_F;
     P.off_rho = h.off_rho; P.off_sig = h.off_sig; P.off_eps = h.off_eps;
     P.obs = h.obs;
+    P.diag = ds.diag;
+    P.debug = h.debug;
     for (int w = 0; w < kMaxWalls; ++w) {
         P.wall[w].mu = ds.mu_dev[w];
         P.wall[w].n_seg[0] = ds.n_seg[w][0];
@@ -1751,6 +1828,11 @@ template <class R, int D> struct Launch {
         k_set_field<R, D><<<grid_blocks(h.n, 256, ds.num_sms), 256, 0, ds.stream>>>(P, (R *)ds.S, ds.id, field,
                                                                                     in);
     }
+    static void diag_particles(const HostParams &h, DevState &ds)
+    {
+        auto P = make_params<R>(h, ds);
+        k_diag_particles<R, D><<<grid_blocks(h.n, 256, ds.num_sms, 4), 256, 0, ds.stream>>>(P, (const R *)ds.S);
+    }
 };
 
 template <class R> struct Dispatch {
@@ -1769,6 +1851,7 @@ template <class R> struct Dispatch {
     MPM_DISPATCH(g2p, (const HostParams &h, DevState &ds), g2p(h, ds))
     MPM_DISPATCH(get_field, (const HostParams &h, DevState &ds, int f, double *o), get_field(h, ds, f, o))
     MPM_DISPATCH(set_field, (const HostParams &h, DevState &ds, int f, const double *i), set_field(h, ds, f, i))
+    MPM_DISPATCH(diag_particles, (const HostParams &h, DevState &ds), diag_particles(h, ds))
 #undef MPM_DISPATCH
 };
 

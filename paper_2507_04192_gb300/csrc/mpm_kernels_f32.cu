@@ -6,7 +6,7 @@ namespace mpm {
 const Ops ops_f32 = {
     Dispatch<float>::init_state, Dispatch<float>::keys,      Dispatch<float>::permute,
     Dispatch<float>::p2g,        Dispatch<float>::grid,      Dispatch<float>::g2p,
-    Dispatch<float>::get_field,  Dispatch<float>::set_field,
+    Dispatch<float>::get_field,  Dispatch<float>::set_field, Dispatch<float>::diag_particles,
 };
 
 const AdjOps adj_ops_f32 = {

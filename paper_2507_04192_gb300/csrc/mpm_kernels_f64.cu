@@ -6,7 +6,7 @@ namespace mpm {
 const Ops ops_f64 = {
     Dispatch<double>::init_state, Dispatch<double>::keys,      Dispatch<double>::permute,
     Dispatch<double>::p2g,        Dispatch<double>::grid,      Dispatch<double>::g2p,
-    Dispatch<double>::get_field,  Dispatch<double>::set_field,
+    Dispatch<double>::get_field,  Dispatch<double>::set_field, Dispatch<double>::diag_particles,
 };
 
 const AdjOps adj_ops_f64 = {

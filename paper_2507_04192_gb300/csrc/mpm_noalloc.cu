@@ -1,10 +1,9 @@
 // mpm_step_noalloc: one explicit MPM step that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation calls are not allowed there), plugins
-// hosted by an application that owns all device memory and forbids others from
-// allocating, and real-time loops that must not hit the allocator's latency or
-// failure modes.  For them this entry point takes the particle state in and
+// Some callers cannot call cudaMalloc: plugins hosted by an application that
+// owns all device memory and forbids others from allocating, and real-time
+// loops that must not hit the allocator's latency (cudaMalloc may synchronise
+// the device) or its failure modes.  For them this entry point takes the particle state in and
 // out through caller-owned device buffers and keeps its only scratch -- the
 // background grid -- in the file-scope device array below.  It performs no
 // allocation of its own: no cudaMalloc, cudaFree, context, stream or library
@@ -270,9 +269,20 @@ extern "C" int mpm_step_noalloc(const mpm_grid_desc *grid, const mpm_material *m
         std::lock_guard<std::mutex> lock(na_mutex);
         if (!na_grid_addr[dev]) {
             double *ptr = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress((void **)&ptr, na_grid);
+            cudaError_t e = cudaGetSymbolAddress((void **)&ptr, na_grid);
             if (e != cudaSuccess || ptr == nullptr) {
                 set_msg(err, err_len, "mpm_step_noalloc: cudaGetSymbolAddress of the scratch grid failed");
+                return MPM_ECUDA;
+            }
+            // load the four kernels now: with lazy module loading a kernel's code is
+            // otherwise loaded (and device memory taken for it) at its first launch
+            cudaFuncAttributes fa;
+            const void *kernels[4] = {(const void *)k_na_clear, (const void *)k_na_p2g, (const void *)k_na_grid,
+                                      (const void *)k_na_g2p};
+            for (const void *k : kernels)
+                if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+            if (e != cudaSuccess) {
+                set_msg(err, err_len, "mpm_step_noalloc: loading the kernels failed");
                 return MPM_ECUDA;
             }
             na_grid_addr[dev] = ptr;

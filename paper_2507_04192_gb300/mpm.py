@@ -83,6 +83,10 @@ def load_library(build_if_missing: bool = True):
             "mpm_monitor_means": (I, [P, I, P, P]),
             "mpm_set_adjoint_memory": (I, [P, C.c_int64]),
             "mpm_step": (I, [P, I]),
+            "mpm_request_sort": (I, [P]),
+            "mpm_set_diagnostics": (I, [P, I]),
+            "mpm_get_diagnostics": (I, [P, P, I]),
+            "mpm_set_debug": (I, [P, I]),
             "mpm_synchronize": (I, [P]),
             "mpm_get_particles": (I, [P, I, P]),
             "mpm_field_width": (I, [P, I]),
@@ -171,6 +175,31 @@ def mpm_set_obstacles(ctx, boxes):
 
 def mpm_step(ctx, n_steps: int):
     _check(ctx, load_library().mpm_step(ctx, int(n_steps)))
+
+
+def mpm_request_sort(ctx):
+    _check(ctx, load_library().mpm_request_sort(ctx))
+
+
+MPM_DIAG_COUNT = 11
+MPM_DEBUG_WITHHOLD_WINDOW_COPY = 1
+
+
+def mpm_set_diagnostics(ctx, enable: bool):
+    _check(ctx, load_library().mpm_set_diagnostics(ctx, int(bool(enable))))
+
+
+def mpm_get_diagnostics(ctx) -> dict:
+    """Conservation sums of the last step run with the diagnostics enabled."""
+    out = np.zeros(MPM_DIAG_COUNT, dtype=np.float64)
+    _check(ctx, load_library().mpm_get_diagnostics(ctx, _dptr(out), MPM_DIAG_COUNT))
+    return {"grid_mass": out[0], "grid_momentum": out[1:4].copy(), "particle_mass": out[4],
+            "particle_momentum": out[5:8].copy(), "grid_nonfinite": int(out[8]), "particle_nonfinite": int(out[9]),
+            "grid_abs_momentum": out[10]}
+
+
+def mpm_set_debug(ctx, flags: int):
+    _check(ctx, load_library().mpm_set_debug(ctx, int(flags)))
 
 
 def mpm_synchronize(ctx):

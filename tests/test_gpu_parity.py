@@ -67,6 +67,13 @@ def test_dam_break_fp32_200_steps():
     gpu, _ = run_gpu(w, 200, mpm.MPM_FP32)
     assert np.abs(gpu["x"] - ref["x"]).max() <= 1e-4 * 1.0
     assert_close(gpu, ref, "rho", 1e-3 * 1000.0)
+    # every other field at the stated FP32 bounds (relative to the field's largest value;
+    # F, dimensionless and near I, absolute)
+    assert_close(gpu, ref, "v", 2e-3 * scale(ref["v"]))
+    assert_close(gpu, ref, "C", 5e-3 * scale(ref["C"]))
+    assert_close(gpu, ref, "F", 1e-4)
+    K = w.material["bulk_K"]
+    assert_close(gpu, ref, "sigma", 5e-3 * scale(ref["sigma"]) + 1e-6 * K)
 
 
 @pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_FP32])

@@ -1,10 +1,11 @@
 """The no-allocation step (mpm_step_noalloc) against the regular step.
 
-Callers that cannot allocate device memory (code inside a CUDA graph capture,
-plugins in an application that owns all device memory, real-time loops) use
+Callers that cannot allocate device memory (plugins in an application that
+owns all device memory, real-time loops that must not enter the allocator) use
 mpm_step_noalloc with their own device buffers; its grid scratch is a static
 device array.  This checks, through the C-ABI, that two calls in a row give the
-same particle state as two steps of mpm_step.  The test allocates its device
+same particle state as two steps of mpm_step, with separate input and output
+buffers and with one buffer updated in place.  The test allocates its device
 buffers with torch (the entry point itself allocates nothing).  Kept in its own
 file so that it is collected last.
 """
@@ -55,10 +56,20 @@ def test_noalloc_matches_regular_step_two_calls(case):
     mpm.mpm_step_noalloc(g, m, n, w.particle_volume, p_mid, p_in, stream)     # second call, into the first buffer
     torch.cuda.synchronize()
     for ref, t in ((s1, t_mid), (s2, t_in)):
-        for f in ("x", "v", "C", "F", "rho") + (("sigma", "eps") if case == "sand3d" else ()):
-            got = t[f].cpu().numpy().reshape(ref[f].shape)
-            scale = max(1.0, float(np.abs(ref[f]).max()))
-            np.testing.assert_allclose(got, ref[f], rtol=0, atol=1e-10 * scale, err_msg=f)
+        _compare(ref, t, case)
+    # in place: the same buffers as input and output, two calls
+    t_ip, p_ip = _device_state(torch, s0, n, d)
+    mpm.mpm_step_noalloc(g, m, n, w.particle_volume, p_ip, p_ip, stream)
+    mpm.mpm_step_noalloc(g, m, n, w.particle_volume, p_ip, p_ip, stream)
+    torch.cuda.synchronize()
+    _compare(s2, t_ip, case)
+
+
+def _compare(ref, t, case):
+    for f in ("x", "v", "C", "F", "rho") + (("sigma", "eps") if case == "sand3d" else ()):
+        got = t[f].cpu().numpy().reshape(ref[f].shape)
+        scale = max(1.0, float(np.abs(ref[f]).max()))
+        np.testing.assert_allclose(got, ref[f], rtol=0, atol=1e-10 * scale, err_msg=f)
 
 
 def test_noalloc_rejects_a_grid_beyond_its_static_scratch():
