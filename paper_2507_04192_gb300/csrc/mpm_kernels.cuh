@@ -144,25 +144,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
                  : "memory");
     return ok != 0u;
 }
-__device__ __forceinline__ uint64_t globaltimer_ns()
+// One poll that may suspend the thread for at most about kPollNs nanoseconds
+// while the phase is incomplete (the suspend-time hint of mbarrier.try_wait).
+constexpr int kPollNs = 1000;
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t phase)
 {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(phase), "n"(kPollNs)
+                 : "memory");
+    return ok != 0u;
 }
-// Bounded wait: false once about one second has passed (device global timer) or
-// after kMaxWaitIters unsuccessful polls, whichever comes first.  A copy that
-// completes normally takes microseconds.
-constexpr int kMaxWaitIters = 1 << 24;
-constexpr uint64_t kMaxWaitNs = 1000000000ull;
+// Bounded wait: false after kMaxWaitIters unsuccessful polls of at most about
+// kPollNs each, i.e. about one second.  A copy that completes normally takes
+// microseconds.
+constexpr int kMaxWaitIters = 1 << 20;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
 {
-    if (mbar_try_wait(bar, phase)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (int it = 1; it < kMaxWaitIters; ++it) {
-        if (mbar_try_wait(bar, phase)) return true;
-        if ((it & 255) == 0 && globaltimer_ns() - t0 > kMaxWaitNs) return false;
-    }
+    for (int it = 0; it < kMaxWaitIters; ++it)
+        if (mbar_poll(bar, phase)) return true;
     return false;
 }
 
@@ -1268,14 +1270,23 @@ template <int D> __host__ __device__ __forceinline__ constexpr int g2p_ncomp(int
     return D + D * D + 1 + (material == 1 ? 7 : 0);
 }
 
-template <class R, int D, bool GENERIC = false, class Raw>
+// Component offsets of the particle state (the layout the host sets up: x, v, C,
+// F, rho, then sigma and eps for Drucker-Prager), as compile-time constants.
+template <int D> struct Lay {
+    static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, RHO = 2 * D + 2 * D * D, SIG = RHO + 1,
+                         EPS = RHO + 7;
+};
+
+template <class R, int D, bool GENERIC, int MAT, class Raw>
 __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__restrict__ S, int64_t p,
                                              const R4<R> *Vw, const int org[3], const R4<R> *__restrict__ Vs,
                                              const R4<R> *__restrict__ V2s = nullptr)
 {
     using Gm = Geo<D>;
+    using Ly = Lay<D>;
     constexpr int J_F = D, J_RHO = D + D * D;
     const int64_t np = P.npad;
+    R *__restrict__ Sp = S + p;                    // component c of this particle at Sp[c np]
     bool bad = false;
     R x[D];
 #pragma unroll
@@ -1335,21 +1346,21 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
             for (int a = 0; a < D; ++a) vo[a] += wk * vi[a];
         }
 #pragma unroll
-        for (int a = 0; a < D; ++a) vnew[a] = vp[a] + P.flip_alpha * (S[(P.off_v + a) * np + p] - vo[a]);
+        for (int a = 0; a < D; ++a) vnew[a] = vp[a] + P.flip_alpha * (Sp[(Ly::V + a) * np] - vo[a]);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         R xn = x[a] + P.dt * vp[a];
         xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
         bad |= !rfinite(xn) || !rfinite(vnew[a]);
-        S[(P.off_x + a) * np + p] = xn;
-        S[(P.off_v + a) * np + p] = vnew[a];
+        Sp[(Ly::X + a) * np] = xn;
+        Sp[(Ly::V + a) * np] = vnew[a];
     }
     // particle matrix for the next P2G: APIC C = B D^-1, TPIC the velocity gradient, PIC none
 #pragma unroll
     for (int q = 0; q < D * D; ++q)
-        S[(P.off_C + q) * np + p] = !GENERIC ? Bm[q] * cscale
-                                             : (P.transfer == 1 ? L[q] : (P.transfer >= 2 ? R(0) : Bm[q] * cscale));
+        Sp[(Ly::C + q) * np] = !GENERIC ? Bm[q] * cscale
+                                        : (P.transfer == 1 ? L[q] : (P.transfer >= 2 ? R(0) : Bm[q] * cscale));
     // F <- (I + dt L) F
     R F[D * D];
 #pragma unroll
@@ -1361,12 +1372,12 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
             R s = R(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += L[a * D + k] * F[k * D + c2];
-            S[(P.off_F + a * D + c2) * np + p] = F[a * D + c2] + P.dt * s;
+            Sp[(Ly::F + a * D + c2) * np] = F[a * D + c2] + P.dt * s;
         }
     const R rho = raw(J_RHO) / (R(1) + P.dt * trL);
-    S[P.off_rho * np + p] = rho;
+    Sp[Ly::RHO * np] = rho;
     bad |= !rfinite(rho);
-    if (P.material == 1) {
+    if constexpr (MAT == 1) {
         R L3[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) L3[q] = R(0);
@@ -1381,10 +1392,10 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
         dp_update(P, L3, s6, e);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            S[(P.off_sig + k) * np + p] = s6[k];
+            Sp[(Ly::SIG + k) * np] = s6[k];
             bad |= !rfinite(s6[k]);
         }
-        S[P.off_eps * np + p] = e;
+        Sp[Ly::EPS * np] = e;
     }
     return !bad;
 }
@@ -1403,7 +1414,7 @@ template <class R, int D> struct G2PSmem {
 // grid window of velocities is staged by one TMA tiled load; the particles'
 // inputs are staged 256 at a time by TMA bulk copies, double-buffered.  All
 // waits are bounded; a timeout is reported in the status word.
-template <class R, int D, bool GENERIC>
+template <class R, int D, bool GENERIC, int MAT>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
     k_g2p(const Params<R> P, const __grid_constant__ CUtensorMap tmapV, R *__restrict__ S,
           const R4<R> *__restrict__ V, const int4 *__restrict__ tiles, int32_t *__restrict__ counters,
@@ -1413,17 +1424,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
     using L = G2PSmem<R, D>;
     constexpr int NT = L::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
-                                                            ~uintptr_t(127));
+    // 128-byte aligned start for the TMA window, by pointer arithmetic on the shared
+    // array (an integer round trip would hide the address space from the compiler and
+    // turn every shared access into a generic one)
+    unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     R4<R> *Vw = reinterpret_cast<R4<R> *>(base);
     R *bufs = reinterpret_cast<R *>(base + L::win_bytes);
     __shared__ __align__(8) uint64_t mbar[3];      // [0], [1]: particle buffers, [2]: grid window
     __shared__ int s_slot;
     const int tid = threadIdx.x;
-    const int nc = g2p_ncomp<D>(P.material);
+    constexpr int nc = g2p_ncomp<D>(MAT);
     constexpr int J_RHO = D + D * D;
-    const int off_F = P.off_F, off_rho = P.off_rho;
-    auto comp = [&](int j) { return j < D ? j : (j < J_RHO ? off_F + (j - D) : off_rho + (j - J_RHO)); };
+    auto comp = [&](int j) { return j < D ? j : (j < J_RHO ? Lay<D>::F + (j - D) : Lay<D>::RHO + (j - J_RHO)); };
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -1470,8 +1482,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
             if (ok && i < t.z) {
                 const int64_t p = (int64_t)t.y + i;
                 const R *bb = bufs + (size_t)cur * L::NCMAX * L::PB + (p - a_cur);
-                bad |= !g2p_particle<R, D, GENERIC>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org, Vs,
-                                                   V2s);
+                bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org,
+                                                        Vs, V2s);
             }
             __syncthreads();
             a_cur = a_next;
@@ -1794,27 +1806,32 @@ template <class R, int D> struct Launch {
                                                            ds.node_list, ds.counters + 4);
     }
     // the APIC transfer has its own instantiation; the others (TPIC, PIC, FLIP) share one
-    template <bool GENERIC> static void g2p_launch(const HostParams &h, DevState &ds)
+    template <bool GENERIC, int MAT> static void g2p_launch(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
         const size_t smem = G2PSmem<R, D>::total;
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_g2p<R, D, GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_g2p<R, D, GENERIC, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
         int64_t nb = ds.max_tiles;
         const int64_t cap = (int64_t)ds.num_sms * (sizeof(R) == 4 ? MPM_G2P_MINB : 2);
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
-        k_g2p<R, D, GENERIC><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(
+        k_g2p<R, D, GENERIC, MAT><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(
             P, ds.tmap_V, (R *)ds.S, (const R4<R> *)ds.V, ds.tiles + ds.max_tiles, ds.counters, ds.status,
             (const R4<R> *)ds.V2);
     }
     static void g2p(const HostParams &h, DevState &ds)
     {
-        if (h.transfer != 0) g2p_launch<true>(h, ds);
-        else g2p_launch<false>(h, ds);
+        if (h.material == 1) {
+            if (h.transfer != 0) g2p_launch<true, 1>(h, ds);
+            else g2p_launch<false, 1>(h, ds);
+        } else {
+            if (h.transfer != 0) g2p_launch<true, 0>(h, ds);
+            else g2p_launch<false, 0>(h, ds);
+        }
     }
     static void get_field(const HostParams &h, DevState &ds, int field, double *out)
     {

@@ -327,6 +327,33 @@ def granular_inverse_3d(n_cells: Tuple[int, int, int] = (192, 192, 96), radius_c
     return w
 
 
+SAND_ALUMINIUM_BARS = dict(kind=1, rho0=2650.0, E=3.0 * 0.7e6 * (1.0 - 2.0 * 0.3), nu=0.3, phi_deg=19.8,
+                          psi_deg=0.0, cohesion=0.0, sigma_t=0.0)
+"""The Drucker-Prager material of the paper's granular benchmarks (Sec. 4.1.2 and
+4.2.2): rho = 2650 kg/m^3, bulk modulus K = 0.7 MPa (E = 3K(1 - 2 nu)), nu = 0.3,
+phi = 19.8 deg, psi = 0, c = 0."""
+
+
+def granular_column_3d(aspect: float, length: float = 0.05, n_cells: Tuple[int, int, int] = (400, 32, 200),
+                       dx: float = 1.0 / 400.0, ppc_axis: int = 2, seed: int = 0, dt: float = 1.0e-5,
+                       steps: int = 200_000, base_mu: float = 1.0e6, sort_every: int = 32) -> Workload:
+    """Quasi-2D granular column against the x- wall (Sec. 4.2.2): base length
+    ``length`` (L0), height aspect * L0 (H0), across the whole y extent of the
+    400 x 32 x 200 grid (dx = 1/400 m); slip side and far walls; the no-slip base
+    taken as a Coulomb floor with mu = base_mu (a node pressed onto the base
+    sticks)."""
+    hgt = aspect * length
+    x = lattice_particles(tuple(n_cells), dx, ppc_axis,
+                          lambda p: (p[:, 0] < length) & (p[:, 2] < hgt),
+                          (0.0, 0.0, 0.0), (length, n_cells[1] * dx, hgt), seed)
+    return Workload(name=f"granular_column_3d_a{aspect:g}", dim=3, n_cells=tuple(n_cells), dx=dx, dt=dt,
+                    gravity=(0.0, 0.0, -9.8), material=dict(SAND_ALUMINIUM_BARS), x=x,
+                    particle_volume=dx ** 3 / ppc_axis ** 3, steps=steps, sort_every=sort_every,
+                    friction=[(4, (1, 1), np.array([base_mu]))],
+                    extras=dict(body_lo=(0.0, 0.0, 0.0), body_hi=(length, n_cells[1] * dx, hgt), seed=seed,
+                                L0=length, H0=hgt, aspect=aspect))
+
+
 WORKLOADS = {
     "dam_break_2d_64": lambda: dam_break_2d(64),
     "granular_cylinder_3d_256x256x128": lambda: granular_cylinder_3d(),
