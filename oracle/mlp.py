@@ -1,9 +1,11 @@
-"""FP64 oracle of the warm-start network (test infrastructure only).
+"""FP64 oracle of the fully connected networks (test infrastructure only).
 
 Plain numpy, float64 arithmetic.  With ``bf16=True`` the values the tensor-core
 path feeds to its GEMMs are rounded to bfloat16 (round to nearest even) at the
 same points: the network input, the weights, the hidden activations and the
-back-propagated pre-activation gradients.  GELU is the exact erf form.
+back-propagated pre-activation gradients.  Hidden layers use GELU (exact erf
+form; the warm-start network) or ReLU (the coordinate network of Eq. nn_apprx,
+Sec. 5.2); the output is lo + (hi - lo) sigmoid(z) or the affine map z itself.
 """
 from __future__ import annotations
 
@@ -32,6 +34,18 @@ def gelu_grad(z):
     return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
+def relu(z):
+    return np.maximum(z, 0.0)
+
+
+def relu_grad(z):
+    """Derivative of max(z, 0), taken as 0 at z = 0."""
+    return (np.asarray(z) > 0.0).astype(np.float64)
+
+
+_ACT = {"gelu": (gelu, gelu_grad), "relu": (relu, relu_grad)}
+
+
 def unpack(params, widths):
     out, o = [], 0
     for l in range(len(widths) - 1):
@@ -48,29 +62,35 @@ def pack(layers):
     return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in layers])
 
 
-def forward(params, widths, x, lo=0.1, hi=0.6, bf16_round=True):
+def forward(params, widths, x, lo=0.1, hi=0.6, bf16_round=True, hidden="gelu", out="sigmoid"):
+    """Output y and the layer inputs xs (as the GEMMs see them) and pre-activations zs."""
     r = bf16 if bf16_round else (lambda a: np.asarray(a, dtype=np.float64))
+    act = _ACT[hidden][0]
     layers = unpack(params, widths)
     xs, zs = [r(x)], []
     for l, (W, b) in enumerate(layers):
         z = xs[-1] @ r(W).T + b
         zs.append(z)
         if l + 1 < len(layers):
-            xs.append(r(gelu(z)))
+            xs.append(r(act(z)))
+    if out == "linear":
+        return zs[-1].copy(), xs, zs
     s = 1.0 / (1.0 + np.exp(-zs[-1]))
     return lo + (hi - lo) * s, xs, zs
 
 
-def loss_and_grad(params, widths, x, t, lo=0.1, hi=0.6, bf16_round=True):
-    """Mean squared error and its gradient with respect to the parameters."""
+def backward(params, widths, x, dy, lo=0.1, hi=0.6, bf16_round=True, hidden="gelu", out="sigmoid"):
+    """Gradient of a scalar L with respect to the parameters, given dL/dy (the
+    output's shape): back-propagation through the layers of ``forward``."""
     r = bf16 if bf16_round else (lambda a: np.asarray(a, dtype=np.float64))
+    dact = _ACT[hidden][1]
     layers = unpack(params, widths)
-    y, xs, zs = forward(params, widths, x, lo, hi, bf16_round)
-    n = y.size
-    e = y - t
-    loss = float((e * e).sum() / n)
-    s = 1.0 / (1.0 + np.exp(-zs[-1]))
-    dz = 2.0 * e / n * (hi - lo) * s * (1.0 - s)
+    _, xs, zs = forward(params, widths, x, lo, hi, bf16_round, hidden, out)
+    if out == "linear":
+        dz = np.asarray(dy, dtype=np.float64)
+    else:
+        s = 1.0 / (1.0 + np.exp(-zs[-1]))
+        dz = np.asarray(dy, dtype=np.float64) * (hi - lo) * s * (1.0 - s)
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):
         W, _ = layers[l]
@@ -80,5 +100,14 @@ def loss_and_grad(params, widths, x, t, lo=0.1, hi=0.6, bf16_round=True):
         grads[l] = (gW, gb)
         if l > 0:
             da = dzr @ r(W)
-            dz = da * gelu_grad(zs[l - 1])
-    return loss, pack(grads)
+            dz = da * dact(zs[l - 1])
+    return pack(grads)
+
+
+def loss_and_grad(params, widths, x, t, lo=0.1, hi=0.6, bf16_round=True, hidden="gelu", out="sigmoid"):
+    """Mean squared error L = mean (y - t)^2 and its gradient with respect to the parameters."""
+    y, _, _ = forward(params, widths, x, lo, hi, bf16_round, hidden, out)
+    n = y.size
+    e = y - t
+    loss = float((e * e).sum() / n)
+    return loss, backward(params, widths, x, 2.0 * e / n, lo, hi, bf16_round, hidden, out)

@@ -135,3 +135,76 @@ def test_weight_gradients_see_the_output_error_only_through_its_bf16_value():
     n_out_bias = widths[-1]
     np.testing.assert_array_equal(g1[:-n_out_bias], g0[:-n_out_bias])
     assert (g1[-n_out_bias:] != g0[-n_out_bias:]).any()
+
+
+# ---- the coordinate network's variants: ReLU hidden layers, linear output, a given output gradient
+
+def test_relu_and_its_derivative():
+    z = np.array([-2.0, -1e-300, 0.0, 1e-300, 3.5])
+    np.testing.assert_array_equal(mlp.relu(z), [0.0, 0.0, 0.0, 1e-300, 3.5])
+    np.testing.assert_array_equal(mlp.relu_grad(z), [0.0, 0.0, 0.0, 1.0, 1.0])
+
+
+def test_linear_one_layer_network_and_its_gradient_in_closed_form():
+    # y = x W^T + b, L = sum(c * y): dL/dW = c^T x, dL/db = sum over the batch of c
+    rng = np.random.default_rng(7)
+    W, b = rng.standard_normal((8, 16)), rng.standard_normal(8)
+    x, c = rng.standard_normal((5, 16)), rng.standard_normal((5, 8))
+    p = mlp.pack([(W, b)])
+    y, _, _ = mlp.forward(p, [16, 8], x, bf16_round=False, out="linear")
+    np.testing.assert_allclose(y, x @ W.T + b, rtol=0, atol=1e-13)
+    g = mlp.backward(p, [16, 8], x, c, bf16_round=False, out="linear")
+    np.testing.assert_allclose(g[:128].reshape(8, 16), c.T @ x, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(g[128:], c.sum(axis=0), rtol=0, atol=1e-13)
+
+
+def test_relu_network_by_hand():
+    # 1 -> 2 -> 1, ReLU, linear output: y = w2 . relu(w1 x + b1) + b2
+    W1, b1 = np.array([[2.0], [-1.0]]), np.array([0.5, 0.25])
+    W2, b2 = np.array([[3.0, 4.0]]), np.array([-1.0])
+    p = mlp.pack([(W1, b1), (W2, b2)])
+    x = np.array([[1.0], [2.0]])          # hidden: (2.5, 0) and (4.5, 0): the second unit is off
+    y, _, _ = mlp.forward(p, [1, 2, 1], x, bf16_round=False, hidden="relu", out="linear")
+    np.testing.assert_allclose(y[:, 0], [3 * 2.5 - 1, 3 * 4.5 - 1], rtol=0, atol=1e-14)
+    g = mlp.backward(p, [1, 2, 1], x, np.ones((2, 1)), bf16_round=False, hidden="relu", out="linear")
+    # dL/dW1 = sum_n W2_0 x_n for the active unit, 0 for the inactive one; dL/db1 likewise
+    np.testing.assert_allclose(g, [3 * 3.0, 0.0, 3 * 2.0, 0.0, 2.5 + 4.5, 0.0, 2.0], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("out", ["linear", "sigmoid"])
+def test_relu_network_gradient_matches_central_differences(out):
+    widths = [8, 16, 16, 8]
+    rng = np.random.default_rng(8)
+    n_par = sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+    p = rng.standard_normal(n_par) * 0.5
+    x = rng.standard_normal((6, widths[0]))
+    c = rng.standard_normal((6, widths[-1]))
+
+    def L(q):
+        y, _, _ = mlp.forward(q, widths, x, bf16_round=False, hidden="relu", out=out)
+        return float((c * y).sum())
+
+    g = mlp.backward(p, widths, x, c, bf16_round=False, hidden="relu", out=out)
+    h = 1e-6
+    for i in rng.choice(n_par, 60, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        assert g[i] == pytest.approx((L(pp) - L(pm)) / (2 * h), rel=1e-5, abs=1e-9)
+
+
+def test_zero_padded_units_stay_inert():
+    # hidden units whose weights in and out are zero have zero gradients (ReLU is off
+    # at 0, and nothing reads them), so padding a layer to a multiple of 8 changes nothing
+    rng = np.random.default_rng(9)
+    W1, b1 = rng.standard_normal((6, 8)), rng.standard_normal(6)
+    W2, b2 = rng.standard_normal((8, 6)), rng.standard_normal(8)
+    W1p, b1p = np.vstack([W1, np.zeros((2, 8))]), np.concatenate([b1, np.zeros(2)])
+    W2p = np.hstack([W2, np.zeros((8, 2))])
+    x, c = rng.standard_normal((4, 8)), rng.standard_normal((4, 8))
+    p, pp = mlp.pack([(W1, b1), (W2, b2)]), mlp.pack([(W1p, b1p), (W2p, b2)])
+    y, _, _ = mlp.forward(p, [8, 6, 8], x, bf16_round=False, hidden="relu", out="linear")
+    yp, _, _ = mlp.forward(pp, [8, 8, 8], x, bf16_round=False, hidden="relu", out="linear")
+    np.testing.assert_allclose(yp, y, rtol=0, atol=1e-14)
+    gp = mlp.unpack(mlp.backward(pp, [8, 8, 8], x, c, bf16_round=False, hidden="relu", out="linear"), [8, 8, 8])
+    assert np.all(gp[0][0][6:] == 0) and np.all(gp[0][1][6:] == 0) and np.all(gp[1][0][:, 6:] == 0)

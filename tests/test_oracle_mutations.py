@@ -274,13 +274,20 @@ MUTANTS = [
      "((u + np.uint64(0x8000)) >> np.uint64(16))", 0),
     ("output range without the lower bound", "mlp.py", "return lo + (hi - lo) * s, xs, zs", "return lo + hi * s, xs, zs", 0),
     ("bias gradient averaged", "mlp.py", "gb = dz.sum(axis=0)", "gb = dz.mean(axis=0)", 0),
-    ("squared-error gradient without the 2", "mlp.py", "dz = 2.0 * e / n", "dz = e / n", 0),
+    ("squared-error gradient without the 2", "mlp.py", "backward(params, widths, x, 2.0 * e / n,",
+     "backward(params, widths, x, e / n,", 0),
     ("backward through unrounded weights", "mlp.py", "da = dzr @ r(W)", "da = dz @ W", 0),
-    ("hidden activations not rounded", "mlp.py", "xs.append(r(gelu(z)))", "xs.append(gelu(z))", 0),
+    ("hidden activations not rounded", "mlp.py", "xs.append(r(act(z)))", "xs.append(act(z))", 0),
     ("network input not rounded", "mlp.py", "xs, zs = [r(x)], []", "xs, zs = [np.asarray(x, dtype=np.float64)], []", 0),
     ("weight gradient from the unrounded error", "mlp.py", "gW = dzr.T @ xs[l]", "gW = dz.T @ xs[l]", 0),
-    ("output sigmoid derivative sign", "mlp.py", "dz = 2.0 * e / n * (hi - lo) * s * (1.0 - s)",
-     "dz = 2.0 * e / n * (hi - lo) * s * (1.0 + s)", 0),
+    ("output sigmoid derivative sign", "mlp.py", "dz = np.asarray(dy, dtype=np.float64) * (hi - lo) * s * (1.0 - s)",
+     "dz = np.asarray(dy, dtype=np.float64) * (hi - lo) * s * (1.0 + s)", 0),
+    ("ReLU derivative 1 at zero", "mlp.py", "(np.asarray(z) > 0.0)", "(np.asarray(z) >= 0.0)", 0),
+    ("leaky ReLU", "mlp.py", "return np.maximum(z, 0.0)", "return np.maximum(z, 0.01 * z)", 0),
+    ("linear output scaled like a sigmoid", "mlp.py", "dz = np.asarray(dy, dtype=np.float64)\n    else:",
+     "dz = 0.25 * np.asarray(dy, dtype=np.float64)\n    else:", 0),
+    ("backward through GELU whatever the hidden activation", "mlp.py", "dact = _ACT[hidden][1]",
+     "dact = _ACT['gelu'][1]", 0),
     # velocity monitors (oracle/__init__.py)
     ("monitor box open at the top", "__init__.py", "inside = np.all((x >= np.asarray(lo, dtype=np.float64)) & "
      "(x <= np.asarray(hi, dtype=np.float64)), axis=1)\n        cnt[l]",
