@@ -456,10 +456,10 @@ int mpm_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, in
 /*
  * A fully connected network on the tensor cores: the learned warm start of the
  * basal-friction inversion (a map from tracked-particle displacements to the
- * per-segment friction field; the paper's coordinate network of Eq. nn_apprx,
- * Sec. 3.2, is the same kind of component).  widths[0..n_layers] (multiples of
- * 8); hidden layers use GELU (exact erf form), the output y = out_lo +
- * (out_hi - out_lo) sigmoid(z).  Weights and Adam state in fp32 with bf16
+ * per-segment friction field) and the paper's coordinate network of Eq.
+ * nn_apprx (Sec. 3.2, 5.2).  widths[0..n_layers] (multiples of 8); by default
+ * hidden layers use GELU (exact erf form) and the output is y = out_lo +
+ * (out_hi - out_lo) sigmoid(z) (see mpm_mlp_set_activations).  Weights and Adam state in fp32 with bf16
  * copies as GEMM operands; activations enter GEMMs as bf16; fp32 accumulation.
  * Parameter vectors (host, fp32) list, per layer, W (out x in, row-major) then b.
  */
@@ -482,6 +482,35 @@ int mpm_mlp_infer(mpm_mlp *mlp, int batch, const float *x, float *y, int device_
  */
 int mpm_mlp_train_step(mpm_mlp *mlp, int batch, const float *x, const float *target, double lr, int update,
                        double *loss_out, int device_ptrs);
+/*
+ * The same training step (update on) with device pointers only and no
+ * synchronisation: queued on the network's stream; the loss before the update
+ * goes to loss_dev (a device double, or NULL).  A bounded tensor-core wait that
+ * ran out is reported by the next synchronising call.  MPM_EINVAL as above.
+ */
+int mpm_mlp_train_step_async(mpm_mlp *mlp, int batch, const float *x_dev, const float *target_dev, double lr,
+                             double *loss_dev);
+/*
+ * Activations (default GELU hidden layers and the scaled sigmoid output): hidden
+ * = MPM_ACT_GELU or MPM_ACT_RELU (max(z, 0), derivative 0 at z = 0); output =
+ * MPM_OUT_SIGMOID (out_lo + (out_hi - out_lo) sigmoid(z)) or MPM_OUT_LINEAR
+ * (y = z: the coordinate network v(x) of Eq. nn_apprx, Sec. 3.2 and 5.2).
+ * MPM_EINVAL for another value.
+ */
+enum { MPM_ACT_GELU = 0, MPM_ACT_RELU = 1 };
+enum { MPM_OUT_SIGMOID = 0, MPM_OUT_LINEAR = 1 };
+int mpm_mlp_set_activations(mpm_mlp *mlp, int hidden, int output);
+/*
+ * Back-propagation of a given output gradient dy = dL/dy (batch x widths[L]) for
+ * a loss L computed outside the network (the chain rule of Sec. 3.2: dL/dtheta =
+ * dL/dy dy/dtheta, with dL/dy from mpm_get_initial_adjoint for a network that
+ * parameterises the initial velocity field): forward at x, backward, and
+ * (update != 0) one Adam step with rate lr.  The parameter gradients are then
+ * readable with mpm_mlp_get_params(which = 1).  batch a multiple of 8;
+ * synchronises.
+ */
+int mpm_mlp_backward(mpm_mlp *mlp, int batch, const float *x, const float *dy, double lr, int update,
+                     int device_ptrs);
 int mpm_mlp_last_error(const mpm_mlp *mlp, char *buf, int len);
 
 #ifdef __cplusplus

@@ -1289,7 +1289,8 @@ template <class R, int D> struct AdjLaunch {
                         P, (const R *)st, (const R4<R> *)GV, (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB,
                         (R *)a.coef);
                     constexpr int NT = 128;
-                    const size_t smem = (size_t)2 * direct_stage_comps<2>() * NT * sizeof(R);
+                    constexpr size_t smem = p2g_direct_smem<R, NT, 2>();
+                    static_assert(smem <= 48 * 1024, "k_p2g_direct shared memory above the default limit");
                     P2GIO<R> io{(const R *)st, (const R *)a.coef, h.n, a.tiles, a.n_tiles, a.cursor, a.posmap,
                                 a.cell_off, (R4<R> *)a.GVB, nullptr};
                     k_p2g_direct<R, NT, 2><<<ds.num_sms * MPM_P2G_MINB, NT, smem, ds.stream>>>(P, io, nullptr,

@@ -758,6 +758,17 @@ __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R>
 // Components staged per particle by k_p2g_direct: P2G's inputs (MAT 0, 1), or x
 // and the 21 scatter coefficients (MAT 2).
 template <int MAT> __host__ __device__ constexpr int direct_stage_comps() { return MAT == 2 ? 24 : kP2GStageComps<3>; }
+// Per warp of k_p2g_direct: its work item's 129 cell offsets (padded to 132) and
+// up to kDirectPmapCap entries of the position map, staged in shared memory at
+// the start of the item (an item holding more particles reads the map from
+// global memory).
+constexpr int kDirectOffPad = 132;
+constexpr int kDirectPmapCap = 1280;
+template <class R, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
+{
+    return (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R) +
+           (size_t)(NT / 32) * (kDirectOffPad + kDirectPmapCap) * sizeof(int32_t);
+}
 
 // P2G without a shared-memory window (3D, register accumulation).  Warps claim
 // work items of 128 cells (two layer groups of a tile) from a global cursor and
@@ -787,6 +798,9 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *stg = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
+    int32_t *const s_off = reinterpret_cast<int32_t *>(smem_raw + (size_t)2 * NCM * NT * sizeof(R)) +
+                           (tid >> 5) * (kDirectOffPad + kDirectPmapCap);
+    int32_t *const s_pm = s_off + kDirectOffPad;
     const int n_items = *io.n_tiles * ITEMS;
     const int64_t ld = io.ld;
     const R mass = ADJ ? R(0) : P.mass;
@@ -810,7 +824,19 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
         const int32_t *pmap = io.posmap + t.y;
-        const int32_t *off = io.cell_off + (int64_t)k * (Gm::TN + 1);
+        const int32_t *goff = io.cell_off + (int64_t)k * (Gm::TN + 1) + cbase;
+        // the item's cell offsets and position map, staged once (coalesced) so that the
+        // per-cell and per-particle lookups below are shared-memory reads
+        __syncwarp();
+        for (int i = lane; i <= CELLS; i += 32) s_off[i] = goff[i];
+        __syncwarp();
+        const int q0 = s_off[0], nq = s_off[CELLS] - q0;
+        const bool pm_staged = nq <= kDirectPmapCap;
+        if (pm_staged)
+            for (int i = lane; i < nq; i += 32) s_pm[i] = pmap[q0 + i];
+        __syncwarp();
+        const int32_t *off = s_off - cbase;           // off[c] for the item's cells c in [cbase, cbase + CELLS]
+        auto slot = [&](int q) { return pm_staged ? s_pm[q - q0] : pmap[q]; };
         const R *St = io.S + t.y;
         const R *S2 = ADJ ? io.src2 + t.y : nullptr;
         R *const Sv = (ADJ || P.save_S == nullptr) ? nullptr : P.save_S + t.y;
@@ -849,11 +875,11 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         bool hp = pc.next(off);
 #pragma unroll
         for (int s0 = 0; s0 < 2; ++s0) {
-            if (hp) issue(s0, pmap[pc.q]);
+            if (hp) issue(s0, slot(pc.q));
             cp_async_commit();
             hp = hp && pc.next(off);
         }
-        int32_t ppos = hp ? pmap[pc.q] : 0;
+        int32_t ppos = hp ? slot(pc.q) : 0;
         bool hc = cc.next(off);
         int stage = 0, cur = -1;
         int bown[D], nb[D];
@@ -888,7 +914,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
                     adj_scatter_factors<R>(P, [&](int j) { return src[j * NT]; }, f);
                 } else {
                     if (Sv != nullptr) {               // the adjoint's copy of this step's state
-                        R *d = Sv + pmap[cc.q];
+                        R *d = Sv + slot(cc.q);
 #pragma unroll
                         for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
                     }
@@ -898,7 +924,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
             if (hp) issue(stage, ppos);
             cp_async_commit();
             hp = hp && pc.next(off);
-            if (hp) ppos = pmap[pc.q];
+            if (hp) ppos = slot(pc.q);
             bool own = true;
 #pragma unroll
             for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
@@ -1752,7 +1778,8 @@ template <class R, int D> struct Launch {
         auto P = make_params<R>(h, ds);
         if constexpr (D == 3 && sizeof(R) == 4 && MPM_P2G_DIRECT) {
             constexpr int NT = kP2GThreads;
-            const size_t smem = (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R);
+            constexpr size_t smem = p2g_direct_smem<R, NT, MAT>();
+            static_assert(smem <= 48 * 1024, "k_p2g_direct shared memory above the default limit");
             const int nb = ds.num_sms * MPM_P2G_MINB;
             P2GIO<R> io{(const R *)ds.S, nullptr, h.npad, ds.tiles, ds.counters + 1, ds.counters + 2,
                         ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags};

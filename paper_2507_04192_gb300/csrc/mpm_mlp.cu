@@ -2,8 +2,9 @@
 // cores: the learned warm start of the basal-friction inversion (a map from
 // tracked-particle observations to per-segment friction coefficients).
 //
-// Layers: z_l = x_l W_l^T + b_l, x_{l+1} = GELU(z_l) (exact erf form) for the
-// hidden layers, output y = lo + (hi - lo) sigmoid(z_last).  Weights are kept in
+// Layers: z_l = x_l W_l^T + b_l, x_{l+1} = GELU(z_l) (exact erf form) or
+// max(z_l, 0) for the hidden layers, output y = lo + (hi - lo) sigmoid(z_last)
+// or y = z_last (the coordinate network of Eq. nn_apprx).  Weights are kept in
 // fp32 (Adam state too) with bf16 copies (and their transposes) as GEMM
 // operands; activations and back-propagated gradients enter the GEMMs as bf16
 // and every GEMM accumulates in fp32 in TMEM.  Loss: mean squared error.
@@ -48,27 +49,48 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Loss and output gradient: L = mean (y - t)^2; dz = dL/dy (hi - lo) s (1 - s).
+// Loss and output gradient: L = mean (y - t)^2; dz = dL/dy (hi - lo) s (1 - s)
+// (dz = dL/dy for the linear output).
 __global__ void k_mse_out(const float *__restrict__ y, const float *__restrict__ t, const float *__restrict__ z,
-                          float *__restrict__ dz, int64_t n, float lo, float hi, double *__restrict__ loss)
+                          float *__restrict__ dz, int64_t n, float lo, float hi, double *__restrict__ loss,
+                          int linear)
 {
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float e = y[i] - t[i];
         acc += (double)e * e;
-        const float s = 1.0f / (1.0f + expf(-z[i]));
-        dz[i] = 2.0f * e / (float)n * (hi - lo) * s * (1.0f - s);
+        if (linear) {
+            dz[i] = 2.0f * e / (float)n;
+        } else {
+            const float s = 1.0f / (1.0f + expf(-z[i]));
+            dz[i] = 2.0f * e / (float)n * (hi - lo) * s * (1.0f - s);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
 }
 
-// dz_prev = da * GELU'(z_prev).
-__global__ void k_gelu_back(const float *__restrict__ da, const float *__restrict__ z, float *__restrict__ dz,
-                            int64_t n)
+// dz_prev = da * GELU'(z_prev), or da * [z_prev > 0] for ReLU.
+__global__ void k_act_back(const float *__restrict__ da, const float *__restrict__ z, float *__restrict__ dz,
+                           int64_t n, int relu)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dz[i] = da[i] * gelu_grad_f(z[i]);
+        dz[i] = relu ? (z[i] > 0.0f ? da[i] : 0.0f) : da[i] * gelu_grad_f(z[i]);
+}
+
+// Output gradient from a given dL/dy: dz = dy (hi - lo) s (1 - s) for the scaled
+// sigmoid, dz = dy for the linear output.
+__global__ void k_out_back(const float *__restrict__ dy, const float *__restrict__ z, float *__restrict__ dz,
+                           int64_t n, float lo, float hi, int linear)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (linear) {
+            dz[i] = dy[i];
+        } else {
+            const float s = 1.0f / (1.0f + expf(-z[i]));
+            dz[i] = dy[i] * (hi - lo) * s * (1.0f - s);
+        }
+    }
 }
 
 // db[c] = sum_r dz[r][c].
@@ -103,6 +125,7 @@ struct mpm_mlp {
     int L = 0, max_batch = 0;
     std::vector<int> w;                           // widths, L + 1
     float lo = 0.f, hi = 1.f;
+    int hidden_act = MPM_ACT_GELU, out_act = MPM_OUT_SIGMOID;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<float *> W, b, gW, gb, mW, vW, mb, vb;     // fp32
@@ -151,10 +174,10 @@ int forward(mpm_mlp *m, int B)
         UmmaEpi epi;
         epi.bias = m->b[l];
         if (l + 1 < m->L) {
-            epi.mode = kEpiBiasGelu;
+            epi.mode = m->hidden_act == MPM_ACT_RELU ? kEpiBiasRelu : kEpiBiasGelu;
             epi.xnext = m->X[l + 1];
         } else {
-            epi.mode = kEpiBiasSigmoid;
+            epi.mode = m->out_act == MPM_OUT_LINEAR ? kEpiBiasLinear : kEpiBiasSigmoid;
             epi.y = m->Y;
             epi.lo = m->lo;
             epi.hi = m->hi;
@@ -205,6 +228,66 @@ int load_x(mpm_mlp *m, int B, const float *x, bool device)
     }
     k_f32_to_bf16<<<blocks_for(n), 256, 0, m->stream>>>(src, m->X[0], n);
     return MPM_OK;
+}
+
+// Back-propagation from dZ[L - 1] (already holding dL/dz of the output layer)
+// and, with update, one Adam step.
+int backward_update(mpm_mlp *m, int B, double lr, int update)
+{
+    const int L = m->L;
+    for (int l = L - 1; l >= 0; --l) {
+        const int Kin = m->w[l], N = m->w[l + 1];
+        const int64_t nz = (int64_t)B * N;
+        k_f32_to_bf16<<<blocks_for(nz), 256, 0, m->stream>>>(m->dZ[l], m->dZb[l], nz);
+        transpose(m, m->dZb[l], m->dZbT[l], B, N);          // N x B
+        transpose(m, m->X[l], m->XT[l], B, Kin);             // Kin x B
+        // dW = dZ^T X : (N x B) (Kin x B)^T
+        cudaError_t e = umma_gemm_tma(N, Kin, B, m->dZbT[l], B, m->XT[l], B, m->gW[l], Kin, UmmaEpi{}, m->status,
+                                      m->stream);
+        if (e != cudaSuccess) return MPM_ECUDA;
+        k_col_sum<<<(N + 255) / 256, 256, 0, m->stream>>>(m->dZ[l], m->gb[l], B, N);
+        if (l > 0) {
+            // dA = dZ W : (B x N) (Kin x N)^T
+            e = umma_gemm_tma(B, Kin, N, m->dZb[l], N, m->WbT[l], N, m->dA, Kin, UmmaEpi{}, m->status, m->stream);
+            if (e != cudaSuccess) return MPM_ECUDA;
+            k_act_back<<<blocks_for((int64_t)B * Kin), 256, 0, m->stream>>>(m->dA, m->Z[l - 1], m->dZ[l - 1],
+                                                                           (int64_t)B * Kin,
+                                                                           m->hidden_act == MPM_ACT_RELU);
+        }
+    }
+    if (update) {
+        m->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+        for (int l = 0; l < L; ++l) {
+            const int64_t nw = (int64_t)m->w[l + 1] * m->w[l], nb = m->w[l + 1];
+            k_adam<<<blocks_for(nw), 256, 0, m->stream>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], nw, (float)lr, b1, b2,
+                                                          1e-8f, c1, c2);
+            k_adam<<<blocks_for(nb), 256, 0, m->stream>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], nb, (float)lr, b1, b2,
+                                                          1e-8f, c1, c2);
+            refresh_bf16(m, l);
+        }
+    }
+    return MPM_OK;
+}
+
+// Queue one training step on the mean squared error (no synchronisation).
+int train_queue(mpm_mlp *m, int B, const float *x, const float *target, double lr, int update, bool device)
+{
+    const int L = m->L;
+    int rc = load_x(m, B, x, device);
+    if (rc != MPM_OK) return rc;
+    const int64_t nout = (int64_t)B * m->w[L];
+    if (cudaMemcpyAsync(m->T, target, sizeof(float) * nout, device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        m->stream) != cudaSuccess)
+        return MPM_ECUDA;
+    rc = forward(m, B);
+    if (rc != MPM_OK) return rc;
+    cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream);
+    k_mse_out<<<blocks_for(nout), 256, 0, m->stream>>>(m->Y, m->T, m->Z[L - 1], m->dZ[L - 1], nout, m->lo, m->hi,
+                                                      m->loss, m->out_act == MPM_OUT_LINEAR);
+    rc = backward_update(m, B, lr, update);
+    return rc != MPM_OK ? rc : check(m);
 }
 
 }  // namespace
@@ -366,56 +449,53 @@ int mpm_mlp_train_step(mpm_mlp *m, int batch, const float *x, const float *targe
                        double *loss_out, int device_ptrs)
 {
     if (!m || !x || !target || batch < 8 || batch > m->max_batch || (batch % 8) || !(lr >= 0)) return MPM_EINVAL;
-    const int L = m->L, B = batch;
-    int rc = load_x(m, B, x, device_ptrs != 0);
-    if (rc != MPM_OK) return rc;
-    const int64_t nout = (int64_t)B * m->w[L];
-    if (cudaMemcpyAsync(m->T, target, sizeof(float) * nout,
-                        device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
-        return MPM_ECUDA;
-    rc = forward(m, B);
-    if (rc != MPM_OK) return rc;
-    cudaMemsetAsync(m->loss, 0, sizeof(double), m->stream);
-    k_mse_out<<<blocks_for(nout), 256, 0, m->stream>>>(m->Y, m->T, m->Z[L - 1], m->dZ[L - 1], nout, m->lo, m->hi,
-                                                      m->loss);
-    for (int l = L - 1; l >= 0; --l) {
-        const int Kin = m->w[l], N = m->w[l + 1];
-        const int64_t nz = (int64_t)B * N;
-        k_f32_to_bf16<<<blocks_for(nz), 256, 0, m->stream>>>(m->dZ[l], m->dZb[l], nz);
-        transpose(m, m->dZb[l], m->dZbT[l], B, N);          // N x B
-        transpose(m, m->X[l], m->XT[l], B, Kin);             // Kin x B
-        // dW = dZ^T X : (N x B) (Kin x B)^T
-        cudaError_t e = umma_gemm_tma(N, Kin, B, m->dZbT[l], B, m->XT[l], B, m->gW[l], Kin, UmmaEpi{}, m->status,
-                                      m->stream);
-        if (e != cudaSuccess) return MPM_ECUDA;
-        k_col_sum<<<(N + 255) / 256, 256, 0, m->stream>>>(m->dZ[l], m->gb[l], B, N);
-        if (l > 0) {
-            // dA = dZ W : (B x N) (Kin x N)^T
-            e = umma_gemm_tma(B, Kin, N, m->dZb[l], N, m->WbT[l], N, m->dA, Kin, UmmaEpi{}, m->status, m->stream);
-            if (e != cudaSuccess) return MPM_ECUDA;
-            k_gelu_back<<<blocks_for((int64_t)B * Kin), 256, 0, m->stream>>>(m->dA, m->Z[l - 1], m->dZ[l - 1],
-                                                                            (int64_t)B * Kin);
-        }
-    }
-    if (update) {
-        m->step++;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
-        for (int l = 0; l < L; ++l) {
-            const int64_t nw = (int64_t)m->w[l + 1] * m->w[l], nb = m->w[l + 1];
-            k_adam<<<blocks_for(nw), 256, 0, m->stream>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], nw, (float)lr, b1, b2,
-                                                          1e-8f, c1, c2);
-            k_adam<<<blocks_for(nb), 256, 0, m->stream>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], nb, (float)lr, b1, b2,
-                                                          1e-8f, c1, c2);
-            refresh_bf16(m, l);
-        }
-    }
-    rc = check(m);
+    int rc = train_queue(m, batch, x, target, lr, update, device_ptrs != 0);
     if (rc != MPM_OK) return rc;
     if (loss_out &&
         cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
         return MPM_ECUDA;
     return sync_status(m);
+}
+
+int mpm_mlp_train_step_async(mpm_mlp *m, int batch, const float *x_dev, const float *target_dev, double lr,
+                             double *loss_dev)
+{
+    if (!m || !x_dev || !target_dev || batch < 8 || batch > m->max_batch || (batch % 8) || !(lr >= 0))
+        return MPM_EINVAL;
+    int rc = train_queue(m, batch, x_dev, target_dev, lr, 1, true);
+    if (rc != MPM_OK) return rc;
+    if (loss_dev &&
+        cudaMemcpyAsync(loss_dev, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess)
+        return MPM_ECUDA;
+    return MPM_OK;
+}
+
+int mpm_mlp_backward(mpm_mlp *m, int batch, const float *x, const float *dy, double lr, int update, int device_ptrs)
+{
+    if (!m || !x || !dy || batch < 8 || batch > m->max_batch || (batch % 8) || !(lr >= 0)) return MPM_EINVAL;
+    const int L = m->L;
+    int rc = load_x(m, batch, x, device_ptrs != 0);
+    if (rc == MPM_OK) rc = forward(m, batch);
+    if (rc != MPM_OK) return rc;
+    const int64_t nout = (int64_t)batch * m->w[L];
+    if (cudaMemcpyAsync(m->T, dy, sizeof(float) * nout, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        m->stream) != cudaSuccess)
+        return MPM_ECUDA;
+    k_out_back<<<blocks_for(nout), 256, 0, m->stream>>>(m->T, m->Z[L - 1], m->dZ[L - 1], nout, m->lo, m->hi,
+                                                       m->out_act == MPM_OUT_LINEAR);
+    rc = backward_update(m, batch, lr, update);
+    if (rc == MPM_OK) rc = check(m);
+    return rc != MPM_OK ? rc : sync_status(m);
+}
+
+int mpm_mlp_set_activations(mpm_mlp *m, int hidden, int output)
+{
+    if (!m || (hidden != MPM_ACT_GELU && hidden != MPM_ACT_RELU) ||
+        (output != MPM_OUT_SIGMOID && output != MPM_OUT_LINEAR))
+        return MPM_EINVAL;
+    m->hidden_act = hidden;
+    m->out_act = output;
+    return MPM_OK;
 }
 
 int mpm_mlp_last_error(const mpm_mlp *m, char *buf, int len)

@@ -62,13 +62,13 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
 #ifndef MPM_UMMA_PERSIST
 #define MPM_UMMA_PERSIST 1
 #endif
-enum UmmaEpilogue { kEpiStore = 0, kEpiBiasGelu = 1, kEpiBiasSigmoid = 2 };
+enum UmmaEpilogue { kEpiStore = 0, kEpiBiasGelu = 1, kEpiBiasSigmoid = 2, kEpiBiasRelu = 3, kEpiBiasLinear = 4 };
 
 struct UmmaEpi {
     int mode = kEpiStore;
     const float *bias = nullptr;      // N
-    __nv_bfloat16 *xnext = nullptr;   // kEpiBiasGelu: bf16 GELU(z), ld = ldc
-    float *y = nullptr;               // kEpiBiasSigmoid: lo + (hi - lo) sigmoid(z), ld = ldc
+    __nv_bfloat16 *xnext = nullptr;   // kEpiBiasGelu / kEpiBiasRelu: bf16 GELU(z) / max(z, 0), ld = ldc
+    float *y = nullptr;               // kEpiBiasSigmoid: lo + (hi - lo) sigmoid(z); kEpiBiasLinear: z; ld = ldc
     float lo = 0.f, hi = 1.f;
 };
 
@@ -101,6 +101,15 @@ __device__ __forceinline__ bool umma_wait_parity(uint64_t *bar, uint32_t parity)
 }
 
 __device__ __forceinline__ float umma_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+// The fused outputs of one accumulator value z (bias added) at offset o.
+__device__ __forceinline__ void umma_epi_outputs(const UmmaEpi &epi, int64_t o, float z)
+{
+    if (epi.mode == kEpiBiasGelu) epi.xnext[o] = __float2bfloat16_rn(umma_gelu(z));
+    else if (epi.mode == kEpiBiasRelu) epi.xnext[o] = __float2bfloat16_rn(fmaxf(z, 0.0f));
+    else if (epi.mode == kEpiBiasSigmoid) epi.y[o] = epi.lo + (epi.hi - epi.lo) / (1.0f + expf(-z));
+    else if (epi.mode == kEpiBiasLinear) epi.y[o] = z;
+}
 
 template <int NT, int STAGES>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
@@ -220,8 +229,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                     const int64_t o = (int64_t)row * ldc + col;
                     if (epi.mode != kEpiStore) z += epi.bias[col];
                     Cout[o] = z;
-                    if (epi.mode == kEpiBiasGelu) epi.xnext[o] = __float2bfloat16_rn(umma_gelu(z));
-                    else if (epi.mode == kEpiBiasSigmoid) epi.y[o] = epi.lo + (epi.hi - epi.lo) / (1.0f + expf(-z));
+                    umma_epi_outputs(epi, o, z);
                 }
             }
         }
@@ -254,8 +262,7 @@ __device__ __forceinline__ void umma_store8(const uint32_t r[8], int row, int co
         const int64_t o = o0 + e;
         if (epi.mode != kEpiStore) z += epi.bias[col];
         Cout[o] = z;
-        if (epi.mode == kEpiBiasGelu) epi.xnext[o] = __float2bfloat16_rn(umma_gelu(z));
-        else if (epi.mode == kEpiBiasSigmoid) epi.y[o] = epi.lo + (epi.hi - epi.lo) / (1.0f + expf(-z));
+        umma_epi_outputs(epi, o, z);
     }
 }
 

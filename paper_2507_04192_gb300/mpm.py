@@ -108,6 +108,9 @@ def load_library(build_if_missing: bool = True):
             "mpm_mlp_infer": (I, [P, I, P, P, I]),
             "mpm_mlp_train_step": (I, [P, I, P, P, D, I, C.POINTER(D), I]),
             "mpm_mlp_last_error": (I, [P, C.c_char_p, I]),
+            "mpm_mlp_train_step_async": (I, [P, I, P, P, D, P]),
+            "mpm_mlp_set_activations": (I, [P, I, I]),
+            "mpm_mlp_backward": (I, [P, I, P, P, D, I, I]),
             "mpm_save_state": (I, [P, I]),
             "mpm_restore_state": (I, [P, I]),
             "mpm_state_blob_size": (L, [P]),
@@ -344,10 +347,15 @@ def mpm_gemm_bf16(M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, status_ptr, strea
         raise MPMError(rc, "mpm_gemm_bf16")
 
 
+MPM_ACT_GELU, MPM_ACT_RELU = 0, 1
+MPM_OUT_SIGMOID, MPM_OUT_LINEAR = 0, 1
+
+
 class MLP:
     """Binding of mpm_mlp_* (argument marshalling only)."""
 
-    def __init__(self, widths, max_batch, out_lo=0.1, out_hi=0.6, stream=0):
+    def __init__(self, widths, max_batch, out_lo=0.1, out_hi=0.6, stream=0, hidden=MPM_ACT_GELU,
+                 output=MPM_OUT_SIGMOID):
         lib = load_library()
         self.widths = list(widths)
         w = (C.c_int * len(widths))(*widths)
@@ -357,6 +365,8 @@ class MLP:
         if rc != MPM_OK:
             raise MPMError(rc, "mpm_mlp_create")
         self.h = h
+        if hidden != MPM_ACT_GELU or output != MPM_OUT_SIGMOID:
+            self._check(lib.mpm_mlp_set_activations(self.h, int(hidden), int(output)))
 
     def _check(self, rc):
         if rc != MPM_OK:
@@ -391,6 +401,19 @@ class MLP:
         self._check(load_library().mpm_mlp_train_step(self.h, x.shape[0], _dptr(x), _dptr(t), float(lr),
                                                       int(bool(update)), C.byref(loss), 0))
         return loss.value
+
+    def train_step_async(self, batch, x_ptr, target_ptr, lr, loss_ptr=0):
+        """Device pointers, no synchronisation (mpm_mlp_train_step_async)."""
+        self._check(load_library().mpm_mlp_train_step_async(self.h, int(batch), C.c_void_p(x_ptr),
+                                                            C.c_void_p(target_ptr), float(lr),
+                                                            C.c_void_p(loss_ptr) if loss_ptr else None))
+
+    def backward(self, x, dy, lr=0.0, update=False):
+        """Back-propagate a given dL/dy (host arrays); with update, one Adam step."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        g = np.ascontiguousarray(dy, dtype=np.float32)
+        self._check(load_library().mpm_mlp_backward(self.h, x.shape[0], _dptr(x), _dptr(g), float(lr),
+                                                    int(bool(update)), 0))
 
     def close(self):
         if self.h:

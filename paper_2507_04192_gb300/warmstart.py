@@ -170,11 +170,17 @@ class WarmStartNet:
         spread (the displacements friction changes differ by orders of magnitude
         between tracks near the front and inside the column)."""
         X = np.asarray(X, dtype=np.float64)
+        Y = np.asarray(Y, dtype=np.float32)
+        # the last 1/16 of the runs (at least one batch) is held back to measure the
+        # network's error: the spread a warm start carries, which sets the step of
+        # the adjoint refinement that follows it (see refine_rate)
+        n_val = max(self.max_batch, len(X) // 16) if len(X) >= 2 * self.max_batch else 0
+        Xv, Yv = X[len(X) - n_val:], Y[len(Y) - n_val:]
+        X, Y = X[:len(X) - n_val], Y[:len(Y) - n_val]
         self.x_mean = X.mean(axis=0)
         sd = X.std(axis=0)
         self.x_scale = np.where(sd > 1e-9, sd, 1.0)          # tracks friction never reaches stay ~0
         Xs = self._standardise(X)
-        Y = np.asarray(Y, dtype=np.float32)
         rng = np.random.default_rng(seed)
         B = self.max_batch
         n = (len(X) // B) * B
@@ -183,7 +189,15 @@ class WarmStartNet:
             order = rng.permutation(len(X))[:n]
             losses = [self.net.train_step(Xs[order[i:i + B]], Y[order[i:i + B]], lr) for i in range(0, n, B)]
             hist.append(float(np.mean(losses)))
+        self.val_rmse = float(np.sqrt(np.mean((self.predict(Xv) - Yv) ** 2))) if n_val else None
         return hist
+
+    def refine_rate(self, default: float = 0.1) -> float:
+        """First Adam step of the adjoint refinement that starts from this network's
+        prediction: Adam moves every coefficient by about its rate in the first
+        steps, so the rate is matched to the network's held-out RMS error instead
+        of the uniform guess's 0.1 (a larger step throws a good warm start away)."""
+        return default if self.val_rmse is None else float(min(default, max(self.val_rmse, 2e-3)))
 
     def predict(self, X) -> np.ndarray:
         X = self._standardise(np.atleast_2d(X))
@@ -218,7 +232,7 @@ def compare(setup: Setup, net: WarmStartNet, mu_seeds, tol: float = 0.05, max_it
             mu_warm = np.clip(net.predict(features(setup, w, z)[None, :])[0], 0.0, 1.0)
             mu_unif = np.full(setup.n_seg, UNIFORM_GUESS)
             res_u = inverse.invert(prob, mu_unif, mu_true, mask, tol, max_iters)
-            res_w = inverse.invert(prob, mu_warm, mu_true, mask, tol, max_iters)
+            res_w = inverse.invert(prob, mu_warm, mu_true, mask, tol, max_iters, lr0=net.refine_rate())
         finally:
             prob.close()
         rows.append(dict(seed=int(s), constrained=int(mask.sum()),
@@ -255,10 +269,9 @@ def main(argv=None):
     hist = net.fit(X, Y, epochs=args.epochs)
     t2 = time.perf_counter()
     rows = compare(setup, net, range(1, args.held_out + 1), max_iters=args.max_iters)
-    net.close()
     summary = {
         "setup": {k: v for k, v in setup.__dict__.items()}, "runs": args.runs, "generate_s": t1 - t0, "train_s": t2 - t1,
-        "train_loss": [hist[0], hist[-1]],
+        "train_loss": [hist[0], hist[-1]], "val_rmse": net.val_rmse, "warm_refine_lr0": net.refine_rate(),
         "uniform": {"converged": sum(r["converged_uniform"] for r in rows),
                     "median_iters": float(np.median([r["iters_uniform"] for r in rows])),
                     "mean_err0": float(np.mean([r["err0_uniform"] for r in rows]))},
@@ -267,6 +280,7 @@ def main(argv=None):
                  "mean_err0": float(np.mean([r["err0_warm"] for r in rows]))},
         "rows": rows,
     }
+    net.close()
     print(json.dumps(summary))
 
 

@@ -148,3 +148,79 @@ def test_network_argument_errors():
     with pytest.raises(mpm.MPMError):
         net.infer(np.zeros((72, 16)))                    # above max_batch
     net.close()
+
+
+# ---- the coordinate network of Eq. nn_apprx (Sec. 5.2): 1 -> 30 -> 30 -> 30 -> 1 with ReLU,
+# padded to multiples of 8 (8 -> 32 -> 32 -> 32 -> 8; the padding is inert), linear output
+
+COORD = [8, 32, 32, 32, 8]
+
+
+def _coord_params(seed):
+    rng = np.random.default_rng(seed)
+    w = [1, 30, 30, 30, 1]
+    layers = []
+    for l in range(4):
+        W = np.zeros((COORD[l + 1], COORD[l]))
+        W[:w[l + 1], :w[l]] = rng.standard_normal((w[l + 1], w[l])) * np.sqrt(2.0 / w[l])
+        b = np.zeros(COORD[l + 1])
+        b[:w[l + 1]] = rng.standard_normal(w[l + 1]) * 0.1
+        layers.append((W, b))
+    return omlp.pack(layers).astype(np.float32)
+
+
+def _coords(batch, seed):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((batch, 8), dtype=np.float32)
+    x[:, 0] = rng.uniform(0.0, 1.0, batch)
+    return x
+
+
+def test_coordinate_network_matches_oracle():
+    p = _coord_params(10)
+    x = _coords(256, 11)
+    net = mpm.MLP(COORD, 256, hidden=mpm.MPM_ACT_RELU, output=mpm.MPM_OUT_LINEAR)
+    net.set_params(p)
+    y = net.infer(x)
+    rng = np.random.default_rng(12)
+    dy = np.zeros((256, 8), dtype=np.float32)
+    dy[:, 0] = rng.standard_normal(256)
+    net.backward(x, dy, lr=0.0, update=False)
+    g = net.get_params(which=1).astype(np.float64)
+    net.close()
+    kw = dict(hidden="relu", out="linear")
+    ref, _, _ = omlp.forward(p.astype(np.float64), COORD, x.astype(np.float64), **kw)
+    scale = np.abs(ref[:, 0]).max()
+    assert np.abs(y[:, 0] - ref[:, 0]).max() <= 5e-3 * scale
+    assert np.abs(y[:, 1:]).max() == 0.0                  # padded outputs: zero weights, zero bias
+    ref_g = omlp.backward(p.astype(np.float64), COORD, x.astype(np.float64), dy.astype(np.float64), **kw)
+    o = 0
+    for l in range(len(COORD) - 1):
+        for n in (COORD[l + 1] * COORD[l], COORD[l + 1]):
+            gs, rs = g[o:o + n], ref_g[o:o + n]
+            assert np.linalg.norm(gs - rs) <= 2e-2 * np.linalg.norm(rs) + 1e-12, (l, n)
+            assert np.all(gs[rs == 0.0] == 0.0)            # inert padding stays exactly zero
+            o += n
+
+
+def test_async_train_step_equals_the_synchronous_one():
+    torch = pytest.importorskip("torch")
+    p = _params(WIDTHS, 13)
+    x, t = _data(256, WIDTHS, 14)
+    a, b = mpm.MLP(WIDTHS, 256), mpm.MLP(WIDTHS, 256)
+    a.set_params(p)
+    b.set_params(p)
+    la = [a.train_step(x, t, lr=1e-3) for _ in range(3)]
+    dx, dt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()                   # the network runs on its own stream
+    lb = []
+    for _ in range(3):
+        b.train_step_async(256, dx.data_ptr(), dt.data_ptr(), 1e-3, loss.data_ptr())
+        torch.cuda.synchronize()
+        lb.append(float(loss.item()))
+    pa, pb = a.get_params(0), b.get_params(0)
+    a.close()
+    b.close()
+    assert lb == pytest.approx(la, rel=1e-6)
+    np.testing.assert_array_equal(pa, pb)
