@@ -286,6 +286,12 @@ __device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, cons
     }
 }
 
+// State component of adjoint component c < 2D + D^2 (the adjoint order is x, v, C, rho [, sigma]).
+template <int D, class R> __device__ __forceinline__ int adj_state_comp(const Params<R> &P, int c)
+{
+    return c < D ? P.off_x + c : (c < 2 * D ? P.off_v + (c - D) : P.off_C + (c - 2 * D));
+}
+
 // Particle state gather (slot order -> load order) and scatter.
 template <class R, int D>
 __global__ void k_adj_save(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
@@ -293,13 +299,14 @@ __global__ void k_adj_save(const Params<R> P, const R *__restrict__ S, const int
 {
     constexpr int NA = adj_ncomp<D>();
     const int nsig = P.material == 1 ? 6 : 0;
-    const int64_t n = P.n, np = P.npad;
+    const int64_t n = P.n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[i];
+        const R *Sp = S + sblock(i, P.ncomp);
 #pragma unroll
-        for (int c = 0; c < NA - 1; ++c) dst[c * n + o] = S[c * np + i];
-        dst[(NA - 1) * n + o] = S[P.off_rho * np + i];
-        for (int k = 0; k < nsig; ++k) dst[(NA + k) * n + o] = S[(P.off_sig + k) * np + i];
+        for (int c = 0; c < NA - 1; ++c) dst[c * n + o] = Sp[adj_state_comp<D>(P, c) * kPB];
+        dst[(NA - 1) * n + o] = Sp[P.off_rho * kPB];
+        for (int k = 0; k < nsig; ++k) dst[(NA + k) * n + o] = Sp[(P.off_sig + k) * kPB];
     }
 }
 
@@ -309,13 +316,14 @@ __global__ void k_adj_restore(const Params<R> P, R *__restrict__ S, const int32_
 {
     constexpr int NA = adj_ncomp<D>();
     const int nsig = P.material == 1 ? 6 : 0;
-    const int64_t n = P.n, np = P.npad;
+    const int64_t n = P.n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[i];
+        R *Sp = S + sblock(i, P.ncomp);
 #pragma unroll
-        for (int c = 0; c < NA - 1; ++c) S[c * np + i] = src[c * n + o];
-        S[P.off_rho * np + i] = src[(NA - 1) * n + o];
-        for (int k = 0; k < nsig; ++k) S[(P.off_sig + k) * np + i] = src[(NA + k) * n + o];
+        for (int c = 0; c < NA - 1; ++c) Sp[adj_state_comp<D>(P, c) * kPB] = src[c * n + o];
+        Sp[P.off_rho * kPB] = src[(NA - 1) * n + o];
+        for (int k = 0; k < nsig; ++k) Sp[(P.off_sig + k) * kPB] = src[(NA + k) * n + o];
     }
 }
 
@@ -324,12 +332,11 @@ template <class R, int D>
 __global__ void k_adj_track(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
                             const int32_t *__restrict__ track_of_id, double *__restrict__ out)
 {
-    const int64_t np = P.npad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
         const int l = track_of_id[id[i]];
         if (l < 0) continue;
 #pragma unroll
-        for (int a = 0; a < D; ++a) out[(int64_t)l * D + a] = (double)S[(P.off_x + a) * np + i];
+        for (int a = 0; a < D; ++a) out[(int64_t)l * D + a] = (double)S[sblock(i, P.ncomp) + (P.off_x + a) * kPB];
     }
 }
 
@@ -385,7 +392,8 @@ __global__ void k_adj_seed_slots(int64_t n, const int32_t *__restrict__ id, cons
 // each monitor region).  Per closed box [lo, hi] (boxes: n_mon x 2 x D doubles,
 // low corner then high corner) the sum of v_p and the count of the particles
 // with x_p inside: sums[l (D + 1) + a] (a < D) and sums[l (D + 1) + D].  x and v
-// are component arrays with stride ld.  Block sums in shared memory, then one
+// point at the first component of a state view (sview: component-major with
+// stride ld > 0, or the blocked particle state with -ld components).  Block sums in shared memory, then one
 // FP64 atomic per monitor and value.
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_monitor_sum(int64_t n, int64_t ld, const R *__restrict__ x,
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(256) k_monitor_sum(int64_t n, int64_t ld, cons
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double xp[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) xp[a] = (double)x[a * ld + i];
+        for (int a = 0; a < D; ++a) xp[a] = (double)sview(x, ld, a, i);
         for (int l = 0; l < n_mon; ++l) {
             const double *b = boxes + (int64_t)l * 2 * D;
             bool in = true;
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(256) k_monitor_sum(int64_t n, int64_t ld, cons
             for (int a = 0; a < D; ++a) in = in && xp[a] >= b[a] && xp[a] <= b[D + a];
             if (!in) continue;
 #pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(&acc[l * (D + 1) + a], (double)v[a * ld + i]);
+            for (int a = 0; a < D; ++a) atomicAdd(&acc[l * (D + 1) + a], (double)sview(v, ld, a, i));
             atomicAdd(&acc[l * (D + 1) + D], 1.0);
         }
     }
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(256) k_monitor_sum(int64_t n, int64_t ld, cons
 
 // Adjoint seed of the monitor loss sum_l |Q_l - z_l|^2: for every particle inside
 // monitor l, lam.v += g_l with g_l = 2 (Q_l - z_l) / |P_l| (membership held fixed).
-// x: component arrays with stride ld, in the order of lam.
+// x: the first position component of a state view (sview), in the order of lam.
 template <class R, int D>
 __global__ void k_monitor_seed(int64_t n, int64_t ld, const R *__restrict__ x, int n_mon,
                                const double *__restrict__ boxes, const double *__restrict__ g, R *__restrict__ lam)
@@ -425,7 +433,7 @@ __global__ void k_monitor_seed(int64_t n, int64_t ld, const R *__restrict__ x, i
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double xp[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) xp[a] = (double)x[a * ld + i];
+        for (int a = 0; a < D; ++a) xp[a] = (double)sview(x, ld, a, i);
         for (int l = 0; l < n_mon; ++l) {
             const double *b = boxes + (int64_t)l * 2 * D;
             bool in = true;

@@ -406,14 +406,15 @@ int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cu
         return MPM_EINVAL;
     }
     const int d = g.dim;
+    // component order: what G2P reads (x, F, rho [, sigma, eps]) first, then v, C
     h.off_x = 0;
-    h.off_v = d;
-    h.off_C = 2 * d;
-    h.off_F = 2 * d + d * d;
-    h.off_rho = 2 * d + 2 * d * d;
+    h.off_F = d;
+    h.off_rho = d + d * d;
     h.off_sig = h.off_rho + 1;
     h.off_eps = h.off_sig + 6;
-    h.ncomp = m.kind == MPM_DRUCKER_PRAGER ? h.off_eps + 1 : h.off_rho + 1;
+    h.off_v = m.kind == MPM_DRUCKER_PRAGER ? h.off_eps + 1 : h.off_rho + 1;
+    h.off_C = h.off_v + d;
+    h.ncomp = h.off_C + d * d;
     c->ops = g.precision == MPM_FP64 ? &ops_f64 : &ops_f32;
     c->aops = g.precision == MPM_FP64 ? &adj_ops_f64 : &adj_ops_f32;
 
@@ -510,7 +511,7 @@ int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, 
     CK(cudaStreamSynchronize(ds.stream), "synchronize before load");
     free_particles(c);
     h.n = n;
-    h.npad = (n + 63) / 64 * 64;
+    h.npad = (n + 63) / 64 * 64;                  // whole blocks of kPB particles
     h.vol0 = particle_volume;
     h.mass = h.rho0 * particle_volume;
     const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
@@ -913,8 +914,8 @@ int mpm_monitor_means(mpm_ctx *c, int n_mon, const double *boxes, double *out)
     cudaError_t e = cudaMemcpyAsync(dboxes, boxes, sizeof(double) * n_mon * 2 * d, cudaMemcpyHostToDevice, ds.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, sizeof(double) * n_mon * (d + 1), ds.stream);
     if (e == cudaSuccess) {
-        const size_t rsz = h.precision == MPM_FP64 ? 8 : 4, rs = rsz * (size_t)h.npad;
-        c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, h.npad, n_mon, dboxes,
+        const size_t rsz = h.precision == MPM_FP64 ? 8 : 4, rs = rsz * (size_t)kPB;
+        c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, -h.ncomp, n_mon, dboxes,
                              dev);
         e = cudaMemcpyAsync(out, dev, sizeof(double) * n_mon * (d + 1), cudaMemcpyDeviceToHost, ds.stream);
     }
@@ -1139,8 +1140,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         if (rc != MPM_OK) return rc;
         if (obs_of_step[t] >= 0) c->aops->track(h, ds, a.d_track_of_id, a.d_xobs + obs_of_step[t] * obs_stride);
         if (mobs_of_step[t] >= 0) {
-            const size_t rs = rsz * (size_t)h.npad;
-            c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, h.npad, a.n_mon,
+            const size_t rs = rsz * (size_t)kPB;
+            c->aops->monitor_sum(h, ds, (char *)ds.S + rs * h.off_x, (char *)ds.S + rs * h.off_v, -h.ncomp, a.n_mon,
                                  a.d_mboxes, a.d_msums + mobs_of_step[t] * msum_stride);
         }
         if (t % K == 0 && t / K < first_kept) c->aops->save(h, ds, ckpt_ptr(t / K));   // recomputed later
@@ -1193,8 +1194,8 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                             a.lam[cur]);
     }
     if (mobs_of_step[n_steps] >= 0) {               // the final state's positions, in the order of lam
-        const size_t rs = rsz * (size_t)h.npad;
-        c->aops->monitor_seed(h, ds, (char *)ds.S + rs * h.off_x, h.npad, a.n_mon, a.d_mboxes,
+        const size_t rs = rsz * (size_t)kPB;
+        c->aops->monitor_seed(h, ds, (char *)ds.S + rs * h.off_x, -h.ncomp, a.n_mon, a.d_mboxes,
                               a.d_mg + mobs_of_step[n_steps] * mg_stride, a.lam[cur]);
     }
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
@@ -1317,6 +1318,26 @@ struct BlobHeader {
     uint64_t magic, n, ncomp, npad, precision, dim, payload, checksum;
 };
 constexpr uint64_t kBlobMagic = 0x4d504d5354415445ull;   // "MPMSTATE"
+// One component of the blocked particle state to or from n consecutive host
+// values: a strided copy over the whole blocks of kPB particles, then the tail.
+cudaError_t copy_component(const HostParams &h, int comp, char *S, char *host, bool to_device, cudaStream_t st)
+{
+    const size_t rs = h.precision == MPM_FP64 ? 8 : 4;
+    const size_t row = kPB * rs, pitch = (size_t)h.ncomp * kPB * rs;
+    const int64_t nfull = h.n / kPB, rem = h.n % kPB;
+    char *dev = S + (size_t)comp * kPB * rs;
+    cudaError_t e = cudaSuccess;
+    if (nfull > 0)
+        e = to_device ? cudaMemcpy2DAsync(dev, pitch, host, row, row, (size_t)nfull, cudaMemcpyHostToDevice, st)
+                      : cudaMemcpy2DAsync(host, row, dev, pitch, row, (size_t)nfull, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && rem > 0) {
+        char *dt = dev + (size_t)nfull * pitch, *ht = host + (size_t)nfull * row;
+        e = to_device ? cudaMemcpyAsync(dt, ht, (size_t)rem * rs, cudaMemcpyHostToDevice, st)
+                      : cudaMemcpyAsync(ht, dt, (size_t)rem * rs, cudaMemcpyDeviceToHost, st);
+    }
+    return e;
+}
+
 }  // namespace
 
 int64_t mpm_state_blob_size(const mpm_ctx *c)
@@ -1340,8 +1361,7 @@ int mpm_export_state(mpm_ctx *c, void *blob, int64_t size)
                   (uint64_t)h.dim, (uint64_t)(need - (int64_t)sizeof(BlobHeader)), 0};
     unsigned char *out = (unsigned char *)blob + sizeof(BlobHeader);
     for (int comp = 0; comp < h.ncomp; ++comp)
-        CK(cudaMemcpyAsync(out + (size_t)comp * h.n * rs, (const char *)ds.S + (size_t)comp * h.npad * rs,
-                           (size_t)h.n * rs, cudaMemcpyDeviceToHost, ds.stream),
+        CK(copy_component(h, comp, (char *)ds.S, (char *)out + (size_t)comp * h.n * rs, false, ds.stream),
            "export state");
     unsigned char *ids = out + (size_t)h.ncomp * h.n * rs;
     CK(cudaMemcpyAsync(ids, ds.id, sizeof(int32_t) * h.n, cudaMemcpyDeviceToHost, ds.stream), "export ids");
@@ -1387,8 +1407,7 @@ int mpm_import_state(mpm_ctx *c, const void *blob, int64_t size)
     }
     DevState &ds = c->ds;
     for (int comp = 0; comp < h.ncomp; ++comp)
-        CK(cudaMemcpyAsync((char *)ds.S + (size_t)comp * h.npad * rs, in + (size_t)comp * h.n * rs, (size_t)h.n * rs,
-                           cudaMemcpyHostToDevice, ds.stream),
+        CK(copy_component(h, comp, (char *)ds.S, (char *)in + (size_t)comp * h.n * rs, true, ds.stream),
            "import state");
     CK(cudaMemcpyAsync(ds.id, ids.data(), sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import ids");
     CK(cudaMemcpyAsync(ds.sim, sims.data(), sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, ds.stream), "import sims");

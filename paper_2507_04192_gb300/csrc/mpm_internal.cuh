@@ -36,6 +36,24 @@ constexpr int kSortItems = 16;
 constexpr int kSortChunk = kSortThreads * kSortItems;
 constexpr int kScanSegments = 1024;              // scratch words after the digit histogram
 
+// Particle state layout: blocks of kPB particles (the slots 32 b .. 32 b + 31);
+// inside a block the components follow each other, component c of the block's
+// particle r at element c kPB + r.  All components of one particle therefore sit
+// at fixed offsets (multiples of kPB elements) from one address, and a warp that
+// reads one component of kPB consecutive particles reads one contiguous line.
+constexpr int kPB = 32;
+// First element of particle p's components (component c at + c kPB).
+__host__ __device__ __forceinline__ int64_t sblock(int64_t p, int ncomp)
+{
+    return (p >> 5) * (int64_t)ncomp * kPB + (p & (kPB - 1));
+}
+// Element of component c of particle i in a state view: component-major with
+// stride ld (ld > 0) or blocked as above with -ld components (ld < 0).
+template <class R> __host__ __device__ __forceinline__ R sview(const R *base, int64_t ld, int c, int64_t i)
+{
+    return ld > 0 ? base[c * ld + i] : base[sblock(i, (int)(-ld)) + (int64_t)c * kPB];
+}
+
 template <int D> struct Geo;
 template <> struct Geo<2> {
     static constexpr int T = 16;                 // cells per tile edge
@@ -84,7 +102,7 @@ struct Params {
     int n_cells[3];
     R dx, inv_dx, dt, gravity[3], L[3];
     R rho0, bulk_K, gamma, inv_rho0, mass, m_eps;
-    R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef;
+    R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef, inv_G_Kqq, inv_K;
     int material, dp_literal, gamma_int, transfer, no_force;
     R flip_alpha;
     R *save_S;                    // P2G: copy of its inputs in slot order (nullptr = none)
@@ -93,7 +111,7 @@ struct Params {
     int n_tiles[3], G_nodes[3], node_tiles[3];
     int64_t nodes_per_sim, tiles_per_sim, node_tiles_per_sim;
     int64_t n, npad;
-    int off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
+    int ncomp, off_x, off_v, off_C, off_F, off_rho, off_sig, off_eps;
     WallDev wall[kMaxWalls];
     Obstacles obs;
     double *diag;                 // conservation sums of the step (nullptr = off), see kDiag*
@@ -108,7 +126,7 @@ template <> struct alignas(32) R4<double> { double x, y, z, w; };
 struct DevState {
     cudaStream_t stream;
     int num_sms;
-    void *S, *S2;                 // particle SoA, ncomp x npad reals
+    void *S, *S2;                 // particle state, ncomp x npad reals in blocks of kPB particles (sblock)
     int32_t *id, *id2;            // load-order id of each sorted slot
     int32_t *sim, *sim2;          // simulation id of each slot
     uint32_t *keys[2];

@@ -111,6 +111,14 @@ __device__ __forceinline__ R wall_mu(const Params<R> &P, int w, int sim, const i
     return static_cast<const R *>(wd.mu)[sim * per_sim + (int64_t)s[1] * wd.n_seg[0] + s[0]];
 }
 
+// Component offsets of the particle state, the order the host sets up: what G2P
+// reads first (x, F, rho, and sigma, eps for Drucker-Prager), then v and C.
+template <int D, int MAT> struct Lay {
+    static constexpr int X = 0, F = D, RHO = D + D * D, SIG = RHO + 1, EPS = RHO + 7;
+    static constexpr int V = MAT == 1 ? RHO + 8 : RHO + 1, C = V + D, NC = C + D * D;
+    static constexpr int G2P_IN = V;             // G2P reads components [0, G2P_IN)
+};
+
 // ------------------------------------------------------------------ TMA / mbarrier helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -220,26 +228,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-// Stage particle positions [p0, p0 + count) of nc state components into a
-// shared buffer (component j at buf + j * pitch), issued by warp 0: lane 0 sets
-// the expected bytes, lanes j < nc copy component comp(j).  The copy starts at
-// p0 rounded down to 8 elements; returns that start.
-template <class R, class CompOf>
-__device__ __forceinline__ int64_t stage_rows(R *buf, int pitch, const R *__restrict__ S, int64_t npad, int64_t p0,
-                                              int count, int nc, CompOf comp, uint64_t *bar)
+// Stage the first ng components of the particle blocks covering slots
+// [a, a + count) (a a multiple of kPB) into a shared buffer, block after block
+// (ng kPB reals each: particle a + l's component c at buf[(l / kPB) ng kPB + c kPB
+// + l % kPB]).  Issued by warp 0: lane 0 sets the expected bytes, lane k copies
+// block k with one bulk copy.
+template <class R>
+__device__ __forceinline__ void stage_blocks(R *buf, const R *__restrict__ S, int ncomp, int ng, int64_t a, int count,
+                                             uint64_t *bar)
 {
-    const int64_t a = p0 & ~int64_t(7);
-    const int len = (int)(((p0 + count - a) + 7) & ~int64_t(7));
+    const int nblk = (count + kPB - 1) / kPB;
+    const uint32_t bytes = (uint32_t)(ng * kPB * sizeof(R));
     if (threadIdx.x < 32) {
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
-            mbar_expect_tx(bar, (uint32_t)(nc * len * sizeof(R)));
+            mbar_expect_tx(bar, (uint32_t)nblk * bytes);
         }
         __syncwarp();
-        for (int j = threadIdx.x; j < nc; j += 32)
-            bulk_g2s(buf + (int64_t)j * pitch, S + (int64_t)comp(j) * npad + a, (uint32_t)(len * sizeof(R)), bar);
+        for (int k = threadIdx.x; k < nblk; k += 32)
+            bulk_g2s(buf + (int64_t)k * ng * kPB, S + ((a >> 5) + k) * (int64_t)ncomp * kPB, bytes, bar);
     }
-    return a;
 }
 
 // ------------------------------------------------------------------ P2G
@@ -263,6 +271,15 @@ template <class R, int D> struct P2GFactors {
 template <int D> __host__ __device__ __forceinline__ constexpr int p2g_ncomp(int material)
 {
     return 2 * D + D * D + 1 + (material == 1 ? 6 : 0);
+}
+// State component of P2G staging slot j (x, v, C, rho, sigma).
+template <int D, int MAT> __host__ __device__ __forceinline__ constexpr int p2g_comp(int j)
+{
+    using Ly = Lay<D, MAT>;
+    return j < D ? Ly::X + j
+                 : (j < 2 * D ? Ly::V + (j - D)
+                              : (j < 2 * D + D * D ? Ly::C + (j - 2 * D)
+                                                   : (j == 2 * D + D * D ? Ly::RHO : Ly::SIG + (j - 2 * D - D * D - 1))));
 }
 
 // P2G factors of one particle from its raw components raw(j) (staging order).
@@ -519,9 +536,7 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
 {
     using Gm = Geo<D>;
     constexpr int NCM = kP2GStageComps<D>;
-    constexpr int NXC = 2 * D + D * D;                // x, v, C: consecutive in the state
     constexpr int NC = p2g_ncomp<D>(MAT);             // components this material stages
-    constexpr int OFF_RHO = 2 * D + 2 * D * D;        // rho (then sigma) follow x, v, C, F
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     int32_t *off = reinterpret_cast<int32_t *>(sm + (D + 1) * Gm::WN);
@@ -530,7 +545,6 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
     __shared__ int s_slot;
     const int n_tiles = counters[1];
     const int tid = threadIdx.x;
-    const int64_t npad = P.npad;
     for (;;) {
         const int k = next_tile(&counters[2], n_tiles, &s_slot);
         if (k < 0) break;
@@ -550,18 +564,14 @@ __global__ void __launch_bounds__(NT, (D == 3 && REG) ? MPM_P2G_MINB : 1)
         R4<R> *Asim = A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = flags + (int64_t)sim * P.node_tiles_per_sim;
         const int32_t *pmap = posmap + t.y;
-        const R *St = S + t.y;
         bool any_escape = false;
 
         R *const Sv = P.save_S == nullptr ? nullptr : P.save_S + t.y;
         auto issue = [&](int stage, int32_t pos) {
             R *dst = stg + stage * NCM * NT + tid;
-            const R *src = St + pos;
+            const R *src = S + sblock((int64_t)t.y + pos, Lay<D, MAT>::NC);
 #pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
-                cp_async_elem(dst + j * NT, src + comp * npad);
-            }
+            for (int j = 0; j < NC; ++j) cp_async_elem(dst + j * NT, src + p2g_comp<D, MAT>(j) * kPB);
         };
         // producer: MPM_P2G_STAGES particles ahead of the consumer, its next slot's position prefetched
         CellCursor<Gm::TN, NT> pc, cc;
@@ -758,16 +768,12 @@ __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R>
 // Components staged per particle by k_p2g_direct: P2G's inputs (MAT 0, 1), or x
 // and the 21 scatter coefficients (MAT 2).
 template <int MAT> __host__ __device__ constexpr int direct_stage_comps() { return MAT == 2 ? 24 : kP2GStageComps<3>; }
-// Per warp of k_p2g_direct: its work item's 129 cell offsets (padded to 132) and
-// up to kDirectPmapCap entries of the position map, staged in shared memory at
-// the start of the item (an item holding more particles reads the map from
-// global memory).
+// Per warp of k_p2g_direct: its work item's 129 cell offsets (padded to 132),
+// staged in shared memory at the start of the item.
 constexpr int kDirectOffPad = 132;
-constexpr int kDirectPmapCap = 1280;
 template <class R, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
 {
-    return (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R) +
-           (size_t)(NT / 32) * (kDirectOffPad + kDirectPmapCap) * sizeof(int32_t);
+    return (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R) + (size_t)(NT / 32) * kDirectOffPad * sizeof(int32_t);
 }
 
 // P2G without a shared-memory window (3D, register accumulation).  Warps claim
@@ -790,17 +796,14 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
     using Gm = Geo<D>;
     constexpr bool ADJ = MAT == 2;
     constexpr int NCM = direct_stage_comps<MAT>();
-    constexpr int NXC = 2 * D + D * D;
     constexpr int NC = ADJ ? 24 : p2g_ncomp<D>(MAT);
-    constexpr int OFF_RHO = 2 * D + 2 * D * D;
     constexpr int CELLS = 128;                       // cells per work item
     constexpr int ITEMS = Gm::TN / CELLS;            // work items per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *stg = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     int32_t *const s_off = reinterpret_cast<int32_t *>(smem_raw + (size_t)2 * NCM * NT * sizeof(R)) +
-                           (tid >> 5) * (kDirectOffPad + kDirectPmapCap);
-    int32_t *const s_pm = s_off + kDirectOffPad;
+                           (tid >> 5) * kDirectOffPad;
     const int n_items = *io.n_tiles * ITEMS;
     const int64_t ld = io.ld;
     const R mass = ADJ ? R(0) : P.mass;
@@ -825,19 +828,15 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
         const int32_t *pmap = io.posmap + t.y;
         const int32_t *goff = io.cell_off + (int64_t)k * (Gm::TN + 1) + cbase;
-        // the item's cell offsets and position map, staged once (coalesced) so that the
-        // per-cell and per-particle lookups below are shared-memory reads
+        // the item's cell offsets, staged once (coalesced) so that the per-cell lookups
+        // below are shared-memory reads (staging the position map as well cost more in
+        // registers than it saved)
         __syncwarp();
         for (int i = lane; i <= CELLS; i += 32) s_off[i] = goff[i];
         __syncwarp();
-        const int q0 = s_off[0], nq = s_off[CELLS] - q0;
-        const bool pm_staged = nq <= kDirectPmapCap;
-        if (pm_staged)
-            for (int i = lane; i < nq; i += 32) s_pm[i] = pmap[q0 + i];
-        __syncwarp();
         const int32_t *off = s_off - cbase;           // off[c] for the item's cells c in [cbase, cbase + CELLS]
-        auto slot = [&](int q) { return pm_staged ? s_pm[q - q0] : pmap[q]; };
-        const R *St = io.S + t.y;
+        auto slot = [&](int q) { return pmap[q]; };
+        const R *St = io.S + t.y;                     // MAT 2: component-major with stride ld
         const R *S2 = ADJ ? io.src2 + t.y : nullptr;
         R *const Sv = (ADJ || P.save_S == nullptr) ? nullptr : P.save_S + t.y;
         auto issue = [&](int stage, int32_t pos) {
@@ -847,13 +846,10 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
                 for (int j = 0; j < 3; ++j) cp_async_elem(dst + j * NT, St + pos + j * ld);
 #pragma unroll
                 for (int j = 0; j < 21; ++j) cp_async_elem(dst + (3 + j) * NT, S2 + pos + j * ld);
-            } else {
-                const R *src = St + pos;
+            } else {                                  // the particle state, in blocks of kPB
+                const R *src = io.S + sblock((int64_t)t.y + pos, Lay<D, MAT>::NC);
 #pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    const int comp = j < NXC ? j : OFF_RHO + (j - NXC);
-                    cp_async_elem(dst + j * NT, src + comp * ld);
-                }
+                for (int j = 0; j < NC; ++j) cp_async_elem(dst + j * NT, src + p2g_comp<D, MAT>(j) * kPB);
             }
         };
         // cursors over this lane's cells cbase + lane + 32 r and their slots
@@ -1122,8 +1118,8 @@ __global__ void __launch_bounds__(256) k_diag_particles(const Params<R> P, const
         dsum[0] += mp;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const R v = S[(int64_t)(P.off_v + a) * P.npad + p];
-            const R x = S[(int64_t)(P.off_x + a) * P.npad + p];
+            const R v = S[sblock(p, P.ncomp) + (P.off_v + a) * kPB];
+            const R x = S[sblock(p, P.ncomp) + (P.off_x + a) * kPB];
             fin = fin && rfinite(v) && rfinite(x);
             dsum[1 + a] += mp * (double)v;
         }
@@ -1183,7 +1179,7 @@ __device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[
         return;
     }
     if ((fs > R(0) && ft < R(0)) || (h > R(0) && ft >= R(0))) {
-        const R dl = fs / (P.G + P.K * P.q_phi * P.q_psi);
+        const R dl = fs * P.inv_G_Kqq;                 // fs / (G + K q_phi q_psi)
         R smn = sm - P.K * P.q_psi * dl;
         R taun = P.k_phi - P.q_phi * smn;
         if (!P.dp_literal && smn > P.sig_t) {
@@ -1196,7 +1192,7 @@ __device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[
         eps += dl * P.eps2_coef;
         return;
     }
-    eps += (sm - P.sig_t) / P.K * (R(1.4142135623730951) / R(3));
+    eps += (sm - P.sig_t) * P.inv_K * (R(1.4142135623730951) / R(3));
     R r = R(1);
     if (!P.dp_literal && tau > P.tau_P) r = P.tau_P / tau;
     s[0] = r * dev[0] + P.sig_t; s[1] = r * dev[1] + P.sig_t; s[2] = r * dev[2] + P.sig_t;
@@ -1296,12 +1292,6 @@ template <int D> __host__ __device__ __forceinline__ constexpr int g2p_ncomp(int
     return D + D * D + 1 + (material == 1 ? 7 : 0);
 }
 
-// Component offsets of the particle state (the layout the host sets up: x, v, C,
-// F, rho, then sigma and eps for Drucker-Prager), as compile-time constants.
-template <int D> struct Lay {
-    static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, RHO = 2 * D + 2 * D * D, SIG = RHO + 1,
-                         EPS = RHO + 7;
-};
 
 template <class R, int D, bool GENERIC, int MAT, class Raw>
 __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__restrict__ S, int64_t p,
@@ -1309,10 +1299,10 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
                                              const R4<R> *__restrict__ V2s = nullptr)
 {
     using Gm = Geo<D>;
-    using Ly = Lay<D>;
+    using Ly = Lay<D, MAT>;
     constexpr int J_F = D, J_RHO = D + D * D;
-    const int64_t np = P.npad;
-    R *__restrict__ Sp = S + p;                    // component c of this particle at Sp[c np]
+    constexpr int64_t np = kPB;                    // component stride inside a particle block
+    R *__restrict__ Sp = S + sblock(p, Ly::NC);    // component c of this particle at Sp[c kPB]
     bool bad = false;
     R x[D];
 #pragma unroll
@@ -1375,10 +1365,14 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
         for (int a = 0; a < D; ++a) vnew[a] = vp[a] + P.flip_alpha * (Sp[(Ly::V + a) * np] - vo[a]);
     }
 #pragma unroll
+    // one finiteness test for the whole new state: a sum of finite values is finite
+    // (values near the overflow threshold are themselves a blown-up state), and a
+    // non-finite term makes it +-inf or NaN
+    R chk = R(0);
     for (int a = 0; a < D; ++a) {
         R xn = x[a] + P.dt * vp[a];
         xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
-        bad |= !rfinite(xn) || !rfinite(vnew[a]);
+        chk += xn + vnew[a];
         Sp[(Ly::X + a) * np] = xn;
         Sp[(Ly::V + a) * np] = vnew[a];
     }
@@ -1402,7 +1396,7 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
         }
     const R rho = raw(J_RHO) / (R(1) + P.dt * trL);
     Sp[Ly::RHO * np] = rho;
-    bad |= !rfinite(rho);
+    chk += rho;
     if constexpr (MAT == 1) {
         R L3[9];
 #pragma unroll
@@ -1419,20 +1413,22 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             Sp[(Ly::SIG + k) * np] = s6[k];
-            bad |= !rfinite(s6[k]);
+            chk += s6[k];
         }
         Sp[Ly::EPS * np] = e;
     }
-    return !bad;
+    return !bad && rfinite(chk);
 }
 
-// Shared-memory layout of the G2P block.
+// Shared-memory layout of the G2P block: the grid window, then two staging
+// buffers of NT / kPB particle blocks (the components G2P reads).
 template <class R, int D> struct G2PSmem {
     static constexpr int NT = 256;
-    static constexpr int PB = NT + 8;
+    static constexpr int NBLK = NT / kPB;
     static constexpr int NCMAX = D + D * D + 8;
     static constexpr size_t win_bytes = (size_t)Geo<D>::WN * sizeof(R4<R>);
-    static constexpr size_t buf_bytes = (size_t)2 * NCMAX * PB * sizeof(R);
+    static constexpr size_t buf_elems = (size_t)NBLK * NCMAX * kPB;
+    static constexpr size_t buf_bytes = 2 * buf_elems * sizeof(R);
     static constexpr size_t total = win_bytes + buf_bytes + 128;
 };
 
@@ -1459,9 +1455,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
     __shared__ __align__(8) uint64_t mbar[3];      // [0], [1]: particle buffers, [2]: grid window
     __shared__ int s_slot;
     const int tid = threadIdx.x;
-    constexpr int nc = g2p_ncomp<D>(MAT);
-    constexpr int J_RHO = D + D * D;
-    auto comp = [&](int j) { return j < D ? j : (j < J_RHO ? Lay<D>::F + (j - D) : Lay<D>::RHO + (j - J_RHO)); };
+    using Ly = Lay<D, MAT>;
+    constexpr int nc = Ly::G2P_IN;                 // x, F, rho [, sigma, eps]: the first nc components
+    static_assert(nc == g2p_ncomp<D>(MAT), "G2P inputs lead the particle state");
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -1488,31 +1484,34 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
             mbar_expect_tx(&mbar[2], (uint32_t)(Gm::WN * sizeof(R4<R>)));
             tma_load_window(Vw, &tmapV, org, sim, D, &mbar[2]);
         }
-        const int nb = (t.z + NT - 1) / NT;
+        // particles in chunks of NT slots aligned to the particle blocks (so a warp's
+        // 32 particles are one block and each of its stores writes one line); slots
+        // of a neighbouring tile at either end are skipped
+        const int64_t a0 = (int64_t)t.y & ~(int64_t)(kPB - 1);
+        const int64_t pend = (int64_t)t.y + t.z;
+        const int nb = (int)((pend - a0 + NT - 1) / NT);
         int cur = 0;
-        int64_t a_cur = stage_rows(bufs, L::PB, S, P.npad, (int64_t)t.y, min(NT, t.z), nc, comp, &mbar[0]);
+        stage_blocks(bufs, S, Ly::NC, nc, a0, (int)(pend - a0 < NT ? pend - a0 : NT), &mbar[0]);
         bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
         phases ^= 4u;
         const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
         const R4<R> *V2s = V2 != nullptr ? V2 + (int64_t)sim * P.nodes_per_sim : nullptr;
         for (int j = 0; j < nb; ++j) {
-            int64_t a_next = 0;
-            if (j + 1 < nb)
-                a_next = stage_rows(bufs + (size_t)(cur ^ 1) * L::NCMAX * L::PB, L::PB, S, P.npad,
-                                    (int64_t)t.y + (int64_t)(j + 1) * NT, min(NT, t.z - (j + 1) * NT), nc, comp,
-                                    &mbar[cur ^ 1]);
+            if (j + 1 < nb) {
+                const int64_t an = a0 + (int64_t)(j + 1) * NT;
+                stage_blocks(bufs + (size_t)(cur ^ 1) * L::buf_elems, S, Ly::NC, nc, an, (int)(pend - an < NT ? pend - an : NT),
+                             &mbar[cur ^ 1]);
+            }
             const bool okb = mbar_wait_bounded(&mbar[cur], (phases >> cur) & 1u);
             phases ^= 1u << cur;
             ok = ok && okb;
-            const int i = j * NT + tid;
-            if (ok && i < t.z) {
-                const int64_t p = (int64_t)t.y + i;
-                const R *bb = bufs + (size_t)cur * L::NCMAX * L::PB + (p - a_cur);
-                bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * L::PB]; }, S, p, Vw, org,
+            const int64_t p = a0 + (int64_t)j * NT + tid;
+            if (ok && p >= t.y && p < pend) {
+                const R *bb = bufs + (size_t)cur * L::buf_elems + (tid >> 5) * (nc * kPB) + (tid & (kPB - 1));
+                bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * kPB]; }, S, p, Vw, org,
                                                         Vs, V2s);
             }
             __syncthreads();
-            a_cur = a_next;
             cur ^= 1;
         }
         timed_out |= !ok;
@@ -1534,23 +1533,23 @@ template <class R, int D>
 __global__ void k_init_state(const Params<R> P, R *__restrict__ S, int32_t *__restrict__ id,
                              const double *__restrict__ x, const double *__restrict__ v)
 {
-    const int64_t np = P.npad;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
          p += (int64_t)gridDim.x * blockDim.x) {
+        R *Sp = S + sblock(p, P.ncomp);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            S[(P.off_x + a) * np + p] = (R)x[p * D + a];
-            S[(P.off_v + a) * np + p] = v ? (R)v[p * D + a] : R(0);
+            Sp[(P.off_x + a) * kPB] = (R)x[p * D + a];
+            Sp[(P.off_v + a) * kPB] = v ? (R)v[p * D + a] : R(0);
         }
 #pragma unroll
         for (int q = 0; q < D * D; ++q) {
-            S[(P.off_C + q) * np + p] = R(0);
-            S[(P.off_F + q) * np + p] = (q % (D + 1) == 0) ? R(1) : R(0);
+            Sp[(P.off_C + q) * kPB] = R(0);
+            Sp[(P.off_F + q) * kPB] = (q % (D + 1) == 0) ? R(1) : R(0);
         }
-        S[P.off_rho * np + p] = P.rho0;
+        Sp[P.off_rho * kPB] = P.rho0;
         if (P.material == 1) {
-            for (int k = 0; k < 6; ++k) S[(P.off_sig + k) * np + p] = R(0);
-            S[P.off_eps * np + p] = R(0);
+            for (int k = 0; k < 6; ++k) Sp[(P.off_sig + k) * kPB] = R(0);
+            Sp[P.off_eps * kPB] = R(0);
         }
         id[p] = (int32_t)p;
     }
@@ -1561,13 +1560,13 @@ __global__ void k_keys(const Params<R> P, const R *__restrict__ S, const int32_t
                        uint32_t *__restrict__ keys, int32_t *__restrict__ vals)
 {
     using Gm = Geo<D>;
-    const int64_t np = P.npad;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
          p += (int64_t)gridDim.x * blockDim.x) {
+        const R *Sp = S + sblock(p, P.ncomp);
         int64_t tile = 0, cell = 0, tstride = 1, cstride = 1;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const int s = base_cell(S[(P.off_x + a) * np + p], P.inv_dx, P.n_cells[a]) + 1;   // [0, N]
+            const int s = base_cell(Sp[(P.off_x + a) * kPB], P.inv_dx, P.n_cells[a]) + 1;   // [0, N]
             tile += (int64_t)(s / Gm::T) * tstride;
             cell += (int64_t)(s % Gm::T) * cstride;
             tstride *= P.n_tiles[a];
@@ -1588,7 +1587,9 @@ __global__ void k_permute(int ncomp, int64_t n, int64_t npad, const R *__restric
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t o = perm[i];
         o = o < 0 ? 0 : (o >= n ? n - 1 : o);       // defensive: never gather outside the state
-        for (int c = 0; c < ncomp; ++c) S2[c * npad + i] = S[c * npad + o];
+        const R *src = S + sblock(o, ncomp);
+        R *dst = S2 + sblock(i, ncomp);
+        for (int c = 0; c < ncomp; ++c) dst[c * kPB] = src[c * kPB];
         id2[i] = id[o];
         sim2[i] = sim[o];
     }
@@ -1599,40 +1600,40 @@ template <class R, int D>
 __global__ void k_get_field(const Params<R> P, const R *__restrict__ S, const int32_t *__restrict__ id,
                             int field, double *__restrict__ out)
 {
-    const int64_t np = P.npad;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[p];
+        const R *Sp = S + sblock(p, P.ncomp);
         switch (field) {
         case 0:
-            for (int a = 0; a < D; ++a) out[o * D + a] = (double)S[(P.off_x + a) * np + p];
+            for (int a = 0; a < D; ++a) out[o * D + a] = (double)Sp[(P.off_x + a) * kPB];
             break;
         case 1:
-            for (int a = 0; a < D; ++a) out[o * D + a] = (double)S[(P.off_v + a) * np + p];
+            for (int a = 0; a < D; ++a) out[o * D + a] = (double)Sp[(P.off_v + a) * kPB];
             break;
         case 2:
-            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)S[(P.off_C + q) * np + p];
+            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)Sp[(P.off_C + q) * kPB];
             break;
         case 3:
-            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)S[(P.off_F + q) * np + p];
+            for (int q = 0; q < D * D; ++q) out[o * D * D + q] = (double)Sp[(P.off_F + q) * kPB];
             break;
         case 4:
-            out[o] = (double)S[P.off_rho * np + p];
+            out[o] = (double)Sp[P.off_rho * kPB];
             break;
         case 5: {
             double s9[9];
             if (P.material == 0) {
-                const double pr = (double)tait(P, S[P.off_rho * np + p]);
+                const double pr = (double)tait(P, Sp[P.off_rho * kPB]);
                 for (int q = 0; q < 9; ++q) s9[q] = (q % 4 == 0) ? -pr : 0.0;
             } else {
                 const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
-                for (int q = 0; q < 9; ++q) s9[q] = (double)S[(P.off_sig + map[q]) * np + p];
+                for (int q = 0; q < 9; ++q) s9[q] = (double)Sp[(P.off_sig + map[q]) * kPB];
             }
             for (int q = 0; q < 9; ++q) out[o * 9 + q] = s9[q];
             break;
         }
         case 6:
-            out[o] = P.material == 1 ? (double)S[P.off_eps * np + p] : 0.0;
+            out[o] = P.material == 1 ? (double)Sp[P.off_eps * kPB] : 0.0;
             break;
         default:
             break;
@@ -1644,38 +1645,38 @@ template <class R, int D>
 __global__ void k_set_field(const Params<R> P, R *__restrict__ S, const int32_t *__restrict__ id, int field,
                             const double *__restrict__ in)
 {
-    const int64_t np = P.npad;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = id[p];
+        R *Sp = S + sblock(p, P.ncomp);
         switch (field) {
         case 0:
-            for (int a = 0; a < D; ++a) S[(P.off_x + a) * np + p] = (R)in[o * D + a];
+            for (int a = 0; a < D; ++a) Sp[(P.off_x + a) * kPB] = (R)in[o * D + a];
             break;
         case 1:
-            for (int a = 0; a < D; ++a) S[(P.off_v + a) * np + p] = (R)in[o * D + a];
+            for (int a = 0; a < D; ++a) Sp[(P.off_v + a) * kPB] = (R)in[o * D + a];
             break;
         case 2:
-            for (int q = 0; q < D * D; ++q) S[(P.off_C + q) * np + p] = (R)in[o * D * D + q];
+            for (int q = 0; q < D * D; ++q) Sp[(P.off_C + q) * kPB] = (R)in[o * D * D + q];
             break;
         case 3:
-            for (int q = 0; q < D * D; ++q) S[(P.off_F + q) * np + p] = (R)in[o * D * D + q];
+            for (int q = 0; q < D * D; ++q) Sp[(P.off_F + q) * kPB] = (R)in[o * D * D + q];
             break;
         case 4:
-            S[P.off_rho * np + p] = (R)in[o];
+            Sp[P.off_rho * kPB] = (R)in[o];
             break;
         case 5: {
             const double *s9 = in + o * 9;
-            S[(P.off_sig + 0) * np + p] = (R)s9[0];
-            S[(P.off_sig + 1) * np + p] = (R)s9[4];
-            S[(P.off_sig + 2) * np + p] = (R)s9[8];
-            S[(P.off_sig + 3) * np + p] = (R)(0.5 * (s9[1] + s9[3]));
-            S[(P.off_sig + 4) * np + p] = (R)(0.5 * (s9[2] + s9[6]));
-            S[(P.off_sig + 5) * np + p] = (R)(0.5 * (s9[5] + s9[7]));
+            Sp[(P.off_sig + 0) * kPB] = (R)s9[0];
+            Sp[(P.off_sig + 1) * kPB] = (R)s9[4];
+            Sp[(P.off_sig + 2) * kPB] = (R)s9[8];
+            Sp[(P.off_sig + 3) * kPB] = (R)(0.5 * (s9[1] + s9[3]));
+            Sp[(P.off_sig + 4) * kPB] = (R)(0.5 * (s9[2] + s9[6]));
+            Sp[(P.off_sig + 5) * kPB] = (R)(0.5 * (s9[5] + s9[7]));
             break;
         }
         case 6:
-            S[P.off_eps * np + p] = (R)in[o];
+            Sp[P.off_eps * kPB] = (R)in[o];
             break;
         default:
             break;
@@ -1712,6 +1713,8 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.q_phi = (R)h.q_phi; P.k_phi = (R)h.k_phi; P.q_psi = (R)h.q_psi;
     P.sig_t = (R)h.sig_t; P.tau_P = (R)h.tau_P; P.alpha_P = (R)h.alpha_P;
     P.eps2_coef = (R)std::sqrt(1.0 / 3.0 + 2.0 / 9.0 * h.q_psi * h.q_psi);
+    P.inv_G_Kqq = h.material == 1 ? (R)(1.0 / (h.G + h.K * h.q_phi * h.q_psi)) : R(0);
+    P.inv_K = h.material == 1 ? (R)(1.0 / h.K) : R(0);
     P.material = h.material;
     P.dp_literal = h.dp_literal;
     P.transfer = h.transfer;
@@ -1726,6 +1729,7 @@ Params<R> make_params(const HostParams &h, const DevState &ds)
     P.node_tiles_per_sim = h.node_tiles_per_sim;
     P.n = h.n;
     P.npad = h.npad;
+    P.ncomp = h.ncomp;
     P.off_x = h.off_x; P.off_v = h.off_v; P.off_C = h.off_C; P.off_F = h.off_F;
     P.off_rho = h.off_rho; P.off_sig = h.off_sig; P.off_eps = h.off_eps;
     P.obs = h.obs;

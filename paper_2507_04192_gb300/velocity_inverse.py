@@ -12,8 +12,9 @@ break:
 
 The loss and dL/dv0 come from the library's checkpointed adjoint
 (mpm_step_adjoint with no friction parameter, then mpm_get_initial_adjoint);
-dL/dalpha and dL/dtheta follow by the chain rule on the host (the network has
-2,911 weights and is evaluated once per iteration on the particles' initial
+dL/dalpha follows by the chain rule on the host; dL/dtheta by back-propagating
+dL/dv0 through the network on the tensor cores (mpm_mlp_backward; the network
+has 1,951 weights, as in the paper's Table 3, and is evaluated once per iteration on the particles' initial
 heights).  Adam (beta 0.9 / 0.999, eps 1e-8) with lr = lr0 * decay^k.
 
     python -m paper_2507_04192_gb300.velocity_inverse [--case tracked|sparse|monitors|field] [--dx 0.01]
@@ -129,77 +130,82 @@ def invert_alpha(problem: VelocityInversion, alpha0: float = 0.1, alpha_true: Op
     return Result(a.copy(), max_iters, False, hist)
 
 
-class CoordinateMLP:
-    """v_x0 = N(y / H0): 1 -> 30 -> 30 -> 30 -> 1 with ReLU, weights He-normal by seed."""
+class CoordinateNet:
+    """v_x0 = N(y / H0): the coordinate network 1 -> 30 -> 30 -> 30 -> 1 with ReLU
+    (Eq. nn_apprx, Sec. 5.2) on the library's tensor-core network (mpm_mlp_*).
+    The tensor-core GEMMs take widths that are multiples of 8, so the network is
+    held as 8 -> 32 -> 32 -> 32 -> 8 with the extra inputs, units and outputs
+    zero: a unit whose weights in and out are zero stays zero under ReLU and gets
+    zero gradients, so the padding never changes (the network is exactly the
+    30-unit one).  Weights He-normal by seed, biases zero; forward and backward in
+    BF16 operands with FP32 accumulation, Adam on FP32 master weights."""
 
-    def __init__(self, widths=(1, 30, 30, 30, 1), seed: int = 0):
+    TRUE = (1, 30, 30, 30, 1)
+    PADDED = (8, 32, 32, 32, 8)
+
+    def __init__(self, max_batch: int, seed: int = 0, stream: int = 0):
+        self.max_batch = (int(max_batch) + 7) // 8 * 8
+        self.net = mpm.MLP(list(self.PADDED), self.max_batch, stream=stream, hidden=mpm.MPM_ACT_RELU,
+                           output=mpm.MPM_OUT_LINEAR)
         rng = np.random.default_rng(seed)
-        self.W = [rng.normal(0.0, np.sqrt(2.0 / widths[i]), (widths[i + 1], widths[i]))
-                  for i in range(len(widths) - 1)]
-        self.b = [np.zeros(widths[i + 1]) for i in range(len(widths) - 1)]
+        flat = []
+        for i in range(len(self.TRUE) - 1):
+            W = np.zeros((self.PADDED[i + 1], self.PADDED[i]))
+            W[:self.TRUE[i + 1], :self.TRUE[i]] = rng.normal(0.0, np.sqrt(2.0 / self.TRUE[i]),
+                                                             (self.TRUE[i + 1], self.TRUE[i]))
+            flat += [W.ravel(), np.zeros(self.PADDED[i + 1])]
+        self.net.set_params(np.concatenate(flat).astype(np.float32))
 
-    @property
-    def n_params(self) -> int:
-        return sum(W.size + b.size for W, b in zip(self.W, self.b))
+    def _inputs(self, s: np.ndarray) -> np.ndarray:
+        x = np.zeros((self.max_batch, self.PADDED[0]), dtype=np.float32)
+        x[:len(s), 0] = s
+        return x
 
-    def flat(self) -> np.ndarray:
-        return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in zip(self.W, self.b)])
+    def forward(self, s: np.ndarray) -> np.ndarray:
+        return self.net.infer(self._inputs(s))[:len(s), 0].astype(np.float64)
 
-    def set_flat(self, p: np.ndarray):
-        o = 0
-        for i, (W, b) in enumerate(zip(self.W, self.b)):
-            self.W[i] = p[o:o + W.size].reshape(W.shape)
-            o += W.size
-            self.b[i] = p[o:o + b.size].copy()
-            o += b.size
+    def step(self, s: np.ndarray, gout: np.ndarray, lr: float):
+        """Back-propagate dL/dN(s) = gout and take one Adam step with rate lr (rows
+        beyond len(s) are padding with zero gradient)."""
+        dy = np.zeros((self.max_batch, self.PADDED[-1]), dtype=np.float32)
+        dy[:len(s), 0] = gout
+        self.net.backward(self._inputs(s), dy, lr=lr, update=True)
 
-    def forward(self, s: np.ndarray):
-        h = [s.reshape(-1, 1)]
-        for i, (W, b) in enumerate(zip(self.W, self.b)):
-            z = h[-1] @ W.T + b
-            h.append(np.maximum(z, 0.0) if i < len(self.W) - 1 else z)
-        return h[-1][:, 0], h
-
-    def backward(self, h, gout: np.ndarray) -> np.ndarray:
-        """Gradient of sum(gout * N(s)) with respect to the flat parameters."""
-        g = gout.reshape(-1, 1)
-        grads = []
-        for i in range(len(self.W) - 1, -1, -1):
-            gW = g.T @ h[i]
-            gb = g.sum(axis=0)
-            grads.append((gW, gb))
-            if i > 0:
-                g = (g @ self.W[i]) * (h[i] > 0.0)
-        grads.reverse()
-        return np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    def close(self):
+        self.net.close()
 
 
-def field_error(net: CoordinateMLP, w) -> float:
+def field_error(net: CoordinateNet, w) -> float:
     """Relative L2 error of N(y / H0) against the reference field over the column's particles."""
     H0 = w.extras["H0"]
     y = w.x[:, 1]
-    pred = net.forward(y / H0)[0]
+    pred = net.forward(y / H0)
     ref = inputs.velocity_profile_field(y, H0)
     return float(np.linalg.norm(pred - ref) / np.linalg.norm(ref))
 
 
 def invert_field(problem: VelocityInversion, epochs: int = 400, lr0: float = 1e-2, decay: float = 0.995,
                  seed: int = 0) -> Result:
+    """Adam (beta 0.9 / 0.999, eps 1e-8, lr0 decay^k) on the coordinate network's
+    weights; each epoch one checkpointed adjoint of the whole horizon gives
+    dL/dv0, the network back-propagates its x component."""
     w = problem.w
     H0 = w.extras["H0"]
-    net = CoordinateMLP(seed=seed)
-    opt = Adam(net.n_params, lr0, decay)
+    net = CoordinateNet(w.n, seed=seed)
     hist = []
     s = w.x[:, 1] / H0
-    for k in range(epochs):
-        vx, h = net.forward(s)
-        v0 = np.zeros_like(w.x)
-        v0[:, 0] = vx
-        loss, g0 = problem.loss_and_grad_v0(v0)
-        g = net.backward(h, g0[:, 0])
-        hist.append({"epoch": k, "loss": loss, "error": field_error(net, w)})
-        net.set_flat(opt.step(net.flat(), g))
-    return Result(net.flat(), epochs, True, hist)
+    try:
+        for k in range(epochs):
+            v0 = np.zeros_like(w.x)
+            v0[:, 0] = net.forward(s)
+            loss, g0 = problem.loss_and_grad_v0(v0)
+            hist.append({"epoch": k, "loss": loss, "error": field_error(net, w)})
+            net.step(s, g0[:, 0], lr0 * decay ** k)
+        hist.append({"epoch": epochs, "loss": None, "error": field_error(net, w)})
+        params = net.net.get_params(0)
+    finally:
+        net.close()
+    return Result(params, epochs, True, hist)
 
 
 def main(argv=None):
@@ -225,7 +231,7 @@ def main(argv=None):
         res = invert_field(prob, args.epochs)
         out = {"case": args.case, "particles": w.n, "n_track": len(w.extras["track_ids"]), "epochs": res.iterations,
                "field_error": res.history[-1]["error"], "loss_first": res.history[0]["loss"],
-               "loss_last": res.history[-1]["loss"]}
+               "loss_last": res.history[-2]["loss"], "network": "tensor-core mpm_mlp (BF16 operands, FP32 accumulate)"}
     else:
         res = invert_alpha(prob, alpha_true=w.extras["alpha_true"], max_iters=args.iters)
         out = {"case": args.case, "particles": w.n, "iterations_to_1pct": res.iterations if res.converged else None,

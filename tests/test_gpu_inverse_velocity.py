@@ -105,3 +105,33 @@ def test_3d_monitors_and_initial_adjoint_match_oracle():
     np.testing.assert_array_equal(cnt, cr)
     assert cnt.min() > 0
     np.testing.assert_allclose(Q, Qr, rtol=0, atol=1e-12 * max(1.0, np.abs(Qr).max()))
+
+
+def test_velocity_field_recovered_by_the_tensor_core_coordinate_network():
+    # Sec. 5.2 "initial velocity field": the coordinate network (1 -> 30 -> 30 -> 30 -> 1,
+    # ReLU) on the library's tensor-core network, trained through the adjoint; a
+    # coarse resolution and a short horizon keep this to seconds
+    w = inputs.dam_break_velocity_inverse(dx=0.02, steps=3000, n_frames=50, frame_every=10, n_track=400,
+                                          checkpoint_every=100)
+    H0 = w.extras["H0"]
+    v_true = np.zeros_like(w.x)
+    v_true[:, 0] = inputs.velocity_profile_field(w.x[:, 1], H0)
+    zx, _ = velocity_inverse.record_observations(w, v_true)
+    prob = velocity_inverse.VelocityInversion(w, zx=zx)
+    res = velocity_inverse.invert_field(prob, epochs=60, lr0=1e-2)
+    prob.close()
+    e0, e1 = res.history[0]["error"], res.history[-1]["error"]
+    losses = [h["loss"] for h in res.history[:-1]]
+    assert losses[-1] < 0.05 * losses[0], losses[::10]
+    assert e1 < 0.5 * e0 and e1 < 0.35, (e0, e1)
+    # the network's padding to multiples of 8 stayed inert: only the 1-30-30-30-1 block moved
+    net = velocity_inverse.CoordinateNet
+    p = res.params
+    o = 0
+    for i in range(4):
+        W = p[o:o + net.PADDED[i + 1] * net.PADDED[i]].reshape(net.PADDED[i + 1], net.PADDED[i])
+        o += W.size
+        b = p[o:o + net.PADDED[i + 1]]
+        o += b.size
+        assert np.all(W[net.TRUE[i + 1]:, :] == 0) and np.all(W[:, net.TRUE[i]:] == 0)
+        assert np.all(b[net.TRUE[i + 1]:] == 0)

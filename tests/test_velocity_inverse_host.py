@@ -1,28 +1,19 @@
 """Host logic of the initial-velocity inversion driver: the coordinate network's
-gradient (central differences) and the Adam update (a quadratic's minimum)."""
+sizes and the Adam update (a quadratic's minimum).  The network itself runs on
+the tensor cores; tests/test_gpu_mlp.py and tests/test_gpu_inverse_velocity.py
+check it against the FP64 oracle of the network."""
 import numpy as np
 import pytest
 
-from paper_2507_04192_gb300.velocity_inverse import Adam, CoordinateMLP
+from paper_2507_04192_gb300.velocity_inverse import Adam, CoordinateNet
 
 
-def test_coordinate_network_gradient_matches_central_differences():
-    net = CoordinateMLP(seed=3)
-    rng = np.random.default_rng(0)
-    s = rng.uniform(0, 1, 64)
-    gout = rng.normal(size=64)
-    out, h = net.forward(s)
-    g = net.backward(h, gout)
-    p0 = net.flat()
-    d = rng.normal(size=p0.size)
-    eps = 1e-6
-    net.set_flat(p0 + eps * d)
-    fp = float((net.forward(s)[0] * gout).sum())
-    net.set_flat(p0 - eps * d)
-    fm = float((net.forward(s)[0] * gout).sum())
-    net.set_flat(p0)
-    assert float((g * d).sum()) == pytest.approx((fp - fm) / (2 * eps), rel=1e-6)
-    assert net.n_params == 2 * 30 + 2 * (30 * 30 + 30) + 31
+def test_coordinate_network_sizes():
+    # the paper's 1 -> 30 -> 30 -> 30 -> 1 network has 1,951 parameters (Table 3); the
+    # tensor-core layout pads each width to a multiple of 8
+    t, p = CoordinateNet.TRUE, CoordinateNet.PADDED
+    assert sum(t[i] * t[i + 1] + t[i + 1] for i in range(4)) == 1951
+    assert all(w % 8 == 0 and w >= v for w, v in zip(p, t))
 
 
 def test_adam_reaches_the_minimum_of_a_quadratic():
