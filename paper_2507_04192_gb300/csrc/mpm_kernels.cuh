@@ -765,6 +765,24 @@ __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R>
     }
 }
 
+// Per-cell node sums of k_p2g_direct (3D): 27 nodes x (m, q0, q1, q2).  (Keeping
+// them as float pairs added with paired fused multiply-adds, as G2P's
+// contraction does, measured slower here: the pairs raised the register spills
+// of this 168-register kernel.)
+template <class R> struct CellSums {
+    R acc[27][4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < 27; ++k)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[k][v] = R(0);
+    }
+    __device__ __forceinline__ void add(const P2GFactors<R, 3> &f, R mp) { p2g_accumulate<R, 3>(f, mp, acc); }
+    __device__ __forceinline__ R m(int k) const { return acc[k][0]; }
+    __device__ __forceinline__ R q(int k, int a) const { return acc[k][1 + a]; }
+};
+
 // Components staged per particle by k_p2g_direct: P2G's inputs (MAT 0, 1), or x
 // and the 21 scatter coefficients (MAT 2).
 template <int MAT> __host__ __device__ constexpr int direct_stage_comps() { return MAT == 2 ? 24 : kP2GStageComps<3>; }
@@ -827,7 +845,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
         uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
         const int32_t *pmap = io.posmap + t.y;
-        const int32_t *goff = io.cell_off + (int64_t)k * (Gm::TN + 1) + cbase;
+        const int32_t *goff = io.cell_off + (int64_t)t.w * (Gm::TN + 1) + cbase;   // t.w: index in key order
         // the item's cell offsets, staged once (coalesced) so that the per-cell lookups
         // below are shared-memory reads (staging the position map as well cost more in
         // registers than it saved)
@@ -880,7 +898,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         int stage = 0, cur = -1;
         int bown[D], nb[D];
         unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
-        R acc[Gm::STENCIL][D + 1];
+        CellSums<R> acc;
         while (hc) {
             if (cc.c != cur) {
                 cur = cc.c;
@@ -897,10 +915,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
                     if ((m & ~hi & 7u) == 0u) reach |= 1u << m;
-#pragma unroll
-                for (int kk = 0; kk < Gm::STENCIL; ++kk)
-#pragma unroll
-                    for (int v = 0; v <= D; ++v) acc[kk][v] = R(0);
+                acc.zero();
             }
             cp_async_wait<1>();
             P2GFactors<R, D> f;
@@ -925,7 +940,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
 #pragma unroll
             for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
             if (own) {
-                p2g_accumulate<R, D>(f, mass, acc);
+                acc.add(f, mass);
             } else {                                   // left its cell since the sort: on its own
                 any_escape = true;
                 p2g_escape3<R>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
@@ -939,8 +954,8 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
 #pragma unroll
                 for (int kk = 0; kk < Gm::STENCIL; ++kk) {
                     R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
-                    if constexpr (ADJ) red_add4(node, acc[kk][1], acc[kk][2], acc[kk][3], R(0));   // (v_bar, 0)
-                    else red_add4(node, acc[kk][0], acc[kk][1], acc[kk][2], acc[kk][3]);          // (m, q)
+                    if constexpr (ADJ) red_add4(node, acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2), R(0));   // (v_bar, 0)
+                    else red_add4(node, acc.m(kk), acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2));          // (m, q)
                 }
             }
         }
@@ -1282,6 +1297,90 @@ __device__ __forceinline__ void g2p_contract(const R w[D][3], const R dw[D][3], 
     }
 }
 
+// The same sums in single precision in 3D with paired arithmetic: the x and y
+// components of a node velocity are adjacent (the low half of its 16-byte
+// load), so the sums of components 0 and 1 run as one paired fused multiply-add
+// (__ffma2_rn, each half rounded as fmaf) against a weight broadcast into both
+// halves; component 2 stays scalar.  The results are bitwise those of the
+// scalar form above, in about two thirds of the instructions.
+template <class Load>
+__device__ __forceinline__ void g2p_contract_x2(const float w[3][3], const float dw[3][3], Load load, float vp[3],
+                                                float M[9], float L[9])
+{
+    auto bc = [](float a) { return make_float2(a, a); };
+    float2 vp01 = make_float2(0.f, 0.f), M01[3], L01[3];
+    float vp2 = 0.f, M2[3] = {0.f, 0.f, 0.f}, L2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M01[b] = L01[b] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+        float2 Yww = make_float2(0.f, 0.f), Ykw = Yww, Ydw = Yww, Ywk = Yww, Ywd = Yww;
+        float yww = 0.f, ykw = 0.f, ydw = 0.f, ywk = 0.f, ywd = 0.f;
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            float2 Xw = make_float2(0.f, 0.f), Xk = Xw, Xd = Xw;
+            float xw = 0.f, xk = 0.f, xd = 0.f;
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const R4<float> v4 = load(k0, k1, k2);
+                const float2 v01 = make_float2(v4.x, v4.y);
+                Xw = __ffma2_rn(bc(w[0][k0]), v01, Xw);
+                xw = fmaf(w[0][k0], v4.z, xw);
+                if (k0 > 0) {
+                    Xk = __ffma2_rn(bc(float(k0) * w[0][k0]), v01, Xk);
+                    xk = fmaf(float(k0) * w[0][k0], v4.z, xk);
+                }
+                Xd = __ffma2_rn(bc(dw[0][k0]), v01, Xd);
+                xd = fmaf(dw[0][k0], v4.z, xd);
+            }
+            Yww = __ffma2_rn(bc(w[1][k1]), Xw, Yww);
+            yww = fmaf(w[1][k1], xw, yww);
+            Ykw = __ffma2_rn(bc(w[1][k1]), Xk, Ykw);
+            ykw = fmaf(w[1][k1], xk, ykw);
+            Ydw = __ffma2_rn(bc(w[1][k1]), Xd, Ydw);
+            ydw = fmaf(w[1][k1], xd, ydw);
+            if (k1 > 0) {
+                Ywk = __ffma2_rn(bc(float(k1) * w[1][k1]), Xw, Ywk);
+                ywk = fmaf(float(k1) * w[1][k1], xw, ywk);
+            }
+            Ywd = __ffma2_rn(bc(dw[1][k1]), Xw, Ywd);
+            ywd = fmaf(dw[1][k1], xw, ywd);
+        }
+        vp01 = __ffma2_rn(bc(w[2][k2]), Yww, vp01);
+        vp2 = fmaf(w[2][k2], yww, vp2);
+        M01[0] = __ffma2_rn(bc(w[2][k2]), Ykw, M01[0]);
+        M2[0] = fmaf(w[2][k2], ykw, M2[0]);
+        M01[1] = __ffma2_rn(bc(w[2][k2]), Ywk, M01[1]);
+        M2[1] = fmaf(w[2][k2], ywk, M2[1]);
+        if (k2 > 0) {
+            M01[2] = __ffma2_rn(bc(float(k2) * w[2][k2]), Yww, M01[2]);
+            M2[2] = fmaf(float(k2) * w[2][k2], yww, M2[2]);
+        }
+        L01[0] = __ffma2_rn(bc(w[2][k2]), Ydw, L01[0]);
+        L2[0] = fmaf(w[2][k2], ydw, L2[0]);
+        L01[1] = __ffma2_rn(bc(w[2][k2]), Ywd, L01[1]);
+        L2[1] = fmaf(w[2][k2], ywd, L2[1]);
+        L01[2] = __ffma2_rn(bc(dw[2][k2]), Yww, L01[2]);
+        L2[2] = fmaf(dw[2][k2], yww, L2[2]);
+    }
+    vp[0] = vp01.x;
+    vp[1] = vp01.y;
+    vp[2] = vp2;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {           // M[a * 3 + b], L[a * 3 + b]; the pairs run over a
+        M[0 * 3 + b] = M01[b].x;
+        M[1 * 3 + b] = M01[b].y;
+        M[2 * 3 + b] = M2[b];
+        L[0 * 3 + b] = L01[b].x;
+        L[1 * 3 + b] = L01[b].y;
+        L[2 * 3 + b] = L2[b];
+    }
+}
+
+#ifndef MPM_G2P_X2
+#define MPM_G2P_X2 1
+#endif
+
 // G2P of one particle: gathers the 3^D node velocities from the shared-memory
 // window (or from the global grid if its stencil left the window), then
 // updates v, C, x, F, rho and the stress.  Returns false on a non-finite state.
@@ -1320,7 +1419,12 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
     }
     R vp[D], M[D * D], L[D * D];
     if (inside) {
-        g2p_contract<R, D>(w, dw, [&](int k0, int k1, int k2) { return Vw[win_index<D>(l, k0, k1, k2)]; }, vp, M, L);
+        if constexpr (D == 3 && sizeof(R) == 4 && MPM_G2P_X2)
+            g2p_contract_x2(w, dw, [&](int k0, int k1, int k2) { return Vw[win_index<D>(l, k0, k1, k2)]; }, vp, M,
+                            L);
+        else
+            g2p_contract<R, D>(w, dw, [&](int k0, int k1, int k2) { return Vw[win_index<D>(l, k0, k1, k2)]; }, vp, M,
+                               L);
     } else {
         g2p_contract<R, D>(w, dw, [&](int k0, int k1, int k2) {
             int a3[3] = {b[0] + 2 + k0, b[1] + 2 + k1, D == 3 ? b[D - 1] + 2 + k2 : 0};
@@ -1422,9 +1526,14 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 
 // Shared-memory layout of the G2P block: the grid window, then two staging
 // buffers of NT / kPB particle blocks (the components G2P reads).
+// Particles per thread in one staged chunk of the G2P block.
+#ifndef MPM_G2P_PPT
+#define MPM_G2P_PPT 1
+#endif
 template <class R, int D> struct G2PSmem {
     static constexpr int NT = 256;
-    static constexpr int NBLK = NT / kPB;
+    static constexpr int CH = NT * (sizeof(R) == 4 ? MPM_G2P_PPT : 1);   // particles per staged chunk
+    static constexpr int NBLK = CH / kPB;
     static constexpr int NCMAX = D + D * D + 8;
     static constexpr size_t win_bytes = (size_t)Geo<D>::WN * sizeof(R4<R>);
     static constexpr size_t buf_elems = (size_t)NBLK * NCMAX * kPB;
@@ -1487,29 +1596,34 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
         // particles in chunks of NT slots aligned to the particle blocks (so a warp's
         // 32 particles are one block and each of its stores writes one line); slots
         // of a neighbouring tile at either end are skipped
+        constexpr int CH = L::CH;
         const int64_t a0 = (int64_t)t.y & ~(int64_t)(kPB - 1);
         const int64_t pend = (int64_t)t.y + t.z;
-        const int nb = (int)((pend - a0 + NT - 1) / NT);
+        const int nb = (int)((pend - a0 + CH - 1) / CH);
         int cur = 0;
-        stage_blocks(bufs, S, Ly::NC, nc, a0, (int)(pend - a0 < NT ? pend - a0 : NT), &mbar[0]);
+        stage_blocks(bufs, S, Ly::NC, nc, a0, (int)(pend - a0 < CH ? pend - a0 : CH), &mbar[0]);
         bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
         phases ^= 4u;
         const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
         const R4<R> *V2s = V2 != nullptr ? V2 + (int64_t)sim * P.nodes_per_sim : nullptr;
         for (int j = 0; j < nb; ++j) {
             if (j + 1 < nb) {
-                const int64_t an = a0 + (int64_t)(j + 1) * NT;
-                stage_blocks(bufs + (size_t)(cur ^ 1) * L::buf_elems, S, Ly::NC, nc, an, (int)(pend - an < NT ? pend - an : NT),
-                             &mbar[cur ^ 1]);
+                const int64_t an = a0 + (int64_t)(j + 1) * CH;
+                stage_blocks(bufs + (size_t)(cur ^ 1) * L::buf_elems, S, Ly::NC, nc, an,
+                             (int)(pend - an < CH ? pend - an : CH), &mbar[cur ^ 1]);
             }
             const bool okb = mbar_wait_bounded(&mbar[cur], (phases >> cur) & 1u);
             phases ^= 1u << cur;
             ok = ok && okb;
-            const int64_t p = a0 + (int64_t)j * NT + tid;
-            if (ok && p >= t.y && p < pend) {
-                const R *bb = bufs + (size_t)cur * L::buf_elems + (tid >> 5) * (nc * kPB) + (tid & (kPB - 1));
-                bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * kPB]; }, S, p, Vw, org,
-                                                        Vs, V2s);
+#pragma unroll 1
+            for (int u = 0; u < CH / NT; ++u) {
+                const int l = u * NT + tid;                // slot within the chunk
+                const int64_t p = a0 + (int64_t)j * CH + l;
+                if (ok && p >= t.y && p < pend) {
+                    const R *bb = bufs + (size_t)cur * L::buf_elems + (l >> 5) * (nc * kPB) + (l & (kPB - 1));
+                    bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * kPB]; }, S, p, Vw, org,
+                                                            Vs, V2s);
+                }
             }
             __syncthreads();
             cur ^= 1;
@@ -1785,8 +1899,9 @@ template <class R, int D> struct Launch {
             constexpr size_t smem = p2g_direct_smem<R, NT, MAT>();
             static_assert(smem <= 48 * 1024, "k_p2g_direct shared memory above the default limit");
             const int nb = ds.num_sms * MPM_P2G_MINB;
-            P2GIO<R> io{(const R *)ds.S, nullptr, h.npad, ds.tiles, ds.counters + 1, ds.counters + 2,
-                        ds.posmap, ds.cell_off, (R4<R> *)ds.A, ds.flags};
+            // tiles in key order (claiming them largest first, as G2P does, measured slower)
+            P2GIO<R> io{(const R *)ds.S, nullptr, h.npad, ds.tiles, ds.counters + 1, ds.counters + 2, ds.posmap,
+                        ds.cell_off, (R4<R> *)ds.A, ds.flags};
             k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, io, ds.escaped, ds.counters + 3);
             if (h.transfer == 3) {                   // FLIP: the momenta without forces, for v_i^n
                 auto P2 = P;

@@ -208,7 +208,8 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp
     return excl;
 }
 
-// Compact list of the non-empty tiles: (tile key, first particle, count, 0).
+// Compact list of the non-empty tiles: (tile key, first particle, count, index in
+// this list); the index stays with a tile in the largest-first copy below.
 __global__ void __launch_bounds__(1024) k_build_tiles(const int32_t *__restrict__ tstart,
                                                       const int32_t *__restrict__ tend, int64_t ntiles,
                                                       int4 *__restrict__ tiles, int64_t max_tiles,
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(1024) k_build_tiles(const int32_t *__restrict_
         const int32_t off = block_exclusive_scan(cnt > 0 ? 1 : 0, warp_sum, total);
         if (cnt > 0) {
             const int64_t idx = carry + off;
-            if (idx < max_tiles) tiles[idx] = make_int4((int32_t)t, s, cnt, 0);
+            if (idx < max_tiles) tiles[idx] = make_int4((int32_t)t, s, cnt, (int32_t)idx);
             else overflow = true;
         }
         carry += total;
