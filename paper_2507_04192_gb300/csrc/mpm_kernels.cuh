@@ -805,16 +805,169 @@ template <class R, int NT, int MAT> __host__ __device__ constexpr size_t p2g_dir
 #ifndef MPM_P2G_DIRECT
 #define MPM_P2G_DIRECT 1
 #endif
+// One work item of the cell-ordered P2G (3D): the CELLS cells [cbase, cbase + CELLS)
+// of compact tile k (key order), one warp, lane l walking cells cbase + l + 32 r.
+// stg: this block's cp.async staging slots (2 stages x NCM x NT reals); s_off:
+// this warp's 132 shared ints for the item's cell offsets.
 template <class R, int NT, int MAT>
-__global__ void __launch_bounds__(NT, MPM_P2G_MINB)
-    k_p2g_direct(const Params<R> P, const P2GIO<R> io, unsigned long long *__restrict__ escaped_count,
-                 int32_t *__restrict__ g2p_cursor)
+__device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<R> &io, R *stg, int32_t *s_off,
+                                                int k, int cbase, bool &any_escape)
 {
     constexpr int D = 3;
     using Gm = Geo<D>;
     constexpr bool ADJ = MAT == 2;
     constexpr int NCM = direct_stage_comps<MAT>();
     constexpr int NC = ADJ ? 24 : p2g_ncomp<D>(MAT);
+    constexpr int CELLS = 128;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t ld = io.ld;
+    const R mass = ADJ ? R(0) : P.mass;
+    const int4 t = io.tiles[k];
+    const int sim = (int)(t.x / P.tiles_per_sim);
+    int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
+    int org[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
+        tl /= P.n_tiles[a];
+    }
+    R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
+    uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
+    const int32_t *pmap = io.posmap + t.y;
+    const int32_t *goff = io.cell_off + (int64_t)t.w * (Gm::TN + 1) + cbase;   // t.w: index in key order
+    // the item's cell offsets, staged once (coalesced) so that the per-cell lookups
+    // below are shared-memory reads (staging the position map as well cost more in
+    // registers than it saved)
+    __syncwarp();
+    for (int i = lane; i <= CELLS; i += 32) s_off[i] = goff[i];
+    __syncwarp();
+    const int32_t *off = s_off - cbase;           // off[c] for the item's cells c in [cbase, cbase + CELLS]
+    auto slot = [&](int q) { return pmap[q]; };
+    const R *St = io.S + t.y;                     // MAT 2: component-major with stride ld
+    const R *S2 = ADJ ? io.src2 + t.y : nullptr;
+    R *const Sv = (ADJ || P.save_S == nullptr) ? nullptr : P.save_S + t.y;
+    auto issue = [&](int stage, int32_t pos) {
+        R *dst = stg + stage * NCM * NT + tid;
+        if constexpr (ADJ) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) cp_async_elem(dst + j * NT, St + pos + j * ld);
+#pragma unroll
+            for (int j = 0; j < 21; ++j) cp_async_elem(dst + (3 + j) * NT, S2 + pos + j * ld);
+        } else {                                  // the particle state, in blocks of kPB
+            const R *src = io.S + sblock((int64_t)t.y + pos, Lay<D, MAT>::NC);
+#pragma unroll
+            for (int j = 0; j < NC; ++j) cp_async_elem(dst + j * NT, src + p2g_comp<D, MAT>(j) * kPB);
+        }
+    };
+    // cursors over this lane's cells cbase + lane + 32 r and their slots
+    struct Cur {
+        int c, q, q1, end;
+        __device__ __forceinline__ bool next(const int32_t *o)
+        {
+            ++q;
+            while (q >= q1) {
+                c += 32;
+                if (c >= end) return false;
+                q = o[c];
+                q1 = o[c + 1];
+            }
+            return true;
+        }
+    };
+    Cur pc{cbase + lane - 32, 0, 0, cbase + CELLS}, cc = pc;
+    bool hp = pc.next(off);
+#pragma unroll
+    for (int s0 = 0; s0 < 2; ++s0) {
+        if (hp) issue(s0, slot(pc.q));
+        cp_async_commit();
+        hp = hp && pc.next(off);
+    }
+    int32_t ppos = hp ? slot(pc.q) : 0;
+    bool hc = cc.next(off);
+    int stage = 0, cur = -1;
+    int bown[D], nb[D];
+    unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
+    CellSums<R> acc;
+    while (hc) {
+        if (cc.c != cur) {
+            cur = cc.c;
+            int r = cur;
+            unsigned hi = 0u;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int ci = r % Gm::T;
+                r /= Gm::T;
+                bown[a] = org[a] + ci - 1;         // base cell index of the cell's particles
+                nb[a] = org[a] + ci + 1;           // its first stencil node
+                hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if ((m & ~hi & 7u) == 0u) reach |= 1u << m;
+            acc.zero();
+        }
+        cp_async_wait<1>();
+        P2GFactors<R, D> f;
+        {
+            const R *src = stg + stage * NCM * NT + tid;
+            if constexpr (ADJ) {
+                adj_scatter_factors<R>(P, [&](int j) { return src[j * NT]; }, f);
+            } else {
+                if (Sv != nullptr) {               // the adjoint's copy of this step's state
+                    R *d = Sv + slot(cc.q);
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
+                }
+                p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
+            }
+        }
+        if (hp) issue(stage, ppos);
+        cp_async_commit();
+        hp = hp && pc.next(off);
+        if (hp) ppos = slot(pc.q);
+        bool own = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
+        if (own) {
+            acc.add(f, mass);
+        } else {                                   // left its cell since the sort: on its own
+            any_escape = true;
+            p2g_escape3<R>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
+                           P.node_tiles[0], P.node_tiles[1]);
+        }
+        stage ^= 1;
+        hc = cc.next(off);
+        if (!hc || cc.c != cur) {                  // the cell is done: its 27 node sums to the grid
+            const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
+            R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];
+#pragma unroll
+            for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+                R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
+                if constexpr (ADJ) red_add4(node, acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2), R(0));   // (v_bar, 0)
+                else red_add4(node, acc.m(kk), acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2));          // (m, q)
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if constexpr (!ADJ) {                          // node tiles reached by the warp's cells
+        const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
+        if (lane < 8 && ((wreach >> lane) & 1u)) {
+            int u[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
+            mark_node_tile(io.flags, P.node_list, P.list_count,
+                           (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
+        }
+    }
+}
+
+template <class R, int NT, int MAT>
+__global__ void __launch_bounds__(NT, MPM_P2G_MINB)
+    k_p2g_direct(const Params<R> P, const P2GIO<R> io, unsigned long long *__restrict__ escaped_count,
+                 int32_t *__restrict__ g2p_cursor)
+{
+    using Gm = Geo<3>;
+    constexpr int NCM = direct_stage_comps<MAT>();
     constexpr int CELLS = 128;                       // cells per work item
     constexpr int ITEMS = Gm::TN / CELLS;            // work items per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -823,8 +976,6 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
     int32_t *const s_off = reinterpret_cast<int32_t *>(smem_raw + (size_t)2 * NCM * NT * sizeof(R)) +
                            (tid >> 5) * kDirectOffPad;
     const int n_items = *io.n_tiles * ITEMS;
-    const int64_t ld = io.ld;
-    const R mass = ADJ ? R(0) : P.mass;
     bool any_escape = false;
     for (;;) {
         int item = 0;
@@ -832,144 +983,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int k = item / ITEMS;
-        const int cbase = (item - k * ITEMS) * CELLS;
-        const int4 t = io.tiles[k];
-        const int sim = (int)(t.x / P.tiles_per_sim);
-        int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
-        int org[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
-            tl /= P.n_tiles[a];
-        }
-        R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
-        uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
-        const int32_t *pmap = io.posmap + t.y;
-        const int32_t *goff = io.cell_off + (int64_t)t.w * (Gm::TN + 1) + cbase;   // t.w: index in key order
-        // the item's cell offsets, staged once (coalesced) so that the per-cell lookups
-        // below are shared-memory reads (staging the position map as well cost more in
-        // registers than it saved)
-        __syncwarp();
-        for (int i = lane; i <= CELLS; i += 32) s_off[i] = goff[i];
-        __syncwarp();
-        const int32_t *off = s_off - cbase;           // off[c] for the item's cells c in [cbase, cbase + CELLS]
-        auto slot = [&](int q) { return pmap[q]; };
-        const R *St = io.S + t.y;                     // MAT 2: component-major with stride ld
-        const R *S2 = ADJ ? io.src2 + t.y : nullptr;
-        R *const Sv = (ADJ || P.save_S == nullptr) ? nullptr : P.save_S + t.y;
-        auto issue = [&](int stage, int32_t pos) {
-            R *dst = stg + stage * NCM * NT + tid;
-            if constexpr (ADJ) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) cp_async_elem(dst + j * NT, St + pos + j * ld);
-#pragma unroll
-                for (int j = 0; j < 21; ++j) cp_async_elem(dst + (3 + j) * NT, S2 + pos + j * ld);
-            } else {                                  // the particle state, in blocks of kPB
-                const R *src = io.S + sblock((int64_t)t.y + pos, Lay<D, MAT>::NC);
-#pragma unroll
-                for (int j = 0; j < NC; ++j) cp_async_elem(dst + j * NT, src + p2g_comp<D, MAT>(j) * kPB);
-            }
-        };
-        // cursors over this lane's cells cbase + lane + 32 r and their slots
-        struct Cur {
-            int c, q, q1, end;
-            __device__ __forceinline__ bool next(const int32_t *o)
-            {
-                ++q;
-                while (q >= q1) {
-                    c += 32;
-                    if (c >= end) return false;
-                    q = o[c];
-                    q1 = o[c + 1];
-                }
-                return true;
-            }
-        };
-        Cur pc{cbase + lane - 32, 0, 0, cbase + CELLS}, cc = pc;
-        bool hp = pc.next(off);
-#pragma unroll
-        for (int s0 = 0; s0 < 2; ++s0) {
-            if (hp) issue(s0, slot(pc.q));
-            cp_async_commit();
-            hp = hp && pc.next(off);
-        }
-        int32_t ppos = hp ? slot(pc.q) : 0;
-        bool hc = cc.next(off);
-        int stage = 0, cur = -1;
-        int bown[D], nb[D];
-        unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
-        CellSums<R> acc;
-        while (hc) {
-            if (cc.c != cur) {
-                cur = cc.c;
-                int r = cur;
-                unsigned hi = 0u;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const int ci = r % Gm::T;
-                    r /= Gm::T;
-                    bown[a] = org[a] + ci - 1;         // base cell index of the cell's particles
-                    nb[a] = org[a] + ci + 1;           // its first stencil node
-                    hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
-                }
-#pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    if ((m & ~hi & 7u) == 0u) reach |= 1u << m;
-                acc.zero();
-            }
-            cp_async_wait<1>();
-            P2GFactors<R, D> f;
-            {
-                const R *src = stg + stage * NCM * NT + tid;
-                if constexpr (ADJ) {
-                    adj_scatter_factors<R>(P, [&](int j) { return src[j * NT]; }, f);
-                } else {
-                    if (Sv != nullptr) {               // the adjoint's copy of this step's state
-                        R *d = Sv + slot(cc.q);
-#pragma unroll
-                        for (int j = 0; j < NC; ++j) d[j * P.n] = src[j * NT];
-                    }
-                    p2g_factors<R, D, MAT>(P, [&](int j) { return src[j * NT]; }, f);
-                }
-            }
-            if (hp) issue(stage, ppos);
-            cp_async_commit();
-            hp = hp && pc.next(off);
-            if (hp) ppos = slot(pc.q);
-            bool own = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) own = own && (f.b[a] == bown[a]);
-            if (own) {
-                acc.add(f, mass);
-            } else {                                   // left its cell since the sort: on its own
-                any_escape = true;
-                p2g_escape3<R>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
-                               P.node_tiles[0], P.node_tiles[1]);
-            }
-            stage ^= 1;
-            hc = cc.next(off);
-            if (!hc || cc.c != cur) {                  // the cell is done: its 27 node sums to the grid
-                const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
-                R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];
-#pragma unroll
-                for (int kk = 0; kk < Gm::STENCIL; ++kk) {
-                    R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
-                    if constexpr (ADJ) red_add4(node, acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2), R(0));   // (v_bar, 0)
-                    else red_add4(node, acc.m(kk), acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2));          // (m, q)
-                }
-            }
-        }
-        cp_async_wait<0>();
-        if constexpr (!ADJ) {                          // node tiles reached by the warp's cells
-            const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
-            if (lane < 8 && ((wreach >> lane) & 1u)) {
-                int u[3];
-#pragma unroll
-                for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
-                mark_node_tile(io.flags, P.node_list, P.list_count,
-                               (int64_t)sim * P.node_tiles_per_sim + lin3<D>(u, P.node_tiles));
-            }
-        }
+        p2g_direct_item<R, NT, MAT>(P, io, stg, s_off, k, (item - k * ITEMS) * CELLS, any_escape);
     }
     if (escaped_count != nullptr) {
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
@@ -1541,6 +1555,70 @@ template <class R, int D> struct G2PSmem {
     static constexpr size_t total = win_bytes + buf_bytes + 128;
 };
 
+// G2P of one tile t (compact list entry) by a block of NT threads: the tile's
+// velocity window by one TMA tensor copy, the particles in chunks of CH slots
+// aligned to the particle blocks, staged by bulk copies into two buffers of
+// buf_elems reals.  Returns false when a bounded wait ran out.
+template <class R, int D, bool GENERIC, int MAT, int NT, int CH>
+__device__ __forceinline__ bool g2p_tile(const Params<R> &P, const CUtensorMap *tmapV, R *__restrict__ S,
+                                         const R4<R> *__restrict__ V, const R4<R> *__restrict__ V2, int4 t,
+                                         R4<R> *Vw, R *bufs, size_t buf_elems, uint64_t *mbar, uint32_t &phases,
+                                         bool &bad)
+{
+    using Gm = Geo<D>;
+    using Ly = Lay<D, MAT>;
+    constexpr int nc = Ly::G2P_IN;
+    const int tid = threadIdx.x;
+    const int sim = (int)(t.x / P.tiles_per_sim);
+    int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
+    int org[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
+        tl /= P.n_tiles[a];
+    }
+    if (tid == 0 && !(P.debug & kDebugWithholdWindowCopy)) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(&mbar[2], (uint32_t)(Gm::WN * sizeof(R4<R>)));
+        tma_load_window(Vw, tmapV, org, sim, D, &mbar[2]);
+    }
+    // particles in chunks of CH slots aligned to the particle blocks (so a warp's
+    // 32 particles are one block and each of its stores writes one line); slots
+    // of a neighbouring tile at either end are skipped
+    const int64_t a0 = (int64_t)t.y & ~(int64_t)(kPB - 1);
+    const int64_t pend = (int64_t)t.y + t.z;
+    const int nb = (int)((pend - a0 + CH - 1) / CH);
+    int cur = 0;
+    stage_blocks(bufs, S, Ly::NC, nc, a0, (int)(pend - a0 < CH ? pend - a0 : CH), &mbar[0]);
+    bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
+    phases ^= 4u;
+    const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
+    const R4<R> *V2s = V2 != nullptr ? V2 + (int64_t)sim * P.nodes_per_sim : nullptr;
+    for (int j = 0; j < nb; ++j) {
+        if (j + 1 < nb) {
+            const int64_t an = a0 + (int64_t)(j + 1) * CH;
+            stage_blocks(bufs + (size_t)(cur ^ 1) * buf_elems, S, Ly::NC, nc, an,
+                         (int)(pend - an < CH ? pend - an : CH), &mbar[cur ^ 1]);
+        }
+        const bool okb = mbar_wait_bounded(&mbar[cur], (phases >> cur) & 1u);
+        phases ^= 1u << cur;
+        ok = ok && okb;
+#pragma unroll 1
+        for (int u = 0; u < CH / NT; ++u) {
+            const int l = u * NT + tid;                // slot within the chunk
+            const int64_t p = a0 + (int64_t)j * CH + l;
+            if (ok && p >= t.y && p < pend) {
+                const R *bb = bufs + (size_t)cur * buf_elems + (l >> 5) * (nc * kPB) + (l & (kPB - 1));
+                bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * kPB]; }, S, p, Vw, org,
+                                                        Vs, V2s);
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    return ok;
+}
+
 // G2P.  Blocks claim tiles dynamically, one thread per particle.  The tile's
 // grid window of velocities is staged by one TMA tiled load; the particles'
 // inputs are staged 256 at a time by TMA bulk copies, double-buffered.  All
@@ -1580,54 +1658,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_G2P_MINB : 1)
         const int k = next_tile(&counters[3], n_tiles, &s_slot);
         if (k < 0) break;
         const int4 t = tiles[k];
-        const int sim = (int)(t.x / P.tiles_per_sim);
-        int64_t tl = t.x - (int64_t)sim * P.tiles_per_sim;
-        int org[3] = {0, 0, 0};
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
-            tl /= P.n_tiles[a];
-        }
-        if (tid == 0 && !(P.debug & kDebugWithholdWindowCopy)) {
-            fence_proxy_async_smem();
-            mbar_expect_tx(&mbar[2], (uint32_t)(Gm::WN * sizeof(R4<R>)));
-            tma_load_window(Vw, &tmapV, org, sim, D, &mbar[2]);
-        }
-        // particles in chunks of NT slots aligned to the particle blocks (so a warp's
-        // 32 particles are one block and each of its stores writes one line); slots
-        // of a neighbouring tile at either end are skipped
-        constexpr int CH = L::CH;
-        const int64_t a0 = (int64_t)t.y & ~(int64_t)(kPB - 1);
-        const int64_t pend = (int64_t)t.y + t.z;
-        const int nb = (int)((pend - a0 + CH - 1) / CH);
-        int cur = 0;
-        stage_blocks(bufs, S, Ly::NC, nc, a0, (int)(pend - a0 < CH ? pend - a0 : CH), &mbar[0]);
-        bool ok = mbar_wait_bounded(&mbar[2], (phases >> 2) & 1u);
-        phases ^= 4u;
-        const R4<R> *Vs = V + (int64_t)sim * P.nodes_per_sim;
-        const R4<R> *V2s = V2 != nullptr ? V2 + (int64_t)sim * P.nodes_per_sim : nullptr;
-        for (int j = 0; j < nb; ++j) {
-            if (j + 1 < nb) {
-                const int64_t an = a0 + (int64_t)(j + 1) * CH;
-                stage_blocks(bufs + (size_t)(cur ^ 1) * L::buf_elems, S, Ly::NC, nc, an,
-                             (int)(pend - an < CH ? pend - an : CH), &mbar[cur ^ 1]);
-            }
-            const bool okb = mbar_wait_bounded(&mbar[cur], (phases >> cur) & 1u);
-            phases ^= 1u << cur;
-            ok = ok && okb;
-#pragma unroll 1
-            for (int u = 0; u < CH / NT; ++u) {
-                const int l = u * NT + tid;                // slot within the chunk
-                const int64_t p = a0 + (int64_t)j * CH + l;
-                if (ok && p >= t.y && p < pend) {
-                    const R *bb = bufs + (size_t)cur * L::buf_elems + (l >> 5) * (nc * kPB) + (l & (kPB - 1));
-                    bad |= !g2p_particle<R, D, GENERIC, MAT>(P, [&](int jj) { return bb[jj * kPB]; }, S, p, Vw, org,
-                                                            Vs, V2s);
-                }
-            }
-            __syncthreads();
-            cur ^= 1;
-        }
+        const bool ok = g2p_tile<R, D, GENERIC, MAT, NT, L::CH>(P, &tmapV, S, V, V2, t, Vw, bufs, L::buf_elems, mbar,
+                                                             phases, bad);
         timed_out |= !ok;
         if (__syncthreads_or(timed_out)) {
             if (tid == 0) atomicOr(status, (int32_t)kStatusTimeout);
