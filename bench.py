@@ -408,13 +408,48 @@ def secondary_measurements(stream, dev):
     reps = 50
     tr = _event_ms(stream, lambda: [net.train_step(xs, ts, 1e-3) for _ in range(reps)]) / reps
     inf = _event_ms(stream, lambda: [net.infer(xs) for _ in range(reps)]) / reps
+    # device-only: inputs resident, no host copies and no synchronisation inside the timed region
+    import torch
+    dx_, dt_ = torch.tensor(xs, device=dev), torch.tensor(ts, device=dev)
+    dl_ = torch.zeros(1, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    for _ in range(5):
+        net.train_step_async(256, dx_.data_ptr(), dt_.data_ptr(), 1e-3, dl_.data_ptr())
+    tr_dev = _event_ms(stream, lambda: [net.train_step_async(256, dx_.data_ptr(), dt_.data_ptr(), 1e-3,
+                                                             dl_.data_ptr()) for _ in range(reps)]) / reps
     net.close()
     fl_fwd = 2 * 256 * sum(W[i] * W[i + 1] for i in range(3))
     out["mlp"] = {"widths": W, "batch": 256, "train_step_ms": tr, "infer_ms": inf,
                   "train_tflops": 3 * fl_fwd / (tr * 1e-3) / 1e12,
                   "note": "host-synchronous calls incl. host<->device copies of x, targets and loss",
-                  "gemm": gemm_measurement(stream)}
+                  "device_train_step_ms": tr_dev, "device_train_tflops": 3 * fl_fwd / (tr_dev * 1e-3) / 1e12,
+                  "device_note": "mpm_mlp_train_step_async on resident device buffers: forward, backward, Adam "
+                                 "(about 30 launches per step at this size; launch- and latency-bound)",
+                  "gemm": gemm_measurement(stream),
+                  "gemm_network_shape": gemm_measurement(stream, shape=(256, 256, 640), reps=200)}
     return out
+
+
+def mlp_device_measurement(reps=20):
+    """The 640-256-256-32 network's training step on resident device buffers at batch 256."""
+    import torch
+
+    from paper_2507_04192_gb300 import mpm
+    stream = torch.cuda.Stream()
+    W = [640, 256, 256, 32]
+    net = mpm.MLP(W, 256, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    net.set_params((rng.standard_normal(net.num_params) * 0.03).astype(np.float32))
+    dx_ = torch.tensor(rng.standard_normal((256, 640)).astype(np.float32), device="cuda")
+    dt_ = torch.tensor(rng.uniform(0.1, 0.6, (256, 32)).astype(np.float32), device="cuda")
+    dl_ = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    step = lambda: net.train_step_async(256, dx_.data_ptr(), dt_.data_ptr(), 1e-3, dl_.data_ptr())
+    for _ in range(3):
+        step()
+    ms = _event_ms(stream, lambda: [step() for _ in range(reps)]) / reps
+    net.close()
+    return {"widths": W, "batch": 256, "train_step_ms": ms}
 
 
 def gemm_measurement(stream, shape=(8192, 2048, 2048), reps=10):
@@ -596,11 +631,15 @@ def main():
     ap.add_argument("--headline-only", action="store_true", help="skip the adjoint, batched and network lines")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 line")
     ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM line (profiling)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="only the network's device-side training step at batch 256 (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         bench_reference(args)
+    elif args.mlp_only:
+        print(json.dumps({"mlp_device": mlp_device_measurement()}), flush=True)
     elif args.gemm_only:
         import torch
         stream = torch.cuda.Stream()

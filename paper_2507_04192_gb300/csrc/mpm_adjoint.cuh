@@ -982,6 +982,151 @@ __device__ __forceinline__ void stencil_moments3(const R w[3][3], const R dw[3][
     }
 }
 
+// The same moments in single precision with paired arithmetic: components PC
+// and PC + 1 of the node field run as one paired fused multiply-add (__ffma2_rn,
+// each half rounded as fmaf) against a factor broadcast into both halves, the
+// third component stays scalar; the sums are bitwise those of the form above.
+// PC is chosen so that the paired components are an aligned pair of the node's
+// 16-byte load.
+template <int PC, bool WITH_G, class Load>
+__device__ __forceinline__ void stencil_moments3_x2(const float w[3][3], const float dw[3][3], float inv_dx, Load load,
+                                                    Mom3<float> &m)
+{
+    constexpr int SC = PC == 0 ? 2 : 0;             // the scalar component
+    auto bc = [](float a) { return make_float2(a, a); };
+    auto z2 = []() { return make_float2(0.f, 0.f); };
+    const float s2 = inv_dx * inv_dx;
+    const float dd[3] = {s2, -2.f * s2, s2};
+    float2 V = z2(), M[3], L[3], Q[3][3], H[6];
+    float v_ = 0.f, M_[3], L_[3], Q_[3][3], H_[6], Lg[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        M[b] = L[b] = z2();
+        M_[b] = L_[b] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            Q[e][b] = z2();
+            Q_[e][b] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        H[q] = z2();
+        H_[q] = 0.f;
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+        float2 fp[9];
+        float fsc[9], gs[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            float f[3], g;
+            load(q % 3, q / 3, k2, f, g);
+            fp[q] = make_float2(f[PC], f[PC + 1]);
+            fsc[q] = f[SC];
+            gs[q] = g;
+        }
+        float2 WW = z2(), DW = z2(), WD = z2(), JW = z2(), WJ = z2(), JDW = z2(), WJD = z2(), JD = z2(), DJ = z2(),
+               DDW = z2(), WDD = z2(), DDp = z2();
+        float ww = 0.f, dw_ = 0.f, wd = 0.f, jw = 0.f, wj = 0.f, jdw = 0.f, wjd = 0.f, jd = 0.f, dj = 0.f, ddw = 0.f,
+              wdd = 0.f, ddp = 0.f;
+        float gWW = 0.f, gDW = 0.f, gWD = 0.f;
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            float2 XW = z2(), XD = z2(), XJ = z2(), XJD = z2(), XDD = z2();
+            float xw = 0.f, xd = 0.f, xj = 0.f, xjd = 0.f, xdd = 0.f, gW = 0.f, gD = 0.f;
+#pragma unroll
+            for (int k0 = 0; k0 < 3; ++k0) {
+                const float2 f = fp[k1 * 3 + k0];
+                const float fs = fsc[k1 * 3 + k0];
+                const float a0 = w[0][k0], b0 = dw[0][k0];
+                XW = __ffma2_rn(bc(a0), f, XW);
+                xw = fmaf(a0, fs, xw);
+                XD = __ffma2_rn(bc(b0), f, XD);
+                xd = fmaf(b0, fs, xd);
+                if (k0 > 0) {
+                    XJ = __ffma2_rn(bc(float(k0) * a0), f, XJ);
+                    xj = fmaf(float(k0) * a0, fs, xj);
+                    XJD = __ffma2_rn(bc(float(k0) * b0), f, XJD);
+                    xjd = fmaf(float(k0) * b0, fs, xjd);
+                }
+                XDD = __ffma2_rn(bc(dd[k0]), f, XDD);
+                xdd = fmaf(dd[k0], fs, xdd);
+                if (WITH_G) {
+                    gW = fmaf(a0, gs[k1 * 3 + k0], gW);
+                    gD = fmaf(b0, gs[k1 * 3 + k0], gD);
+                }
+            }
+            const float a1 = w[1][k1], b1 = dw[1][k1], j1 = float(k1) * a1, jd1 = float(k1) * b1, c1 = dd[k1];
+            WW = __ffma2_rn(bc(a1), XW, WW);     ww = fmaf(a1, xw, ww);
+            DW = __ffma2_rn(bc(a1), XD, DW);     dw_ = fmaf(a1, xd, dw_);
+            WD = __ffma2_rn(bc(b1), XW, WD);     wd = fmaf(b1, xw, wd);
+            JW = __ffma2_rn(bc(a1), XJ, JW);     jw = fmaf(a1, xj, jw);
+            WJ = __ffma2_rn(bc(j1), XW, WJ);     wj = fmaf(j1, xw, wj);
+            JDW = __ffma2_rn(bc(a1), XJD, JDW);  jdw = fmaf(a1, xjd, jdw);
+            WJD = __ffma2_rn(bc(jd1), XW, WJD);  wjd = fmaf(jd1, xw, wjd);
+            JD = __ffma2_rn(bc(b1), XJ, JD);     jd = fmaf(b1, xj, jd);
+            DJ = __ffma2_rn(bc(j1), XD, DJ);     dj = fmaf(j1, xd, dj);
+            DDW = __ffma2_rn(bc(a1), XDD, DDW);  ddw = fmaf(a1, xdd, ddw);
+            WDD = __ffma2_rn(bc(c1), XW, WDD);   wdd = fmaf(c1, xw, wdd);
+            DDp = __ffma2_rn(bc(b1), XD, DDp);   ddp = fmaf(b1, xd, ddp);
+            if (WITH_G) {
+                gWW = fmaf(a1, gW, gWW);
+                gDW = fmaf(a1, gD, gDW);
+                gWD = fmaf(b1, gW, gWD);
+            }
+        }
+        const float a2 = w[2][k2], b2 = dw[2][k2], j2 = float(k2) * a2, jd2 = float(k2) * b2, c2 = dd[k2];
+        V = __ffma2_rn(bc(a2), WW, V);                 v_ = fmaf(a2, ww, v_);
+        M[0] = __ffma2_rn(bc(a2), JW, M[0]);           M_[0] = fmaf(a2, jw, M_[0]);
+        M[1] = __ffma2_rn(bc(a2), WJ, M[1]);           M_[1] = fmaf(a2, wj, M_[1]);
+        M[2] = __ffma2_rn(bc(j2), WW, M[2]);           M_[2] = fmaf(j2, ww, M_[2]);
+        L[0] = __ffma2_rn(bc(a2), DW, L[0]);           L_[0] = fmaf(a2, dw_, L_[0]);
+        L[1] = __ffma2_rn(bc(a2), WD, L[1]);           L_[1] = fmaf(a2, wd, L_[1]);
+        L[2] = __ffma2_rn(bc(b2), WW, L[2]);           L_[2] = fmaf(b2, ww, L_[2]);
+        Q[0][0] = __ffma2_rn(bc(a2), JDW, Q[0][0]);    Q_[0][0] = fmaf(a2, jdw, Q_[0][0]);
+        Q[1][1] = __ffma2_rn(bc(a2), WJD, Q[1][1]);    Q_[1][1] = fmaf(a2, wjd, Q_[1][1]);
+        Q[2][2] = __ffma2_rn(bc(jd2), WW, Q[2][2]);    Q_[2][2] = fmaf(jd2, ww, Q_[2][2]);
+        Q[0][1] = __ffma2_rn(bc(a2), JD, Q[0][1]);     Q_[0][1] = fmaf(a2, jd, Q_[0][1]);
+        Q[0][2] = __ffma2_rn(bc(b2), JW, Q[0][2]);     Q_[0][2] = fmaf(b2, jw, Q_[0][2]);
+        Q[1][0] = __ffma2_rn(bc(a2), DJ, Q[1][0]);     Q_[1][0] = fmaf(a2, dj, Q_[1][0]);
+        Q[1][2] = __ffma2_rn(bc(b2), WJ, Q[1][2]);     Q_[1][2] = fmaf(b2, wj, Q_[1][2]);
+        Q[2][0] = __ffma2_rn(bc(j2), DW, Q[2][0]);     Q_[2][0] = fmaf(j2, dw_, Q_[2][0]);
+        Q[2][1] = __ffma2_rn(bc(j2), WD, Q[2][1]);     Q_[2][1] = fmaf(j2, wd, Q_[2][1]);
+        H[0] = __ffma2_rn(bc(a2), DDW, H[0]);          H_[0] = fmaf(a2, ddw, H_[0]);
+        H[1] = __ffma2_rn(bc(a2), WDD, H[1]);          H_[1] = fmaf(a2, wdd, H_[1]);
+        H[2] = __ffma2_rn(bc(c2), WW, H[2]);           H_[2] = fmaf(c2, ww, H_[2]);
+        H[3] = __ffma2_rn(bc(a2), DDp, H[3]);          H_[3] = fmaf(a2, ddp, H_[3]);
+        H[4] = __ffma2_rn(bc(b2), DW, H[4]);           H_[4] = fmaf(b2, dw_, H_[4]);
+        H[5] = __ffma2_rn(bc(b2), WD, H[5]);           H_[5] = fmaf(b2, wd, H_[5]);
+        if (WITH_G) {
+            Lg[0] = fmaf(a2, gDW, Lg[0]);
+            Lg[1] = fmaf(a2, gWD, Lg[1]);
+            Lg[2] = fmaf(b2, gWW, Lg[2]);
+        }
+    }
+    auto put = [](float *dst, float2 pr, float sc) {    // dst[c] for c = 0, 1, 2
+        dst[PC] = pr.x;
+        dst[PC + 1] = pr.y;
+        dst[SC] = sc;
+    };
+    put(m.V, V, v_);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        put(m.M[b], M[b], M_[b]);
+        put(m.L[b], L[b], L_[b]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) put(m.Q[e][b], Q[e][b], Q_[e][b]);
+        m.Lg[b] = Lg[b];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) put(m.H[q], H[q], H_[q]);
+}
+
+#ifndef MPM_ADJ_X2
+#define MPM_ADJ_X2 1
+#endif
+
 __device__ __forceinline__ int hidx3(int b, int a)
 {
     return b == a ? b : (b + a == 1 ? 3 : (b + a == 2 ? 4 : 5));
@@ -1006,14 +1151,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3_MINB : 1)
         AdjStencil<R, D> s;
         adj_stencil<R, D>(P, x, s);
         Mom3<R> m;
-        stencil_moments3<R, false>(s.w, s.dw, P.inv_dx, [&](int k0, int k1, int k2, R f[3], R &g) {
+        auto loadv = [&](int k0, int k1, int k2, R f[3], R &g) {
             const int a3[3] = {s.b[0] + 2 + k0, s.b[1] + 2 + k1, s.b[2] + 2 + k2};
             const R4<R> v4 = GV[lin3<D>(a3, P.G_nodes)];
             f[0] = v4.x;
             f[1] = v4.y;
             f[2] = v4.z;
             g = R(0);
-        }, m);
+        };
+        if constexpr (sizeof(R) == 4 && MPM_ADJ_X2) stencil_moments3_x2<0, false>(s.w, s.dw, P.inv_dx, loadv, m);
+        else stencil_moments3<R, false>(s.w, s.dw, P.inv_dx, loadv, m);
         R vp[D], Lf[D * D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -1137,14 +1284,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ3P_MINB : 1)
         AdjStencil<R, D> s;
         adj_stencil<R, D>(P, x, s);
         Mom3<R> m;
-        stencil_moments3<R, true>(s.w, s.dw, P.inv_dx, [&](int k0, int k1, int k2, R f[3], R &g) {
+        auto loadab = [&](int k0, int k1, int k2, R f[3], R &g) {
             const int a3[3] = {s.b[0] + 2 + k0, s.b[1] + 2 + k1, s.b[2] + 2 + k2};
             const R4<R> ab = GAB[lin3<D>(a3, P.G_nodes)];
             g = ab.x;
             f[0] = ab.y;
             f[1] = ab.z;
             f[2] = ab.w;
-        }, m);
+        };
+        if constexpr (sizeof(R) == 4 && MPM_ADJ_X2) stencil_moments3_x2<1, true>(s.w, s.dw, P.inv_dx, loadab, m);
+        else stencil_moments3<R, true>(s.w, s.dw, P.inv_dx, loadab, m);
         // stress-force coefficient Fm (P_a += Fm_ab d_b w)
         const bool sand = P.material == 1;
         R Fm[D * D];
