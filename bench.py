@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (2.7M 3D collapse, FP32 vs FP64 plain); adjoint/forward ratio"
 WORKLOAD = "granular_cylinder_3d_256x256x128"
+FORWARD_KERNELS = ("sort", "p2g", "grid", "g2p")      # kernel classes of a forward step
 
 
 def dist_env():
@@ -346,6 +347,20 @@ def secondary_measurements(stream, dev):
     fwd3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0), sim.step(steps3))) for _ in range(2))
     adj3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
                                           mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3)))) for _ in range(2))
+    # per-step costs inside the sweep (CUDA events around each launch group): the
+    # forward steps (first pass and recompute) and the reverse steps
+    mpm.mpm_set_timing(sim.ctx, True)
+    mpm.mpm_reset_timing(sim.ctx)
+    mpm.mpm_restore_state(sim.ctx, 0)
+    mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3))
+    kt3 = {k: mpm.mpm_get_timing(sim.ctx, k) for k in mpm.KERNELS}
+    mpm.mpm_reset_timing(sim.ctx)
+    mpm.mpm_restore_state(sim.ctx, 0)
+    sim.step(steps3)
+    kf3 = {k: mpm.mpm_get_timing(sim.ctx, k) for k in FORWARD_KERNELS}
+    mpm.mpm_set_timing(sim.ctx, False)
+    fwd_step3 = sum(kf3[k][0] for k in FORWARD_KERNELS) / steps3
+    rev_step3 = kt3["reverse"][0] / max(1, kt3["reverse"][1])
     # the same sweep keeping every segment of the first pass in HBM (no recomputation)
     mpm.mpm_set_adjoint_memory(sim.ctx, 1 << 38)
     adj3k = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
@@ -355,6 +370,10 @@ def secondary_measurements(stream, dev):
                                      f"checkpoint 60, 16x16 floor patches, fp32)",
                          "forward_ms": fwd3, "adjoint_ms": adj3, "adjoint_over_forward": (adj3 - fwd3) / fwd3,
                          "total_over_forward": adj3 / fwd3,
+                         "reverse_step_ms": rev_step3, "forward_step_ms": fwd_step3,
+                         "reverse_step_over_forward_step": rev_step3 / fwd_step3,
+                         "sweep_ms_by_class": {k: v[0] for k, v in kt3.items()},
+                         "sweep_launches_by_class": {k: v[1] for k, v in kt3.items()},
                          "kept_segments": {"adjoint_ms": adj3k, "adjoint_over_forward": (adj3k - fwd3) / fwd3,
                                            "total_over_forward": adj3k / fwd3,
                                            "note": "mpm_set_adjoint_memory: all ten 60-step segments of the "
@@ -380,7 +399,7 @@ def secondary_measurements(stream, dev):
     mpm.mpm_set_timing(sim.ctx, True)
     mpm.mpm_reset_timing(sim.ctx)
     ms = _event_ms(stream, lambda: sim.step(dsteps))
-    kt = {k: mpm.mpm_get_timing(sim.ctx, k)[0] / dsteps for k in mpm.KERNELS}
+    kt = {k: mpm.mpm_get_timing(sim.ctx, k)[0] / dsteps for k in FORWARD_KERNELS}
     xd = sim.get("x")
     sim.close()
     dnodes = count_active_nodes(xd, wd.dx, wd.n_cells)
@@ -524,7 +543,7 @@ def bench_ours(args):
         st1 = sim.stats()
         launches = st1["launches"] - st0["launches"]
         sorts = st1["sorts"] - st0["sorts"]
-        ktimes = {k: mpm.mpm_get_timing(sim.ctx, k) for k in mpm.KERNELS} if timing else None
+        ktimes = {k: mpm.mpm_get_timing(sim.ctx, k) for k in FORWARD_KERNELS} if timing else None
         sim.close()
         return ms, launches, ktimes, sorts
 

@@ -392,7 +392,8 @@ enum {
     MPM_KERNEL_P2G = 1,
     MPM_KERNEL_GRID = 2,
     MPM_KERNEL_G2P = 3,
-    MPM_KERNEL_COUNT = 4
+    MPM_KERNEL_REVERSE = 4,     /* one reverse step of mpm_step_adjoint (all its kernels) */
+    MPM_KERNEL_COUNT = 5
 };
 int mpm_set_timing(mpm_ctx *ctx, int enable);
 int mpm_get_timing(mpm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);

@@ -240,11 +240,11 @@ __device__ __forceinline__ int64_t wall_seg(const Params<R> &P, int w, const int
 }
 
 // Adjoint of the wall chain: ob (adjoint of the output) -> adjoint of u, in place;
-// d<ob, out>/d mu is added to mu_bar (per wall segment) for walls with friction.
-template <class R, int D>
+// d<ob, out>/d mu goes to emit(w, segment, value) for walls with friction.
+template <class R, int D, class Emit>
 __device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, const int a3[3],
                                                const R chain[2 * D][3], const bool applied[2 * D], R ob[3],
-                                               double *const mu_bar[kMaxWalls])
+                                               double *const mu_bar[kMaxWalls], Emit emit)
 {
     constexpr int floor_w = 2 * (D - 1);
 #pragma unroll
@@ -281,8 +281,8 @@ __device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, cons
             if (bb != ax) ob[bb] = s * ob[bb] + k * u[bb];
         ob[ax] = -dot * mu * sgn / vt;
         if (mu_bar[w] != nullptr)
-            atomicAdd(&mu_bar[w][(int64_t)sim * P.wall[w].n_seg[0] * P.wall[w].n_seg[1] + wall_seg<R, D>(P, w, a3)],
-                      (double)(-dot * vn / vt));
+            emit(w, (int64_t)sim * P.wall[w].n_seg[0] * P.wall[w].n_seg[1] + wall_seg<R, D>(P, w, a3),
+                 (double)(-dot * vn / vt));
     }
 }
 
@@ -657,7 +657,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_
 // Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P)
 // over the node tiles the forward step updated (the list GL it saved: GL[0] tiles,
 // then their indices), blocks striding the list; GVB is cleared behind, ready for
-// the next reverse step.
+// the next reverse step.  The dL/dmu terms of a warp's nodes are summed per wall
+// segment across the warp (nodes of a floor row share segments) before one FP64
+// atomic per segment.
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA,
                                                       R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB,
@@ -665,6 +667,7 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
                                                       int32_t *__restrict__ scatter_cursor)
 {
     using Gm = Geo<D>;
+    static_assert(Gm::TN % 256 == 0, "whole warps per node tile");
     if (scatter_cursor != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *scatter_cursor = 0;
     const int n_list = GL[0];
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
         u[a] = (int)(r % P.node_tiles[a]);
         r /= P.node_tiles[a];
     }
-    for (int t = threadIdx.x; t < Gm::TN; t += blockDim.x) {
+    for (int t = threadIdx.x; t < Gm::TN; t += blockDim.x) {       // the same trip count in every lane
         int a3[3] = {0, 0, 0};
         int rr = t;
         bool ok = true;
@@ -686,32 +689,58 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
             rr /= Gm::T;
             ok = ok && a3[a] < P.G_nodes[a];
         }
-        if (!ok) continue;
-        const int64_t i = lin3<D>(a3, P.G_nodes);
-        const R4<R> b4 = GVB[i];
-        GVB[i] = R4<R>{R(0), R(0), R(0), R(0)};
-        const R4<R> acc = GA[i];
-        if (!(acc.x > P.m_eps)) {
-            GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
-            continue;
+        // this node's dL/dmu term (one wall with friction per node; a node where two
+        // such walls meet adds its second term at once)
+        int pw = -1;
+        int64_t pidx = 0;
+        double pval = 0.0;
+        auto emit = [&](int w, int64_t idx, double v) {
+            if (pw < 0) {
+                pw = w;
+                pidx = idx;
+                pval = v;
+            } else {
+                atomicAdd(&mu_bar.w[w][idx], v);
+            }
+        };
+        if (ok) {
+            const int64_t i = lin3<D>(a3, P.G_nodes);
+            const R4<R> b4 = GVB[i];
+            GVB[i] = R4<R>{R(0), R(0), R(0), R(0)};
+            const R4<R> acc = GA[i];
+            if (!(acc.x > P.m_eps)) {
+                GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
+            } else {
+                const R inv_m = R(1) / acc.x;
+                R vel[3] = {acc.y * inv_m + P.dt * P.gravity[0], acc.z * inv_m + P.dt * P.gravity[1],
+                            D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
+                R chain[2 * D][3];
+                bool applied[2 * D];
+                const unsigned removed = obstacle_contact<R, D>(P, a3, vel);
+                walls_forward<R, D>(P, 0, a3, vel, chain, applied);
+                R ob[3] = {b4.x, b4.y, b4.z};
+                walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w, emit);
+#pragma unroll
+                for (int a = 0; a < D; ++a)              // the obstacle projections (their own transposes)
+                    if ((removed >> a) & 1u) ob[a] = R(0);
+                const R Pv[3] = {acc.y, acc.z, acc.w};
+                R mb = R(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
+                GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
+            }
         }
-        const R inv_m = R(1) / acc.x;
-        R vel[3] = {acc.y * inv_m + P.dt * P.gravity[0], acc.z * inv_m + P.dt * P.gravity[1],
-                    D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
-        R chain[2 * D][3];
-        bool applied[2 * D];
-        const unsigned removed = obstacle_contact<R, D>(P, a3, vel);
-        walls_forward<R, D>(P, 0, a3, vel, chain, applied);
-        R ob[3] = {b4.x, b4.y, b4.z};
-        walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w);
-#pragma unroll
-        for (int a = 0; a < D; ++a)                  // the obstacle projections (their own transposes)
-            if ((removed >> a) & 1u) ob[a] = R(0);
-        const R Pv[3] = {acc.y, acc.z, acc.w};
-        R mb = R(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
-        GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
+        // lanes holding a term for the same (wall, segment) add them; the lowest adds to mu_bar
+        const unsigned full = 0xffffffffu;
+        const unsigned holders = __ballot_sync(full, pw >= 0);
+        if (pw >= 0) {
+            const unsigned long long key = ((unsigned long long)pw << 56) ^ (unsigned long long)pidx;
+            const unsigned peers = __match_any_sync(holders, key);
+            const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+            double sum = 0.0;
+            for (unsigned m = peers; m != 0u; m &= m - 1u) sum += __shfl_sync(peers, pval, __ffs(m) - 1);
+            if (lane == leader) atomicAdd(&mu_bar.w[pw][pidx], sum);
+        }
     }
     }
 }
@@ -1446,11 +1475,11 @@ template <class R, int D> struct AdjLaunch {
                         P, (const R *)st, (const R4<R> *)GV, (const R *)lam_in, (R *)lam_out, (R4<R> *)a.GVB,
                         (R *)a.coef);
                     constexpr int NT = 128;
-                    constexpr size_t smem = p2g_direct_smem<R, NT, 2>();
+                    constexpr size_t smem = p2g_direct_smem<R, 3, NT, 2>();
                     static_assert(smem <= 48 * 1024, "k_p2g_direct shared memory above the default limit");
                     P2GIO<R> io{(const R *)st, (const R *)a.coef, h.n, a.tiles, a.n_tiles, a.cursor, a.posmap,
                                 a.cell_off, (R4<R> *)a.GVB, nullptr};
-                    k_p2g_direct<R, NT, 2><<<ds.num_sms * MPM_P2G_MINB, NT, smem, ds.stream>>>(P, io, nullptr,
+                    k_p2g_direct<R, 3, NT, 2><<<ds.num_sms * MPM_P2G_MINB, NT, smem, ds.stream>>>(P, io, nullptr,
                                                                                                nullptr);
                 }
             } else {

@@ -1230,8 +1230,11 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                 ad.posmap = a.gen_posmap + (int64_t)g * n;
                 ad.cell_off = a.gen_celloff + (int64_t)g * ds.max_tiles * TNc;
             }
-            c->aops->step(h, ds, ad, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
-                          a.lam[cur ^ 1], mub);
+            {
+                TimingScope ts(c, MPM_KERNEL_REVERSE);
+                c->aops->step(h, ds, ad, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
+                              a.lam[cur ^ 1], mub);
+            }
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
                 const int o = obs_of_step[t];

@@ -738,29 +738,31 @@ __device__ __forceinline__ void adj_scatter_factors(const Params<R> &P, Raw raw,
     }
 }
 
-// A particle that left its sort cell, scattered on its own to the grid (27 vector
-// atomics), with its node tiles marked when fsim is set.  Kept out of line: the
+// A particle that left its sort cell, scattered on its own to the grid (3^D vector
+// atomics), with its node tiles marked when flags is set (tbase: the first tile of
+// its simulation in the list's numbering over all simulations).  Kept out of line: the
 // path is rare and its registers would otherwise count against the accumulating
 // loop.  The factors go by value: a reference kept them in local memory for every
 // particle (P2G 0.166 -> 0.145 ms on the 2.76M-particle collapse by value; having
 // the callee recompute them from the staged slots measured 0.188 ms).
-// Node values are stored (m, q) for P2G; with fsim == nullptr (the adjoint's v_bar
+// Node values are stored (m, q) for P2G; with flags == nullptr (the adjoint's v_bar
 // scatter, no mass channel) as (q, 0), the grid adjoint's layout.
-template <class R>
-__device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R> *Asim, int Gx, int Gy,
-                                         uint32_t *fsim, int32_t *list, int32_t *count, int ntx, int nty)
+template <class R, int D>
+__device__ __noinline__ void p2g_escape(const P2GFactors<R, D> f, R mass, R4<R> *Asim, int Gx, int Gy,
+                                        uint32_t *flags, int64_t tbase, int32_t *list, int32_t *count, int ntx,
+                                        int nty)
 {
-    for (int kk = 0; kk < 27; ++kk) {
-        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = kk / 9;
-        R m, mom[3];
-        p2g_node<R, 3>(f, mass, k0, k1, k2, m, mom);
-        const int a0 = f.b[0] + 2 + k0, a1 = f.b[1] + 2 + k1, a2 = f.b[2] + 2 + k2;
+    for (int kk = 0; kk < Geo<D>::STENCIL; ++kk) {
+        const int k0 = kk % 3, k1 = (kk / 3) % 3, k2 = D == 3 ? kk / 9 : 0;
+        R m, mom[D];
+        p2g_node<R, D>(f, mass, k0, k1, k2, m, mom);
+        const int a0 = f.b[0] + 2 + k0, a1 = f.b[1] + 2 + k1, a2 = D == 3 ? f.b[D - 1] + 2 + k2 : 0;
         R4<R> *node = &Asim[((int64_t)a2 * Gy + a1) * Gx + a0];
-        if (fsim != nullptr) red_add4(node, m, mom[0], mom[1], mom[2]);
-        else red_add4(node, mom[0], mom[1], mom[2], R(0));
-        if (fsim != nullptr) {
-            const int u0 = a0 / Geo<3>::T, u1 = a1 / Geo<3>::T, u2 = a2 / Geo<3>::T;
-            mark_node_tile(fsim, list, count, ((int64_t)u2 * nty + u1) * ntx + u0);
+        if (flags != nullptr) red_add4(node, m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
+        else red_add4(node, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0), R(0));
+        if (flags != nullptr) {                  // the list holds tiles by their index over all simulations
+            const int u0 = a0 / Geo<D>::T, u1 = a1 / Geo<D>::T, u2 = a2 / Geo<D>::T;
+            mark_node_tile(flags, list, count, tbase + ((int64_t)u2 * nty + u1) * ntx + u0);
         }
     }
 }
@@ -769,56 +771,74 @@ __device__ __noinline__ void p2g_escape3(const P2GFactors<R, 3> f, R mass, R4<R>
 // them as float pairs added with paired fused multiply-adds, as G2P's
 // contraction does, measured slower here: the pairs raised the register spills
 // of this 168-register kernel.)
-template <class R> struct CellSums {
-    R acc[27][4];
+template <class R, int D> struct CellSums {
+    R acc[Geo<D>::STENCIL][D + 1];
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int k = 0; k < 27; ++k)
+        for (int k = 0; k < Geo<D>::STENCIL; ++k)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[k][v] = R(0);
+            for (int v = 0; v <= D; ++v) acc[k][v] = R(0);
     }
-    __device__ __forceinline__ void add(const P2GFactors<R, 3> &f, R mp) { p2g_accumulate<R, 3>(f, mp, acc); }
+    __device__ __forceinline__ void add(const P2GFactors<R, D> &f, R mp) { p2g_accumulate<R, D>(f, mp, acc); }
     __device__ __forceinline__ R m(int k) const { return acc[k][0]; }
-    __device__ __forceinline__ R q(int k, int a) const { return acc[k][1 + a]; }
+    __device__ __forceinline__ R q(int k, int a) const { return a < D ? acc[k][1 + a] : R(0); }
 };
 
 // Components staged per particle by k_p2g_direct: P2G's inputs (MAT 0, 1), or x
 // and the 21 scatter coefficients (MAT 2).
-template <int MAT> __host__ __device__ constexpr int direct_stage_comps() { return MAT == 2 ? 24 : kP2GStageComps<3>; }
+template <int D, int MAT> __host__ __device__ constexpr int direct_stage_comps()
+{
+    return MAT == 2 ? 24 : kP2GStageComps<D>;
+}
 // Per warp of k_p2g_direct: its work item's 129 cell offsets (padded to 132),
 // staged in shared memory at the start of the item.
 constexpr int kDirectOffPad = 132;
-template <class R, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
+// Cells per work item and cp.async stages per thread of the cell-ordered P2G.  In
+// 2D (16 particles per cell in the dense fluids) a lane walks long runs of one
+// cell's particles, so the pipeline is deeper and the items shorter (more of
+// them to balance the SMs).
+#ifndef MPM_P2G2_CELLS
+#define MPM_P2G2_CELLS 32
+#endif
+#ifndef MPM_P2G2_STAGES
+#define MPM_P2G2_STAGES 4
+#endif
+template <int D> __host__ __device__ constexpr int direct_cells() { return D == 3 ? 128 : MPM_P2G2_CELLS; }
+template <int D> __host__ __device__ constexpr int direct_stages() { return D == 3 ? 2 : MPM_P2G2_STAGES; }
+template <class R, int D, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
 {
-    return (size_t)2 * direct_stage_comps<MAT>() * NT * sizeof(R) + (size_t)(NT / 32) * kDirectOffPad * sizeof(int32_t);
+    return (size_t)direct_stages<D>() * direct_stage_comps<D, MAT>() * NT * sizeof(R) +
+           (size_t)(NT / 32) * kDirectOffPad * sizeof(int32_t);
 }
 
-// P2G without a shared-memory window (3D, register accumulation).  Warps claim
-// work items of 128 cells (two layer groups of a tile) from a global cursor and
-// never synchronise with each other: lane l walks cells base + l, + 32, + 64,
-// + 96 through a two-stage cp.async pipeline, sums the particles still in their
-// cell in registers and adds the 27 node sums of a cell straight to the grid
-// with vector atomics (27 per cell instead of 108 shared-memory atomics plus the
-// window pass); particles that left their cell are scattered on their own.  The
-// warp marks the node tiles its cells reach.
+// P2G without a shared-memory window (register accumulation, single precision).
+// Warps claim work items of 128 cells (two layer groups of a 3D tile, half of a
+// 2D tile) from a global cursor and never synchronise with each other: lane l
+// walks cells base + l, + 32, + 64, + 96 through a two-stage cp.async pipeline,
+// sums the particles still in their cell in registers and adds the 3^D node sums
+// of a cell straight to the grid with vector atomics (27 per cell in 3D instead
+// of 108 shared-memory atomics plus the window pass); particles that left their
+// cell are scattered on their own.  The warp marks the node tiles its cells reach.
 #ifndef MPM_P2G_DIRECT
 #define MPM_P2G_DIRECT 1
 #endif
-// One work item of the cell-ordered P2G (3D): the CELLS cells [cbase, cbase + CELLS)
+// One work item of the cell-ordered P2G: the CELLS cells [cbase, cbase + CELLS)
 // of compact tile k (key order), one warp, lane l walking cells cbase + l + 32 r.
-// stg: this block's cp.async staging slots (2 stages x NCM x NT reals); s_off:
-// this warp's 132 shared ints for the item's cell offsets.
-template <class R, int NT, int MAT>
+// stg: this block's cp.async staging slots (ST stages x NCM x NT reals); s_off:
+// this warp's 132 shared ints for the item's cell offsets.  MAT 2 (the adjoint's
+// v_bar scatter) is 3D only.
+template <class R, int D, int NT, int MAT>
 __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<R> &io, R *stg, int32_t *s_off,
                                                 int k, int cbase, bool &any_escape)
 {
-    constexpr int D = 3;
     using Gm = Geo<D>;
     constexpr bool ADJ = MAT == 2;
-    constexpr int NCM = direct_stage_comps<MAT>();
+    static_assert(!ADJ || D == 3, "the v_bar scatter is 3D");
+    constexpr int NCM = direct_stage_comps<D, MAT>();
     constexpr int NC = ADJ ? 24 : p2g_ncomp<D>(MAT);
-    constexpr int CELLS = 128;
+    constexpr int CELLS = direct_cells<D>();
+    constexpr int ST = direct_stages<D>();
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t ld = io.ld;
     const R mass = ADJ ? R(0) : P.mass;
@@ -831,8 +851,8 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
         org[a] = (int)(tl % P.n_tiles[a]) * Gm::T;
         tl /= P.n_tiles[a];
     }
+    if constexpr (D == 2) org[2] = 0;
     R4<R> *Asim = io.A + (int64_t)sim * P.nodes_per_sim;
-    uint32_t *fsim = ADJ ? nullptr : io.flags + (int64_t)sim * P.node_tiles_per_sim;
     const int32_t *pmap = io.posmap + t.y;
     const int32_t *goff = io.cell_off + (int64_t)t.w * (Gm::TN + 1) + cbase;   // t.w: index in key order
     // the item's cell offsets, staged once (coalesced) so that the per-cell lookups
@@ -877,7 +897,7 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
     Cur pc{cbase + lane - 32, 0, 0, cbase + CELLS}, cc = pc;
     bool hp = pc.next(off);
 #pragma unroll
-    for (int s0 = 0; s0 < 2; ++s0) {
+    for (int s0 = 0; s0 < ST; ++s0) {
         if (hp) issue(s0, slot(pc.q));
         cp_async_commit();
         hp = hp && pc.next(off);
@@ -885,9 +905,10 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
     int32_t ppos = hp ? slot(pc.q) : 0;
     bool hc = cc.next(off);
     int stage = 0, cur = -1;
-    int bown[D], nb[D];
+    int bown[D], nb[3];
+    if constexpr (D == 2) nb[2] = 0;
     unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
-    CellSums<R> acc;
+    CellSums<R, D> acc;
     while (hc) {
         if (cc.c != cur) {
             cur = cc.c;
@@ -902,11 +923,11 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
                 hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
             }
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if ((m & ~hi & 7u) == 0u) reach |= 1u << m;
+            for (int m = 0; m < (1 << D); ++m)
+                if ((m & ~hi & ((1u << D) - 1u)) == 0u) reach |= 1u << m;
             acc.zero();
         }
-        cp_async_wait<1>();
+        cp_async_wait<ST - 1>();
         P2GFactors<R, D> f;
         {
             const R *src = stg + stage * NCM * NT + tid;
@@ -932,14 +953,15 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
             acc.add(f, mass);
         } else {                                   // left its cell since the sort: on its own
             any_escape = true;
-            p2g_escape3<R>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], fsim, P.node_list, P.list_count,
-                           P.node_tiles[0], P.node_tiles[1]);
+            p2g_escape<R, D>(f, mass, Asim, P.G_nodes[0], P.G_nodes[1], ADJ ? nullptr : io.flags,
+                             (int64_t)sim * P.node_tiles_per_sim, P.node_list, P.list_count, P.node_tiles[0],
+                             P.node_tiles[1]);
         }
-        stage ^= 1;
+        stage = stage + 1 == ST ? 0 : stage + 1;
         hc = cc.next(off);
-        if (!hc || cc.c != cur) {                  // the cell is done: its 27 node sums to the grid
+        if (!hc || cc.c != cur) {                  // the cell is done: its 3^D node sums to the grid
             const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
-            R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];
+            R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];   // nb[2] = 0 in 2D
 #pragma unroll
             for (int kk = 0; kk < Gm::STENCIL; ++kk) {
                 R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
@@ -951,8 +973,8 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
     cp_async_wait<0>();
     if constexpr (!ADJ) {                          // node tiles reached by the warp's cells
         const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
-        if (lane < 8 && ((wreach >> lane) & 1u)) {
-            int u[3];
+        if (lane < (1 << D) && ((wreach >> lane) & 1u)) {
+            int u[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < D; ++a) u[a] = org[a] / Gm::T + ((lane >> a) & 1);
             mark_node_tile(io.flags, P.node_list, P.list_count,
@@ -961,19 +983,23 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
     }
 }
 
-template <class R, int NT, int MAT>
-__global__ void __launch_bounds__(NT, MPM_P2G_MINB)
+// Resident 128-thread blocks per SM of the 2D cell-ordered P2G.
+#ifndef MPM_P2G2_MINB
+#define MPM_P2G2_MINB 4
+#endif
+template <class R, int D, int NT, int MAT>
+__global__ void __launch_bounds__(NT, D == 3 ? MPM_P2G_MINB : MPM_P2G2_MINB)
     k_p2g_direct(const Params<R> P, const P2GIO<R> io, unsigned long long *__restrict__ escaped_count,
                  int32_t *__restrict__ g2p_cursor)
 {
-    using Gm = Geo<3>;
-    constexpr int NCM = direct_stage_comps<MAT>();
-    constexpr int CELLS = 128;                       // cells per work item
+    using Gm = Geo<D>;
+    constexpr int NCM = direct_stage_comps<D, MAT>();
+    constexpr int CELLS = direct_cells<D>();         // cells per work item
     constexpr int ITEMS = Gm::TN / CELLS;            // work items per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *stg = reinterpret_cast<R *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
-    int32_t *const s_off = reinterpret_cast<int32_t *>(smem_raw + (size_t)2 * NCM * NT * sizeof(R)) +
+    int32_t *const s_off = reinterpret_cast<int32_t *>(smem_raw + (size_t)direct_stages<D>() * NCM * NT * sizeof(R)) +
                            (tid >> 5) * kDirectOffPad;
     const int n_items = *io.n_tiles * ITEMS;
     bool any_escape = false;
@@ -983,7 +1009,7 @@ __global__ void __launch_bounds__(NT, MPM_P2G_MINB)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         const int k = item / ITEMS;
-        p2g_direct_item<R, NT, MAT>(P, io, stg, s_off, k, (item - k * ITEMS) * CELLS, any_escape);
+        p2g_direct_item<R, D, NT, MAT>(P, io, stg, s_off, k, (item - k * ITEMS) * CELLS, any_escape);
     }
     if (escaped_count != nullptr) {
         const unsigned ball = __ballot_sync(0xffffffffu, any_escape);
@@ -1482,11 +1508,11 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 #pragma unroll
         for (int a = 0; a < D; ++a) vnew[a] = vp[a] + P.flip_alpha * (Sp[(Ly::V + a) * np] - vo[a]);
     }
-#pragma unroll
     // one finiteness test for the whole new state: a sum of finite values is finite
     // (values near the overflow threshold are themselves a blown-up state), and a
     // non-finite term makes it +-inf or NaN
     R chk = R(0);
+#pragma unroll
     for (int a = 0; a < D; ++a) {
         R xn = x[a] + P.dt * vp[a];
         xn = xn < R(0) ? R(0) : (xn > P.L[a] ? P.L[a] : xn);
@@ -1926,22 +1952,31 @@ template <class R, int D> struct Launch {
     template <int MAT> static void p2g_launch(const HostParams &h, DevState &ds)
     {
         auto P = make_params<R>(h, ds);
-        if constexpr (D == 3 && sizeof(R) == 4 && MPM_P2G_DIRECT) {
-            constexpr int NT = kP2GThreads;
-            constexpr size_t smem = p2g_direct_smem<R, NT, MAT>();
+        if constexpr (sizeof(R) == 4 && MPM_P2G_DIRECT) {
+            constexpr int NT = 128;
+            constexpr size_t smem = p2g_direct_smem<R, D, NT, MAT>();
             static_assert(smem <= 48 * 1024, "k_p2g_direct shared memory above the default limit");
-            const int nb = ds.num_sms * MPM_P2G_MINB;
+            // persistent: as many blocks as fit on the GPU at once (3D: the launch
+            // bound's MPM_P2G_MINB per SM; 2D: more, its accumulators are 27 values)
+            static int per_sm = 0;
+            if (per_sm == 0) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2g_direct<R, D, NT, MAT>, NT, smem) !=
+                        cudaSuccess ||
+                    per_sm < 1)
+                    per_sm = MPM_P2G_MINB;
+            }
+            const int nb = ds.num_sms * per_sm;
             // tiles in key order (claiming them largest first, as G2P does, measured slower)
             P2GIO<R> io{(const R *)ds.S, nullptr, h.npad, ds.tiles, ds.counters + 1, ds.counters + 2, ds.posmap,
                         ds.cell_off, (R4<R> *)ds.A, ds.flags};
-            k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, io, ds.escaped, ds.counters + 3);
+            k_p2g_direct<R, D, NT, MAT><<<nb, NT, smem, ds.stream>>>(P, io, ds.escaped, ds.counters + 3);
             if (h.transfer == 3) {                   // FLIP: the momenta without forces, for v_i^n
                 auto P2 = P;
                 P2.no_force = 1;
                 P2.save_S = nullptr;
                 cudaMemsetAsync(ds.counters + 2, 0, sizeof(int32_t), ds.stream);
                 io.A = (R4<R> *)ds.A2;
-                k_p2g_direct<R, NT, MAT><<<nb, NT, smem, ds.stream>>>(P2, io, ds.escaped, ds.counters + 3);
+                k_p2g_direct<R, D, NT, MAT><<<nb, NT, smem, ds.stream>>>(P2, io, ds.escaped, ds.counters + 3);
             }
             return;
         }

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_EINVAL", -2: "MPM_ENOMEM", -3: "MPM_ECUDA"
 MPM_FP32, MPM_FP64 = 0, 1
 MPM_FLUID, MPM_DRUCKER_PRAGER = 0, 1
 FIELDS = {"x": 0, "v": 1, "C": 2, "F": 3, "rho": 4, "sigma": 5, "eps": 6}
-KERNELS = {"sort": 0, "p2g": 1, "grid": 2, "g2p": 3}
+KERNELS = {"sort": 0, "p2g": 1, "grid": 2, "g2p": 3, "reverse": 4}
 
 
 class GridDesc(C.Structure):

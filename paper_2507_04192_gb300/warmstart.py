@@ -98,6 +98,17 @@ class Setup3D:
         return float(w.extras["body_hi"][0] - w.extras["body_lo"][0])
 
 
+def setup_3d_full() -> Setup3D:
+    """The inverse problem at scale: the 1.36M-particle collapse (radius 30 dx,
+    height 60 dx, 192 x 192 x 96 cells, dx = 1/256 m), floor friction over 16 x 16
+    patches, 128 tracks observed 10 times over a 600-step horizon (checkpoint 60).
+    The time step is 2.5e-5 s (15 ms of flow; a Courant number of 0.17 for the
+    P-wave speed of this sand), so that the base of the column has begun to slide
+    by the last observation."""
+    return Setup3D(n_cells=(192, 192, 96), dx=1.0 / 256.0, radius_cells=30.0, height_cells=60.0, patches=16,
+                   n_track=128, n_obs=10, steps=600, dt=2.5e-5, checkpoint_every=60)
+
+
 def observe_batch(w, mus: np.ndarray, precision=mpm.MPM_FP32, stream: int = 0) -> np.ndarray:
     """Tracked positions (B, n_obs, n_track, dim) of B independent runs of workload
     ``w`` that differ only in their floor friction ``mus`` (B, n_seg); one batched
@@ -257,11 +268,12 @@ def main(argv=None):
     ap.add_argument("--held-out", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--max-iters", type=int, default=300)
-    ap.add_argument("--setup", choices=["2d", "3d"], default="2d",
-                    help="2d: 96^2 dam breaks, 32 floor segments; 3d: 64x64x32 granular collapses, 4x4 floor patches")
+    ap.add_argument("--setup", choices=["2d", "3d", "3d-full"], default="2d",
+                    help="2d: 96^2 dam breaks, 32 floor segments; 3d: 64x64x32 granular collapses, 4x4 floor "
+                         "patches; 3d-full: the 1.36M-particle collapse, 16x16 floor patches")
     ap.add_argument("--batch", type=int, default=256)
     args = ap.parse_args(argv)
-    setup = Setup() if args.setup == "2d" else Setup3D()
+    setup = {"2d": Setup, "3d": Setup3D, "3d-full": setup_3d_full}[args.setup]()
     t0 = time.perf_counter()
     X, Y = generate(setup, args.runs, batch=args.batch)
     t1 = time.perf_counter()

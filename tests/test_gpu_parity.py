@@ -180,6 +180,40 @@ def test_fast_particles_take_the_out_of_tile_path():
     assert np.abs(gpu["x"] - ref["x"]).max() <= 1e-9
 
 
+def test_fast_particles_fp32_cell_ordered_p2g_escape_path():
+    """The 2D single-precision P2G sums per cell; particles that left their cell
+    since the last sort (here: every particle, several cells away) are scattered
+    one by one.  Both paths against the oracle."""
+    w = inputs.dam_break_2d(64, 0.2, 0.2)
+    w.x = w.x + 0.3
+    w.v = np.tile([4.0, 1.0], (w.n, 1))
+    ref = run_oracle(w, 64)
+    gpu, stats = run_gpu(w, 64, mpm.MPM_FP32, sort_every=64)
+    assert stats["escaped"] > 0
+    assert np.abs(gpu["x"] - ref["x"]).max() <= 1e-4
+    assert np.abs(gpu["v"] - ref["v"]).max() <= 1e-4 * np.abs(ref["v"]).max()
+
+
+def test_batched_2d_fluid_fp32_matches_oracle_per_simulation():
+    # the 2D cell-ordered P2G over several simulations of one context (per-simulation
+    # grid offsets and friction), each against its own oracle run
+    base = inputs.dam_break_inverse_2d(32, n_seg=8, steps=80)
+    mus = [inputs.friction_field(8, s) for s in (1, 2, 3)]
+    B = len(mus)
+    sim = mpm.Simulation(2, base.n_cells, base.dx, base.dt, base.gravity, base.material, mpm.MPM_FP32, 8, batch=B)
+    sim.load(np.concatenate([base.x] * B), None, base.particle_volume,
+             np.repeat(np.arange(B, dtype=np.int32), base.n))
+    sim.set_friction(2, (8, 1), np.concatenate(mus))
+    sim.step(80)
+    xb = sim.get("x").reshape(B, base.n, 2)
+    sim.close()
+    for b, mu in enumerate(mus):
+        w = inputs.dam_break_inverse_2d(32, n_seg=8, steps=80)
+        w.friction = [(2, (8, 1), mu)]
+        ref = run_oracle(w, 80)
+        assert np.abs(xb[b] - ref["x"]).max() <= 1e-4
+
+
 def test_set_field_roundtrip_and_errors():
     w = inputs.dam_break_2d(32, 0.25, 0.25)
     sim = mpm.Simulation.from_workload(w, mpm.MPM_FP64)
