@@ -612,7 +612,12 @@ def bench_ours(args):
             "data": "synthetic",
             "config": workload_config(world),
             "fp64": ({"value": value64, "unit": "particle-steps/s", "steps": steps64,
-                      "ms_per_step": ms64 / steps64} if not args.no_fp64 else None),
+                      "ms_per_step": ms64 / steps64,
+                      "bound": "fp64 alu",
+                      "ceiling_note": "ncu: the FP64 P2G and G2P keep the FP64 pipe busy on 81-87 % of their "
+                                      "active cycles (profiles/k_p2g_k_g2p_fp64_granular_cylinder_3d_128x128x64.md): "
+                                      "at most about 1.2x faster with the same FP64 instruction count"}
+                     if not args.no_fp64 else None),
             "kernels_ms_per_step": {k: kt[k][0] / max(1, args.steps) for k in kt},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -640,6 +645,48 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def profile_run(what: str, steps: int):
+    """A short run of one workload for ncu (no timing): ``forward`` steps the
+    2.76M-particle collapse in FP32, ``fp64`` the 345,648-particle collapse
+    (128 x 128 x 64 cells) in FP64, ``batched`` the 256 batched 96^2 dam breaks,
+    ``adjoint`` runs one 120-step adjoint of the 1.36M-particle inverse problem
+    (checkpoint 60), ``adjoint-small`` the same on its 96 x 96 x 48 counterpart
+    (169,680 particles, a few GB on the device).  Prints one JSON line with the
+    sizes."""
+    from paper_2507_04192_gb300 import inputs, mpm
+    if what == "forward":
+        w = inputs.granular_cylinder_3d()
+        sim = mpm.Simulation.from_workload(w, mpm.MPM_FP32)
+        sim.step(steps)
+        out = {"particles": w.n}
+    elif what == "fp64":
+        w = inputs.granular_cylinder_3d((128, 128, 64), 19, 38, dx=1 / 128.0, dt=2e-5)
+        sim = mpm.Simulation.from_workload(w, mpm.MPM_FP64)
+        sim.step(steps)
+        out = {"particles": w.n}
+    elif what == "batched":
+        wb = inputs.dam_break_2d(96)
+        B = 256
+        sim = mpm.Simulation(2, wb.n_cells, wb.dx, wb.dt, wb.gravity, wb.material, mpm.MPM_FP32, wb.sort_every,
+                             batch=B)
+        sim.load(np.tile(wb.x, (B, 1)), None, wb.particle_volume, np.repeat(np.arange(B, dtype=np.int32), wb.n))
+        sim.set_friction(2, (32, 1), np.stack([inputs.friction_field(32, 1_000_000 + i) for i in range(B)]).reshape(-1))
+        sim.step(steps)
+        out = {"particles": B * wb.n}
+    else:
+        w3 = (inputs.granular_inverse_3d() if what == "adjoint" else
+              inputs.granular_inverse_3d((96, 96, 48), 15, 30, steps=120, checkpoint_every=60))
+        obs = [s for s in w3.extras["obs_steps"] if s <= 120]
+        sim = mpm.Simulation.from_workload(w3, mpm.MPM_FP32)
+        mpm.mpm_set_observations(sim.ctx, w3.extras["track_ids"], obs,
+                                 np.zeros((len(obs), len(w3.extras["track_ids"]), 3)))
+        loss, _ = mpm.mpm_step_adjoint(sim.ctx, 120, 60, 4, len(w3.extras["mu_true"]))
+        out = {"particles": w3.n, "loss": loss}
+    sim.synchronize()
+    sim.close()
+    print(json.dumps({"profile": what, "steps": steps, **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -652,11 +699,15 @@ def main():
     ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM line (profiling)")
     ap.add_argument("--mlp-only", action="store_true",
                     help="only the network's device-side training step at batch 256 (profiling)")
+    ap.add_argument("--profile", choices=["forward", "fp64", "batched", "adjoint", "adjoint-small"],
+                    help="a short untimed run of one workload for ncu (--steps sets its length)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         bench_reference(args)
+    elif args.profile:
+        profile_run(args.profile, args.steps)
     elif args.mlp_only:
         print(json.dumps({"mlp_device": mlp_device_measurement()}), flush=True)
     elif args.gemm_only:

@@ -101,7 +101,7 @@ template <class R>
 struct Params {
     int n_cells[3];
     R dx, inv_dx, dt, gravity[3], L[3];
-    R rho0, bulk_K, gamma, inv_rho0, mass, m_eps;
+    R rho0, bulk_K, gamma, inv_rho0, mass, m_eps, K_over_gamma;
     R K, G, q_phi, k_phi, q_psi, sig_t, tau_P, alpha_P, eps2_coef, inv_G_Kqq, inv_K;
     int material, dp_literal, gamma_int, transfer, no_force;
     R flip_alpha;

@@ -92,17 +92,26 @@ class InversionResult:
 
 
 def invert(problem: FrictionInversion, mu0, mu_true=None, mask=None, tol: float = 0.05, max_iters: int = 300,
-           lr0: float = 0.1, decay: float = 0.97, callback: Optional[Callable[[dict], None]] = None
+           lr0=0.1, decay: float = 0.97, callback: Optional[Callable[[dict], None]] = None
            ) -> InversionResult:
     """Adam (beta 0.9 / 0.999, eps 1e-8) with lr = lr0 * decay^k, mu clamped to [0, 1].
+    ``lr0`` is one rate, or one per segment (an array): Adam's update is taken
+    element by element, so a per-segment rate scales each segment's steps.
 
     Stops when the relative L2 error of mu on ``mask`` (the segments the
     observations constrain) falls to ``tol``, or after ``max_iters`` updates.
     """
     torch = _torch()
     mu = torch.tensor(np.asarray(mu0, dtype=np.float64), requires_grad=True)
-    opt = torch.optim.Adam([mu], lr=lr0, betas=(0.9, 0.999), eps=1e-8)
-    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=decay)
+    per_segment = np.ndim(lr0) > 0
+    if per_segment:
+        lr_vec = torch.tensor(np.broadcast_to(np.asarray(lr0, dtype=np.float64), mu.shape).copy())
+        b1, b2, eps = 0.9, 0.999, 1e-8
+        m1 = torch.zeros_like(mu, requires_grad=False)
+        m2 = torch.zeros_like(mu, requires_grad=False)
+    else:
+        opt = torch.optim.Adam([mu], lr=lr0, betas=(0.9, 0.999), eps=1e-8)
+        sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=decay)
     history = []
     for k in range(max_iters + 1):
         err = relative_error(mu.detach().numpy(), mu_true, mask) if mu_true is not None else None
@@ -110,15 +119,26 @@ def invert(problem: FrictionInversion, mu0, mu_true=None, mask=None, tol: float 
             return InversionResult(mu.detach().numpy().copy(), k, True, history)
         if k == max_iters:
             break
-        opt.zero_grad()
+        if mu.grad is not None:
+            mu.grad = None
         loss = friction_loss(mu, problem)
         loss.backward()
-        rec = {"iter": k, "loss": float(loss.detach()), "error": err, "lr": opt.param_groups[0]["lr"]}
+        lr_now = float((lr_vec * decay ** k).max()) if per_segment else opt.param_groups[0]["lr"]
+        rec = {"iter": k, "loss": float(loss.detach()), "error": err, "lr": lr_now}
         history.append(rec)
         if callback:
             callback(rec)
-        opt.step()
-        sched.step()
+        if per_segment:                  # the update of torch.optim.Adam, with an elementwise rate
+            with torch.no_grad():
+                g = mu.grad
+                m1.mul_(b1).add_(g, alpha=1.0 - b1)
+                m2.mul_(b2).addcmul_(g, g, value=1.0 - b2)
+                t = k + 1
+                denom = (m2.sqrt() / np.sqrt(1.0 - b2 ** t)).add_(eps)
+                mu.sub_(lr_vec * decay ** k / (1.0 - b1 ** t) * m1 / denom)
+        else:
+            opt.step()
+            sched.step()
         with torch.no_grad():
             mu.clamp_(0.0, 1.0)
     return InversionResult(mu.detach().numpy().copy(), max_iters, False, history)

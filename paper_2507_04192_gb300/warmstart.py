@@ -171,6 +171,7 @@ class WarmStartNet:
         self.net.set_params(np.concatenate(p).astype(np.float32))
         self.x_mean = np.zeros(n_in)
         self.x_scale = np.ones(n_in)
+        self.val_rmse, self.val_rmse_seg = None, None
 
     def _standardise(self, X):
         return ((np.asarray(X, dtype=np.float64) - self.x_mean) / self.x_scale).astype(np.float32)
@@ -200,15 +201,25 @@ class WarmStartNet:
             order = rng.permutation(len(X))[:n]
             losses = [self.net.train_step(Xs[order[i:i + B]], Y[order[i:i + B]], lr) for i in range(0, n, B)]
             hist.append(float(np.mean(losses)))
-        self.val_rmse = float(np.sqrt(np.mean((self.predict(Xv) - Yv) ** 2))) if n_val else None
+        if n_val:
+            err = self.predict(Xv) - Yv
+            self.val_rmse = float(np.sqrt(np.mean(err ** 2)))
+            self.val_rmse_seg = np.sqrt(np.mean(err ** 2, axis=0))
+        else:
+            self.val_rmse, self.val_rmse_seg = None, None
         return hist
 
-    def refine_rate(self, default: float = 0.1) -> float:
+    def refine_rate(self, default: float = 0.1):
         """First Adam step of the adjoint refinement that starts from this network's
-        prediction: Adam moves every coefficient by about its rate in the first
-        steps, so the rate is matched to the network's held-out RMS error instead
-        of the uniform guess's 0.1 (a larger step throws a good warm start away)."""
-        return default if self.val_rmse is None else float(min(default, max(self.val_rmse, 2e-3)))
+        prediction, per segment: Adam moves every coefficient by about its rate in
+        the first steps, so each segment's rate is the network's held-out RMS error
+        on that segment (at most the uniform guess's 0.1, at least 2e-3).  Segments
+        the observations pin down are predicted well and refined with small steps;
+        segments they do not reach keep the large step (a single rate for all would
+        either throw a good warm start away or freeze the rest)."""
+        if self.val_rmse_seg is None:
+            return default
+        return np.clip(self.val_rmse_seg, 2e-3, default)
 
     def predict(self, X) -> np.ndarray:
         X = self._standardise(np.atleast_2d(X))
@@ -283,7 +294,9 @@ def main(argv=None):
     rows = compare(setup, net, range(1, args.held_out + 1), max_iters=args.max_iters)
     summary = {
         "setup": {k: v for k, v in setup.__dict__.items()}, "runs": args.runs, "generate_s": t1 - t0, "train_s": t2 - t1,
-        "train_loss": [hist[0], hist[-1]], "val_rmse": net.val_rmse, "warm_refine_lr0": net.refine_rate(),
+        "train_loss": [hist[0], hist[-1]], "val_rmse": net.val_rmse,
+        "warm_refine_lr0": {"min": float(np.min(net.refine_rate())), "median": float(np.median(net.refine_rate())),
+                            "max": float(np.max(net.refine_rate()))},
         "uniform": {"converged": sum(r["converged_uniform"] for r in rows),
                     "median_iters": float(np.median([r["iters_uniform"] for r in rows])),
                     "mean_err0": float(np.mean([r["err0_uniform"] for r in rows]))},

@@ -68,6 +68,28 @@ def test_masked_error_target_and_the_clamp():
     assert res.mu.min() >= 0.0 and res.mu.max() <= 1.0
 
 
+def test_per_segment_rates_follow_torch_adam():
+    # one rate per segment takes Adam's update element by element: a uniform
+    # array gives torch.optim.Adam's trajectory, and a segment with a tenfold
+    # smaller rate moves tenfold less in the first step
+    m = np.array([0.15, 0.3, 0.45, 0.6])
+    prob = Quadratic(m, [1.0, 2.0, 0.5, 4.0])
+    ref = inverse.invert(prob, np.full(4, 0.35), mu_true=None, max_iters=40)
+    vec = inverse.invert(prob, np.full(4, 0.35), mu_true=None, max_iters=40, lr0=np.full(4, 0.1))
+    np.testing.assert_allclose(vec.mu, ref.mu, rtol=0, atol=1e-12)
+    np.testing.assert_allclose([h["lr"] for h in vec.history], [h["lr"] for h in ref.history], rtol=1e-12)
+    one = inverse.invert(prob, np.full(4, 0.35), mu_true=None, max_iters=1, lr0=np.array([0.1, 0.01, 0.1, 0.1]))
+    step = np.abs(one.mu - 0.35)
+    np.testing.assert_allclose(step, [0.1, 0.01, 0.1, 0.1], rtol=1e-6)
+
+
+def test_refine_rate_per_segment_from_held_out_error():
+    net = types.SimpleNamespace(val_rmse_seg=np.array([0.001, 0.03, 0.5]))
+    rates = warmstart.WarmStartNet.refine_rate(net)
+    np.testing.assert_allclose(rates, [2e-3, 0.03, 0.1])
+    assert warmstart.WarmStartNet.refine_rate(types.SimpleNamespace(val_rmse_seg=None)) == 0.1
+
+
 def test_relative_error_by_hand():
     assert inverse.relative_error([1.0, 2.0, 2.0], [1.0, 2.0, 4.0]) == pytest.approx(2.0 / np.sqrt(21.0))
     assert inverse.relative_error([0.0, 2.0, 9.0], [1.0, 2.0, 4.0], np.array([True, True, False])) == \
