@@ -240,11 +240,11 @@ __device__ __forceinline__ int64_t wall_seg(const Params<R> &P, int w, const int
 }
 
 // Adjoint of the wall chain: ob (adjoint of the output) -> adjoint of u, in place;
-// d<ob, out>/d mu goes to emit(w, segment, value) for walls with friction.
-template <class R, int D, class Emit>
+// d<ob, out>/d mu is added to mu_bar (per wall segment) for walls with friction.
+template <class R, int D>
 __device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, const int a3[3],
                                                const R chain[2 * D][3], const bool applied[2 * D], R ob[3],
-                                               double *const mu_bar[kMaxWalls], Emit emit)
+                                               double *const mu_bar[kMaxWalls])
 {
     constexpr int floor_w = 2 * (D - 1);
 #pragma unroll
@@ -281,8 +281,8 @@ __device__ __forceinline__ void walls_backward(const Params<R> &P, int sim, cons
             if (bb != ax) ob[bb] = s * ob[bb] + k * u[bb];
         ob[ax] = -dot * mu * sgn / vt;
         if (mu_bar[w] != nullptr)
-            emit(w, (int64_t)sim * P.wall[w].n_seg[0] * P.wall[w].n_seg[1] + wall_seg<R, D>(P, w, a3),
-                 (double)(-dot * vn / vt));
+            atomicAdd(&mu_bar[w][(int64_t)sim * P.wall[w].n_seg[0] * P.wall[w].n_seg[1] + wall_seg<R, D>(P, w, a3)],
+                      (double)(-dot * vn / vt));
     }
 }
 
@@ -657,9 +657,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? MPM_ADJ_MINB : 1) k_adj_
 // Adjoint of the grid update per node: GVB (adjoint of v) -> GAB (adjoint of m, P)
 // over the node tiles the forward step updated (the list GL it saved: GL[0] tiles,
 // then their indices), blocks striding the list; GVB is cleared behind, ready for
-// the next reverse step.  The dL/dmu terms of a warp's nodes are summed per wall
-// segment across the warp (nodes of a floor row share segments) before one FP64
-// atomic per segment.
+// the next reverse step.
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R4<R> *__restrict__ GA,
                                                       R4<R> *__restrict__ GVB, R4<R> *__restrict__ GAB,
@@ -667,7 +665,6 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
                                                       int32_t *__restrict__ scatter_cursor)
 {
     using Gm = Geo<D>;
-    static_assert(Gm::TN % 256 == 0, "whole warps per node tile");
     if (scatter_cursor != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *scatter_cursor = 0;
     const int n_list = GL[0];
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
@@ -679,7 +676,7 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
         u[a] = (int)(r % P.node_tiles[a]);
         r /= P.node_tiles[a];
     }
-    for (int t = threadIdx.x; t < Gm::TN; t += blockDim.x) {       // the same trip count in every lane
+    for (int t = threadIdx.x; t < Gm::TN; t += blockDim.x) {
         int a3[3] = {0, 0, 0};
         int rr = t;
         bool ok = true;
@@ -689,58 +686,32 @@ __global__ void __launch_bounds__(256) k_adj_grid_bwd(const Params<R> P, const R
             rr /= Gm::T;
             ok = ok && a3[a] < P.G_nodes[a];
         }
-        // this node's dL/dmu term (one wall with friction per node; a node where two
-        // such walls meet adds its second term at once)
-        int pw = -1;
-        int64_t pidx = 0;
-        double pval = 0.0;
-        auto emit = [&](int w, int64_t idx, double v) {
-            if (pw < 0) {
-                pw = w;
-                pidx = idx;
-                pval = v;
-            } else {
-                atomicAdd(&mu_bar.w[w][idx], v);
-            }
-        };
-        if (ok) {
-            const int64_t i = lin3<D>(a3, P.G_nodes);
-            const R4<R> b4 = GVB[i];
-            GVB[i] = R4<R>{R(0), R(0), R(0), R(0)};
-            const R4<R> acc = GA[i];
-            if (!(acc.x > P.m_eps)) {
-                GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
-            } else {
-                const R inv_m = R(1) / acc.x;
-                R vel[3] = {acc.y * inv_m + P.dt * P.gravity[0], acc.z * inv_m + P.dt * P.gravity[1],
-                            D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
-                R chain[2 * D][3];
-                bool applied[2 * D];
-                const unsigned removed = obstacle_contact<R, D>(P, a3, vel);
-                walls_forward<R, D>(P, 0, a3, vel, chain, applied);
-                R ob[3] = {b4.x, b4.y, b4.z};
-                walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w, emit);
-#pragma unroll
-                for (int a = 0; a < D; ++a)              // the obstacle projections (their own transposes)
-                    if ((removed >> a) & 1u) ob[a] = R(0);
-                const R Pv[3] = {acc.y, acc.z, acc.w};
-                R mb = R(0);
-#pragma unroll
-                for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
-                GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
-            }
+        if (!ok) continue;
+        const int64_t i = lin3<D>(a3, P.G_nodes);
+        const R4<R> b4 = GVB[i];
+        GVB[i] = R4<R>{R(0), R(0), R(0), R(0)};
+        const R4<R> acc = GA[i];
+        if (!(acc.x > P.m_eps)) {
+            GAB[i] = R4<R>{R(0), R(0), R(0), R(0)};
+            continue;
         }
-        // lanes holding a term for the same (wall, segment) add them; the lowest adds to mu_bar
-        const unsigned full = 0xffffffffu;
-        const unsigned holders = __ballot_sync(full, pw >= 0);
-        if (pw >= 0) {
-            const unsigned long long key = ((unsigned long long)pw << 56) ^ (unsigned long long)pidx;
-            const unsigned peers = __match_any_sync(holders, key);
-            const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-            double sum = 0.0;
-            for (unsigned m = peers; m != 0u; m &= m - 1u) sum += __shfl_sync(peers, pval, __ffs(m) - 1);
-            if (lane == leader) atomicAdd(&mu_bar.w[pw][pidx], sum);
-        }
+        const R inv_m = R(1) / acc.x;
+        R vel[3] = {acc.y * inv_m + P.dt * P.gravity[0], acc.z * inv_m + P.dt * P.gravity[1],
+                    D == 3 ? acc.w * inv_m + P.dt * P.gravity[2] : R(0)};
+        R chain[2 * D][3];
+        bool applied[2 * D];
+        const unsigned removed = obstacle_contact<R, D>(P, a3, vel);
+        walls_forward<R, D>(P, 0, a3, vel, chain, applied);
+        R ob[3] = {b4.x, b4.y, b4.z};
+        walls_backward<R, D>(P, 0, a3, chain, applied, ob, mu_bar.w);
+#pragma unroll
+        for (int a = 0; a < D; ++a)                  // the obstacle projections (their own transposes)
+            if ((removed >> a) & 1u) ob[a] = R(0);
+        const R Pv[3] = {acc.y, acc.z, acc.w};
+        R mb = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) mb -= ob[a] * Pv[a] * inv_m * inv_m;
+        GAB[i] = R4<R>{mb, ob[0] * inv_m, ob[1] * inv_m, D == 3 ? ob[2] * inv_m : R(0)};
     }
     }
 }
