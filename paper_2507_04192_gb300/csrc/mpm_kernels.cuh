@@ -2033,8 +2033,17 @@ template <class R, int D> struct Launch {
             cudaFuncSetAttribute(k_g2p<R, D, GENERIC, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
+        // persistent: as many blocks as fit at once (3D FP32: the launch bound's two
+        // per SM; 2D: three, its registers and shared memory allow it)
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_g2p<R, D, GENERIC, MAT>, G2PSmem<R, D>::NT,
+                                                              smem) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = sizeof(R) == 4 ? MPM_G2P_MINB : 2;
+        }
         int64_t nb = ds.max_tiles;
-        const int64_t cap = (int64_t)ds.num_sms * (sizeof(R) == 4 ? MPM_G2P_MINB : 2);
+        const int64_t cap = (int64_t)ds.num_sms * per_sm;
         if (nb > cap) nb = cap;
         if (nb < 1) nb = 1;
         k_g2p<R, D, GENERIC, MAT><<<(int)nb, G2PSmem<R, D>::NT, smem, ds.stream>>>(
