@@ -387,10 +387,19 @@ def secondary_measurements(stream, dev):
     sim.set_friction(2, (32, 1), np.stack([inputs.friction_field(32, 1_000_000 + i) for i in range(B)]).reshape(-1))
     sim.step(5)
     ms = _event_ms(stream, lambda: sim.step(bsteps))
+    xb = sim.get("x").reshape(B, nb, 2)
     sim.close()
+    # compulsory traffic: the 13-word fluid state read and written once per particle,
+    # 32 B per active node of each simulation's grid (counted on a sample of 16)
+    bnodes = int(round(np.mean([count_active_nodes(xb[i], wb.dx, wb.n_cells) for i in range(0, B, B // 16)]) * B))
+    bbytes = B * nb * 2 * 13 * 4 + bnodes * 32
+    peak, _ = load_peaks()
     out["batched_forward"] = {"workload": f"{B} x dam_break_2d_96 ({B * nb} particles, {bsteps} steps, fp32)",
                               "value": B * nb * bsteps / (ms * 1e-3), "unit": "particle-steps/s",
-                              "ms_per_step": ms / bsteps}
+                              "ms_per_step": ms / bsteps,
+                              "step_roofline": {"bytes_per_step": bbytes, "active_nodes": bnodes,
+                                                "achieved": bbytes / (ms / bsteps * 1e-3) / 1e9, "peak": peak,
+                                                "frac": bbytes / (ms / bsteps * 1e-3) / 1e9 / peak, "unit": "GB/s"}}
     # the 3D dam break with two rigid columns (1.92M fluid particles, FP32)
     wd = inputs.dam_break_3d()
     sim = mpm.Simulation.from_workload(wd, mpm.MPM_FP32, stream=stream.cuda_stream)
