@@ -320,9 +320,13 @@ int mpm_monitor_means(mpm_ctx *ctx, int n_mon, const double *boxes, double *out)
  * rho, sigma) for Drucker-Prager; the zone and contact branches of the forward
  * step are held fixed), batch 1.  Device memory: checkpoints of
  * (2 dim + dim^2 + 1) reals per particle each (+ 6 for Drucker-Prager), plus
- * checkpoint_every states with their grids (more with mpm_set_adjoint_memory),
- * plus in 3D single precision 21 reals per particle of scatter coefficients and
- * the sort tables of each sort generation the kept states span.
+ * two banks of checkpoint_every states with their grids (more segments with
+ * mpm_set_adjoint_memory), plus in 3D single precision 21 reals per particle of
+ * scatter coefficients and the sort tables of each sort generation the kept
+ * states span.  With the default memory setting and more than one segment, the
+ * reverse steps of a segment run on a second stream the library owns while the
+ * segment before it is recomputed on the context's stream; the call returns
+ * with all of that work ordered before later work on the context's stream.
  * MPM_EINVAL for n_steps or checkpoint_every < 1, a NULL loss_out (or a NULL
  * dL_dmu_out with wall >= 0), a batch other than 1, a transfer other than APIC,
  * a wall without a friction field, or an observation beyond n_steps;
@@ -338,7 +342,8 @@ int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, 
  * pass: the last 1 + bytes / (one segment's size) segments are then reversed
  * without recomputation (Sec. 3.3.2 trades memory for recomputation; a GPU with
  * memory to spare can keep the whole horizon).  Default 0: only the last
- * segment is kept and every other one is recomputed from its checkpoint.  A
+ * segment is kept and every other one is recomputed from its checkpoint (into
+ * the other of two banks, while the segment after it is reversed).  A
  * segment of K states takes K x ((2 dim + dim^2 + 1 [+ 6]) reals per particle
  * + two grids of 4 reals per node + 4 bytes per particle) plus the sort tables
  * of its sort generations.  The result does not depend on the setting.

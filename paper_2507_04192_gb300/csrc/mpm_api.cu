@@ -13,6 +13,14 @@
 #include "../../include/mpm.h"
 #include "mpm_adjoint.cuh"
 
+// Reverse sweep of one segment overlapped with the recompute of the one before it.
+#ifndef MPM_ADJ_OVERLAP
+#define MPM_ADJ_OVERLAP 1
+#endif
+#ifndef MPM_ADJ_RPRIO
+#define MPM_ADJ_RPRIO 1
+#endif
+
 using namespace mpm;
 static_assert(MPM_DIAG_COUNT == kDiagCount, "diagnostics slots");
 
@@ -57,6 +65,10 @@ struct AdjHost {
     int gen_cap = 0;
     int4 *gen_tiles = nullptr;
     int32_t *gen_ntiles = nullptr, *gen_posmap = nullptr, *gen_celloff = nullptr;
+    // the reverse sweep's stream and, per bank of kept states, the events that order
+    // it against the recompute: bank filled (recomputed) and bank read (reversed)
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_read[2] = {nullptr, nullptr};
 };
 
 // One saved copy of the particle state on the device.
@@ -150,6 +162,13 @@ void free_adjoint(mpm_ctx *c)
     dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim);
     dfree(a.d_mboxes); dfree(a.d_msums); dfree(a.d_mg);
     dfree(a.coef); dfree(a.gen_tiles); dfree(a.gen_ntiles); dfree(a.gen_posmap); dfree(a.gen_celloff);
+    for (int b = 0; b < 2; ++b) {
+        if (a.ev_filled[b]) cudaEventDestroy(a.ev_filled[b]);
+        if (a.ev_read[b]) cudaEventDestroy(a.ev_read[b]);
+        a.ev_filled[b] = a.ev_read[b] = nullptr;
+    }
+    if (a.rstream) cudaStreamDestroy(a.rstream);
+    a.rstream = nullptr;
     a.gen_cap = 0;
     a.ckpt_cap = a.seg_cap = 0;
     a.allocated = false;
@@ -196,19 +215,20 @@ cudaEvent_t take_event(mpm_ctx *c)
 struct TimingScope {
     mpm_ctx *c;
     int kernel;
+    cudaStream_t stream;
     cudaEvent_t start = nullptr;
-    TimingScope(mpm_ctx *c_, int k) : c(c_), kernel(k)
+    TimingScope(mpm_ctx *c_, int k, cudaStream_t s = nullptr) : c(c_), kernel(k), stream(s ? s : c_->ds.stream)
     {
         if (c->timing) {
             start = take_event(c);
-            cudaEventRecord(start, c->ds.stream);
+            cudaEventRecord(start, stream);
         }
     }
     ~TimingScope()
     {
         if (c->timing) {
             cudaEvent_t stop = take_event(c);
-            cudaEventRecord(stop, c->ds.stream);
+            cudaEventRecord(stop, stream);
             c->pending.push_back({kernel, start, stop});
         }
     }
@@ -1000,8 +1020,12 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     const size_t seg_bytes = (size_t)K * (st_bytes + 2 * gbytes + fbytes + (size_t)n * 4) + gens_seg * gen_bytes;
     int64_t m_keep = 1 + (int64_t)(c->adj_budget > 0 ? c->adj_budget / (int64_t)seg_bytes : 0);
     if (m_keep > n_ckpt) m_keep = n_ckpt;
-    const int64_t KS = m_keep * K;                 // kept-state slots
-    const int gens = split ? (int)(m_keep * gens_seg) : 0;
+    // with one kept segment the reverse sweep of segment k runs on a second stream
+    // while segment k - 1 is recomputed into the other of two banks of K slots
+    const bool overlap = MPM_ADJ_OVERLAP && m_keep == 1 && n_ckpt >= 2;
+    const int64_t banks = overlap ? 2 : m_keep;
+    const int64_t KS = banks * K;                  // kept-state slots
+    const int gens = split ? (int)(banks * gens_seg) : 0;
     // buffers
     if (a.ckpt_cap < n_ckpt) {
         dfree(a.ckpt);
@@ -1084,22 +1108,22 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     auto seg_id_ptr = [&](int64_t j) { return a.seg_id + (int64_t)seg_ids[j] * n; };
     // state j of a segment: after the step's sort, P2G copies the state it reads and
     // the grid update saves its grid; the order's ids are copied once per sort
-    auto keep_state = [&](int j) -> int {
+    auto keep_state = [&](int j, int jfirst, int gbase, int gend) -> int {
         if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
             int rc = do_sort(c);
             if (rc != MPM_OK) return rc;
         }
         seg_gen[j] = c->sorts;
-        if (j > 0 && seg_gen[j] == seg_gen[j - 1]) {
+        if (j > jfirst && seg_gen[j] == seg_gen[j - 1]) {
             seg_ids[j] = seg_ids[j - 1];
             seg_tab[j] = seg_tab[j - 1];
         } else {
             seg_ids[j] = j;
             CK(cudaMemcpyAsync(a.seg_id + (int64_t)j * n, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
                                ds.stream), "segment order");
-            if (j == 0) next_gen = 0;
+            if (j == jfirst) next_gen = gbase;
             seg_tab[j] = -1;
-            if (split && next_gen < a.gen_cap) {       // the sort tables of this generation
+            if (split && next_gen < gend) {            // the sort tables of this generation
                 const int g = next_gen++;
                 seg_tab[j] = g;
                 CK(cudaMemcpyAsync(a.gen_tiles + (int64_t)g * ds.max_tiles, ds.tiles, sizeof(int4) * ds.max_tiles,
@@ -1132,7 +1156,7 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     c->aops->save(h, ds, ckpt_ptr(0));
     for (int t = 1; t <= n_steps; ++t) {
         if (t - 1 >= last_t0) {
-            int rc = keep_state((int)(t - 1 - last_t0));
+            int rc = keep_state((int)(t - 1 - last_t0), 0, 0, overlap ? gens_seg : a.gen_cap);
             if (rc != MPM_OK) return rc;
         }
         int rc = step_many(c, 1);
@@ -1198,26 +1222,76 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
         c->aops->monitor_seed(h, ds, (char *)ds.S + rs * h.off_x, -h.ncomp, a.n_mon, a.d_mboxes,
                               a.d_mg + mobs_of_step[n_steps] * mg_stride, a.lam[cur]);
     }
+    // With overlap the reverse steps run on a second stream: while segment k is
+    // reversed there from one bank, segment k - 1 is recomputed on the context's
+    // stream into the other bank, once the reverse of segment k + 1 has released it.
+    cudaStream_t rstream = ds.stream;
+    if (overlap) {
+        if (a.rstream == nullptr) {
+            // the reverse steps are the sweep's critical path: their blocks are scheduled
+            // first, the recompute's fill what is left
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+            CK(cudaStreamCreateWithPriority(&a.rstream, cudaStreamNonBlocking, MPM_ADJ_RPRIO ? hi : lo),
+               "reverse stream");
+            for (int b = 0; b < 2; ++b) {
+                CK(cudaEventCreateWithFlags(&a.ev_filled[b], cudaEventDisableTiming), "bank event");
+                CK(cudaEventCreateWithFlags(&a.ev_read[b], cudaEventDisableTiming), "bank event");
+            }
+        }
+        rstream = a.rstream;
+    }
+    DevState dr = ds;                                 // the reverse steps' launch state
+    dr.stream = rstream;
+    auto bank_of = [&](int64_t k) { return overlap ? (int)((n_ckpt - 1 - k) % 2) : 0; };
+    // recompute segment k from its checkpoint into its bank (on the context's stream)
+    auto recompute = [&](int64_t k) -> int {
+        const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
+        const int bk = bank_of(k), s0 = bk * K;
+        const int g0 = overlap ? bk * gens_seg : 0, g1 = overlap ? g0 + gens_seg : a.gen_cap;
+        c->aops->restore(h, ds, ckpt_ptr(k));
+        c->need_sort = true;
+        for (int j = 0; j < t1 - t0; ++j) {
+            int rc = keep_state(s0 + j, s0, g0, g1);
+            if (rc == MPM_OK) rc = step_many(c, 1);
+            stop_keeping();
+            if (rc != MPM_OK) return rc;
+        }
+        return MPM_OK;
+    };
+    // on an error the reverse stream is drained before returning
+    auto join = [&](int rc) {
+        if (overlap) cudaStreamSynchronize(rstream);
+        return rc;
+    };
+    if (overlap) CK(cudaEventRecord(a.ev_filled[0], ds.stream), "bank event");   // the last segment and the seeds
     for (int64_t k = n_ckpt - 1; k >= 0; --k) {
         const int t0 = (int)(k * K), t1 = (int)std::min<int64_t>((k + 1) * K, n_steps);
-        const int base = k >= first_kept ? (int)((k - first_kept) * K) : 0;
-        if (k < first_kept) {                          // recompute the segment from its checkpoint
-            c->aops->restore(h, ds, ckpt_ptr(k));
-            c->need_sort = true;
-            for (int j = 0; j < t1 - t0; ++j) {
-                int rc = keep_state(j);
-                if (rc == MPM_OK) rc = step_many(c, 1);
-                stop_keeping();
+        int base;                                      // slot of the segment's first state
+        if (overlap) {
+            if (k >= 1) {
+                const int bn = bank_of(k - 1);
+                if (k + 1 <= n_ckpt - 1) CK(cudaStreamWaitEvent(ds.stream, a.ev_read[bn], 0), "bank wait");
+                int rc = recompute(k - 1);
+                if (rc != MPM_OK) return join(rc);
+                CK(cudaEventRecord(a.ev_filled[bn], ds.stream), "bank event");
+            }
+            CK(cudaStreamWaitEvent(rstream, a.ev_filled[bank_of(k)], 0), "bank wait");
+            base = bank_of(k) * K;
+        } else {
+            base = k >= first_kept ? (int)((k - first_kept) * K) : 0;
+            if (k < first_kept) {
+                int rc = recompute(k);
                 if (rc != MPM_OK) return rc;
             }
         }
         for (int t = t1 - 1; t >= t0; --t) {
             const int j = base + t - t0;               // the kept state's slot
             if (seg_gen[j] != lam_gen) {             // a sort between the two states: re-order
-                c->aops->reorder(h, ds, NA, a.lam_id, a.lam_pos, seg_id_ptr(j), a.lam[cur], a.lam[cur ^ 1]);
+                c->aops->reorder(h, dr, NA, a.lam_id, a.lam_pos, seg_id_ptr(j), a.lam[cur], a.lam[cur ^ 1]);
                 cur ^= 1;
                 CK(cudaMemcpyAsync(a.lam_id, seg_id_ptr(j), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
-                                   ds.stream), "adjoint order");
+                                   rstream), "adjoint order");
                 lam_gen = seg_gen[j];
             }
             AdjDev ad = a.grid;
@@ -1231,23 +1305,25 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
                 ad.cell_off = a.gen_celloff + (int64_t)g * ds.max_tiles * TNc;
             }
             {
-                TimingScope ts(c, MPM_KERNEL_REVERSE);
-                c->aops->step(h, ds, ad, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
+                TimingScope ts(c, MPM_KERNEL_REVERSE, rstream);
+                c->aops->step(h, dr, ad, seg_ptr(j), gridA_ptr(j), gridV_ptr(j), gridL_ptr(j), a.lam[cur],
                               a.lam[cur ^ 1], mub);
             }
             cur ^= 1;
             if (t >= 1 && obs_of_step[t] >= 0) {
                 const int o = obs_of_step[t];
-                c->aops->seed_slots(h, ds, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride,
+                c->aops->seed_slots(h, dr, a.lam_id, a.d_track_of_id, a.d_xobs + o * obs_stride,
                                     a.d_z + o * obs_stride, a.lam[cur]);
             }
             if (t >= 1 && mobs_of_step[t] >= 0)     // S^t is the state kept for step j, in the order of lam
-                c->aops->monitor_seed(h, ds, seg_ptr(j), n, a.n_mon, a.d_mboxes,
+                c->aops->monitor_seed(h, dr, seg_ptr(j), n, a.n_mon, a.d_mboxes,
                                       a.d_mg + mobs_of_step[t] * mg_stride, a.lam[cur]);
         }
+        if (overlap) CK(cudaEventRecord(a.ev_read[bank_of(k)], rstream), "bank event");
         int rc = check_launch(c, "mpm_step_adjoint");
-        if (rc != MPM_OK) return rc;
+        if (rc != MPM_OK) return join(rc);
     }
+    if (overlap) CK(cudaStreamWaitEvent(ds.stream, a.ev_read[bank_of(0)], 0), "join the reverse stream");
     // leave the context at the end-of-horizon state
     CK(cudaMemcpyAsync(ds.S, a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, cudaMemcpyDeviceToDevice, ds.stream),
        "restore final state");
