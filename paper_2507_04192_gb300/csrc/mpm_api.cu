@@ -17,9 +17,6 @@
 #ifndef MPM_ADJ_OVERLAP
 #define MPM_ADJ_OVERLAP 1
 #endif
-#ifndef MPM_ADJ_RPRIO
-#define MPM_ADJ_RPRIO 1
-#endif
 
 using namespace mpm;
 static_assert(MPM_DIAG_COUNT == kDiagCount, "diagnostics slots");
@@ -1228,12 +1225,9 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     cudaStream_t rstream = ds.stream;
     if (overlap) {
         if (a.rstream == nullptr) {
-            // the reverse steps are the sweep's critical path: their blocks are scheduled
-            // first, the recompute's fill what is left
-            int lo = 0, hi = 0;
-            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
-            CK(cudaStreamCreateWithPriority(&a.rstream, cudaStreamNonBlocking, MPM_ADJ_RPRIO ? hi : lo),
-               "reverse stream");
+            // (giving it the highest stream priority measured no different: 445.0 against
+            // 445.2 ms on the 1.36M-particle problem)
+            CK(cudaStreamCreateWithFlags(&a.rstream, cudaStreamNonBlocking), "reverse stream");
             for (int b = 0; b < 2; ++b) {
                 CK(cudaEventCreateWithFlags(&a.ev_filled[b], cudaEventDisableTiming), "bank event");
                 CK(cudaEventCreateWithFlags(&a.ev_read[b], cudaEventDisableTiming), "bank event");
