@@ -58,7 +58,7 @@ def test_dam_break_fp64_200_steps():
     assert_close(gpu, ref, "rho", 1e-9 * 1000.0)
     assert_close(gpu, ref, "sigma", 1e-6 * scale(ref["sigma"]))
     assert_close(gpu, ref, "F", 1e-7)
-    assert stats["steps"] == 200 and stats["sorts"] >= 200 // 8
+    assert stats["steps"] == 200 and stats["sorts"] >= 200 // w.sort_every
 
 
 def test_dam_break_fp32_200_steps():
