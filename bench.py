@@ -347,22 +347,29 @@ def secondary_measurements(stream, dev):
     fwd3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0), sim.step(steps3))) for _ in range(2))
     adj3 = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
                                           mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3)))) for _ in range(2))
-    # per-step costs inside the sweep (CUDA events around each launch group): the
-    # forward steps (first pass and recompute) and the reverse steps
+    # time per kernel class inside the default sweep (CUDA events around each launch
+    # group; there the reverse steps of a segment overlap the recompute of the one
+    # before it, so they share the GPU)
     mpm.mpm_set_timing(sim.ctx, True)
     mpm.mpm_reset_timing(sim.ctx)
     mpm.mpm_restore_state(sim.ctx, 0)
     mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3))
     kt3 = {k: mpm.mpm_get_timing(sim.ctx, k) for k in mpm.KERNELS}
+    # one forward step and one reverse step on their own: a plain forward run, and
+    # the sweep that keeps every segment (no recompute runs beside its reverse steps)
     mpm.mpm_reset_timing(sim.ctx)
     mpm.mpm_restore_state(sim.ctx, 0)
     sim.step(steps3)
     kf3 = {k: mpm.mpm_get_timing(sim.ctx, k) for k in FORWARD_KERNELS}
+    mpm.mpm_set_adjoint_memory(sim.ctx, 1 << 38)
+    mpm.mpm_reset_timing(sim.ctx)
+    mpm.mpm_restore_state(sim.ctx, 0)
+    mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3))
+    kr3 = mpm.mpm_get_timing(sim.ctx, "reverse")
     mpm.mpm_set_timing(sim.ctx, False)
     fwd_step3 = sum(kf3[k][0] for k in FORWARD_KERNELS) / steps3
-    rev_step3 = kt3["reverse"][0] / max(1, kt3["reverse"][1])
+    rev_step3 = kr3[0] / max(1, kr3[1])
     # the same sweep keeping every segment of the first pass in HBM (no recomputation)
-    mpm.mpm_set_adjoint_memory(sim.ctx, 1 << 38)
     adj3k = min(_event_ms(stream, lambda: (mpm.mpm_restore_state(sim.ctx, 0),
                                            mpm.mpm_step_adjoint(sim.ctx, steps3, 60, 4, len(mu3)))) for _ in range(2))
     sim.close()
@@ -372,6 +379,8 @@ def secondary_measurements(stream, dev):
                          "total_over_forward": adj3 / fwd3,
                          "reverse_step_ms": rev_step3, "forward_step_ms": fwd_step3,
                          "reverse_step_over_forward_step": rev_step3 / fwd_step3,
+                         "step_note": "one reverse step timed in the sweep that keeps every segment (nothing runs "
+                                      "beside it), one forward step in a plain forward run",
                          "sweep_ms_by_class": {k: v[0] for k, v in kt3.items()},
                          "sweep_launches_by_class": {k: v[1] for k, v in kt3.items()},
                          "kept_segments": {"adjoint_ms": adj3k, "adjoint_over_forward": (adj3k - fwd3) / fwd3,
