@@ -331,19 +331,24 @@ __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFact
         fx[a] = x[a] * P.inv_dx - R(f.b[a]);
         bspline(fx[a], P.inv_dx, f.w[a], dw[a]);
     }
-    const R mp = P.mass;
+    const R mp = P.mass, mdx = P.mass * P.dx;
+    R fxdx[D];
+#pragma unroll
+    for (int c2 = 0; c2 < D; ++c2) fxdx[c2] = fx[c2] * P.dx;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         R u0 = v[a];
 #pragma unroll
-        for (int c2 = 0; c2 < D; ++c2) u0 -= C[a * D + c2] * fx[c2] * P.dx;
+        for (int c2 = 0; c2 < D; ++c2) u0 = fma(-C[a * D + c2], fxdx[c2], u0);
+        const R mu0 = mp * u0;
 #pragma unroll
         for (int b2 = 0; b2 < D; ++b2) {
-            const R mc = mp * C[a * D + b2] * P.dx;
+            const R mc = C[a * D + b2] * mdx;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                R e = mc * R(j) * f.w[b2][j] + Fm[a * D + b2] * dw[b2][j];
-                if (b2 == 0) e += mp * u0 * f.w[0][j];
+                R e = Fm[a * D + b2] * dw[b2][j];
+                if (j > 0) e = fma(j == 1 ? mc : mc + mc, f.w[b2][j], e);
+                if (b2 == 0) e = fma(mu0, f.w[0][j], e);
                 f.E[a][b2][j] = e;
             }
         }
@@ -382,8 +387,8 @@ __device__ __forceinline__ void p2g_accumulate(const P2GFactors<R, D> &f, R mp, 
                 const int k = k1 * 3 + k0;
                 acc[k][0] = fma(mp * f.w[0][k0], f.w[1][k1], acc[k][0]);
 #pragma unroll
-                for (int a = 0; a < D; ++a)
-                    acc[k][1 + a] += f.E[a][0][k0] * f.w[1][k1] + f.w[0][k0] * f.E[a][1][k1];
+                for (int a = 0; a < D; ++a)           // two chained fused multiply-adds per value
+                    acc[k][1 + a] = fma(f.E[a][0][k0], f.w[1][k1], fma(f.w[0][k0], f.E[a][1][k1], acc[k][1 + a]));
             }
     } else {
 #pragma unroll
@@ -1227,7 +1232,7 @@ __device__ __forceinline__ void dp_update(const Params<R> &P, const R L[9], R s[
     t[3] = S01 + M01 + M10 + twoG * d3;
     t[4] = S02 + M02 + M20 + twoG * d4;
     t[5] = S12 + M12 + M21 + twoG * d5;
-    const R sm = (t[0] + t[1] + t[2]) / R(3);
+    const R sm = (t[0] + t[1] + t[2]) * R(1.0 / 3.0);     // the mean stress (a product: no divide)
     R dev[6] = {t[0] - sm, t[1] - sm, t[2] - sm, t[3], t[4], t[5]};
     const R tau = rsqrt_(R(0.5) * (dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]) +
                          dev[3] * dev[3] + dev[4] * dev[4] + dev[5] * dev[5]);
