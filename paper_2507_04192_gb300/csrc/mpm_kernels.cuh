@@ -331,6 +331,12 @@ __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFact
         fx[a] = x[a] * P.inv_dx - R(f.b[a]);
         bspline(fx[a], P.inv_dx, f.w[a], dw[a]);
     }
+    // two forms of the same sums: with hoisted products and chained fused
+    // multiply-adds (3D sand P2G 0.1252 -> 0.1231 ms on the 2.76M-particle collapse,
+    // 2D 0.170 -> 0.168 ms on the batched dam breaks), or as written below it, which
+    // the 3D fluid kernel keeps (the hoisted form raised its spills: 0.098 -> 0.105
+    // ms on the 1.92M-particle dam break)
+    if constexpr (!(D == 3 && MAT == 0)) {
     const R mp = P.mass, mdx = P.mass * P.dx;
     R fxdx[D];
 #pragma unroll
@@ -352,6 +358,25 @@ __device__ __forceinline__ void p2g_factors(const Params<R> &P, Raw raw, P2GFact
                 f.E[a][b2][j] = e;
             }
         }
+    }
+    } else {
+    const R mp = P.mass;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R u0 = v[a];
+#pragma unroll
+        for (int c2 = 0; c2 < D; ++c2) u0 -= C[a * D + c2] * fx[c2] * P.dx;
+#pragma unroll
+        for (int b2 = 0; b2 < D; ++b2) {
+            const R mc = mp * C[a * D + b2] * P.dx;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                R e = mc * R(j) * f.w[b2][j] + Fm[a * D + b2] * dw[b2][j];
+                if (b2 == 0) e += mp * u0 * f.w[0][j];
+                f.E[a][b2][j] = e;
+            }
+        }
+    }
     }
 }
 
