@@ -1606,9 +1606,12 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 #ifndef MPM_G2P_PPT
 #define MPM_G2P_PPT 1
 #endif
+#ifndef MPM_G2P2_PPT
+#define MPM_G2P2_PPT 1
+#endif
 template <class R, int D> struct G2PSmem {
     static constexpr int NT = 256;
-    static constexpr int CH = NT * (sizeof(R) == 4 ? MPM_G2P_PPT : 1);   // particles per staged chunk
+    static constexpr int CH = NT * (sizeof(R) == 4 ? (D == 3 ? MPM_G2P_PPT : MPM_G2P2_PPT) : 1);   // per chunk
     static constexpr int NBLK = CH / kPB;
     static constexpr int NCMAX = D + D * D + 8;
     static constexpr size_t win_bytes = (size_t)Geo<D>::WN * sizeof(R4<R>);
