@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "mpm_internal.cuh"
 
@@ -840,7 +841,10 @@ constexpr int kDirectOffPad = 132;
 #ifndef MPM_P2G2_STAGES
 #define MPM_P2G2_STAGES 3
 #endif
-template <int D> __host__ __device__ constexpr int direct_cells() { return D == 3 ? 128 : MPM_P2G2_CELLS; }
+#ifndef MPM_P2G3_CELLS
+#define MPM_P2G3_CELLS 128
+#endif
+template <int D> __host__ __device__ constexpr int direct_cells() { return D == 3 ? MPM_P2G3_CELLS : MPM_P2G2_CELLS; }
 template <int D> __host__ __device__ constexpr int direct_stages() { return D == 3 ? 2 : MPM_P2G2_STAGES; }
 template <class R, int D, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
 {
@@ -916,7 +920,7 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
         }
     };
     // cursors over this lane's cells cbase + lane + 32 r and their slots
-    struct Cur {
+    struct CurMulti {
         int c, q, q1, end;
         __device__ __forceinline__ bool next(const int32_t *o)
         {
@@ -930,7 +934,16 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
             return true;
         }
     };
-    Cur pc{cbase + lane - 32, 0, 0, cbase + CELLS}, cc = pc;
+    // one cell per lane (32-cell items): the cursor walks that cell's particles only
+    struct CurOne {
+        int c, q, q1;
+        __device__ __forceinline__ bool next(const int32_t *) { return ++q < q1; }
+    };
+    using Cur = std::conditional_t<CELLS == 32, CurOne, CurMulti>;
+    Cur pc;
+    if constexpr (CELLS == 32) pc = CurOne{cbase + lane, off[cbase + lane] - 1, off[cbase + lane + 1]};
+    else pc = CurMulti{cbase + lane - 32, 0, 0, cbase + CELLS};
+    Cur cc = pc;
     bool hp = pc.next(off);
 #pragma unroll
     for (int s0 = 0; s0 < ST; ++s0) {
@@ -1607,7 +1620,7 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 #define MPM_G2P_PPT 1
 #endif
 #ifndef MPM_G2P2_PPT
-#define MPM_G2P2_PPT 1
+#define MPM_G2P2_PPT 2
 #endif
 template <class R, int D> struct G2PSmem {
     static constexpr int NT = 256;
