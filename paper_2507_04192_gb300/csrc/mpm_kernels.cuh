@@ -831,10 +831,12 @@ template <int D, int MAT> __host__ __device__ constexpr int direct_stage_comps()
 // Per warp of k_p2g_direct: its work item's 129 cell offsets (padded to 132),
 // staged in shared memory at the start of the item.
 constexpr int kDirectOffPad = 132;
-// Cells per work item and cp.async stages per thread of the cell-ordered P2G.  In
-// 2D (16 particles per cell in the dense fluids) a lane walks long runs of one
-// cell's particles, so the pipeline is deeper and the items shorter (more of
-// them to balance the SMs).
+// Cells per work item and cp.async stages per thread of the cell-ordered P2G.
+// Items of 32 cells give each lane one cell (its cursor walks that cell's
+// particles only) and more items to balance the SMs: on the 2.76M-particle
+// collapse P2G 0.123 ms with 128-cell items (four cells per lane), 0.118 with 64,
+// 0.105 with 32; on the batched 2D dam breaks 0.167 -> 0.152 ms.  In 2D (16
+// particles per cell in the dense fluids) the pipeline is one stage deeper.
 #ifndef MPM_P2G2_CELLS
 #define MPM_P2G2_CELLS 32
 #endif
@@ -842,10 +844,13 @@ constexpr int kDirectOffPad = 132;
 #define MPM_P2G2_STAGES 3
 #endif
 #ifndef MPM_P2G3_CELLS
-#define MPM_P2G3_CELLS 128
+#define MPM_P2G3_CELLS 32
+#endif
+#ifndef MPM_P2G3_STAGES
+#define MPM_P2G3_STAGES 2
 #endif
 template <int D> __host__ __device__ constexpr int direct_cells() { return D == 3 ? MPM_P2G3_CELLS : MPM_P2G2_CELLS; }
-template <int D> __host__ __device__ constexpr int direct_stages() { return D == 3 ? 2 : MPM_P2G2_STAGES; }
+template <int D> __host__ __device__ constexpr int direct_stages() { return D == 3 ? MPM_P2G3_STAGES : MPM_P2G2_STAGES; }
 template <class R, int D, int NT, int MAT> __host__ __device__ constexpr size_t p2g_direct_smem()
 {
     return (size_t)direct_stages<D>() * direct_stage_comps<D, MAT>() * NT * sizeof(R) +
