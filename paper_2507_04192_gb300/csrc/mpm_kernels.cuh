@@ -963,23 +963,38 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
     if constexpr (D == 2) nb[2] = 0;
     unsigned reach = 0u;                          // node tiles (bit dz dy dx) this lane's cells reach
     CellSums<R, D> acc;
+    auto open_cell = [&](int c) {                 // a new cell: its base, first node, reach; zero sums
+        cur = c;
+        int r = cur;
+        unsigned hi = 0u;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int ci = r % Gm::T;
+            r /= Gm::T;
+            bown[a] = org[a] + ci - 1;         // base cell index of the cell's particles
+            nb[a] = org[a] + ci + 1;           // its first stencil node
+            hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
+        }
+#pragma unroll
+        for (int m = 0; m < (1 << D); ++m)
+            if ((m & ~hi & ((1u << D) - 1u)) == 0u) reach |= 1u << m;
+        acc.zero();
+    };
+    auto close_cell = [&]() {                     // the cell is done: its 3^D node sums to the grid
+        const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
+        R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];   // nb[2] = 0 in 2D
+#pragma unroll
+        for (int kk = 0; kk < Gm::STENCIL; ++kk) {
+            R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
+            if constexpr (ADJ) red_add4(node, acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2), R(0));   // (v_bar, 0)
+            else red_add4(node, acc.m(kk), acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2));          // (m, q)
+        }
+    };
+    constexpr bool ONE = CELLS == 32;             // one cell per lane: opened before, closed after the loop
+    if (ONE && hc) open_cell(cc.c);
     while (hc) {
-        if (cc.c != cur) {
-            cur = cc.c;
-            int r = cur;
-            unsigned hi = 0u;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const int ci = r % Gm::T;
-                r /= Gm::T;
-                bown[a] = org[a] + ci - 1;         // base cell index of the cell's particles
-                nb[a] = org[a] + ci + 1;           // its first stencil node
-                hi |= (ci + 3 >= Gm::T ? 1u : 0u) << a;
-            }
-#pragma unroll
-            for (int m = 0; m < (1 << D); ++m)
-                if ((m & ~hi & ((1u << D) - 1u)) == 0u) reach |= 1u << m;
-            acc.zero();
+        if constexpr (!ONE) {
+            if (cc.c != cur) open_cell(cc.c);
         }
         cp_async_wait<ST - 1>();
         P2GFactors<R, D> f;
@@ -1013,17 +1028,11 @@ __device__ __forceinline__ void p2g_direct_item(const Params<R> &P, const P2GIO<
         }
         stage = stage + 1 == ST ? 0 : stage + 1;
         hc = cc.next(off);
-        if (!hc || cc.c != cur) {                  // the cell is done: its 3^D node sums to the grid
-            const int sx = P.G_nodes[0], sxy = P.G_nodes[0] * P.G_nodes[1];
-            R4<R> *base = Asim + ((int64_t)nb[2] * P.G_nodes[1] + nb[1]) * sx + nb[0];   // nb[2] = 0 in 2D
-#pragma unroll
-            for (int kk = 0; kk < Gm::STENCIL; ++kk) {
-                R4<R> *node = base + (kk % 3) + ((kk / 3) % 3) * sx + (kk / 9) * sxy;
-                if constexpr (ADJ) red_add4(node, acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2), R(0));   // (v_bar, 0)
-                else red_add4(node, acc.m(kk), acc.q(kk, 0), acc.q(kk, 1), acc.q(kk, 2));          // (m, q)
-            }
+        if constexpr (!ONE) {
+            if (!hc || cc.c != cur) close_cell();
         }
     }
+    if (ONE && cur >= 0) close_cell();
     cp_async_wait<0>();
     if constexpr (!ADJ) {                          // node tiles reached by the warp's cells
         const unsigned wreach = __reduce_or_sync(0xffffffffu, reach);
