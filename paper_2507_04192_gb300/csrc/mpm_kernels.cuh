@@ -1629,9 +1629,11 @@ __device__ __forceinline__ bool g2p_particle(const Params<R> &P, Raw raw, R *__r
 
 // Shared-memory layout of the G2P block: the grid window, then two staging
 // buffers of NT / kPB particle blocks (the components G2P reads).
-// Particles per thread in one staged chunk of the G2P block.
+// Particles per thread in one staged chunk of the G2P block (3D, 2D): chunks of 512
+// particles halve the block barriers per particle (3D dam break G2P 0.071 -> 0.067
+// ms, 2D batched 0.080 -> 0.074 ms; the 2.76M-particle collapse 0.118 -> 0.116).
 #ifndef MPM_G2P_PPT
-#define MPM_G2P_PPT 1
+#define MPM_G2P_PPT 2
 #endif
 #ifndef MPM_G2P2_PPT
 #define MPM_G2P2_PPT 2
