@@ -151,6 +151,18 @@ int mpm_load_particles(mpm_ctx *ctx, int64_t n, const double *x, const double *v
                        double particle_volume, const int32_t *sim_id);
 
 /*
+ * mpm_load_particles from device memory: x_dev (n x dim doubles), v_dev (n x dim
+ * doubles or NULL) and sim_id_dev (n int32 or NULL) are device pointers the
+ * caller owns (e.g. the data_ptr() of CUDA tensors); they are read on the
+ * context's stream, so work the caller queued on that stream before the call
+ * is ordered before the read, and the call returns after the copy (they may be
+ * freed then).  The same checks as mpm_load_particles, made on the device, with
+ * the same statuses.
+ */
+int mpm_load_particles_dev(mpm_ctx *ctx, int64_t n, const double *x_dev, const double *v_dev,
+                           double particle_volume, const int32_t *sim_id_dev);
+
+/*
  * Overwrite one particle field from a host array in load order, with
  * mpm_field_width() values per particle (the caller keeps ownership; it is
  * copied before the call returns).  Returns MPM_EINVAL for a NULL array, an
@@ -255,6 +267,14 @@ int mpm_synchronize(mpm_ctx *ctx);
  * unknown field, MPM_ESTATE before any particles are loaded, and any status the
  * queued steps recorded (MPM_ENAN, MPM_ETIMEOUT). */
 int mpm_get_particles(mpm_ctx *ctx, int field, double *out);
+
+/* mpm_get_particles into device memory: out_dev (n x the field's width doubles,
+ * load order) is a device pointer the caller owns; the copy is queued on the
+ * context's stream and the call returns without waiting (later work on that
+ * stream sees the values).  MPM_EINVAL for a NULL pointer or an unknown field,
+ * MPM_ESTATE before any particles are loaded; statuses the queued steps record
+ * are reported by the next synchronising call. */
+int mpm_get_particles_dev(mpm_ctx *ctx, int field, double *out_dev);
 
 /* Number of doubles per particle of a field (or a negative status). */
 int mpm_field_width(const mpm_ctx *ctx, int field);

@@ -334,6 +334,125 @@ int make_tensor_map_V(mpm_ctx *c)
 
 }  // namespace
 
+namespace {
+
+// Positions outside [0, L] or not finite and simulation ids outside [0, batch):
+// counted on the device for the device-pointer load.
+__global__ void k_check_load(int64_t n, int d, const double *__restrict__ x, const int32_t *__restrict__ sim,
+                             int batch, double L0, double L1, double L2, int32_t *__restrict__ bad)
+{
+    const double L[3] = {L0, L1, L2};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = true;
+        for (int a = 0; a < d; ++a) {
+            const double xa = x[p * d + a];
+            ok = ok && (xa >= 0.0 && xa <= L[a]);
+        }
+        if (!ok) atomicOr(bad, 1);
+        if (sim != nullptr && (sim[p] < 0 || sim[p] >= batch)) atomicOr(bad, 2);
+    }
+}
+
+// mpm_load_particles and mpm_load_particles_dev: x, v, sim_id in host memory, or
+// (device) in device memory read on the context's stream.
+int load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, double particle_volume,
+                   const int32_t *sim_id, bool device)
+{
+    const char *who = device ? "mpm_load_particles_dev" : "mpm_load_particles";
+    if (!c || n <= 0 || !x || !(particle_volume > 0)) return fail(c, MPM_EINVAL, std::string(who) + ": bad argument");
+    if (n > (int64_t)1 << 30) return fail(c, MPM_EINVAL, std::string(who) + ": too many particles");
+    const int d = c->grid.dim;
+    DevState &ds = c->ds;
+    HostParams &h = c->hp;
+    if (device) {                                  // the same checks, on the device
+        int32_t *bad = nullptr;
+        int rc = dalloc(c, &bad, 1, "load check");
+        if (rc != MPM_OK) return rc;
+        int32_t hbad = 0;
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), ds.stream);
+        if (e == cudaSuccess) {
+            const int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ds.num_sms * 8);
+            k_check_load<<<nb, 256, 0, ds.stream>>>(n, d, x, sim_id, c->grid.batch, h.n_cells[0] * h.dx,
+                                                    h.n_cells[1] * h.dx, d == 3 ? h.n_cells[2] * h.dx : 0.0, bad);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ds.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ds.stream);
+        dfree(bad);
+        if (e != cudaSuccess) return cuda_fail(c, e, "mpm_load_particles_dev: check");
+        if (hbad & 1)
+            return fail(c, MPM_EINVAL, "mpm_load_particles_dev: position outside the domain or not finite");
+        if (hbad & 2) return fail(c, MPM_EINVAL, "mpm_load_particles_dev: simulation id out of range");
+    } else {
+        for (int64_t p = 0; p < n; ++p)
+            for (int a = 0; a < d; ++a) {
+                const double xa = x[p * d + a];
+                if (!(xa >= 0.0 && xa <= c->hp.n_cells[a] * c->hp.dx))
+                    return fail(c, MPM_EINVAL, "mpm_load_particles: position outside the domain or not finite");
+            }
+        if (sim_id)
+            for (int64_t p = 0; p < n; ++p)
+                if (sim_id[p] < 0 || sim_id[p] >= c->grid.batch)
+                    return fail(c, MPM_EINVAL, "mpm_load_particles: simulation id out of range");
+    }
+    CK(cudaStreamSynchronize(ds.stream), "synchronize before load");
+    free_particles(c);
+    h.n = n;
+    h.npad = (n + 63) / 64 * 64;                  // whole blocks of kPB particles
+    h.vol0 = particle_volume;
+    h.mass = h.rho0 * particle_volume;
+    const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
+    const int nblk = (int)((n + kSortChunk - 1) / kSortChunk);
+    {
+        const int64_t all_tiles = (int64_t)c->grid.batch * h.tiles_per_sim;
+        ds.max_tiles = all_tiles < n ? all_tiles : n;
+    }
+    const int TN = c->grid.dim == 2 ? Geo<2>::TN : Geo<3>::TN;
+    int rc = MPM_OK;
+    // 64 elements of slack: bulk copies of the last component may read up to 7 past npad
+    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state");
+    if (rc == MPM_OK)
+        rc = dalloc(c, (unsigned char **)&ds.S2, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.id, n, "ids");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.id2, n, "ids (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.sim, n, "sim ids");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.sim2, n, "sim ids (sort)");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[0], n, "keys");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[1], n, "keys");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk + kScanSegments, "histogram");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, 2 * ds.max_tiles, "tile list");     // key order + G2P order
+    if (rc == MPM_OK) rc = dalloc(c, &ds.perm, n, "permutation");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.posmap, n, "position map");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.cell_off, (size_t)ds.max_tiles * (TN + 1), "cell offsets");
+    if (rc == MPM_OK) rc = dalloc(c, &ds.staging, (size_t)n * 9, "staging");
+    if (rc != MPM_OK) {
+        free_particles(c);
+        return rc;
+    }
+    const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ds.staging, x, sizeof(double) * n * d, kind, ds.stream), "copy x");
+    double *vdev = nullptr;
+    if (v) {
+        vdev = ds.staging + (size_t)n * d;
+        CK(cudaMemcpyAsync(vdev, v, sizeof(double) * n * d, kind, ds.stream), "copy v");
+    }
+    if (sim_id) {
+        CK(cudaMemcpyAsync(ds.sim, sim_id, sizeof(int32_t) * n, kind, ds.stream), "copy sim ids");
+    } else {
+        CK(cudaMemsetAsync(ds.sim, 0, sizeof(int32_t) * n, ds.stream), "zero sim ids");
+    }
+    c->ops->init_state(h, ds, ds.staging, vdev);
+    c->launches++;
+    CK(cudaGetLastError(), "init state");
+    CK(cudaStreamSynchronize(ds.stream), "load particles");
+    c->need_sort = true;
+    return MPM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream, mpm_ctx **out)
@@ -510,74 +629,13 @@ void mpm_destroy(mpm_ctx *c)
 int mpm_load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, double particle_volume,
                        const int32_t *sim_id)
 {
-    if (!c || n <= 0 || !x || !(particle_volume > 0)) return fail(c, MPM_EINVAL, "mpm_load_particles: bad argument");
-    if (n > (int64_t)1 << 30) return fail(c, MPM_EINVAL, "mpm_load_particles: too many particles");
-    const int d = c->grid.dim;
-    for (int64_t p = 0; p < n; ++p)
-        for (int a = 0; a < d; ++a) {
-            const double xa = x[p * d + a];
-            if (!(xa >= 0.0 && xa <= c->hp.n_cells[a] * c->hp.dx))
-                return fail(c, MPM_EINVAL, "mpm_load_particles: position outside the domain or not finite");
-        }
-    if (sim_id)
-        for (int64_t p = 0; p < n; ++p)
-            if (sim_id[p] < 0 || sim_id[p] >= c->grid.batch)
-                return fail(c, MPM_EINVAL, "mpm_load_particles: simulation id out of range");
-    DevState &ds = c->ds;
-    HostParams &h = c->hp;
-    CK(cudaStreamSynchronize(ds.stream), "synchronize before load");
-    free_particles(c);
-    h.n = n;
-    h.npad = (n + 63) / 64 * 64;                  // whole blocks of kPB particles
-    h.vol0 = particle_volume;
-    h.mass = h.rho0 * particle_volume;
-    const size_t rsz = c->grid.precision == MPM_FP64 ? 8 : 4;
-    const int nblk = (int)((n + kSortChunk - 1) / kSortChunk);
-    {
-        const int64_t all_tiles = (int64_t)c->grid.batch * h.tiles_per_sim;
-        ds.max_tiles = all_tiles < n ? all_tiles : n;
-    }
-    const int TN = c->grid.dim == 2 ? Geo<2>::TN : Geo<3>::TN;
-    int rc = MPM_OK;
-    // 64 elements of slack: bulk copies of the last component may read up to 7 past npad
-    if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&ds.S, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state");
-    if (rc == MPM_OK)
-        rc = dalloc(c, (unsigned char **)&ds.S2, ((size_t)h.ncomp * h.npad + 64) * rsz, "particle state (sort)");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.id, n, "ids");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.id2, n, "ids (sort)");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.sim, n, "sim ids");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.sim2, n, "sim ids (sort)");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[0], n, "keys");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.keys[1], n, "keys");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[0], n, "values");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.vals[1], n, "values");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.hist, (size_t)kRadixBins * nblk + kScanSegments, "histogram");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.tiles, 2 * ds.max_tiles, "tile list");     // key order + G2P order
-    if (rc == MPM_OK) rc = dalloc(c, &ds.perm, n, "permutation");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.posmap, n, "position map");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.cell_off, (size_t)ds.max_tiles * (TN + 1), "cell offsets");
-    if (rc == MPM_OK) rc = dalloc(c, &ds.staging, (size_t)n * 9, "staging");
-    if (rc != MPM_OK) {
-        free_particles(c);
-        return rc;
-    }
-    CK(cudaMemcpyAsync(ds.staging, x, sizeof(double) * n * d, cudaMemcpyHostToDevice, ds.stream), "copy x");
-    double *vdev = nullptr;
-    if (v) {
-        vdev = ds.staging + (size_t)n * d;
-        CK(cudaMemcpyAsync(vdev, v, sizeof(double) * n * d, cudaMemcpyHostToDevice, ds.stream), "copy v");
-    }
-    if (sim_id) {
-        CK(cudaMemcpyAsync(ds.sim, sim_id, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ds.stream), "copy sim ids");
-    } else {
-        CK(cudaMemsetAsync(ds.sim, 0, sizeof(int32_t) * n, ds.stream), "zero sim ids");
-    }
-    c->ops->init_state(h, ds, ds.staging, vdev);
-    c->launches++;
-    CK(cudaGetLastError(), "init state");
-    CK(cudaStreamSynchronize(ds.stream), "load particles");
-    c->need_sort = true;
-    return MPM_OK;
+    return load_particles(c, n, x, v, particle_volume, sim_id, false);
+}
+
+int mpm_load_particles_dev(mpm_ctx *c, int64_t n, const double *x_dev, const double *v_dev, double particle_volume,
+                           const int32_t *sim_id_dev)
+{
+    return load_particles(c, n, x_dev, v_dev, particle_volume, sim_id_dev, true);
 }
 
 int mpm_set_particle_field(mpm_ctx *c, int field, const double *values)
@@ -777,6 +835,17 @@ int mpm_get_particles(mpm_ctx *c, int field, double *out)
     CK(cudaMemcpyAsync(out, ds.staging, sizeof(double) * c->hp.n * wdt, cudaMemcpyDeviceToHost, ds.stream),
        "copy field to host");
     return read_status(c);
+}
+
+int mpm_get_particles_dev(mpm_ctx *c, int field, double *out_dev)
+{
+    if (!c || !out_dev) return fail(c, MPM_EINVAL, "mpm_get_particles_dev: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_get_particles_dev: no particles loaded");
+    if (field_width(c, field) < 0) return fail(c, MPM_EINVAL, "mpm_get_particles_dev: unknown field");
+    c->ops->get_field(c->hp, c->ds, field, out_dev);      // written on the context's stream, no wait
+    c->launches++;
+    CK(cudaGetLastError(), "get field");
+    return MPM_OK;
 }
 
 int mpm_field_width(const mpm_ctx *c, int field)

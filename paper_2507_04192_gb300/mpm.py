@@ -75,6 +75,7 @@ def load_library(build_if_missing: bool = True):
             "mpm_create": (I, [C.POINTER(GridDesc), C.POINTER(Material), P, C.POINTER(P)]),
             "mpm_destroy": (None, [P]),
             "mpm_load_particles": (I, [P, L, P, P, D, P]),
+            "mpm_load_particles_dev": (I, [P, L, P, P, D, P]),
             "mpm_set_particle_field": (I, [P, I, P]),
             "mpm_set_friction_field": (I, [P, I, P, P]),
             "mpm_set_obstacles": (I, [P, I, P]),
@@ -89,6 +90,7 @@ def load_library(build_if_missing: bool = True):
             "mpm_set_debug": (I, [P, I]),
             "mpm_synchronize": (I, [P]),
             "mpm_get_particles": (I, [P, I, P]),
+            "mpm_get_particles_dev": (I, [P, I, P]),
             "mpm_field_width": (I, [P, I]),
             "mpm_num_particles": (L, [P]),
             "mpm_last_error": (I, [P, C.c_char_p, I]),
@@ -159,6 +161,16 @@ def mpm_load_particles(ctx, x: np.ndarray, v: Optional[np.ndarray], particle_vol
                                                   float(particle_volume), None if sid is None else _dptr(sid)))
 
 
+def mpm_load_particles_dev(ctx, n: int, x_ptr: int, v_ptr: Optional[int], particle_volume: float,
+                           sim_id_ptr: Optional[int] = None):
+    """mpm_load_particles from device pointers (e.g. tensor.data_ptr() of float64 and
+    int32 CUDA tensors) read on the context's stream."""
+    _check(ctx, load_library().mpm_load_particles_dev(ctx, int(n), C.c_void_p(x_ptr),
+                                                      None if v_ptr is None else C.c_void_p(v_ptr),
+                                                      float(particle_volume),
+                                                      None if sim_id_ptr is None else C.c_void_p(sim_id_ptr)))
+
+
 def mpm_set_particle_field(ctx, field: str, values: np.ndarray):
     a = np.ascontiguousarray(values, dtype=np.float64)
     _check(ctx, load_library().mpm_set_particle_field(ctx, FIELDS[field], _dptr(a)))
@@ -225,6 +237,12 @@ def mpm_get_particles(ctx, field: str, out: Optional[np.ndarray] = None) -> np.n
     assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.size == n * w
     _check(ctx, load_library().mpm_get_particles(ctx, FIELDS[field], _dptr(out)))
     return out
+
+
+def mpm_get_particles_dev(ctx, field: str, out_ptr: int):
+    """mpm_get_particles into a device pointer (n x width float64, load order),
+    queued on the context's stream without waiting."""
+    _check(ctx, load_library().mpm_get_particles_dev(ctx, FIELDS[field], C.c_void_p(out_ptr)))
 
 
 def mpm_set_timing(ctx, enable: bool):
