@@ -357,6 +357,31 @@ int mpm_step_adjoint(mpm_ctx *ctx, int n_steps, int checkpoint_every, int wall, 
                      double *dL_dmu_out);
 
 /*
+ * One step and its vector-Jacobian product (Eq. dzda for a single step, Sec.
+ * 3.1): from the current state S^t, runs the step to S^{t+1} (the context is
+ * left there) and, given lam_next = dL/dS^{t+1}, writes lam_prev = dL/dS^t and,
+ * for wall >= 0, this step's d<lam_next, S^{t+1}>/dmu of the wall's friction
+ * field (n_seg[0] x n_seg[1] doubles; wall = -1: none, dL_dmu_out may be NULL).
+ * A caller chains it backwards over stored states (mpm_save_state before each
+ * forward step, mpm_restore_state before each call), adding the gradient of
+ * its loss at each observed state to lam between calls: the per-step form of
+ * mpm_step_adjoint, for an autograd function of one step.  Adjoint layout (host
+ * memory, load order, doubles): per particle mpm_adjoint_width() values, the
+ * adjoints of x (dim), v (dim), C (dim^2, row-major), rho (1) and, for
+ * Drucker-Prager, sigma (6: xx yy zz xy xz yz); the zone and contact branches
+ * of the step are held fixed, as in mpm_step_adjoint.  APIC transfer, batch 1.
+ * MPM_EINVAL for a NULL array (or NULL dL_dmu_out with wall >= 0), a batch
+ * other than 1, a transfer other than APIC, a wall without a friction field;
+ * MPM_ESTATE before any particles are loaded; MPM_ENOMEM; and any status the
+ * step recorded.  Synchronises.
+ */
+int mpm_step_adjoint_1(mpm_ctx *ctx, int wall, const double *lam_next, double *lam_prev, double *dL_dmu_out);
+
+/* Adjoint values per particle of mpm_step_adjoint_1 (2 dim + dim^2 + 1, + 6 for
+ * Drucker-Prager), or a negative status. */
+int mpm_adjoint_width(const mpm_ctx *ctx);
+
+/*
  * Device memory (bytes) mpm_step_adjoint may use, beyond what one segment of
  * checkpoint_every states needs, to keep more segments of the first forward
  * pass: the last 1 + bytes / (one segment's size) segments are then reversed

@@ -455,6 +455,15 @@ __global__ void k_adj_gather(int64_t n, int w, int off, const int32_t *__restric
         for (int k = 0; k < w; ++k) out[(int64_t)id[i] * w + k] = (double)lam[(int64_t)(off + k) * n + i];
 }
 
+// The inverse: an adjoint state from a load-order array, lam[(off + k) n + s] = in[id[s] w + k].
+template <class R>
+__global__ void k_adj_scatter_in(int64_t n, int w, int off, const int32_t *__restrict__ id,
+                                 const double *__restrict__ in, R *__restrict__ lam)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < w; ++k) lam[(int64_t)(off + k) * n + i] = (R)in[(int64_t)id[i] * w + k];
+}
+
 template <class R>
 __global__ void k_adj_zero(R *__restrict__ p, int64_t count)
 {
@@ -1427,6 +1436,11 @@ template <class R, int D> struct AdjLaunch {
     {
         k_adj_gather<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, w, off, id, (const R *)lam, out);
     }
+    static void scatter_in(const HostParams &h, DevState &ds, int w, int off, const int32_t *id, const double *in,
+                           void *lam)
+    {
+        k_adj_scatter_in<R><<<pblocks(h, ds), 256, 0, ds.stream>>>(h.n, w, off, id, in, (R *)lam);
+    }
     static void zero(DevState &ds, void *p, int64_t count)
     {
         k_adj_zero<R><<<grid_blocks(count, 256, ds.num_sms, 8), 256, 0, ds.stream>>>((R *)p, count);
@@ -1503,6 +1517,8 @@ template <class R> struct AdjDispatch {
                      monitor_seed(h, ds, x, ld, nm, b, g, lam))
     MPM_ADJ_DISPATCH(gather, (const HostParams &h, DevState &ds, int w, int off, const int32_t *id, const void *lam,
                               double *out), gather(h, ds, w, off, id, lam, out))
+    MPM_ADJ_DISPATCH(scatter_in, (const HostParams &h, DevState &ds, int w, int off, const int32_t *id,
+                                  const double *in, void *lam), scatter_in(h, ds, w, off, id, in, lam))
 #undef MPM_ADJ_DISPATCH
     static void zero(const HostParams &, DevState &ds, void *p, int64_t count) { AdjLaunch<R, 2>::zero(ds, p, count); }
 };

@@ -453,6 +453,79 @@ int load_particles(mpm_ctx *c, int64_t n, const double *x, const double *v, doub
 
 }  // namespace
 
+namespace {
+
+// The adjoint's device buffers, (re)allocated when too small: n_ckpt checkpoints,
+// KS kept states with their grids and orders, gens generations of sort tables
+// (3D single precision), the two adjoint states and grids, the final state.
+int adj_buffers(mpm_ctx *c, int64_t n_ckpt, int64_t KS, int gens)
+{
+    AdjHost &a = c->adj;
+    const HostParams &h = c->hp;
+    DevState &ds = c->ds;
+    const int NA = adj_ncomp_material(h.dim, c->mat.kind == MPM_DRUCKER_PRAGER ? 1 : 0);
+    const size_t rsz = h.precision == MPM_FP64 ? 8 : 4;
+    const int64_t n = h.n;
+    const size_t st_bytes = (size_t)NA * n * rsz;
+    const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+    const size_t fbytes = ((size_t)(h.node_tiles_per_sim + 1) * sizeof(int32_t) + 255) / 256 * 256;
+    const bool split = h.dim == 3 && h.precision == MPM_FP32;
+    const int64_t TNc = 512 + 1;
+    if (a.ckpt_cap < n_ckpt) {
+        dfree(a.ckpt);
+        int rc = dalloc(c, (unsigned char **)&a.ckpt, st_bytes * n_ckpt, "checkpoints");
+        if (rc != MPM_OK) return rc;
+        a.ckpt_cap = n_ckpt;
+    }
+    if (a.seg_cap < KS) {
+        dfree(a.seg);
+        dfree(a.seg_id);
+        int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * KS, "segment states");
+        if (rc == MPM_OK) rc = dalloc(c, &a.seg_id, (size_t)n * KS, "segment orders");
+        if (rc != MPM_OK) return rc;
+        a.seg_cap = KS;
+    }
+    if (a.seg_grid_cap < KS) {
+        dfree(a.seg_grid);
+        int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * KS, "segment grids");
+        if (rc != MPM_OK) return rc;
+        // nodes a step does not touch keep finite values from earlier steps (never read)
+        CK(cudaMemsetAsync(a.seg_grid, 0, (2 * gbytes + fbytes) * KS, ds.stream), "zero segment grids");
+        a.seg_grid_cap = KS;
+    }
+    if (split && a.gen_cap < gens) {
+        dfree(a.coef); dfree(a.gen_tiles); dfree(a.gen_ntiles); dfree(a.gen_posmap); dfree(a.gen_celloff);
+        int rc = dalloc(c, (unsigned char **)&a.coef, (size_t)21 * n * rsz, "scatter coefficients");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_tiles, (size_t)gens * ds.max_tiles, "generation tiles");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_ntiles, (size_t)gens, "generation tile counts");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_posmap, (size_t)gens * n, "generation position maps");
+        if (rc == MPM_OK) rc = dalloc(c, &a.gen_celloff, (size_t)gens * ds.max_tiles * TNc, "generation offsets");
+        if (rc != MPM_OK) return rc;
+        a.gen_cap = gens;
+    }
+    if (!a.allocated) {
+        // a failed earlier attempt may have left some of these allocated
+        dfree(a.lam[0]); dfree(a.lam[1]); dfree(a.grid.GVB); dfree(a.grid.GAB);
+        dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim); dfree(a.lam_id); dfree(a.lam_pos);
+        int rc = MPM_OK;
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[0], st_bytes, "adjoint state");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[1], st_bytes, "adjoint state");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GVB, gbytes, "adjoint grid");
+        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GAB, gbytes, "adjoint grid");
+        if (rc == MPM_OK)
+            rc = dalloc(c, (unsigned char **)&a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, "final state");
+        if (rc == MPM_OK) rc = dalloc(c, &a.final_id, n, "final ids");
+        if (rc == MPM_OK) rc = dalloc(c, &a.final_sim, n, "final sims");
+        if (rc == MPM_OK) rc = dalloc(c, &a.lam_id, n, "adjoint order");
+        if (rc == MPM_OK) rc = dalloc(c, &a.lam_pos, n, "adjoint order");
+        if (rc != MPM_OK) return rc;
+        a.allocated = true;
+    }
+    return MPM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mpm_create(const mpm_grid_desc *grid, const mpm_material *material, void *cuda_stream, mpm_ctx **out)
@@ -1023,6 +1096,110 @@ int mpm_set_adjoint_memory(mpm_ctx *c, int64_t bytes)
     return MPM_OK;
 }
 
+int mpm_adjoint_width(const mpm_ctx *c)
+{
+    if (!c) return MPM_EINVAL;
+    return adj_ncomp_material(c->grid.dim, c->mat.kind == MPM_DRUCKER_PRAGER ? 1 : 0);
+}
+
+int mpm_step_adjoint_1(mpm_ctx *c, int wall, const double *lam_next, double *lam_prev, double *dL_dmu_out)
+{
+    if (!c || !lam_next || !lam_prev || (wall >= 0 && !dL_dmu_out))
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint_1: bad argument");
+    if (c->hp.n == 0) return fail(c, MPM_ESTATE, "mpm_step_adjoint_1: no particles loaded");
+    if (c->grid.batch != 1) return fail(c, MPM_EINVAL, "mpm_step_adjoint_1: batch must be 1");
+    if (c->grid.transfer != MPM_TRANSFER_APIC)
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint_1: the adjoint follows the APIC transfer");
+    if (wall < -1 || wall >= 2 * c->grid.dim || (wall >= 0 && c->ds.mu_dev[wall] == nullptr))
+        return fail(c, MPM_EINVAL, "mpm_step_adjoint_1: the wall has no friction field");
+    AdjHost &a = c->adj;
+    a.lam0 = -1;
+    const HostParams &h = c->hp;
+    DevState &ds = c->ds;
+    const int d = h.dim;
+    const int NA = adj_ncomp_material(d, c->mat.kind == MPM_DRUCKER_PRAGER ? 1 : 0);
+    const size_t rsz = h.precision == MPM_FP64 ? 8 : 4;
+    const int64_t n = h.n;
+    const size_t gbytes = (size_t)h.nodes_per_sim * 4 * rsz;
+    const bool split = d == 3 && h.precision == MPM_FP32;
+    const int64_t TNc = 512 + 1;
+    // one kept state with its grids and, for the cell-ordered v_bar scatter, one
+    // generation of sort tables (the buffers of mpm_step_adjoint, at least one slot)
+    int rc = adj_buffers(c, 0, 1, split ? 1 : 0);
+    if (rc != MPM_OK) return rc;
+    MuBar mub{};
+    if (wall >= 0) {
+        const int64_t cnt = (int64_t)ds.n_seg[wall][0] * ds.n_seg[wall][1];
+        if (a.d_mubar[wall] == nullptr) {
+            rc = dalloc(c, &a.d_mubar[wall], cnt, "dL/dmu");
+            if (rc != MPM_OK) return rc;
+        }
+        CK(cudaMemsetAsync(a.d_mubar[wall], 0, sizeof(double) * cnt, ds.stream), "zero dL/dmu");
+        mub.w[wall] = a.d_mubar[wall];
+    }
+    double *io = nullptr;                          // lam_next in, lam_prev out (load order, doubles)
+    rc = dalloc(c, &io, (size_t)n * NA, "adjoint transfer");
+    if (rc != MPM_OK) return rc;
+    auto done = [&](int r) {
+        dfree(io);
+        return r;
+    };
+    // the step S^t -> S^{t+1}, keeping S^t, its grids and its sort tables
+    if (c->need_sort || c->steps_since_sort >= c->grid.sort_every) {
+        rc = do_sort(c);
+        if (rc != MPM_OK) return done(rc);
+    }
+    int32_t *order = a.seg_id;                     // the order of S^t (and of S^{t+1})
+    cudaError_t e = cudaMemcpyAsync(order, ds.id, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream);
+    AdjDev ad = a.grid;
+    if (e == cudaSuccess && split) {
+        e = cudaMemcpyAsync(a.gen_tiles, ds.tiles, sizeof(int4) * ds.max_tiles, cudaMemcpyDeviceToDevice, ds.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(a.gen_ntiles, ds.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, ds.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(a.gen_posmap, ds.posmap, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ds.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(a.gen_celloff, ds.cell_off, sizeof(int32_t) * ds.max_tiles * TNc,
+                                cudaMemcpyDeviceToDevice, ds.stream);
+        ad.coef = a.coef;
+        ad.cursor = ds.counters + 5;
+        ad.tiles = a.gen_tiles;
+        ad.n_tiles = a.gen_ntiles;
+        ad.posmap = a.gen_posmap;
+        ad.cell_off = a.gen_celloff;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.grid.GVB, 0, gbytes, ds.stream);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "mpm_step_adjoint_1: keep"));
+    void *st = a.seg;
+    void *GA = a.seg_grid, *GV = (char *)a.seg_grid + gbytes;
+    int32_t *GL = (int32_t *)((char *)a.seg_grid + 2 * gbytes);
+    ds.save_S = st;
+    ds.save_A = GA;
+    ds.save_V = GV;
+    ds.save_L = GL;
+    rc = step_many(c, 1);
+    ds.save_S = ds.save_A = ds.save_V = nullptr;
+    ds.save_L = nullptr;
+    if (rc != MPM_OK) return done(rc);
+    // the reverse step: lam_next in the particle order of S^{t+1}, to lam_prev
+    e = cudaMemcpyAsync(io, lam_next, sizeof(double) * n * NA, cudaMemcpyHostToDevice, ds.stream);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "mpm_step_adjoint_1: copy lam_next"));
+    c->aops->scatter_in(h, ds, NA, 0, order, io, a.lam[0]);
+    {
+        TimingScope ts(c, MPM_KERNEL_REVERSE);
+        c->aops->step(h, ds, ad, st, GA, GV, GL, a.lam[0], a.lam[1], mub);
+    }
+    c->aops->gather(h, ds, NA, 0, order, a.lam[1], io);
+    rc = check_launch(c, "mpm_step_adjoint_1");
+    if (rc != MPM_OK) return done(rc);
+    e = cudaMemcpyAsync(lam_prev, io, sizeof(double) * n * NA, cudaMemcpyDeviceToHost, ds.stream);
+    if (e == cudaSuccess && wall >= 0)
+        e = cudaMemcpyAsync(dL_dmu_out, a.d_mubar[wall],
+                            sizeof(double) * ds.n_seg[wall][0] * ds.n_seg[wall][1], cudaMemcpyDeviceToHost, ds.stream);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "mpm_step_adjoint_1: copy out"));
+    return done(read_status(c));
+}
+
 int mpm_get_initial_adjoint(mpm_ctx *c, int field, double *out)
 {
     if (!c || !out) return fail(c, MPM_EINVAL, "mpm_get_initial_adjoint: bad argument");
@@ -1092,56 +1269,9 @@ int mpm_step_adjoint(mpm_ctx *c, int n_steps, int checkpoint_every, int wall, do
     const int64_t banks = overlap ? 2 : m_keep;
     const int64_t KS = banks * K;                  // kept-state slots
     const int gens = split ? (int)(banks * gens_seg) : 0;
-    // buffers
-    if (a.ckpt_cap < n_ckpt) {
-        dfree(a.ckpt);
-        int rc = dalloc(c, (unsigned char **)&a.ckpt, st_bytes * n_ckpt, "checkpoints");
+    {
+        int rc = adj_buffers(c, n_ckpt, KS, gens);
         if (rc != MPM_OK) return rc;
-        a.ckpt_cap = n_ckpt;
-    }
-    if (a.seg_cap < KS) {
-        dfree(a.seg);
-        dfree(a.seg_id);
-        int rc = dalloc(c, (unsigned char **)&a.seg, st_bytes * KS, "segment states");
-        if (rc == MPM_OK) rc = dalloc(c, &a.seg_id, (size_t)n * KS, "segment orders");
-        if (rc != MPM_OK) return rc;
-        a.seg_cap = KS;
-    }
-    if (a.seg_grid_cap < KS) {
-        dfree(a.seg_grid);
-        int rc = dalloc(c, (unsigned char **)&a.seg_grid, (2 * gbytes + fbytes) * KS, "segment grids");
-        if (rc != MPM_OK) return rc;
-        // nodes a step does not touch keep finite values from earlier steps (never read)
-        CK(cudaMemsetAsync(a.seg_grid, 0, (2 * gbytes + fbytes) * KS, ds.stream), "zero segment grids");
-        a.seg_grid_cap = KS;
-    }
-    if (split && a.gen_cap < gens) {
-        dfree(a.coef); dfree(a.gen_tiles); dfree(a.gen_ntiles); dfree(a.gen_posmap); dfree(a.gen_celloff);
-        int rc = dalloc(c, (unsigned char **)&a.coef, (size_t)21 * n * rsz, "scatter coefficients");
-        if (rc == MPM_OK) rc = dalloc(c, &a.gen_tiles, (size_t)gens * ds.max_tiles, "generation tiles");
-        if (rc == MPM_OK) rc = dalloc(c, &a.gen_ntiles, (size_t)gens, "generation tile counts");
-        if (rc == MPM_OK) rc = dalloc(c, &a.gen_posmap, (size_t)gens * n, "generation position maps");
-        if (rc == MPM_OK) rc = dalloc(c, &a.gen_celloff, (size_t)gens * ds.max_tiles * TNc, "generation offsets");
-        if (rc != MPM_OK) return rc;
-        a.gen_cap = gens;
-    }
-    if (!a.allocated) {
-        // a failed earlier attempt may have left some of these allocated
-        dfree(a.lam[0]); dfree(a.lam[1]); dfree(a.grid.GVB); dfree(a.grid.GAB);
-        dfree(a.final_S); dfree(a.final_id); dfree(a.final_sim); dfree(a.lam_id); dfree(a.lam_pos);
-        int rc = MPM_OK;
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[0], st_bytes, "adjoint state");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.lam[1], st_bytes, "adjoint state");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GVB, gbytes, "adjoint grid");
-        if (rc == MPM_OK) rc = dalloc(c, (unsigned char **)&a.grid.GAB, gbytes, "adjoint grid");
-        if (rc == MPM_OK)
-            rc = dalloc(c, (unsigned char **)&a.final_S, ((size_t)h.ncomp * h.npad + 64) * rsz, "final state");
-        if (rc == MPM_OK) rc = dalloc(c, &a.final_id, n, "final ids");
-        if (rc == MPM_OK) rc = dalloc(c, &a.final_sim, n, "final sims");
-        if (rc == MPM_OK) rc = dalloc(c, &a.lam_id, n, "adjoint order");
-        if (rc == MPM_OK) rc = dalloc(c, &a.lam_pos, n, "adjoint order");
-        if (rc != MPM_OK) return rc;
-        a.allocated = true;
     }
     MuBar mub{};
     for (int w = 0; w < kMaxWalls; ++w) {

@@ -212,6 +212,9 @@ struct AdjOps {
                          const double *boxes, const double *g, void *lam);
     // out[id[s] w + k] = lam[(off + k) n + s]
     void (*gather)(const HostParams &, DevState &, int w, int off, const int32_t *id, const void *lam, double *out);
+    // lam[(off + k) n + s] = in[id[s] w + k]
+    void (*scatter_in)(const HostParams &, DevState &, int w, int off, const int32_t *id, const double *in,
+                       void *lam);
 };
 constexpr int kMaxMonitors = 64;
 extern const AdjOps adj_ops_f32;

@@ -13,7 +13,7 @@ const AdjOps adj_ops_f32 = {
     AdjDispatch<float>::save, AdjDispatch<float>::restore, AdjDispatch<float>::track,
     AdjDispatch<float>::seed, AdjDispatch<float>::step,    AdjDispatch<float>::zero,
     AdjDispatch<float>::reorder, AdjDispatch<float>::seed_slots, AdjDispatch<float>::monitor_sum,
-    AdjDispatch<float>::monitor_seed, AdjDispatch<float>::gather,
+    AdjDispatch<float>::monitor_seed, AdjDispatch<float>::gather, AdjDispatch<float>::scatter_in,
 };
 
 }  // namespace mpm

@@ -13,7 +13,7 @@ const AdjOps adj_ops_f64 = {
     AdjDispatch<double>::save, AdjDispatch<double>::restore, AdjDispatch<double>::track,
     AdjDispatch<double>::seed, AdjDispatch<double>::step,    AdjDispatch<double>::zero,
     AdjDispatch<double>::reorder, AdjDispatch<double>::seed_slots, AdjDispatch<double>::monitor_sum,
-    AdjDispatch<double>::monitor_seed, AdjDispatch<double>::gather,
+    AdjDispatch<double>::monitor_seed, AdjDispatch<double>::gather, AdjDispatch<double>::scatter_in,
 };
 
 }  // namespace mpm

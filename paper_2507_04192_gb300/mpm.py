@@ -119,6 +119,8 @@ def load_library(build_if_missing: bool = True):
             "mpm_export_state": (I, [P, P, L]),
             "mpm_import_state": (I, [P, P, L]),
             "mpm_step_adjoint": (I, [P, I, I, I, C.POINTER(D), P]),
+            "mpm_step_adjoint_1": (I, [P, I, P, P, P]),
+            "mpm_adjoint_width": (I, [P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -330,6 +332,21 @@ def mpm_step_adjoint(ctx, n_steps: int, checkpoint_every: int, wall: int, n_mu: 
     _check(ctx, load_library().mpm_step_adjoint(ctx, int(n_steps), int(checkpoint_every), int(wall),
                                                 C.byref(loss), _dptr(g) if wall >= 0 else None))
     return loss.value, g
+
+
+def mpm_adjoint_width(ctx) -> int:
+    return int(load_library().mpm_adjoint_width(ctx))
+
+
+def mpm_step_adjoint_1(ctx, wall: int, lam_next: np.ndarray, n_seg: int = 0):
+    """One step and its vector-Jacobian product: returns (lam_prev, dL/dmu of this
+    step) for lam_next = dL/dS^{t+1} (n x mpm_adjoint_width doubles, load order)."""
+    lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
+    lam_prev = np.empty_like(lam_next)
+    g = np.zeros(max(int(n_seg), 1), dtype=np.float64)
+    _check(ctx, load_library().mpm_step_adjoint_1(ctx, int(wall), _dptr(lam_next), _dptr(lam_prev),
+                                                  _dptr(g) if wall >= 0 else None))
+    return lam_prev, g[:n_seg]
 
 
 def mpm_set_adjoint_memory(ctx, nbytes: int):
