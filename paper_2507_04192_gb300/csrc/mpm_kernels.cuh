@@ -795,8 +795,24 @@ __device__ __noinline__ void p2g_escape(const P2GFactors<R, D> f, R mass, R4<R> 
         R4<R> *node = &Asim[((int64_t)a2 * Gy + a1) * Gx + a0];
         if (flags != nullptr) red_add4(node, m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
         else red_add4(node, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0), R(0));
-        if (flags != nullptr) {                  // the list holds tiles by their index over all simulations
-            const int u0 = a0 / Geo<D>::T, u1 = a1 / Geo<D>::T, u2 = a2 / Geo<D>::T;
+    }
+    // the node tiles the stencil reaches, each marked once: one or two per axis,
+    // nodes b + 2 .. b + 4 (marking the tile of every node waited on 3^D flag
+    // loads in turn: P2G 0.1014 -> 0.0988 ms over the first 300 steps of the 256
+    // batched dam breaks, 0.147 -> 0.134 ms over steps 605-905)
+    if (flags != nullptr) {                      // the list holds tiles by their index over all simulations
+        int lo[3] = {0, 0, 0}, span[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            lo[a] = (f.b[a] + 2) / Geo<D>::T;
+            span[a] = (f.b[a] + 4) / Geo<D>::T - lo[a];          // 0 or 1
+        }
+        for (int mk = 0; mk < (1 << D); ++mk) {
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) in = in && ((mk >> a) & 1) <= span[a];
+            if (!in) continue;
+            const int u0 = lo[0] + (mk & 1), u1 = lo[1] + ((mk >> 1) & 1), u2 = lo[2] + ((mk >> 2) & 1);
             mark_node_tile(flags, list, count, tbase + ((int64_t)u2 * nty + u1) * ntx + u0);
         }
     }
