@@ -158,13 +158,15 @@ def random_velocities(n: int, dim: int, scale: float, seed: int) -> np.ndarray:
 
 def dam_break_2d(n_cells: int = 64, width: float = 0.25, height: float = 0.5,
                  ppc_axis: int = 4, seed: int = 0, dt: float = 1.0e-4,
-                 steps: int = 200, sort_every: int = 16) -> Workload:
+                 steps: int = 200, sort_every: int = 32) -> Workload:
     """Water column ``width`` x ``height`` at the left wall of the unit square.
 
     At 64 cells and 4 points per cell and axis this is 16 x 32 cells x 16 = 8,192
-    particles; at 128 cells 32,768; at 96 cells 18,432.  Sorted every 16 steps
-    (the front moves about a third of a cell in that time; particles that leave
-    their cell between sorts take P2G's escape path).
+    particles; at 128 cells 32,768; at 96 cells 18,432.  Sorted every 32 steps:
+    particles that leave their cell between sorts take P2G's escape path, and on
+    the 256 batched 96^2 dam breaks the first 300 steps took 0.2062 ms per step
+    sorting every 16 steps, 0.1981 every 24 and 0.1945 every 32 (later windows
+    the same within 1 %).
     """
     dx = 1.0 / n_cells
     x = lattice_particles((n_cells, n_cells), dx, ppc_axis,
