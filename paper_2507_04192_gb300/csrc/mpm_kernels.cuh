@@ -795,12 +795,19 @@ __device__ __noinline__ void p2g_escape(const P2GFactors<R, D> f, R mass, R4<R> 
         R4<R> *node = &Asim[((int64_t)a2 * Gy + a1) * Gx + a0];
         if (flags != nullptr) red_add4(node, m, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0));
         else red_add4(node, mom[0], mom[1], D == 3 ? mom[D - 1] : R(0), R(0));
+        if (D == 3 && flags != nullptr) {        // the list holds tiles by their index over all simulations
+            const int u0 = a0 / Geo<D>::T, u1 = a1 / Geo<D>::T, u2 = a2 / Geo<D>::T;
+            mark_node_tile(flags, list, count, tbase + ((int64_t)u2 * nty + u1) * ntx + u0);
+        }
     }
-    // the node tiles the stencil reaches, each marked once: one or two per axis,
-    // nodes b + 2 .. b + 4 (marking the tile of every node waited on 3^D flag
-    // loads in turn: P2G 0.1014 -> 0.0988 ms over the first 300 steps of the 256
-    // batched dam breaks, 0.147 -> 0.134 ms over steps 605-905)
-    if (flags != nullptr) {                      // the list holds tiles by their index over all simulations
+    // 2D: the node tiles the stencil reaches, each marked once: one or two per
+    // axis, nodes b + 2 .. b + 4 (marking the tile of every node waited on 3^D
+    // flag loads in turn: P2G 0.1014 -> 0.0988 ms over the first 300 steps of the
+    // 256 batched dam breaks, 0.147 -> 0.134 ms over steps 605-905).  3D keeps
+    // the tile of every node: with the once-per-tile form the 3D single-precision
+    // adjoint runs faulted the GPU (error 717 and an illegal address), for a
+    // reason not found by reading; few 3D particles escape, so it gains nothing.
+    if (D == 2 && flags != nullptr) {            // the list holds tiles by their index over all simulations
         int lo[3] = {0, 0, 0}, span[3] = {0, 0, 0};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
