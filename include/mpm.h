@@ -476,11 +476,10 @@ int mpm_get_stats(mpm_ctx *ctx, int64_t *out, int n);
  * stream) and returns without waiting.  The first call on each device resolves
  * the device address of the static scratch (cudaGetSymbolAddress) and loads
  * the four kernels (cudaFuncGetAttributes, so that lazy module loading takes no
- * memory at a later launch); make that first call before any stream capture.
- * The address is kept per device ordinal for the life of the process: it is
- * valid in the device's primary context (the runtime's) only, and not after a
- * cudaDeviceReset.  Every call on a device shares the
- * scratch and clears it before use, so calls whose work overlaps on the GPU
+ * memory at a later launch).  The address is kept per device ordinal for the
+ * life of the process: it is valid in the device's primary context (the
+ * runtime's) only, and not after a cudaDeviceReset.  Every call on a device
+ * shares the scratch and clears it before use, so calls whose work overlaps on the GPU
  * race: serialise them.  A grid of more than 131072 nodes ((N_x + 3)(N_y + 3)
  * [(N_z + 3)]) is rejected with MPM_EINVAL, and so are the parameters that
  * mpm_create rejects; both checks come before any device use.  On failure a
