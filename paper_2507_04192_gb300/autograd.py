@@ -39,7 +39,6 @@ class Stepper:
         self.n_seg = self.seg_shape[0] * self.seg_shape[1] if self.wall >= 0 else 0
         self.width = mpm.mpm_adjoint_width(sim.ctx)
         self._start = mpm.mpm_export_state(sim.ctx)
-        self._t = 0
         self._tag = None
 
     # -- the context's state as a tensor ------------------------------------------
@@ -64,7 +63,6 @@ class Stepper:
     def reset(self):
         """Back to the state the context held when the stepper was made; returns it."""
         mpm.mpm_import_state(self.sim.ctx, self._start)
-        self._t = 0
         return self._mark(self._gather())
 
     def state(self):
@@ -99,7 +97,6 @@ def _make_step():
                 st.sim.set_friction(st.wall, st.seg_shape, ctx.mu)
             ctx.mu_shape, ctx.mu_dtype = mu.shape, mu.dtype
             st.sim.step(1)
-            st._t += 1
             return st._gather()
 
         @staticmethod
